@@ -1,0 +1,257 @@
+"""Python binding of the CPU oracle (ctypes over oracle/oracle.c).
+
+TEST INFRASTRUCTURE ONLY: tests, the smoke check and the benchmark's CPU
+baseline may use it; the product path (the CUDA library and its binding) never
+imports it.  It shares no code with the CUDA path; both are fed from the seeded
+input generators in ``paper_2501_00011_gb300.synth``.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SOURCES = ["oracle.c", "adjoint.c"]
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "OK", 1: "MAX_STEPS", 2: "H_TOO_SMALL", 3: "ERR_FAIL", 4: "CONV_FAIL",
+          5: "NONFINITE", 6: "BAD_INPUT"}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no FMA contraction) into oracle/_build."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES if os.path.exists(os.path.join(_HERE, s))]
+    deps = srcs + [os.path.join(_HERE, "oracle.h")]
+    if not force and os.path.exists(_SO) and all(os.path.getmtime(_SO) >= os.path.getmtime(d) for d in deps):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC", "-shared",
+           "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Mech(ct.Structure):
+    _fields_ = [("n_species", ct.c_int32), ("n_reactions", ct.c_int32),
+                ("kind", ct.c_void_p), ("n_reac", ct.c_void_p), ("reac", ct.c_void_p),
+                ("n_prod", ct.c_void_p), ("prod", ct.c_void_p),
+                ("yld", ct.c_void_p), ("A", ct.c_void_p), ("Ea", ct.c_void_p),
+                ("B", ct.c_void_p), ("J", ct.c_void_p)]
+
+
+class _Opts(ct.Structure):
+    _fields_ = [("rtol", ct.c_double), ("atol", ct.c_double),
+                ("max_order", ct.c_int32), ("max_steps", ct.c_int32),
+                ("fixed_h", ct.c_double), ("fixed_order", ct.c_int32),
+                ("newton_maxiter", ct.c_int32), ("newton_tol", ct.c_double),
+                ("init_D", ct.c_void_p), ("y_hist", ct.c_void_p)]
+
+
+class _Stats(ct.Structure):
+    _fields_ = [("status", ct.c_int32), ("steps", ct.c_int32), ("rejects", ct.c_int32),
+                ("conv_fails", ct.c_int32), ("newton_iters", ct.c_int32), ("f_evals", ct.c_int32),
+                ("jac_evals", ct.c_int32), ("solves", ct.c_int32), ("final_order", ct.c_int32),
+                ("pad", ct.c_int32), ("final_h", ct.c_double)]
+
+
+STATS_DTYPE = np.dtype([("status", "<i4"), ("steps", "<i4"), ("rejects", "<i4"),
+                        ("conv_fails", "<i4"), ("newton_iters", "<i4"), ("f_evals", "<i4"),
+                        ("jac_evals", "<i4"), ("solves", "<i4"), ("final_order", "<i4"),
+                        ("pad", "<i4"), ("final_h", "<f8")])
+assert STATS_DTYPE.itemsize == ct.sizeof(_Stats)
+
+
+class _Tape(ct.Structure):
+    _fields_ = [("cap", ct.c_int32), ("n", ct.c_int32), ("overflow", ct.c_int32), ("pad", ct.c_int32),
+                ("kind", ct.c_void_p), ("q", ct.c_void_p), ("val", ct.c_void_p), ("y", ct.c_void_p)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ct.CDLL(build())
+            P = ct.c_void_p
+            L.orc_rate_constants.argtypes = [P, ct.c_double, ct.c_double, P, P, P]
+            L.orc_deriv.argtypes = [P, P, P, P]
+            L.orc_jacobian.argtypes = [P, P, P, P]
+            L.orc_lu_factor.argtypes = [ct.c_int, P, P]
+            L.orc_lu_factor.restype = ct.c_int
+            L.orc_lu_solve.argtypes = [ct.c_int, P, P, P]
+            L.orc_rescale.argtypes = [ct.c_int, ct.c_int, ct.c_double, P]
+            L.orc_grid_eta.argtypes = [ct.c_double, ct.c_int, ct.c_double]
+            L.orc_grid_eta.restype = ct.c_double
+            L.orc_integrate.argtypes = [P, P, P, ct.c_double, P, P, P]
+            L.orc_integrate.restype = ct.c_int
+            L.orc_solve_cells.argtypes = [P, ct.c_int64, P, P, P, P, P, ct.c_double, P, P]
+            L.orc_solve_cells.restype = ct.c_int
+            if hasattr(L, "orc_adjoint"):
+                L.orc_adjoint.argtypes = [P, P, P, P, P, P, P]
+                L.orc_adjoint.restype = ct.c_int
+                L.orc_replay.argtypes = [P, P, P, P, ct.c_double, ct.c_int, P]
+                L.orc_replay.restype = ct.c_int
+                L.orc_tangent.argtypes = [P, P, P, P, P, P, P]
+                L.orc_tangent.restype = ct.c_int
+            _lib = L
+        return _lib
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else ct.c_void_p(a.ctypes.data)
+
+
+class OracleMechanism:
+    """Keeps the arrays of a synth.Mechanism alive behind an orc_mech struct."""
+
+    def __init__(self, mech):
+        self.mech = mech
+        self.S, self.R = mech.n_species, mech.n_reactions
+        self._arrs = dict(
+            kind=np.ascontiguousarray(mech.kind, np.int32),
+            n_reac=np.ascontiguousarray(mech.n_reac, np.int32),
+            reac=np.ascontiguousarray(mech.reac, np.int32),
+            n_prod=np.ascontiguousarray(mech.n_prod, np.int32),
+            prod=np.ascontiguousarray(mech.prod, np.int32),
+            yld=np.ascontiguousarray(mech.yld, np.float64),
+            A=np.ascontiguousarray(mech.A, np.float64), Ea=np.ascontiguousarray(mech.Ea, np.float64),
+            B=np.ascontiguousarray(mech.B, np.float64), J=np.ascontiguousarray(mech.J, np.float64))
+        assert self._arrs["reac"].shape[1] == 3 and self._arrs["prod"].shape[1] == 8
+        a = self._arrs
+        self.c = _Mech(self.S, self.R, *(a[k].ctypes.data for k in
+                                         ("kind", "n_reac", "reac", "n_prod", "prod", "yld", "A", "Ea", "B", "J")))
+        self.n_phot = int(np.count_nonzero(a["kind"] == 1))
+
+    @property
+    def ref(self):
+        return ct.byref(self.c)
+
+
+def _mk(mech) -> OracleMechanism:
+    return mech if isinstance(mech, OracleMechanism) else OracleMechanism(mech)
+
+
+def rate_constants(mech, T: float, P: float, jphot=None, theta=None) -> np.ndarray:
+    m = _mk(mech)
+    kt = np.empty(m.R)
+    jp = None if jphot is None else np.ascontiguousarray(jphot, np.float64)
+    th = None if theta is None else np.ascontiguousarray(theta, np.float64)
+    lib().orc_rate_constants(m.ref, float(T), float(P), _p(jp), _p(th), _p(kt))
+    return kt
+
+
+def deriv(mech, kt, y) -> np.ndarray:
+    m = _mk(mech)
+    kt = np.ascontiguousarray(kt, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    f = np.empty(m.S)
+    lib().orc_deriv(m.ref, _p(kt), _p(y), _p(f))
+    return f
+
+
+def jacobian(mech, kt, y) -> np.ndarray:
+    m = _mk(mech)
+    kt = np.ascontiguousarray(kt, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    J = np.empty((m.S, m.S))
+    lib().orc_jacobian(m.ref, _p(kt), _p(y), _p(J))
+    return J
+
+
+def lu_solve_dense(A, b) -> np.ndarray:
+    A = np.array(A, np.float64, order="C")
+    b = np.array(b, np.float64)
+    n = A.shape[0]
+    piv = np.empty(n, np.int32)
+    if lib().orc_lu_factor(n, _p(A), _p(piv)) != 0:
+        raise ZeroDivisionError("exactly singular matrix")
+    lib().orc_lu_solve(n, _p(A), _p(piv), _p(b))
+    return b
+
+
+def rescale(D, q: int, eta: float) -> np.ndarray:
+    D = np.array(D, np.float64, order="C")
+    lib().orc_rescale(D.shape[1], int(q), float(eta), _p(D))
+    return D
+
+
+def grid_eta(err: float, p: int, bias: float) -> float:
+    return lib().orc_grid_eta(float(err), int(p), float(bias))
+
+
+@dataclass
+class Tape:
+    kind: np.ndarray
+    q: np.ndarray
+    val: np.ndarray
+    y: np.ndarray
+
+    @property
+    def n_steps(self) -> int:
+        return int(np.count_nonzero(self.kind == 2))
+
+
+def _opts(rtol, atol, max_order=5, max_steps=5000, fixed_h=0.0, fixed_order=0, newton_maxiter=0,
+          newton_tol=0.0, init_D=None, y_hist=None):
+    return _Opts(rtol, atol, max_order, max_steps, fixed_h, fixed_order, newton_maxiter, newton_tol,
+                 None if init_D is None else init_D.ctypes.data,
+                 None if y_hist is None else y_hist.ctypes.data)
+
+
+def integrate(mech, kt, y0, dt, rtol, atol, max_order=5, max_steps=5000, fixed_h=0.0, fixed_order=0,
+              newton_maxiter=0, newton_tol=0.0, init_D=None, n_hist=0, tape_cap=0):
+    """Integrate one cell.  Returns (y, stats-dict[, y_hist][, tape])."""
+    m = _mk(mech)
+    y = np.array(y0, np.float64)
+    kt = np.ascontiguousarray(kt, np.float64)
+    D = None if init_D is None else np.ascontiguousarray(init_D, np.float64)
+    hist = np.zeros((n_hist, m.S)) if n_hist else None
+    o = _opts(rtol, atol, max_order, max_steps, fixed_h, fixed_order, newton_maxiter, newton_tol, D, hist)
+    st = _Stats()
+    tape = None
+    tp = None
+    if tape_cap:
+        tape = Tape(np.zeros(tape_cap, np.int32), np.zeros(tape_cap, np.int32), np.zeros(tape_cap),
+                    np.zeros((tape_cap, m.S)))
+        tp = _Tape(tape_cap, 0, 0, 0, tape.kind.ctypes.data, tape.q.ctypes.data, tape.val.ctypes.data,
+                   tape.y.ctypes.data)
+    lib().orc_integrate(m.ref, _p(kt), _p(y), float(dt), ct.byref(o), ct.byref(st),
+                        None if tp is None else ct.byref(tp))
+    stats = {k: getattr(st, k) for k, _ in _Stats._fields_ if k != "pad"}
+    out = [y, stats]
+    if n_hist:
+        out.append(hist)
+    if tape_cap:
+        if tp.overflow:
+            raise RuntimeError("tape overflow")
+        n = tp.n
+        out.append(Tape(tape.kind[:n].copy(), tape.q[:n].copy(), tape.val[:n].copy(), tape.y[:n].copy()))
+    return tuple(out)
+
+
+def solve_cells(mech, cells, dt, rtol, atol, max_order=5, max_steps=5000, theta=None, jphot="cells"):
+    """Solve every cell of a synth.Cells batch once over [0, dt].
+
+    Returns (y [S, C], stats structured array [C]).  ``jphot="cells"`` uses the
+    batch's per-cell photolysis rates when it has them."""
+    m = _mk(mech)
+    y = np.array(cells.y, np.float64, order="C")
+    C = y.shape[1]
+    T = np.ascontiguousarray(cells.T, np.float64)
+    P = np.ascontiguousarray(cells.P, np.float64)
+    jp = cells.J if (isinstance(jphot, str) and jphot == "cells") else jphot
+    jp = None if jp is None else np.ascontiguousarray(jp, np.float64)
+    th = None if theta is None else np.ascontiguousarray(theta, np.float64)
+    st = np.zeros(C, STATS_DTYPE)
+    o = _opts(rtol, atol, max_order, max_steps)
+    lib().orc_solve_cells(m.ref, C, _p(T), _p(P), _p(jp), _p(th), _p(y), float(dt), ct.byref(o), _p(st))
+    return y, st

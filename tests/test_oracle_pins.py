@@ -1,0 +1,400 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test checks the oracle against a value the mathematics fixes without the
+oracle's own formulas: hand-worked numbers, physical constants, closed-form
+solutions of linear and quadratic kinetics, textbook BDF coefficients,
+polynomial interpolation, finite differences, numpy's dense solve and scipy's
+Radau integrator.  A dropped term, a wrong sign, a transposed operand or a
+wrong index anywhere in rates, f, J, the LU, the history rescale, the BDF
+recurrence or the step control fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2501_00011_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                k, *v = line.split()
+                vals[k] = np.array([float(x) for x in v])
+    return vals
+
+
+def hand_mechanism():
+    return synth.mechanism_from_list(3, [
+        dict(reac=[0], prod=[1], A=0.5),
+        dict(reac=[0], prod=[2], J=0.25),
+        dict(reac=[0, 1], prod=[2], A=1e-20),
+    ], name="hand")
+
+
+# ------------------------------------------------------------------ rates, f, J
+
+def test_rates_f_jac_hand_worked(oracle_lib):
+    g = _read_golden("hand_mechanism.txt")
+    m = hand_mechanism()
+    kt = oracle_lib.rate_constants(m, g["T"][0], g["P"][0])
+    np.testing.assert_allclose(kt, g["kt"], rtol=1e-9)
+    f = oracle_lib.deriv(m, g["kt"], g["y"])
+    np.testing.assert_allclose(f, g["f"], rtol=1e-14, atol=1e-15)
+    J = oracle_lib.jacobian(m, g["kt"], g["y"])
+    np.testing.assert_allclose(J.ravel(), g["J"], rtol=1e-14, atol=1e-15)
+
+
+def test_bimolecular_rate_uses_loschmidt_number(oracle_lib):
+    # at 273.15 K and 101325 Pa the number density of an ideal gas is the
+    # Loschmidt constant 2.686780111e25 m^-3 = 2.686780111e19 cm^-3 (CODATA)
+    m = synth.mechanism_from_list(2, [dict(reac=[0, 1], prod=[], A=1e-19)])
+    kt = oracle_lib.rate_constants(m, 273.15, 101325.0)
+    assert kt[0] == pytest.approx(2.686780111, rel=1e-9)
+    # a termolecular rate carries n_air twice
+    m3 = synth.mechanism_from_list(3, [dict(reac=[0, 1, 2], prod=[], A=1e-38)])
+    kt3 = oracle_lib.rate_constants(m3, 273.15, 101325.0)
+    assert kt3[0] == pytest.approx(2.686780111 ** 2, rel=1e-9)
+
+
+def test_arrhenius_special_values(oracle_lib):
+    ln2 = math.log(2.0)
+    m = synth.mechanism_from_list(1, [
+        dict(reac=[0], prod=[], A=3.0, Ea=300.0 * ln2, B=1.7),   # T=300: (T/300)^B = 1, exp = 1/2
+        dict(reac=[0], prod=[], A=3.0, Ea=0.0, B=2.0),           # T=300: plain A
+        dict(reac=[0], prod=[], J=0.125),                        # photolysis: J itself
+    ])
+    kt = oracle_lib.rate_constants(m, 300.0, 1e5)
+    np.testing.assert_allclose(kt, [1.5, 3.0, 0.125], rtol=1e-15)
+    kt600 = oracle_lib.rate_constants(m, 600.0, 1e5)       # (600/300)^2 = 4
+    assert kt600[1] == pytest.approx(12.0, rel=1e-15)
+    # per-cell photolysis override and log-multiplier theta
+    kt2 = oracle_lib.rate_constants(m, 300.0, 1e5, jphot=[0.5], theta=[0.0, ln2, 0.0])
+    np.testing.assert_allclose(kt2, [1.5, 6.0, 0.5], rtol=1e-15)
+
+
+def _mechanisms():
+    return [synth.mechanism_small(), synth.mechanism_tropo()]
+
+
+@pytest.mark.parametrize("mi", [0, 1])
+def test_f_conserves_atom_weights(oracle_lib, mi):
+    m = _mechanisms()[mi]
+    w = m.weights.astype(float)
+    cells = synth.random_cells(m.n_species, 5, seed=7)
+    for c in range(5):
+        kt = oracle_lib.rate_constants(m, cells.T[c], cells.P[c])
+        f = oracle_lib.deriv(m, kt, cells.y[:, c])
+        assert abs(w @ f) <= 1e-14 * np.sum(np.abs(w * f))
+
+
+@pytest.mark.parametrize("mi", [0, 1])
+def test_jacobian_matches_central_differences(oracle_lib, mi):
+    m = _mechanisms()[mi]
+    cells = synth.random_cells(m.n_species, 2, seed=11)
+    w = m.weights.astype(float)
+    for c in range(2):
+        kt = oracle_lib.rate_constants(m, cells.T[c], cells.P[c])
+        y = cells.y[:, c]
+        J = oracle_lib.jacobian(m, kt, y)
+        Jfd = np.empty_like(J)
+        for l in range(m.n_species):
+            # mass-action f is at most quadratic in each y_l, so central
+            # differences are exact up to rounding; a large step keeps the
+            # cancellation error small
+            e = 1e-2 * max(abs(y[l]), 1e-12)
+            yp, ym = y.copy(), y.copy()
+            yp[l] += e
+            ym[l] -= e
+            Jfd[:, l] = (oracle_lib.deriv(m, kt, yp) - oracle_lib.deriv(m, kt, ym)) / (2 * e)
+        # rounding floor of the difference quotient: eps times the size of the
+        # terms summed into f_i (for quadratic terms sum_l |J_il| |y_l| bounds
+        # them) divided by the step
+        steps = 1e-2 * np.maximum(np.abs(y), 1e-12)
+        terms = np.abs(J) @ np.abs(y)
+        floor = 64 * np.finfo(float).eps * terms[:, None] / steps[None, :]
+        assert np.all(np.abs(J - Jfd) <= 1e-6 * np.abs(J) + floor)
+        # conservation also holds column-wise: w^T J = 0
+        assert np.max(np.abs(w @ J)) <= 1e-13 * np.max(np.abs(w[:, None] * J))
+
+
+def test_dense_lu_matches_numpy(oracle_lib):
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 7, 72):
+        A = rng.standard_normal((n, n))
+        if n > 1:
+            A[0, 0] = 0.0                     # forces a row exchange
+        b = rng.standard_normal(n)
+        x = oracle_lib.lu_solve_dense(A, b)
+        np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-12)
+        assert np.linalg.norm(A @ x - b) <= 1e-12 * np.linalg.norm(A) * np.linalg.norm(x) * n
+
+
+# ------------------------------------------------------------ history rescale
+
+@pytest.mark.parametrize("q", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("eta", [0.1, 0.37, 1.0, 2.5, 9.5])
+def test_rescale_reproduces_polynomial_interpolation(oracle_lib, q, eta):
+    # differences of a degree-q polynomial sampled at spacing h, rescaled by
+    # eta, must equal the differences of the same polynomial at spacing eta*h
+    rng = np.random.default_rng(q)
+    coef = rng.standard_normal((q + 1, 4))          # 4 independent components
+    h = 0.3
+
+    def diffs(hh):
+        vals = np.array([sum(coef[p] * (-j * hh) ** p for p in range(q + 1)) for j in range(q + 1)])
+        D = [vals[0]]
+        cur = vals
+        for _ in range(q):
+            cur = cur[:-1] - cur[1:]
+            D.append(cur[0])
+        return np.array(D)
+
+    D = diffs(h)
+    out = oracle_lib.rescale(D, q, eta)
+    np.testing.assert_allclose(out, diffs(eta * h), rtol=1e-10, atol=1e-12)
+
+
+def test_grid_eta_definition(oracle_lib):
+    g = [2.0 ** (i / 8.0) for i in range(-26, 27)]
+    for err in (0.0, 1e-9, 1e-3, 0.05, 0.3, 1.0, 2.0, 1e3):
+        for p in range(1, 7):
+            for bias in (2.0, 3.0):
+                eta = oracle_lib.grid_eta(err, p, bias)
+                i = int(round(8 * math.log2(eta)))
+                assert eta == pytest.approx(g[i + 26], rel=1e-15)
+                ok = bias * err * eta ** (p + 1) <= 1.0 * (1 + 1e-12)
+                assert ok or i == -26
+                if i < 26:
+                    assert bias * err * g[i + 27] ** (p + 1) > 1.0 * (1 - 1e-12)
+
+
+# ------------------------------------------------------------- BDF machinery
+
+K1, K2 = 0.3, 0.1
+
+
+def chain_mechanism(k1=K1, k2=K2):
+    return synth.mechanism_from_list(3, [dict(reac=[0], prod=[1], A=k1), dict(reac=[1], prod=[2], A=k2)])
+
+
+def chain_matrix(k1=K1, k2=K2):
+    return np.array([[-k1, 0.0, 0.0], [k1, -k2, 0.0], [0.0, k2, 0.0]])
+
+
+def chain_exact(t, y0, k1=K1, k2=K2):
+    A0, B0, C0 = y0
+    A = A0 * np.exp(-k1 * t)
+    B = A0 * k1 / (k2 - k1) * (np.exp(-k1 * t) - np.exp(-k2 * t)) + B0 * np.exp(-k2 * t)
+    return np.array([A, B, A0 + B0 + C0 - A - B])
+
+
+def test_backward_euler_fixed_step_equals_matrix_power(oracle_lib):
+    m = chain_mechanism()
+    kt = oracle_lib.rate_constants(m, 300.0, 1e5)
+    y0 = np.array([1.0, 0.2, 0.0])
+    h, n = 0.25, 40
+    y, st, hist = oracle_lib.integrate(m, kt, y0, n * h, 1e-6, 1e-12, fixed_h=h, fixed_order=1,
+                                       newton_tol=1e-8, newton_maxiter=10, n_hist=n)
+    assert st["status"] == 0 and st["steps"] == n
+    inv = np.linalg.inv(np.eye(3) - h * chain_matrix())
+    ref = y0.copy()
+    for k in range(n):
+        ref = inv @ ref
+        np.testing.assert_allclose(hist[k], ref, rtol=1e-12, atol=1e-14)
+
+
+BDF_ALPHA = {   # textbook BDF-k: sum_j alpha_j y_{n+1-j} = h f_{n+1} (Hairer & Wanner, Solving ODEs II, III.1)
+    1: [1.0, -1.0],
+    2: [3 / 2, -2.0, 1 / 2],
+    3: [11 / 6, -3.0, 3 / 2, -1 / 3],
+    4: [25 / 12, -4.0, 3.0, -4 / 3, 1 / 4],
+    5: [137 / 60, -5.0, 5.0, -10 / 3, 5 / 4, -1 / 5],
+}
+
+
+def _backward_differences(vals):
+    """vals[0] = y_n, vals[j] = y_{n-j}; returns D_m = nabla^m y_n, m = 0..len-1."""
+    D = [vals[0]]
+    cur = np.array(vals)
+    for _ in range(len(vals) - 1):
+        cur = cur[:-1] - cur[1:]
+        D.append(cur[0])
+    return np.array(D)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_constant_step_bdf_k_matches_textbook_recurrence(oracle_lib, k):
+    m = chain_mechanism()
+    kt = oracle_lib.rate_constants(m, 300.0, 1e5)
+    A = chain_matrix()
+    y0 = np.array([1.0, 0.2, 0.0])
+    h, n = 0.2, 30
+    start = [chain_exact(-j * h, y0) for j in range(k + 1)]   # exact y_0, y_-1, ..., y_-k
+    D0 = _backward_differences(start)
+    y, st, hist = oracle_lib.integrate(m, kt, y0, n * h, 1e-6, 1e-12, fixed_h=h, fixed_order=k,
+                                       init_D=D0, newton_tol=1e-8, newton_maxiter=10, n_hist=n)
+    assert st["status"] == 0
+    a = BDF_ALPHA[k]
+    seq = list(reversed(start))           # y_-k ... y_0
+    lhs = a[0] * np.eye(3) - h * A
+    for step in range(n):
+        rhs = -sum(a[j] * seq[-j] for j in range(1, k + 1))
+        seq.append(np.linalg.solve(lhs, rhs))
+        np.testing.assert_allclose(hist[step], seq[-1], rtol=1e-11, atol=1e-13)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_fixed_order_convergence_slope(oracle_lib, k):
+    m = chain_mechanism()
+    kt = oracle_lib.rate_constants(m, 300.0, 1e5)
+    y0 = np.array([1.0, 0.0, 0.0])
+    T = 4.0
+    errs = []
+    for n in (40, 80):
+        h = T / n
+        start = [chain_exact(-j * h, y0) for j in range(k + 1)]
+        y, st = oracle_lib.integrate(m, kt, y0, T, 1e-6, 1e-12, fixed_h=h, fixed_order=k,
+                                     init_D=_backward_differences(start), newton_tol=1e-8,
+                                     newton_maxiter=10)
+        errs.append(np.max(np.abs(y - chain_exact(T, y0))))
+    slope = math.log2(errs[0] / errs[1])
+    assert abs(slope - k) < 0.25
+
+
+# -------------------------------------------------- adaptive solve vs closed forms
+
+# A locally error-controlled BDF accumulates global error over its accepted
+# steps.  On these non-expanding problems (linear decay, relaxation to
+# equilibrium, second-order decay) an error made at one step is never
+# amplified later, so the global error is at most the sum of the local errors.
+# A weighted-RMS local error of 1 allows sqrt(S) on one component, and the
+# estimate d/(q+1) is asymptotic, hence the bound 2 sqrt(S) x (accepted steps)
+# x tolerance; separately the error must shrink with the tolerance.  scipy's BDF lands at 1.5-47x the local
+# tolerance on the same problems.
+def _check_global(y, ref, rtol, atol, st):
+    assert st["status"] == 0
+    err = np.abs(y - ref) / (rtol * np.abs(ref) + atol)
+    bound = 2.0 * math.sqrt(y.size) * max(5, st["steps"])
+    assert err.max() <= bound, (err.max(), st["steps"])
+
+
+def test_adaptive_chain_stiff(oracle_lib):
+    k1, k2 = 50.0, 0.02
+    m = chain_mechanism(k1, k2)
+    kt = oracle_lib.rate_constants(m, 300.0, 1e5)
+    y0 = np.array([1.0, 0.0, 0.0])
+    rtol, atol = 1e-6, 1e-12
+    y, st = oracle_lib.integrate(m, kt, y0, 600.0, rtol, atol)
+    assert st["status"] == 0
+    _check_global(y, chain_exact(600.0, y0, k1, k2), rtol, atol, st)
+
+
+def test_adaptive_error_shrinks_with_tolerance(oracle_lib):
+    k1, k2 = 50.0, 0.02
+    m = chain_mechanism(k1, k2)
+    kt = oracle_lib.rate_constants(m, 300.0, 1e5)
+    y0 = np.array([1.0, 0.0, 0.0])
+    ref = chain_exact(600.0, y0, k1, k2)
+    errs = []
+    for rtol in (1e-4, 1e-6, 1e-8):
+        y, st = oracle_lib.integrate(m, kt, y0, 600.0, rtol, 1e-14)
+        assert st["status"] == 0
+        errs.append(np.max(np.abs(y - ref)))
+    assert errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10
+
+
+def test_adaptive_reversible_pair(oracle_lib):
+    kf, kb = 3.0, 1.0
+    m = synth.mechanism_from_list(2, [dict(reac=[0], prod=[1], A=kf), dict(reac=[1], prod=[0], A=kb)])
+    kt = oracle_lib.rate_constants(m, 300.0, 1e5)
+    y0 = np.array([0.9, 0.1])
+    rtol, atol = 1e-6, 1e-12
+    for t_end in (0.05, 1.0, 600.0):
+        y, st = oracle_lib.integrate(m, kt, y0, t_end, rtol, atol)
+        Aeq = (y0.sum()) * kb / (kf + kb)
+        A = Aeq + (y0[0] - Aeq) * math.exp(-(kf + kb) * t_end)
+        _check_global(y, np.array([A, y0.sum() - A]), rtol, atol, st)
+
+
+def test_adaptive_paper_test_mechanism(oracle_lib):
+    # Test-environment section: species A produces B and C through two Arrhenius
+    # reactions; A starts at 1, B and C at 0, and every cell adds an offset of
+    # 0.1 per flattened value (0.1 on the first, 0.2 on the second, ...).
+    T, P = 272.5, 101253.3
+    m = synth.mechanism_from_list(3, [dict(reac=[0], prod=[1], A=0.004, Ea=120.0, B=0.5),
+                                      dict(reac=[0], prod=[2], A=0.012, Ea=50.0, B=-0.3)])
+    kt = oracle_lib.rate_constants(m, T, P)
+    k1, k2 = kt
+    n_cells = 5
+    base = np.array([1.0, 0.0, 0.0])
+    rtol, atol = 1e-7, 1e-12
+    for c in range(n_cells):
+        y0 = base + 0.1 * (np.arange(3) + 3 * c + 1)
+        y, st = oracle_lib.integrate(m, kt, y0, 600.0, rtol, atol)
+        assert st["status"] == 0
+        ks = k1 + k2
+        A = y0[0] * math.exp(-ks * 600.0)
+        ref = np.array([A, y0[1] + (y0[0] - A) * k1 / ks, y0[2] + (y0[0] - A) * k2 / ks])
+        _check_global(y, ref, rtol, atol, st)
+
+
+def test_adaptive_second_order_self_reaction(oracle_lib):
+    # 2A -> B with k~ (per mixing ratio): 1/A = 1/A0 + 2 k~ t, B = B0 + (A0 - A)/2
+    n_air = 2.5e19
+    P = n_air * 1.380649e-23 * 300.0 * 1e6
+    m = synth.mechanism_from_list(2, [dict(reac=[0, 0], prod=[1], yld=[1.0], A=4e-17)])
+    kt = oracle_lib.rate_constants(m, 300.0, P)
+    y0 = np.array([1e-3, 0.0])
+    rtol, atol = 1e-6, 1e-14
+    y, st = oracle_lib.integrate(m, kt, y0, 600.0, rtol, atol)
+    assert st["status"] == 0
+    A = 1.0 / (1.0 / y0[0] + 2.0 * kt[0] * 600.0)
+    _check_global(y, np.array([A, (y0[0] - A) / 2.0]), rtol, atol, st)
+
+
+def test_adaptive_small_mechanism_vs_radau(oracle_lib):
+    scipy_integrate = pytest.importorskip("scipy.integrate")
+    wl = synth.workload_small()
+    m = oracle_lib.OracleMechanism(wl.mech)
+    y, st = oracle_lib.solve_cells(m, wl.cells, wl.dt, wl.rtol, wl.atol)
+    assert np.all(st["status"] == 0)
+    for c in range(3):
+        kt = oracle_lib.rate_constants(m, wl.cells.T[c], wl.cells.P[c])
+        sol = scipy_integrate.solve_ivp(lambda t, yy: oracle_lib.deriv(m, kt, yy), (0.0, wl.dt),
+                                        wl.cells.y[:, c], method="Radau", rtol=1e-12, atol=1e-20,
+                                        jac=lambda t, yy: oracle_lib.jacobian(m, kt, yy))
+        _check_global(y[:, c], sol.y[:, -1], wl.rtol, wl.atol,
+                      {k: st[k][c] for k in ("status", "steps")})
+
+
+# ------------------------------------------------------ invariants and status
+
+@pytest.mark.parametrize("which", ["small", "tropo"])
+def test_conservation_and_nonnegativity(oracle_lib, which):
+    wl = synth.workload_small() if which == "small" else synth.workload_tropo(24)
+    y, st = oracle_lib.solve_cells(wl.mech, wl.cells, wl.dt, wl.rtol, wl.atol)
+    assert np.all(st["status"] == 0)
+    w = wl.mech.weights.astype(float)
+    before, after = w @ wl.cells.y, w @ y
+    # exact BDF steps preserve linear invariants; the corrector stops at a
+    # tolerance and the y >= 0 projection moves mass by at most ~atol per step
+    assert np.all(np.abs(after - before) <= 10 * wl.rtol * before + 1e3 * wl.atol)
+    assert y.min() >= -1e-20
+
+
+def test_failure_status_keeps_input(oracle_lib):
+    wl = synth.workload_tropo(4)
+    cells = synth.subset(wl.cells, np.arange(4))
+    cells.T[1] = float("nan")
+    cells.y[3, 2] = float("inf")
+    y, st = oracle_lib.solve_cells(wl.mech, cells, wl.dt, wl.rtol, wl.atol, max_steps=3)
+    assert st["status"][1] == 6 and st["status"][2] == 6
+    assert st["status"][0] == 1 and st["status"][3] == 1          # MAX_STEPS
+    np.testing.assert_array_equal(y[:, [0, 3]], cells.y[:, [0, 3]])
