@@ -1,0 +1,194 @@
+/*
+ * chemgpu.h -- C ABI of the GB300 multi-cell stiff chemistry solver.
+ *
+ * The library integrates a gas-phase mass-action mechanism independently in
+ * every grid cell of a batch with an implicit BDF / modified-Newton method,
+ * entirely on the GPU: per-cell rate constants and derivative f(y), the
+ * analytic sparse Jacobian, and a static-order sparse LU factor/solve of the
+ * Newton iteration matrix I - c*J.
+ *
+ * Paper: "Adapting atmospheric chemistry components for efficient GPU
+ * accelerators" (arXiv 2501.00011).  The chemistry follows its Background
+ * section (reaction form c1 y1 + ... -> c_{m+1} y_{m+1} + ..., per-reaction
+ * rate of change -c_i r_j / +c_i r_j, derivative f_i = sum_j (dy_i/dt)_j);
+ * the batching of all cells into one structure with the cell loop inside the
+ * solver follows its Implementations section (Multi-cells); its Conclusions
+ * name the whole ODE solve on the GPU, which is what this library does.  The
+ * integrator (BDF orders 1-5, modified Newton, error and step/order control)
+ * stands for the CVODE solver the Background section names.
+ *
+ * Conventions for every entry point:
+ *   - return value 0 = success, negative = error (CHEM_E*); on error nothing
+ *     was launched and chem_last_error() (thread-local) describes it;
+ *   - "mem" arguments say where a pointer lives: CHEM_MEM_HOST (pageable or
+ *     pinned host memory) or CHEM_MEM_DEVICE (memory of the current CUDA
+ *     device);
+ *   - "stream" is a cudaStream_t (NULL = the legacy default stream); device
+ *     work is enqueued on it and the call returns without waiting, except
+ *     where a host buffer is read back;
+ *   - pointers passed in are borrowed for the duration of the call only;
+ *   - state arrays are [n_species][n_cells] with the cell index at unit
+ *     stride, FP64, in mol/mol; T in K; P in Pa.
+ * No entry point aborts the process or traps the GPU.  A cell that cannot be
+ * integrated keeps its input state and reports a non-zero status.
+ */
+#ifndef CHEMGPU_H
+#define CHEMGPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CHEM_MAX_REAC 3
+#define CHEM_MAX_PROD 8
+#define CHEM_MAX_SPECIES 128
+
+/* error codes (negative returns) */
+#define CHEM_EINVAL (-1)   /* bad argument or mechanism table */
+#define CHEM_ENOMEM (-2)   /* device or host allocation failed */
+#define CHEM_ECUDA (-3)    /* a CUDA runtime call failed */
+#define CHEM_ESTATE (-4)   /* call out of order (e.g. solve before set_state) */
+
+/* where a pointer lives */
+#define CHEM_MEM_HOST 0
+#define CHEM_MEM_DEVICE 1
+
+/* reaction kinds */
+#define CHEM_THERMAL 0     /* k = A exp(-Ea/T) (T/300)^B, times n_air^(n_reac-1) */
+#define CHEM_PHOTOLYSIS 1  /* first-order rate J (s^-1), optionally per cell */
+
+/* per-cell status */
+#define CHEM_CELL_OK 0
+#define CHEM_CELL_MAX_STEPS 1
+#define CHEM_CELL_H_TOO_SMALL 2
+#define CHEM_CELL_ERR_FAIL 3
+#define CHEM_CELL_CONV_FAIL 4
+#define CHEM_CELL_NONFINITE 5
+#define CHEM_CELL_BAD_INPUT 6
+
+/* drivers */
+#define CHEM_DRIVER_PLAIN 0       /* one warp per cell, cells assigned by block */
+#define CHEM_DRIVER_PERSISTENT 1  /* resident warps pop cells from a device queue */
+
+/*
+ * One reaction: reactant slots reac[0..n_reac-1] (a species listed twice is a
+ * second-order dependence, e.g. 2A), products prod[0..n_prod-1] with yields.
+ * Mass action: r = k~ * prod_s y[reac[s]]; each reactant slot loses r, each
+ * product gains yield * r (Background section, per-reaction rate of change).
+ */
+typedef struct {
+  int32_t kind;                   /* CHEM_THERMAL or CHEM_PHOTOLYSIS */
+  int32_t n_reac;                 /* 1..CHEM_MAX_REAC */
+  int32_t reac[CHEM_MAX_REAC];
+  int32_t n_prod;                 /* 0..CHEM_MAX_PROD */
+  int32_t prod[CHEM_MAX_PROD];
+  double yield[CHEM_MAX_PROD];
+  double A, Ea_over_R, B;         /* thermal parameters */
+  double J;                       /* photolysis rate (s^-1) */
+} chem_reaction;
+
+typedef struct chem_mech chem_mech;
+typedef struct chem_cells chem_cells;
+
+/* Structure of a compiled mechanism (sizes of its sparse tables and of the
+ * per-cell work, and algorithmic FP64 operation counts per kernel step). */
+typedef struct {
+  int32_t n_species, n_reactions, n_photolysis;
+  int32_t nnz_jac;                 /* nonzeros of J plus the diagonal */
+  int32_t nnz_lu;                  /* nonzeros after the static-order fill */
+  int32_t n_pairs;                 /* (reaction, reactant slot) partials */
+  int32_t passes_f, passes_jac, passes_lu, passes_fwd, passes_bwd;  /* warp passes */
+  int32_t ops_f, ops_jac, ops_lu, ops_fwd, ops_bwd;                 /* scheduled ops */
+  double flops_f, flops_jac, flops_lu, flops_solve;                 /* algorithmic flops */
+  int32_t smem_per_cell_fp64, smem_per_cell_fp32;                   /* bytes */
+} chem_mech_info;
+
+typedef struct {
+  double rtol, atol;
+  int32_t max_order;               /* 1..5 (default 5) */
+  int32_t max_steps;               /* default 5000 */
+  int32_t lu_precision;            /* 64 (default) or 32: LU factor/solve in FP32 */
+  int32_t driver;                  /* CHEM_DRIVER_* */
+  int32_t cells_per_block;         /* warps (= concurrent cells) per block; 0 = auto */
+  int32_t blocks_per_sm;           /* persistent driver: resident blocks per SM; 0 = auto */
+  int32_t record_adjoint;          /* 1: record the step tape for chem_sensitivity */
+  int32_t tape_steps;              /* tape capacity in accepted steps per cell (0 = 400) */
+} chem_opts;
+
+typedef struct {
+  int32_t status, steps, rejects, conv_fails, newton_iters, f_evals, jac_evals, solves,
+      final_order, pad;
+  double final_h;
+} chem_cell_stats;
+
+/* Fill opts with the defaults (rtol 1e-4, atol 1e-10, order 5, 5000 steps, FP64 LU,
+ * plain driver, automatic launch shape, no adjoint). */
+void chem_opts_default(chem_opts *opts);
+
+/* Compile a mechanism: validate the tables (species indices in range, yields
+ * finite, rate parameters finite, n_species <= CHEM_MAX_SPECIES), build the
+ * Jacobian pattern, a static Markowitz pivot order, the LU fill and the warp
+ * programs, and copy them to the current device.  rx: n_reactions entries,
+ * borrowed.  *out is owned by the caller and released with
+ * chem_mechanism_destroy.  Errors: CHEM_EINVAL, CHEM_ENOMEM, CHEM_ECUDA. */
+int chem_mechanism_create(int32_t n_species, int32_t n_reactions, const chem_reaction *rx,
+                          chem_mech **out);
+void chem_mechanism_destroy(chem_mech *mech);   /* NULL is a no-op */
+int chem_mechanism_info(const chem_mech *mech, chem_mech_info *out);
+/* Jacobian pattern after the static ordering: position of each species in the
+ * pivot order (pos[n_species]) and the LU fill as a dense 0/1 matrix in pivot
+ * order (fill[n_species*n_species], row-major; may be NULL). */
+int chem_mechanism_structure(const chem_mech *mech, int32_t *pos, uint8_t *fill);
+
+/* Allocate the device state of n_cells cells for a mechanism (which must
+ * outlive the batch).  opts NULL = defaults.  *out released with
+ * chem_cells_destroy.  Errors: CHEM_EINVAL, CHEM_ENOMEM, CHEM_ECUDA. */
+int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *opts,
+                      chem_cells **out);
+void chem_cells_destroy(chem_cells *cells);      /* NULL is a no-op */
+
+/* Copy T[n_cells], P[n_cells] and y[n_species][n_cells] into the batch (D2D for
+ * CHEM_MEM_DEVICE, H2D otherwise), asynchronously on stream.  Resets the
+ * adjoint tape.  Errors: CHEM_EINVAL, CHEM_ECUDA. */
+int chem_cells_set_state(chem_cells *cells, const double *T, const double *P, const double *y,
+                         int32_t mem, void *stream);
+/* Per-cell photolysis rates J[n_photolysis][n_cells] (photolysis reactions in
+ * reaction order); NULL reverts to the mechanism's J.  Errors as above. */
+int chem_cells_set_photolysis(chem_cells *cells, const double *J, int32_t mem, void *stream);
+/* Per-reaction log multipliers theta[n_reactions], shared by all cells:
+ * k~_j -> k~_j exp(theta_j).  NULL reverts to theta = 0. */
+int chem_cells_set_theta(chem_cells *cells, const double *theta, int32_t mem, void *stream);
+
+/* Integrate every cell over [0, dt] (dt > 0) on stream; the integrator starts
+ * afresh and the new state replaces the old.  Asynchronous; per-cell outcomes
+ * are read with chem_get_stats.  Errors: CHEM_EINVAL, CHEM_ESTATE, CHEM_ECUDA. */
+int chem_solve_step(chem_cells *cells, double dt, void *stream);
+
+/* Copy the state y[n_species][n_cells] out (synchronises stream when mem is
+ * CHEM_MEM_HOST). */
+int chem_get_state(const chem_cells *cells, double *y, int32_t mem, void *stream);
+/* Copy the per-cell statistics of the last solve (out[n_cells]); synchronises
+ * stream when mem is CHEM_MEM_HOST. */
+int chem_get_stats(const chem_cells *cells, chem_cell_stats *out, int32_t mem, void *stream);
+
+/* Diagnostics for kernel-level parity.  For every cell, with the cell's T, P,
+ * photolysis rates and theta from the batch (set_state must have been
+ * called), evaluate on the GPU with the same device routines the solve uses:
+ *   chem_eval_deriv:        f = f(y)                          (step a2)
+ *   chem_eval_newton_solve: x = (I - c J(y))^{-1} b           (steps a3-a5,
+ *                           in the batch's LU precision)
+ * y, b, f, x are [n_species][n_cells].  With CHEM_MEM_HOST the call allocates
+ * device scratch, copies, and synchronises stream before returning. */
+int chem_eval_deriv(chem_cells *cells, const double *y, double *f, int32_t mem, void *stream);
+int chem_eval_newton_solve(chem_cells *cells, double c, const double *y, const double *b, double *x,
+                           int32_t mem, void *stream);
+
+/* Thread-local description of the last error ("" if none). */
+const char *chem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,302 @@
+"""Thin ctypes binding of libchemgpu.so (include/chemgpu.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  Arrays may be torch tensors (CUDA or CPU) or numpy arrays; CUDA
+tensors are passed as device pointers, everything else as host pointers.
+There is no CPU fallback: if the library is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+import numpy as np
+
+from . import synth
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "_lib", "libchemgpu.so")
+
+MEM_HOST, MEM_DEVICE = 0, 1
+DRIVERS = {"plain": 0, "persistent": 1}
+STATUS = {0: "OK", 1: "MAX_STEPS", 2: "H_TOO_SMALL", 3: "ERR_FAIL", 4: "CONV_FAIL",
+          5: "NONFINITE", 6: "BAD_INPUT"}
+
+# every symbol include/chemgpu.h declares
+EXPORTS = ["chem_opts_default", "chem_mechanism_create", "chem_mechanism_destroy",
+           "chem_mechanism_info", "chem_mechanism_structure", "chem_cells_create",
+           "chem_cells_destroy", "chem_cells_set_state", "chem_cells_set_photolysis",
+           "chem_cells_set_theta", "chem_solve_step", "chem_get_state", "chem_get_stats",
+           "chem_eval_deriv", "chem_eval_newton_solve", "chem_last_error"]
+
+
+class Reaction(ct.Structure):
+    _fields_ = [("kind", ct.c_int32), ("n_reac", ct.c_int32), ("reac", ct.c_int32 * 3),
+                ("n_prod", ct.c_int32), ("prod", ct.c_int32 * 8), ("yld", ct.c_double * 8),
+                ("A", ct.c_double), ("Ea_over_R", ct.c_double), ("B", ct.c_double), ("J", ct.c_double)]
+
+
+class Opts(ct.Structure):
+    _fields_ = [("rtol", ct.c_double), ("atol", ct.c_double), ("max_order", ct.c_int32),
+                ("max_steps", ct.c_int32), ("lu_precision", ct.c_int32), ("driver", ct.c_int32),
+                ("cells_per_block", ct.c_int32), ("blocks_per_sm", ct.c_int32),
+                ("record_adjoint", ct.c_int32), ("tape_steps", ct.c_int32)]
+
+
+class MechInfo(ct.Structure):
+    _fields_ = [(n, ct.c_int32) for n in (
+        "n_species", "n_reactions", "n_photolysis", "nnz_jac", "nnz_lu", "n_pairs",
+        "passes_f", "passes_jac", "passes_lu", "passes_fwd", "passes_bwd",
+        "ops_f", "ops_jac", "ops_lu", "ops_fwd", "ops_bwd")] + \
+        [(n, ct.c_double) for n in ("flops_f", "flops_jac", "flops_lu", "flops_solve")] + \
+        [("smem_per_cell_fp64", ct.c_int32), ("smem_per_cell_fp32", ct.c_int32)]
+
+
+STATS_DTYPE = np.dtype([("status", "<i4"), ("steps", "<i4"), ("rejects", "<i4"),
+                        ("conv_fails", "<i4"), ("newton_iters", "<i4"), ("f_evals", "<i4"),
+                        ("jac_evals", "<i4"), ("solves", "<i4"), ("final_order", "<i4"),
+                        ("pad", "<i4"), ("final_h", "<f8")])
+
+_lib = None
+_lock = threading.Lock()
+
+
+class ChemError(RuntimeError):
+    pass
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or SO_PATH
+        if not os.path.exists(p):
+            raise ChemError(f"CUDA library not built: {p} (run paper_2501_00011_gb300.build.build())")
+        L = ct.CDLL(p)
+        V = ct.c_void_p
+        L.chem_opts_default.argtypes = [V]
+        L.chem_mechanism_create.argtypes = [ct.c_int32, ct.c_int32, V, ct.POINTER(V)]
+        L.chem_mechanism_destroy.argtypes = [V]
+        L.chem_mechanism_info.argtypes = [V, V]
+        L.chem_mechanism_structure.argtypes = [V, V, V]
+        L.chem_cells_create.argtypes = [V, ct.c_int64, V, ct.POINTER(V)]
+        L.chem_cells_destroy.argtypes = [V]
+        L.chem_cells_set_state.argtypes = [V, V, V, V, ct.c_int32, V]
+        L.chem_cells_set_photolysis.argtypes = [V, V, ct.c_int32, V]
+        L.chem_cells_set_theta.argtypes = [V, V, ct.c_int32, V]
+        L.chem_solve_step.argtypes = [V, ct.c_double, V]
+        L.chem_get_state.argtypes = [V, V, ct.c_int32, V]
+        L.chem_get_stats.argtypes = [V, V, ct.c_int32, V]
+        L.chem_eval_deriv.argtypes = [V, V, V, ct.c_int32, V]
+        L.chem_eval_newton_solve.argtypes = [V, ct.c_double, V, V, V, ct.c_int32, V]
+        L.chem_last_error.restype = ct.c_char_p
+        for name in EXPORTS:
+            if name not in ("chem_opts_default", "chem_mechanism_destroy", "chem_cells_destroy",
+                            "chem_last_error"):
+                getattr(L, name).restype = ct.c_int
+        _lib = L
+        return L
+
+
+def _check(rc: int, what: str):
+    if rc < 0:
+        raise ChemError(f"{what} failed ({rc}): {load().chem_last_error().decode()}")
+    return rc
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return ct.c_void_p(getattr(stream, "cuda_stream", stream))
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+def _ptr(a, dtype=np.float64):
+    """(pointer, mem, keepalive) for a torch tensor or numpy array of float64."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float64 or not a.is_contiguous():
+                raise ChemError("tensors must be contiguous float64")
+            return ct.c_void_p(a.data_ptr()), (MEM_DEVICE if a.is_cuda else MEM_HOST), a
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return ct.c_void_p(arr.ctypes.data), MEM_HOST, arr
+
+
+def reactions_from_synth(m: synth.Mechanism):
+    R = m.n_reactions
+    arr = (Reaction * max(R, 1))()
+    for j in range(R):
+        r = arr[j]
+        r.kind = int(m.kind[j])
+        r.n_reac = int(m.n_reac[j])
+        for s in range(3):
+            r.reac[s] = int(m.reac[j, s]) if s < m.n_reac[j] else 0
+        r.n_prod = int(m.n_prod[j])
+        for p in range(8):
+            r.prod[p] = int(m.prod[j, p]) if p < m.n_prod[j] else 0
+            r.yld[p] = float(m.yld[j, p]) if p < m.n_prod[j] else 0.0
+        r.A, r.Ea_over_R, r.B, r.J = float(m.A[j]), float(m.Ea[j]), float(m.B[j]), float(m.J[j])
+    return arr
+
+
+class Mechanism:
+    """A compiled mechanism on the current CUDA device."""
+
+    def __init__(self, mech: synth.Mechanism):
+        L = load()
+        self.synth = mech
+        self.n_species, self.n_reactions = mech.n_species, mech.n_reactions
+        rx = reactions_from_synth(mech)
+        h = ct.c_void_p()
+        _check(L.chem_mechanism_create(self.n_species, self.n_reactions, ct.cast(rx, ct.c_void_p),
+                                       ct.byref(h)), "chem_mechanism_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = MechInfo()
+        _check(load().chem_mechanism_info(self._h, ct.byref(inf)), "chem_mechanism_info")
+        return {k: getattr(inf, k) for k, _ in MechInfo._fields_}
+
+    def structure(self):
+        S = self.n_species
+        pos = np.zeros(S, np.int32)
+        fill = np.zeros((S, S), np.uint8)
+        _check(load().chem_mechanism_structure(self._h, ct.c_void_p(pos.ctypes.data),
+                                               ct.c_void_p(fill.ctypes.data)), "chem_mechanism_structure")
+        return pos, fill
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().chem_mechanism_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Cells:
+    """Device state of a batch of cells."""
+
+    def __init__(self, mech: Mechanism, n_cells: int, rtol: float = 1e-4, atol: float = 1e-10,
+                 max_order: int = 5, max_steps: int = 5000, lu_precision: int = 64,
+                 driver: str = "plain", cells_per_block: int = 0, blocks_per_sm: int = 0,
+                 record_adjoint: bool = False, tape_steps: int = 0):
+        L = load()
+        self.mech = mech
+        self.n_cells = int(n_cells)
+        o = Opts()
+        L.chem_opts_default(ct.byref(o))
+        o.rtol, o.atol, o.max_order, o.max_steps = rtol, atol, max_order, max_steps
+        o.lu_precision, o.driver = lu_precision, DRIVERS[driver]
+        o.cells_per_block, o.blocks_per_sm = cells_per_block, blocks_per_sm
+        o.record_adjoint, o.tape_steps = int(record_adjoint), tape_steps
+        self.opts = o
+        h = ct.c_void_p()
+        _check(L.chem_cells_create(mech.handle, self.n_cells, ct.byref(o), ct.byref(h)), "chem_cells_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_state(self, T, P, y, stream=None):
+        (pt, mt, k1), (pp, mp, k2), (py, my, k3) = _ptr(T), _ptr(P), _ptr(y)
+        if not (mt == mp == my):
+            raise ChemError("T, P and y must all be on the host or all on the device")
+        _check(load().chem_cells_set_state(self._h, pt, pp, py, mt, _stream_ptr(stream)), "chem_cells_set_state")
+
+    def set_photolysis(self, J, stream=None):
+        if J is None:
+            _check(load().chem_cells_set_photolysis(self._h, None, MEM_HOST, None), "chem_cells_set_photolysis")
+            return
+        pj, mj, keep = _ptr(J)
+        _check(load().chem_cells_set_photolysis(self._h, pj, mj, _stream_ptr(stream)), "chem_cells_set_photolysis")
+
+    def set_theta(self, theta, stream=None):
+        if theta is None:
+            _check(load().chem_cells_set_theta(self._h, None, MEM_HOST, None), "chem_cells_set_theta")
+            return
+        pt, mt, keep = _ptr(theta)
+        _check(load().chem_cells_set_theta(self._h, pt, mt, _stream_ptr(stream)), "chem_cells_set_theta")
+
+    def solve_step(self, dt: float, stream=None):
+        _check(load().chem_solve_step(self._h, float(dt), _stream_ptr(stream)), "chem_solve_step")
+
+    def get_state(self, out=None, stream=None):
+        """Returns y [S, C]; into `out` (tensor/array) if given, else a new numpy array."""
+        if out is None:
+            out = np.empty((self.mech.n_species, self.n_cells))
+        po, mo, keep = _ptr(out)
+        if isinstance(out, np.ndarray) and keep is not out:
+            raise ChemError("out must be a contiguous float64 array")
+        _check(load().chem_get_state(self._h, po, mo, _stream_ptr(stream)), "chem_get_state")
+        return out
+
+    def get_stats(self, stream=None) -> np.ndarray:
+        st = np.zeros(self.n_cells, STATS_DTYPE)
+        _check(load().chem_get_stats(self._h, ct.c_void_p(st.ctypes.data), MEM_HOST, _stream_ptr(stream)),
+               "chem_get_stats")
+        return st
+
+    def eval_deriv(self, y, stream=None):
+        """f(y) for every cell ([S, C] numpy in, numpy out), on the GPU."""
+        yy = np.ascontiguousarray(y, np.float64)
+        f = np.empty_like(yy)
+        _check(load().chem_eval_deriv(self._h, ct.c_void_p(yy.ctypes.data), ct.c_void_p(f.ctypes.data), MEM_HOST,
+                                      _stream_ptr(stream)), "chem_eval_deriv")
+        return f
+
+    def eval_newton_solve(self, c: float, y, b, stream=None):
+        """x = (I - c J(y))^{-1} b for every cell, on the GPU."""
+        yy = np.ascontiguousarray(y, np.float64)
+        bb = np.ascontiguousarray(b, np.float64)
+        x = np.empty_like(yy)
+        _check(load().chem_eval_newton_solve(self._h, float(c), ct.c_void_p(yy.ctypes.data), ct.c_void_p(bb.ctypes.data),
+                                             ct.c_void_p(x.ctypes.data), MEM_HOST, _stream_ptr(stream)),
+               "chem_eval_newton_solve")
+        return x
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().chem_cells_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve(mech: Mechanism, cells: synth.Cells, dt: float, rtol: float, atol: float, n_steps: int = 1,
+          **opts):
+    """Convenience: host arrays in, (y [S, C], stats) out, through the C ABI."""
+    c = Cells(mech, cells.n_cells, rtol=rtol, atol=atol, **opts)
+    try:
+        c.set_state(cells.T, cells.P, cells.y)
+        if cells.J is not None:
+            c.set_photolysis(cells.J)
+        for _ in range(n_steps):
+            c.solve_step(dt)
+        y = c.get_state()
+        return y, c.get_stats()
+    finally:
+        c.close()

@@ -1,0 +1,344 @@
+// capi.cpp -- the extern "C" entry points declared in include/chemgpu.h.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+using namespace chemgpu;
+
+struct chem_mech {
+  Mechanism m;
+};
+
+struct chem_cells {
+  const chem_mech *mech = nullptr;
+  int64_t n = 0;
+  chem_opts opts{};
+  double *T = nullptr, *P = nullptr, *y = nullptr, *J = nullptr, *theta = nullptr;
+  chem_cell_stats *stats = nullptr;
+  int *queue = nullptr;
+  bool have_state = false, use_J = false, use_theta = false;
+  int device = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return CHEM_ECUDA;
+}
+
+cudaMemcpyKind kind_in(int32_t mem) { return mem == CHEM_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+cudaMemcpyKind kind_out(int32_t mem) { return mem == CHEM_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+int check_mem(int32_t mem) {
+  if (mem != CHEM_MEM_HOST && mem != CHEM_MEM_DEVICE) return fail(CHEM_EINVAL, "mem must be CHEM_MEM_HOST or CHEM_MEM_DEVICE");
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void chem_opts_default(chem_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->rtol = 1e-4;
+  o->atol = 1e-10;
+  o->max_order = 5;
+  o->max_steps = 5000;
+  o->lu_precision = 64;
+  o->driver = CHEM_DRIVER_PLAIN;
+}
+
+const char *chem_last_error(void) { return g_err.c_str(); }
+
+int chem_mechanism_create(int32_t n_species, int32_t n_reactions, const chem_reaction *rx, chem_mech **out) {
+  g_err.clear();
+  if (!out) return fail(CHEM_EINVAL, "out is NULL");
+  *out = nullptr;
+  chem_mech *h = new (std::nothrow) chem_mech();
+  if (!h) return fail(CHEM_ENOMEM, "host allocation failed");
+  std::string msg;
+  int rc = compile_mechanism(n_species, n_reactions, rx, h->m, msg);
+  if (rc == 0) rc = upload_mechanism(h->m, msg);
+  if (rc != 0) {
+    delete h;
+    return fail(rc, msg);
+  }
+  *out = h;
+  return 0;
+}
+
+void chem_mechanism_destroy(chem_mech *h) {
+  if (!h) return;
+  free_mechanism(h->m);
+  delete h;
+}
+
+int chem_mechanism_info(const chem_mech *h, chem_mech_info *o) {
+  if (!h || !o) return fail(CHEM_EINVAL, "NULL argument");
+  const Mechanism &m = h->m;
+  std::memset(o, 0, sizeof(*o));
+  o->n_species = m.S;
+  o->n_reactions = m.R;
+  o->n_photolysis = m.n_phot;
+  o->nnz_jac = m.nnz_jac;
+  o->nnz_lu = m.nnz_lu;
+  o->n_pairs = m.n_pairs;
+  o->passes_f = m.f_prog.n_pass();
+  o->passes_jac = m.m_prog.n_pass();
+  o->passes_lu = m.lu_prog.n_pass();
+  o->passes_fwd = m.fwd_prog.n_pass();
+  o->passes_bwd = m.bwd_prog.n_pass();
+  o->ops_f = m.f_prog.n_ops;
+  o->ops_jac = m.m_prog.n_ops;
+  o->ops_lu = m.lu_prog.n_ops;
+  o->ops_fwd = m.fwd_prog.n_ops;
+  o->ops_bwd = m.bwd_prog.n_ops;
+  o->flops_f = m.flops_f;
+  o->flops_jac = m.flops_jac;
+  o->flops_lu = m.flops_lu;
+  o->flops_solve = m.flops_solve;
+  o->smem_per_cell_fp64 = (int32_t)smem_per_cell(m.dev, 64);
+  o->smem_per_cell_fp32 = (int32_t)smem_per_cell(m.dev, 32);
+  return 0;
+}
+
+int chem_mechanism_structure(const chem_mech *h, int32_t *pos, uint8_t *fill) {
+  if (!h || !pos) return fail(CHEM_EINVAL, "NULL argument");
+  const Mechanism &m = h->m;
+  for (int i = 0; i < m.S; ++i) pos[i] = m.pos[i];
+  if (fill) std::memcpy(fill, m.fill.data(), m.fill.size());
+  return 0;
+}
+
+int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *opts, chem_cells **out) {
+  g_err.clear();
+  if (!out) return fail(CHEM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!mech) return fail(CHEM_EINVAL, "mechanism is NULL");
+  if (n_cells < 0 || n_cells > ((int64_t)1 << 31)) return fail(CHEM_EINVAL, "n_cells must be in 0..2^31");
+  chem_opts o;
+  if (opts) o = *opts; else chem_opts_default(&o);
+  if (!(o.rtol > 0.0) || !(o.atol > 0.0)) return fail(CHEM_EINVAL, "rtol and atol must be > 0");
+  if (o.max_order < 1 || o.max_order > QMAX) return fail(CHEM_EINVAL, "max_order must be 1..5");
+  if (o.max_steps < 1) return fail(CHEM_EINVAL, "max_steps must be >= 1");
+  if (o.lu_precision != 64 && o.lu_precision != 32) return fail(CHEM_EINVAL, "lu_precision must be 64 or 32");
+  if (o.driver != CHEM_DRIVER_PLAIN && o.driver != CHEM_DRIVER_PERSISTENT) return fail(CHEM_EINVAL, "bad driver");
+  if (o.cells_per_block < 0 || o.cells_per_block > MAX_WARPS_PER_BLOCK || o.blocks_per_sm < 0) return fail(CHEM_EINVAL, "bad launch shape");
+  const int wmax = max_warps_per_block(mech->m.dev, o.lu_precision);
+  if (wmax < 1) return fail(CHEM_EINVAL, "mechanism working set does not fit in shared memory");
+  if (o.cells_per_block > wmax) return fail(CHEM_EINVAL, "cells_per_block exceeds the shared-memory limit");
+  if (o.cells_per_block == 0) o.cells_per_block = (o.driver == CHEM_DRIVER_PERSISTENT) ? wmax : 1;
+
+  chem_cells *c = new (std::nothrow) chem_cells();
+  if (!c) return fail(CHEM_ENOMEM, "host allocation failed");
+  c->mech = mech;
+  c->n = n_cells;
+  c->opts = o;
+  cudaGetDevice(&c->device);
+  const int S = mech->m.S, R = mech->m.R;
+  const size_t n = (size_t)(n_cells > 0 ? n_cells : 1);
+  cudaError_t e = cudaSuccess;
+  if ((e = cudaMalloc(&c->T, n * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&c->P, n * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&c->y, n * S * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&c->stats, n * sizeof(chem_cell_stats))) != cudaSuccess ||
+      (e = cudaMalloc(&c->queue, 2 * sizeof(long long))) != cudaSuccess ||
+      (e = cudaMalloc(&c->theta, (R > 0 ? R : 1) * sizeof(double))) != cudaSuccess ||
+      (mech->m.n_phot > 0 && (e = cudaMalloc(&c->J, n * mech->m.n_phot * sizeof(double))) != cudaSuccess)) {
+    chem_cells_destroy(c);
+    return fail(CHEM_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  if ((e = cudaMemset(c->stats, 0, n * sizeof(chem_cell_stats))) != cudaSuccess) {
+    chem_cells_destroy(c);
+    return cuda_fail(e, "cudaMemset");
+  }
+  *out = c;
+  return 0;
+}
+
+void chem_cells_destroy(chem_cells *c) {
+  if (!c) return;
+  cudaFree(c->T);
+  cudaFree(c->P);
+  cudaFree(c->y);
+  cudaFree(c->J);
+  cudaFree(c->theta);
+  cudaFree(c->stats);
+  cudaFree(c->queue);
+  delete c;
+}
+
+int chem_cells_set_state(chem_cells *c, const double *T, const double *P, const double *y, int32_t mem, void *stream) {
+  g_err.clear();
+  if (!c || !T || !P || !y) return fail(CHEM_EINVAL, "NULL argument");
+  if (int rc = check_mem(mem)) return rc;
+  if (c->n == 0) { c->have_state = true; return 0; }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)c->n, S = (size_t)c->mech->m.S;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(c->T, T, n * sizeof(double), kind_in(mem), s)) != cudaSuccess) return cuda_fail(e, "set_state T");
+  if ((e = cudaMemcpyAsync(c->P, P, n * sizeof(double), kind_in(mem), s)) != cudaSuccess) return cuda_fail(e, "set_state P");
+  if ((e = cudaMemcpyAsync(c->y, y, n * S * sizeof(double), kind_in(mem), s)) != cudaSuccess) return cuda_fail(e, "set_state y");
+  c->have_state = true;
+  return 0;
+}
+
+int chem_cells_set_photolysis(chem_cells *c, const double *J, int32_t mem, void *stream) {
+  g_err.clear();
+  if (!c) return fail(CHEM_EINVAL, "NULL argument");
+  if (!J) { c->use_J = false; return 0; }
+  if (int rc = check_mem(mem)) return rc;
+  const size_t np = (size_t)c->mech->m.n_phot;
+  if (np == 0 || c->n == 0) { c->use_J = false; return 0; }
+  cudaError_t e = cudaMemcpyAsync(c->J, J, np * (size_t)c->n * sizeof(double), kind_in(mem), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_photolysis");
+  c->use_J = true;
+  return 0;
+}
+
+int chem_cells_set_theta(chem_cells *c, const double *theta, int32_t mem, void *stream) {
+  g_err.clear();
+  if (!c) return fail(CHEM_EINVAL, "NULL argument");
+  if (!theta) { c->use_theta = false; return 0; }
+  if (int rc = check_mem(mem)) return rc;
+  const size_t R = (size_t)c->mech->m.R;
+  if (R == 0) return 0;
+  cudaError_t e = cudaMemcpyAsync(c->theta, theta, R * sizeof(double), kind_in(mem), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_theta");
+  c->use_theta = true;
+  return 0;
+}
+
+int chem_solve_step(chem_cells *c, double dt, void *stream) {
+  g_err.clear();
+  if (!c) return fail(CHEM_EINVAL, "NULL argument");
+  if (!(dt > 0.0) || !(dt < 1e300)) return fail(CHEM_EINVAL, "dt must be positive and finite");
+  if (!c->have_state) return fail(CHEM_ESTATE, "solve_step before set_state");
+  if (c->n == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  CellsDev cd;
+  cd.n_cells = c->n;
+  cd.T = c->T;
+  cd.P = c->P;
+  cd.J = c->use_J ? c->J : nullptr;
+  cd.theta = c->use_theta ? c->theta : nullptr;
+  cd.y = c->y;
+  cd.stats = c->stats;
+  cd.queue = nullptr;
+  if (c->opts.driver == CHEM_DRIVER_PERSISTENT) {
+    cudaError_t e = cudaMemsetAsync(c->queue, 0, sizeof(long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+    cd.queue = c->queue;
+  }
+  LaunchCfg cfg;
+  cfg.lu_precision = c->opts.lu_precision;
+  cfg.driver = c->opts.driver;
+  cfg.warps_per_block = c->opts.cells_per_block;
+  cfg.blocks_per_sm = c->opts.blocks_per_sm;
+  cfg.rtol = c->opts.rtol;
+  cfg.atol = c->opts.atol;
+  cfg.dt = dt;
+  cfg.max_order = c->opts.max_order;
+  cfg.max_steps = c->opts.max_steps;
+  cudaError_t e = launch_solve(c->mech->m.dev, cd, cfg, s);
+  if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
+  return 0;
+}
+
+int chem_get_state(const chem_cells *c, double *y, int32_t mem, void *stream) {
+  g_err.clear();
+  if (!c || !y) return fail(CHEM_EINVAL, "NULL argument");
+  if (int rc = check_mem(mem)) return rc;
+  if (c->n == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(y, c->y, (size_t)c->n * c->mech->m.S * sizeof(double), kind_out(mem), s);
+  if (e != cudaSuccess) return cuda_fail(e, "get_state");
+  if (mem == CHEM_MEM_HOST && (e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "get_state sync");
+  return 0;
+}
+
+int chem_get_stats(const chem_cells *c, chem_cell_stats *out, int32_t mem, void *stream) {
+  g_err.clear();
+  if (!c || !out) return fail(CHEM_EINVAL, "NULL argument");
+  if (int rc = check_mem(mem)) return rc;
+  if (c->n == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(out, c->stats, (size_t)c->n * sizeof(chem_cell_stats), kind_out(mem), s);
+  if (e != cudaSuccess) return cuda_fail(e, "get_stats");
+  if (mem == CHEM_MEM_HOST && (e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "get_stats sync");
+  return 0;
+}
+
+namespace {
+
+CellsDev cells_dev(chem_cells *c) {
+  CellsDev cd;
+  cd.n_cells = c->n;
+  cd.T = c->T;
+  cd.P = c->P;
+  cd.J = c->use_J ? c->J : nullptr;
+  cd.theta = c->use_theta ? c->theta : nullptr;
+  cd.y = c->y;
+  cd.stats = c->stats;
+  cd.queue = nullptr;
+  return cd;
+}
+
+int probe(chem_cells *c, int mode, double cc, const double *y, const double *b, double *out, int32_t mem, void *stream) {
+  g_err.clear();
+  if (!c || !y || !out || (mode == 1 && !b)) return fail(CHEM_EINVAL, "NULL argument");
+  if (int rc = check_mem(mem)) return rc;
+  if (!c->have_state) return fail(CHEM_ESTATE, "diagnostic before set_state");
+  if (c->n == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)c->n * c->mech->m.S * sizeof(double);
+  const double *dy = y, *db = b;
+  double *dout = out, *tmp = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (mem == CHEM_MEM_HOST) {
+    if ((e = cudaMalloc(&tmp, 3 * bytes)) != cudaSuccess) return fail(CHEM_ENOMEM, "cudaMalloc for diagnostic scratch");
+    double *ty = tmp, *tb = tmp + bytes / sizeof(double), *to = tmp + 2 * (bytes / sizeof(double));
+    if ((e = cudaMemcpyAsync(ty, y, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (b && (e = cudaMemcpyAsync(tb, b, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)) {
+      cudaFree(tmp);
+      return cuda_fail(e, "diagnostic copy-in");
+    }
+    dy = ty;
+    db = b ? tb : nullptr;
+    dout = to;
+  }
+  e = launch_probe(c->mech->m.dev, cells_dev(c), c->opts.lu_precision, mode, cc, dy, db, dout, s);
+  if (e == cudaSuccess && mem == CHEM_MEM_HOST) {
+    e = cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "diagnostic kernel");
+  return 0;
+}
+
+}  // namespace
+
+int chem_eval_deriv(chem_cells *c, const double *y, double *f, int32_t mem, void *stream) {
+  return probe(c, 0, 0.0, y, nullptr, f, mem, stream);
+}
+
+int chem_eval_newton_solve(chem_cells *c, double cc, const double *y, const double *b, double *x, int32_t mem,
+                           void *stream) {
+  return probe(c, 1, cc, y, b, x, mem, stream);
+}
+
+}  // extern "C"

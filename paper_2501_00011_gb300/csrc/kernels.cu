@@ -1,0 +1,759 @@
+// kernels.cu -- the multi-cell BDF / modified-Newton solve on sm_103a.
+//
+// One warp integrates one cell (Implementations section of the paper:
+// all cells' data in one structure, the cell loop inside the solver; its
+// Conclusions: the whole solver on the GPU).  Per cell:
+//   a1  rate constants k~_j(T, P[, J_cell][, theta])         lanes over reactions
+//   a2  f(y): rates r_j, then the species-major gather       f program
+//   a3/a4  M = I - c J(y_pred) straight into the LU slots    partials + M program
+//   a5  static-order sparse LU, forward/back substitution    LU / fwd / bwd programs
+//   a6  modified Newton, a7 error test and step/order control, history update
+// The cell's sparse working set (LU values, f/J scratch) lives in shared
+// memory; per-species vectors and the BDF history live in registers, species
+// s = lane + 32 k.  All control decisions are warp-uniform: every lane
+// computes the same reductions (butterfly sums are order-symmetric).
+//
+// FP64 on GB300 issues one warp instruction per 16 SM cycles whether 1 or 32
+// lanes are active, so the sparse work is packed into 32-wide passes by the
+// host scheduler and scalar control is kept to few instructions.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace chemgpu {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int NEWTON_MAXITER = 3;
+constexpr double CRDOWN = 0.3, RDIV = 2.0, NLSCOEF = 0.1, DGMAX = 0.3, THRESH = 1.5;
+constexpr int MSBP = 20, MXNEF = 7, MXNCF = 10;
+constexpr double ETA_CF = 0.25, ETA_MXF = 0.2, ETA_CST_SAFETY = 0.9, ETA_CST_MIN = 0.1, STRETCH = 1e-3;
+constexpr double K_BOLTZMANN = 1.380649e-23;
+
+struct SolveParams {
+  double rtol, atol, dt;
+  int max_order, max_steps;
+  int cell_bytes;      // shared memory per warp
+  int wd_pad;          // Wd length rounded so WL starts 16-byte aligned
+  int warps_per_block;
+};
+
+// Newton-Raphson refinement of the hardware reciprocal approximation:
+// r <- r (2 - x r), twice (quadratic convergence from the ~2^-23 estimate).
+__device__ __forceinline__ double recip_nr(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  return r;
+}
+__device__ __forceinline__ double lu_recip(double x) { return recip_nr(x); }
+__device__ __forceinline__ float lu_recip(float x) { return __frcp_rn(x); }
+
+__device__ __forceinline__ ushort4 ld_op(const ushort4 *p) {
+  const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+  return make_ushort4((unsigned short)(v.x & 0xffff), (unsigned short)(v.x >> 16),
+                      (unsigned short)(v.y & 0xffff), (unsigned short)(v.y >> 16));
+}
+
+// Run a warp program over the work array W (see internal.h for the op forms).
+template <typename T, bool NEG>
+__device__ __forceinline__ void run_prog(const ProgramDev pr, T *__restrict__ W, const int lane) {
+  const int np = pr.n_pass;
+  const ushort4 *ops = pr.ops + lane;
+  constexpr int PF = 4;   // passes prefetched ahead
+  const ushort4 empty = make_ushort4(OP_EMPTY, 0, 0, 0);
+  ushort4 buf[PF];
+#pragma unroll
+  for (int i = 0; i < PF; ++i) buf[i] = (i < np) ? ld_op(ops + i * WARP) : empty;
+  for (int p0 = 0; p0 < np; p0 += PF) {
+#pragma unroll
+    for (int i = 0; i < PF; ++i) {
+      const int p = p0 + i;
+      if (p >= np) break;
+      const ushort4 op = buf[i];
+      buf[i] = (p + PF < np) ? ld_op(ops + (size_t)(p + PF) * WARP) : empty;
+      if (op.x != OP_EMPTY) {
+        if (op.x & OP_RECIP) {
+          W[op.x & 0x7fff] = -lu_recip(W[op.y]);
+        } else {
+          const T a = W[op.y], b = W[op.z], c = W[op.w];
+          W[op.x] = NEG ? fma(-a, b, c) : fma(a, b, c);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+
+// Largest grid factor g_i with err <= thr[p][i] (thr decreasing in i), else g_min.
+__device__ __forceinline__ double grid_eta(const double *thr, const double *g, double err, int p, int lane) {
+  const double *tp = thr + p * GRID_N;
+  const bool ok0 = err <= __ldg(tp + lane);
+  const bool ok1 = (lane + WARP < GRID_N) && err <= __ldg(tp + lane + WARP);
+  const int cnt = __popc(__ballot_sync(FULL, ok0)) + __popc(__ballot_sync(FULL, ok1));
+  return __ldg(g + (cnt > 0 ? cnt - 1 : 0));
+}
+
+template <typename T, int KS>
+struct Cell {
+  const MechDev &M;
+  const SolveParams &P;
+  double *Wd;
+  T *WL;
+  int lane;
+  int pos[KS];        // pivot position of this lane's species
+  bool own[KS];       // species index < S
+  double Sd;      // number of species as a double (norm divisor)
+
+  __device__ Cell(const MechDev &m, const SolveParams &p, double *wd, T *wl, int l)
+      : M(m), P(p), Wd(wd), WL(wl), lane(l) {
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const int s = lane + WARP * k;
+      own[k] = s < M.S;
+      pos[k] = own[k] ? __ldg(M.sp_pos + s) : 0;
+    }
+    Sd = (double)M.S;
+  }
+
+  __device__ double wrms(const double (&v)[KS], const double (&w)[KS]) const {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < KS; ++k)
+      if (own[k]) {
+        const double t = v[k] * w[k];
+        s = fma(t, t, s);
+      }
+    s = warp_sum(s);
+    return sqrt(s / Sd);
+  }
+
+  __device__ void weights(const double (&y)[KS], double (&w)[KS]) const {
+#pragma unroll
+    for (int k = 0; k < KS; ++k) w[k] = own[k] ? 1.0 / (P.rtol * fabs(y[k]) + P.atol) : 0.0;
+  }
+
+  // a2: f(y) into registers
+  __device__ void eval_f(const double (&y)[KS], double (&f)[KS]) {
+#pragma unroll
+    for (int k = 0; k < KS; ++k)
+      if (own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
+    __syncwarp();
+    for (int j = lane; j < M.R; j += WARP) {
+      const uint2 sl = __ldg(reinterpret_cast<const uint2 *>(M.rx_slots) + j);
+      double r = Wd[M.d_KT + j] * Wd[sl.x & 0xffff];
+      if (M.max_reac > 1) r *= Wd[sl.x >> 16];
+      if (M.max_reac > 2) r *= Wd[sl.y & 0xffff];
+      Wd[M.d_RT + j] = r;
+    }
+    __syncwarp();
+    run_prog<double, false>(M.f_prog, Wd, lane);
+#pragma unroll
+    for (int k = 0; k < KS; ++k) f[k] = own[k] ? Wd[M.d_F + lane + WARP * k] : 0.0;
+    __syncwarp();
+  }
+
+  // a3-a5: M = I - c J(y) in the LU slots, then factor
+  __device__ void form_and_factor(double c, const double (&y)[KS]) {
+#pragma unroll
+    for (int k = 0; k < KS; ++k)
+      if (own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
+    for (int i = lane; i < M.m_clear; i += WARP) WL[i] = (T)0;
+    __syncwarp();
+    for (int k = lane; k < M.S; k += WARP) WL[__ldg(M.lu_diag + k)] = (T)1;
+    const double mc = -c;
+    for (int pr = lane; pr < M.n_pairs; pr += WARP) {
+      const int j = __ldg(M.pair_rx + pr);
+      const unsigned o = __ldg(reinterpret_cast<const unsigned *>(M.pair_other) + pr);
+      double p = mc * Wd[M.d_KT + j];
+      if (M.max_reac > 1) p *= Wd[o & 0xffff];
+      if (M.max_reac > 2) p *= Wd[o >> 16];
+      WL[M.L_P + pr] = (T)p;
+    }
+    __syncwarp();
+    run_prog<T, false>(M.m_prog, WL, lane);
+    run_prog<T, false>(M.lu_prog, WL, lane);
+  }
+
+  // a5: x = M^{-1} b with the factored M
+  __device__ void solve(const double (&b)[KS], double (&x)[KS]) {
+#pragma unroll
+    for (int k = 0; k < KS; ++k)
+      if (own[k]) WL[M.L_X + pos[k]] = (T)b[k];
+    __syncwarp();
+    run_prog<T, false>(M.fwd_prog, WL, lane);
+    run_prog<T, true>(M.bwd_prog, WL, lane);
+#pragma unroll
+    for (int k = 0; k < KS; ++k) x[k] = own[k] ? (double)WL[M.L_X + pos[k]] : 0.0;
+    __syncwarp();
+  }
+};
+
+// History rescale for a step ratio eta at order q: D'_i = sum_{m>=i} T_im(eta) D_m,
+// T_im a polynomial in eta whose coefficients the host precomputed.
+template <int KS>
+__device__ __forceinline__ void rescale(double (&D)[NROW][KS], int q, double eta, const double *coef, int lane) {
+  // lane (i-1)*QMAX + (m-1) evaluates T_im
+  double tv = 0.0;
+  if (lane < QMAX * QMAX) {
+    const double *cp = coef + lane * (QMAX + 1);
+    tv = __ldg(cp + QMAX);
+#pragma unroll
+    for (int p = QMAX - 1; p >= 0; --p) tv = fma(tv, eta, __ldg(cp + p));
+  }
+  double nd[QMAX][KS];
+#pragma unroll
+  for (int i = 1; i <= QMAX; ++i) {
+    if (i > q) break;
+#pragma unroll
+    for (int k = 0; k < KS; ++k) nd[i - 1][k] = 0.0;
+#pragma unroll
+    for (int mm = 1; mm <= QMAX; ++mm) {
+      if (mm > q) break;
+      if (mm < i) continue;
+      const double t = __shfl_sync(FULL, tv, (i - 1) * QMAX + (mm - 1));
+#pragma unroll
+      for (int k = 0; k < KS; ++k) nd[i - 1][k] = fma(t, D[mm][k], nd[i - 1][k]);
+    }
+  }
+#pragma unroll
+  for (int i = 1; i <= QMAX; ++i) {
+    if (i > q) break;
+#pragma unroll
+    for (int k = 0; k < KS; ++k) D[i][k] = nd[i - 1][k];
+  }
+}
+
+template <int KS>
+__device__ __forceinline__ void get_row(const double (&D)[NROW][KS], int r, double (&out)[KS]) {
+#pragma unroll
+  for (int k = 0; k < KS; ++k) out[k] = 0.0;
+#pragma unroll
+  for (int m = 0; m < NROW; ++m)
+    if (m == r) {
+#pragma unroll
+      for (int k = 0; k < KS; ++k) out[k] = D[m][k];
+    }
+}
+
+
+// Inputs of one cell: y0 into registers, a1 rate constants into Wd[KT].
+// Returns true (warp-uniform) if any input or rate constant is not finite or
+// T, P are not positive.
+template <int KS>
+__device__ bool load_cell(const MechDev &M, const CellsDev &C, double *Wd, const int lane, const int64_t cell,
+                          const bool (&own)[KS], double (&y0)[KS]) {
+  const int64_t NC = C.n_cells;
+  const int R = M.R;
+  const double Tc = C.T[cell], Pc = C.P[cell];
+  bool bad = !(Tc > 0.0) || !(Pc > 0.0) || !isfinite(Tc) || !isfinite(Pc);
+#pragma unroll
+  for (int k = 0; k < KS; ++k) {
+    y0[k] = own[k] ? C.y[(int64_t)(lane + WARP * k) * NC + cell] : 0.0;
+    if (own[k] && !isfinite(y0[k])) bad = true;
+  }
+  if (!__any_sync(FULL, bad)) {
+    const double n_air = Pc / (K_BOLTZMANN * Tc) * 1e-6;
+    for (int j = lane; j < R; j += WARP) {
+      double kj;
+      if (__ldg(M.rx_kind + j) == CHEM_PHOTOLYSIS) {
+        kj = C.J ? C.J[(int64_t)__ldg(M.rx_phot + j) * NC + cell] : __ldg(M.rx_J + j);
+      } else {
+        kj = __ldg(M.rx_A + j) * exp(-__ldg(M.rx_Ea + j) / Tc) * pow(Tc / 300.0, __ldg(M.rx_B + j));
+        const int nr = __ldg(M.rx_nreac + j);
+        for (int r = 1; r < nr; ++r) kj *= n_air;
+      }
+      if (C.theta) kj *= exp(C.theta[j]);
+      Wd[M.d_KT + j] = kj;
+      if (!isfinite(kj)) bad = true;
+    }
+  }
+  bad = __any_sync(FULL, bad);
+  __syncwarp();
+  return bad;
+}
+
+template <typename T, int KS>
+__device__ void solve_cell(const MechDev &M, const CellsDev &C, const SolveParams &P, double *Wd, T *WL,
+                           const int lane, const int64_t cell, const double *gam, const double *igam) {
+  const int R = M.R;
+  const int64_t NC = C.n_cells;
+  chem_cell_stats st = {};
+  int status = CHEM_CELL_OK;
+
+  for (int k = lane; k < M.d_nconst; k += WARP) Wd[__ldg(M.d_const_idx + k)] = __ldg(M.d_const_val + k);
+  for (int k = lane; k < M.L_nconst; k += WARP) WL[__ldg(M.L_const_idx + k)] = (T)__ldg(M.L_const_val + k);
+
+  Cell<T, KS> cl(M, P, Wd, WL, lane);
+  double y0[KS];
+  const bool bad = load_cell<KS>(M, C, Wd, lane, cell, cl.own, y0);
+
+  const double dt = P.dt;
+  int q = 1;
+  double h = 0.0;
+  double D[NROW][KS];
+  if (bad) {
+    status = CHEM_CELL_BAD_INPUT;
+  } else {
+    double w[KS], f[KS], tmp[KS], f0[KS];
+    cl.weights(y0, w);
+    // initial step (order 1)
+    cl.eval_f(y0, f0);
+    st.f_evals++;
+    const double d0 = cl.wrms(y0, w), d1 = cl.wrms(f0, w);
+    double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 * dt : 0.01 * d0 / d1;
+    if (h0 > dt) h0 = dt;
+#pragma unroll
+    for (int k = 0; k < KS; ++k) tmp[k] = y0[k] + h0 * f0[k];
+    cl.eval_f(tmp, f);
+    st.f_evals++;
+#pragma unroll
+    for (int k = 0; k < KS; ++k) tmp[k] = f[k] - f0[k];
+    const double d2 = cl.wrms(tmp, w) / h0;
+    const double dm = d1 > d2 ? d1 : d2;
+    const double h1 = (dm <= 1e-15) ? fmax(1e-6 * dt, h0 * 1e-3) : sqrt(0.01 / dm);
+    h = fmin(fmin(100.0 * h0, h1), dt);
+#pragma unroll
+    for (int m = 0; m < NROW; ++m)
+#pragma unroll
+      for (int k = 0; k < KS; ++k) D[m][k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      D[0][k] = y0[k];
+      D[1][k] = h * f0[k];
+    }
+
+    double t = 0.0, cM = 0.0, rho = 1.0;
+    int n_eq = 0, have_M = 0, force_M = 0, n_since_M = 0, nef = 0, ncf = 0, last = 0;
+    const int qmax = P.max_order;
+    double ypred[KS], psi[KS], d[KS], y[KS], x[KS];
+
+    for (;;) {
+      if (st.steps >= P.max_steps) { status = CHEM_CELL_MAX_STEPS; break; }
+      if (dt - t <= h * (1.0 + STRETCH)) {
+        const double hn = dt - t;
+        if (hn != h) {
+          rescale<KS>(D, q, hn / h, M.rescale_coef, lane);
+          h = hn;
+          n_eq = 0;
+        }
+        last = 1;
+      } else {
+        last = 0;
+      }
+      if (!last && t + h == t) { status = CHEM_CELL_H_TOO_SMALL; break; }
+
+      const double c = h * igam[q];
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        ypred[k] = D[0][k];
+        psi[k] = 0.0;
+      }
+#pragma unroll
+      for (int m = 1; m <= QMAX; ++m) {
+        if (m > q) break;
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+          ypred[k] += D[m][k];
+          psi[k] = fma(gam[m], D[m][k], psi[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < KS; ++k) psi[k] *= igam[q];
+
+      int fresh = 0;
+      if (!have_M || force_M || fabs(c / cM - 1.0) > DGMAX || n_since_M >= MSBP) {
+        cl.form_and_factor(c, ypred);
+        have_M = 1;
+        cM = c;
+        n_since_M = 0;
+        rho = 1.0;
+        fresh = 1;
+        st.jac_evals++;
+      }
+      force_M = 0;
+      const double scale = (c == cM) ? 1.0 : 2.0 / (1.0 + c / cM);
+      const double tol = NLSCOEF * (double)(q + 1);
+
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        d[k] = 0.0;
+        y[k] = ypred[k];
+      }
+      double del = 0.0, del_prev = 0.0;
+      int conv = 0;
+      for (int it = 0; it < NEWTON_MAXITER; ++it) {
+        cl.eval_f(y, f);
+        st.f_evals++;
+#pragma unroll
+        for (int k = 0; k < KS; ++k) tmp[k] = c * f[k] - psi[k] - d[k];
+        cl.solve(tmp, x);
+        st.solves++;
+        if (scale != 1.0) {
+#pragma unroll
+          for (int k = 0; k < KS; ++k) x[k] *= scale;
+        }
+        del = cl.wrms(x, w);
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+          d[k] += x[k];
+          y[k] = ypred[k] + d[k];
+        }
+        st.newton_iters++;
+        if (it > 0) rho = fmax(CRDOWN * rho, del / del_prev);
+        if (del * fmin(1.0, rho) <= tol) { conv = 1; break; }
+        if (it > 0 && del > RDIV * del_prev) break;
+        del_prev = del;
+      }
+      if (!conv) {
+        st.conv_fails++;
+        ncf++;
+        if (ncf >= MXNCF) { status = CHEM_CELL_CONV_FAIL; break; }
+        if (!fresh) {
+          force_M = 1;
+        } else {
+          rescale<KS>(D, q, ETA_CF, M.rescale_coef, lane);
+          h *= ETA_CF;
+          n_eq = 0;
+        }
+        continue;
+      }
+
+      // inequality constraint y >= 0
+      {
+        bool neg = false;
+#pragma unroll
+        for (int k = 0; k < KS; ++k) neg |= cl.own[k] && y[k] < 0.0;
+        if (__any_sync(FULL, neg)) {
+          double vs = 0.0, eta_c = 1.0;
+#pragma unroll
+          for (int k = 0; k < KS; ++k)
+            if (cl.own[k] && y[k] < 0.0) {
+              const double v = y[k] * w[k];
+              vs = fma(v, v, vs);
+              const double r = (D[0][k] > 0.0) ? D[0][k] / (D[0][k] - y[k]) : 0.0;
+              eta_c = fmin(eta_c, r);
+            }
+          vs = warp_sum(vs);
+          eta_c = warp_min(eta_c);
+          if (sqrt(vs / cl.Sd) <= tol) {
+#pragma unroll
+            for (int k = 0; k < KS; ++k)
+              if (cl.own[k] && y[k] < 0.0) {
+                d[k] -= y[k];
+                y[k] = 0.0;
+              }
+          } else {
+            st.rejects++;
+            nef++;
+            if (nef >= MXNEF) { status = CHEM_CELL_ERR_FAIL; break; }
+            double eta = ETA_CST_SAFETY * eta_c;
+            if (eta < ETA_CST_MIN) eta = ETA_CST_MIN;
+            rescale<KS>(D, q, eta, M.rescale_coef, lane);
+            h *= eta;
+            n_eq = 0;
+            continue;
+          }
+        }
+      }
+
+      // local error test
+      const double err = cl.wrms(d, w) / (double)(q + 1);
+      if (!(err <= 1.0)) {
+        st.rejects++;
+        nef++;
+        if (nef >= MXNEF) { status = CHEM_CELL_ERR_FAIL; break; }
+        double eta = grid_eta(M.grid_thr2, M.grid_g, err, q, lane);
+        if (nef >= 2 && eta > ETA_MXF) eta = ETA_MXF;
+        if (nef >= 3 && q > 1) q -= 1;
+        rescale<KS>(D, q, eta, M.rescale_coef, lane);
+        h *= eta;
+        n_eq = 0;
+        continue;
+      }
+
+      // accept: update the backward differences
+      t = last ? dt : t + h;
+      st.steps++;
+      n_since_M++;
+      nef = 0;
+      ncf = 0;
+      {
+        double dq1[KS];
+        get_row<KS>(D, q + 1, dq1);
+#pragma unroll
+        for (int m = 2; m < NROW; ++m)
+          if (m == q + 2) {
+#pragma unroll
+            for (int k = 0; k < KS; ++k) D[m][k] = d[k] - dq1[k];
+          }
+#pragma unroll
+        for (int m = 1; m < NROW; ++m)
+          if (m == q + 1) {
+#pragma unroll
+            for (int k = 0; k < KS; ++k) D[m][k] = d[k];
+          }
+#pragma unroll
+        for (int m = QMAX; m >= 0; --m) {
+          if (m > q) continue;
+#pragma unroll
+          for (int k = 0; k < KS; ++k) D[m][k] += D[m + 1][k];
+        }
+      }
+      if (last) break;
+      n_eq++;
+
+      double eta = grid_eta(M.grid_thr2, M.grid_g, err, q, lane);
+      int qn = q;
+      if (n_eq >= q + 1) {
+        if (q > 1) {
+          double row[KS];
+          get_row<KS>(D, q, row);
+          const double e = cl.wrms(row, w) / (double)q;
+          const double em = grid_eta(M.grid_thr2, M.grid_g, e, q - 1, lane);
+          if (em > eta) { eta = em; qn = q - 1; }
+        }
+        if (q < qmax) {
+          double row[KS];
+          get_row<KS>(D, q + 2, row);
+          const double e = cl.wrms(row, w) / (double)(q + 2);
+          const double ep = grid_eta(M.grid_thr3, M.grid_g, e, q + 1, lane);
+          if (ep > eta) { eta = ep; qn = q + 1; }
+        }
+      }
+      if (eta >= THRESH) {
+        q = qn;
+        rescale<KS>(D, q, eta, M.rescale_coef, lane);
+        h *= eta;
+        n_eq = 0;
+      }
+      double y_acc[KS];
+#pragma unroll
+      for (int k = 0; k < KS; ++k) y_acc[k] = D[0][k];
+      cl.weights(y_acc, w);
+    }
+    if (status == CHEM_CELL_OK) {
+      bool nf = false;
+#pragma unroll
+      for (int k = 0; k < KS; ++k) nf |= cl.own[k] && !isfinite(D[0][k]);
+      if (__any_sync(FULL, nf)) status = CHEM_CELL_NONFINITE;
+    }
+    if (status == CHEM_CELL_OK) {
+#pragma unroll
+      for (int k = 0; k < KS; ++k)
+        if (cl.own[k]) C.y[(int64_t)(lane + WARP * k) * NC + cell] = D[0][k];
+    }
+  }
+  if (lane == 0) {
+    st.status = status;
+    st.final_order = q;
+    st.final_h = h;
+    C.stats[cell] = st;
+  }
+  __syncwarp();
+}
+
+__constant__ double c_gam[QMAX + 2];
+__constant__ double c_igam[QMAX + 2];
+
+template <typename T, int KS>
+__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const MechDev M, const CellsDev C, const SolveParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & (WARP - 1);
+  const int warp = threadIdx.x / WARP;
+  double *Wd = reinterpret_cast<double *>(smem + (size_t)warp * P.cell_bytes);
+  T *WL = reinterpret_cast<T *>(Wd + P.wd_pad);
+  double gam[QMAX + 2], igam[QMAX + 2];
+#pragma unroll
+  for (int m = 0; m < QMAX + 2; ++m) {
+    gam[m] = c_gam[m];
+    igam[m] = c_igam[m];
+  }
+  if (C.queue) {
+    for (;;) {
+      long long cell = 0;
+      if (lane == 0) cell = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(C.queue), 1ull);
+      cell = __shfl_sync(FULL, cell, 0);
+      if (cell >= C.n_cells) break;
+      solve_cell<T, KS>(M, C, P, Wd, WL, lane, cell, gam, igam);
+    }
+  } else {
+    const int64_t cell = (int64_t)blockIdx.x * P.warps_per_block + warp;
+    if (cell < C.n_cells) solve_cell<T, KS>(M, C, P, Wd, WL, lane, cell, gam, igam);
+  }
+}
+
+
+// Diagnostic: per cell, f(y) (mode 0) or x = (I - c J(y))^{-1} b (mode 1),
+// using the same device routines as the solve.
+template <typename T, int KS>
+__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) probe_kernel(const MechDev M, const CellsDev C, const SolveParams P,
+                                                                  int mode, double c, const double *yin, const double *bin,
+                                                                  double *out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & (WARP - 1);
+  const int warp = threadIdx.x / WARP;
+  const int64_t cell = (int64_t)blockIdx.x * P.warps_per_block + warp;
+  if (cell >= C.n_cells) return;
+  double *Wd = reinterpret_cast<double *>(smem + (size_t)warp * P.cell_bytes);
+  T *WL = reinterpret_cast<T *>(Wd + P.wd_pad);
+  for (int k = lane; k < M.d_nconst; k += WARP) Wd[__ldg(M.d_const_idx + k)] = __ldg(M.d_const_val + k);
+  for (int k = lane; k < M.L_nconst; k += WARP) WL[__ldg(M.L_const_idx + k)] = (T)__ldg(M.L_const_val + k);
+  Cell<T, KS> cl(M, P, Wd, WL, lane);
+  double y0[KS];
+  load_cell<KS>(M, C, Wd, lane, cell, cl.own, y0);
+  const int64_t NC = C.n_cells;
+  double y[KS], b[KS], r[KS];
+#pragma unroll
+  for (int k = 0; k < KS; ++k) {
+    const int64_t i = (int64_t)(lane + WARP * k) * NC + cell;
+    y[k] = cl.own[k] ? yin[i] : 0.0;
+    b[k] = (cl.own[k] && bin) ? bin[i] : 0.0;
+  }
+  if (mode == 0) {
+    cl.eval_f(y, r);
+  } else {
+    cl.form_and_factor(c, y);
+    cl.solve(b, r);
+  }
+#pragma unroll
+  for (int k = 0; k < KS; ++k)
+    if (cl.own[k]) out[(int64_t)(lane + WARP * k) * NC + cell] = r[k];
+}
+
+template <typename T, int KS>
+cudaError_t launch_probe_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int mode, double c,
+                           const double *y, const double *b, double *out, cudaStream_t stream) {
+  const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
+  cudaError_t e = cudaFuncSetAttribute(probe_kernel<T, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int blocks = (int)((C.n_cells + P.warps_per_block - 1) / P.warps_per_block);
+  probe_kernel<T, KS><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, P, mode, c, y, b, out);
+  return cudaGetLastError();
+}
+
+template <typename T, int KS>
+cudaError_t launch_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int blocks, cudaStream_t stream) {
+  const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
+  static int configured_bytes[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && configured_bytes[dev] < (int)smem) {
+    cudaError_t e = cudaFuncSetAttribute(solve_kernel<T, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured_bytes[dev] = (int)smem;
+  }
+  solve_kernel<T, KS><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, P);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t smem_per_cell(const MechDev &m, int lu_precision) {
+  const size_t wd = (size_t)((m.Wd_len + 1) & ~1) * sizeof(double);
+  const size_t wl = (size_t)m.WL_len * (lu_precision == 32 ? sizeof(float) : sizeof(double));
+  return (wd + wl + 15) & ~(size_t)15;
+}
+
+int max_warps_per_block(const MechDev &m, int lu_precision) {
+  int dev = 0, smem_block = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int w = (int)(smem_block / smem_per_cell(m, lu_precision));
+  return w < MAX_WARPS_PER_BLOCK ? w : MAX_WARPS_PER_BLOCK;
+}
+
+cudaError_t set_constants() {
+  double gam[QMAX + 2], igam[QMAX + 2];
+  gam[0] = igam[0] = 0.0;
+  for (int k = 1; k <= QMAX + 1; ++k) {
+    double g = 0.0;
+    for (int i = 1; i <= k; ++i) g += 1.0 / (double)i;
+    gam[k] = g;
+    igam[k] = 1.0 / g;
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_gam, gam, sizeof(gam));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_igam, igam, sizeof(igam));
+}
+
+cudaError_t launch_probe(const MechDev &M, const CellsDev &C, int lu_precision, int mode, double c, const double *y,
+                         const double *b, double *out, cudaStream_t stream) {
+  if (C.n_cells <= 0) return cudaSuccess;
+  SolveParams P{};
+  P.wd_pad = (M.Wd_len + 1) & ~1;
+  P.cell_bytes = (int)smem_per_cell(M, lu_precision);
+  P.warps_per_block = 1;
+  const int KS = (M.S + WARP - 1) / WARP;
+  const bool f32 = lu_precision == 32;
+#define CHEM_PROBE(KSV)                                                                       \
+  case KSV:                                                                                   \
+    return f32 ? launch_probe_t<float, KSV>(M, C, P, mode, c, y, b, out, stream)              \
+               : launch_probe_t<double, KSV>(M, C, P, mode, c, y, b, out, stream);
+  switch (KS) {
+    CHEM_PROBE(1)
+    CHEM_PROBE(2)
+    CHEM_PROBE(3)
+    CHEM_PROBE(4)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef CHEM_PROBE
+}
+
+cudaError_t launch_solve(const MechDev &M, const CellsDev &C, const LaunchCfg &cfg, cudaStream_t stream) {
+  if (C.n_cells <= 0) return cudaSuccess;
+  SolveParams P;
+  P.rtol = cfg.rtol;
+  P.atol = cfg.atol;
+  P.dt = cfg.dt;
+  P.max_order = cfg.max_order;
+  P.max_steps = cfg.max_steps;
+  P.wd_pad = (M.Wd_len + 1) & ~1;
+  P.cell_bytes = (int)smem_per_cell(M, cfg.lu_precision);
+  P.warps_per_block = cfg.warps_per_block;
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  int blocks;
+  if (cfg.driver == CHEM_DRIVER_PERSISTENT) {
+    blocks = n_sm * (cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : 1);
+    const int64_t need = (C.n_cells + P.warps_per_block - 1) / P.warps_per_block;
+    if (blocks > need) blocks = (int)need;
+  } else {
+    blocks = (int)((C.n_cells + P.warps_per_block - 1) / P.warps_per_block);
+  }
+  const int KS = (M.S + WARP - 1) / WARP;
+  const bool f32 = cfg.lu_precision == 32;
+#define CHEM_LAUNCH(KSV)                                                               \
+  case KSV:                                                                            \
+    return f32 ? launch_t<float, KSV>(M, C, P, blocks, stream)                         \
+               : launch_t<double, KSV>(M, C, P, blocks, stream);
+  switch (KS) {
+    CHEM_LAUNCH(1)
+    CHEM_LAUNCH(2)
+    CHEM_LAUNCH(3)
+    CHEM_LAUNCH(4)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef CHEM_LAUNCH
+}
+
+}  // namespace chemgpu

@@ -1,0 +1,504 @@
+// mechanism.cpp -- host-side mechanism compiler.
+//
+// Turns reaction tables (Background section of the paper: reactions
+// c1 y1 + ... -> c_{m+1} y_{m+1} + ..., each adding -c_i r_j to its reactants
+// and +c_i r_j to its products) into the device tables the solve kernels run:
+//   * the net stoichiometry nu_ij and the f(y) gather (a2);
+//   * the Jacobian pattern J_il = sum_j nu_ij dr_j/dy_l plus the diagonal (a3);
+//   * a static Markowitz pivot order, the symbolic LU fill, and the warp
+//     programs that form M = I - c J in the LU slots, factor it and run the
+//     forward/back substitutions (a4, a5).
+// The CVODE solver the paper names stores its Jacobian in a SPARSE matrix
+// (Background section); here the sparse structure is analysed once per
+// mechanism and baked into race-free 32-lane programs.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "internal.h"
+
+namespace chemgpu {
+
+namespace {
+
+// ---------------------------------------------------------------- scheduler
+// Places ops into passes of at most 32 so that no two ops of a pass touch the
+// same location unless both only read it; ops keep the program order of every
+// location they share.
+struct Scheduler {
+  std::vector<int> lastw, lastr;
+  std::vector<std::vector<Op>> passes;
+  std::vector<int> kind;
+  int n_ops = 0;
+  explicit Scheduler(int n_loc) : lastw(n_loc, -1), lastr(n_loc, -1) {}
+
+  void add(const Op &op, int k, const int *reads, int nr, int write) {
+    int e = 0;
+    for (int i = 0; i < nr; ++i) e = std::max(e, lastw[reads[i]] + 1);
+    e = std::max(e, lastw[write] + 1);
+    e = std::max(e, lastr[write] + 1);
+    int p = e;
+    while (p < (int)passes.size() && (kind[p] != k || passes[p].size() >= (size_t)WARP)) ++p;
+    if (p == (int)passes.size()) {
+      passes.emplace_back();
+      kind.push_back(k);
+    }
+    passes[p].push_back(op);
+    for (int i = 0; i < nr; ++i) lastr[reads[i]] = std::max(lastr[reads[i]], p);
+    lastw[write] = p;
+    n_ops++;
+  }
+  void fma(int t, int a, int b, int c) {
+    const int r[3] = {a, b, c};
+    add(Op{(uint16_t)t, (uint16_t)a, (uint16_t)b, (uint16_t)c}, 0, r, 3, t);
+  }
+  void recip(int t, int a) {
+    const int r[1] = {a};
+    add(Op{(uint16_t)(t | OP_RECIP), (uint16_t)a, 0, 0}, 1, r, 1, t);
+  }
+  HostProgram finish() const {
+    HostProgram hp;
+    for (const auto &p : passes) {
+      for (const Op &o : p) hp.ops.push_back(o);
+      for (size_t i = p.size(); i < (size_t)WARP; ++i) hp.ops.push_back(Op{OP_EMPTY, 0, 0, 0});
+    }
+    hp.n_ops = n_ops;
+    return hp;
+  }
+};
+
+// target = (fresh ? 0 : target) + sum_k W[coef_k] * W[src_k], split into chunks
+// of at most L terms accumulated in separate temporaries and then combined.
+void add_sum(Scheduler &s, int target, bool fresh, const std::vector<std::pair<int, int>> &terms,
+             int L, int &temp_next, int ZERO, int ONE) {
+  if (terms.empty()) {
+    if (fresh) s.fma(target, ZERO, ZERO, ZERO);
+    return;
+  }
+  std::vector<int> temps;
+  for (size_t c0 = 0; c0 < terms.size(); c0 += L) {
+    const size_t c1 = std::min(terms.size(), c0 + (size_t)L);
+    int acc;
+    bool first_fresh;
+    if (c0 == 0) {
+      acc = target;
+      first_fresh = fresh;
+    } else {
+      acc = temp_next++;
+      temps.push_back(acc);
+      first_fresh = true;
+    }
+    for (size_t k = c0; k < c1; ++k) {
+      const int c = (k == c0 && first_fresh) ? ZERO : acc;
+      s.fma(acc, terms[k].first, terms[k].second, c);
+    }
+  }
+  for (int t : temps) s.fma(target, ONE, t, target);
+}
+
+std::vector<int> markowitz_order(int S, std::vector<uint8_t> B) {
+  std::vector<int> order;
+  std::vector<uint8_t> alive(S, 1);
+  for (int step = 0; step < S; ++step) {
+    long best = -1;
+    int bv = -1;
+    for (int v = 0; v < S; ++v) {
+      if (!alive[v]) continue;
+      long r = 0, c = 0;
+      for (int u = 0; u < S; ++u) {
+        if (!alive[u] || u == v) continue;
+        r += B[v * S + u];
+        c += B[u * S + v];
+      }
+      const long score = r * c;
+      if (bv < 0 || score < best) { best = score; bv = v; }
+    }
+    order.push_back(bv);
+    for (int a = 0; a < S; ++a) {
+      if (!alive[a] || a == bv || !B[a * S + bv]) continue;
+      for (int b = 0; b < S; ++b)
+        if (alive[b] && b != bv && B[bv * S + b]) B[a * S + b] = 1;
+    }
+    alive[bv] = 0;
+  }
+  return order;
+}
+
+struct ConstTable {
+  std::map<double, int> idx;
+  std::vector<double> vals;
+  int base = 0;
+  int get(double v) {
+    auto it = idx.find(v);
+    if (it != idx.end()) return it->second;
+    const int i = base + (int)vals.size();
+    idx[v] = i;
+    vals.push_back(v);
+    return i;
+  }
+};
+
+constexpr int CHUNK = 8;
+
+}  // namespace
+
+int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::string &msg) {
+  if (S < 1 || S > CHEM_MAX_SPECIES) { msg = "n_species must be in 1..128"; return CHEM_EINVAL; }
+  if (R < 0 || R > 16384) { msg = "n_reactions must be in 0..16384"; return CHEM_EINVAL; }
+  if (R > 0 && !rx) { msg = "reaction table is NULL"; return CHEM_EINVAL; }
+  for (int j = 0; j < R; ++j) {
+    const chem_reaction &r = rx[j];
+    if (r.kind != CHEM_THERMAL && r.kind != CHEM_PHOTOLYSIS) { msg = "reaction " + std::to_string(j) + ": bad kind"; return CHEM_EINVAL; }
+    if (r.n_reac < 1 || r.n_reac > CHEM_MAX_REAC) { msg = "reaction " + std::to_string(j) + ": n_reac must be 1..3"; return CHEM_EINVAL; }
+    if (r.n_prod < 0 || r.n_prod > CHEM_MAX_PROD) { msg = "reaction " + std::to_string(j) + ": n_prod must be 0..8"; return CHEM_EINVAL; }
+    for (int s = 0; s < r.n_reac; ++s)
+      if (r.reac[s] < 0 || r.reac[s] >= S) { msg = "reaction " + std::to_string(j) + ": reactant index out of range"; return CHEM_EINVAL; }
+    for (int p = 0; p < r.n_prod; ++p) {
+      if (r.prod[p] < 0 || r.prod[p] >= S) { msg = "reaction " + std::to_string(j) + ": product index out of range"; return CHEM_EINVAL; }
+      if (!std::isfinite(r.yield[p])) { msg = "reaction " + std::to_string(j) + ": non-finite yield"; return CHEM_EINVAL; }
+    }
+    if (r.kind == CHEM_THERMAL && !(std::isfinite(r.A) && std::isfinite(r.Ea_over_R) && std::isfinite(r.B))) {
+      msg = "reaction " + std::to_string(j) + ": non-finite Arrhenius parameters"; return CHEM_EINVAL;
+    }
+    if (r.kind == CHEM_PHOTOLYSIS && !std::isfinite(r.J)) { msg = "reaction " + std::to_string(j) + ": non-finite J"; return CHEM_EINVAL; }
+  }
+  m.S = S;
+  m.R = R;
+  m.rx.assign(rx, rx + R);
+  m.max_reac = 1;
+  m.n_phot = 0;
+  for (int j = 0; j < R; ++j) {
+    m.max_reac = std::max(m.max_reac, (int)rx[j].n_reac);
+    m.n_phot += rx[j].kind == CHEM_PHOTOLYSIS;
+  }
+
+  // net stoichiometry nu_ij (reaction j, species i), in species order per reaction
+  std::vector<std::vector<std::pair<int, double>>> nu(R);
+  for (int j = 0; j < R; ++j) {
+    std::map<int, double> acc;
+    for (int s = 0; s < rx[j].n_reac; ++s) acc[rx[j].reac[s]] -= 1.0;
+    for (int p = 0; p < rx[j].n_prod; ++p) acc[rx[j].prod[p]] += rx[j].yield[p];
+    for (auto &kv : acc)
+      if (kv.second != 0.0) nu[j].push_back(kv);
+  }
+
+  // Jacobian pattern (original species order) with the diagonal
+  std::vector<uint8_t> P(S * S, 0);
+  for (int i = 0; i < S; ++i) P[i * S + i] = 1;
+  int n_pairs = 0;
+  for (int j = 0; j < R; ++j)
+    for (int s = 0; s < rx[j].n_reac; ++s) {
+      n_pairs++;
+      const int l = rx[j].reac[s];
+      for (auto &kv : nu[j]) P[kv.first * S + l] = 1;
+    }
+  m.n_pairs = n_pairs;
+  m.nnz_jac = 0;
+  for (uint8_t v : P) m.nnz_jac += v;
+
+  // static pivot order and symbolic fill in pivot order
+  const std::vector<int> order = markowitz_order(S, P);
+  m.pos.assign(S, 0);
+  for (int k = 0; k < S; ++k) m.pos[order[k]] = k;
+  std::vector<uint8_t> F(S * S, 0);
+  for (int i = 0; i < S; ++i)
+    for (int l = 0; l < S; ++l)
+      if (P[i * S + l]) F[m.pos[i] * S + m.pos[l]] = 1;
+  for (int k = 0; k < S; ++k)
+    for (int i = k + 1; i < S; ++i) {
+      if (!F[i * S + k]) continue;
+      for (int j = k + 1; j < S; ++j)
+        if (F[k * S + j]) F[i * S + j] = 1;
+    }
+  m.fill = F;
+  std::vector<int> slot(S * S, -1);
+  int nnz = 0;
+  for (int i = 0; i < S; ++i)
+    for (int j = 0; j < S; ++j)
+      if (F[i * S + j]) slot[i * S + j] = nnz++;
+  m.nnz_lu = nnz;
+
+  // ---- per-cell array layouts
+  // Wd (double): y[S], ONE, ZERO, kt[R], rates[R], f[S], f temps, nu constants
+  MechDev &d = m.dev;
+  d.S = S;
+  d.R = R;
+  d.max_reac = m.max_reac;
+  d.n_phot = m.n_phot;
+  d.n_pairs = n_pairs;
+  d.d_Y = 0;
+  d.d_ONE = S;
+  d.d_ZERO = S + 1;
+  d.d_KT = S + 2;
+  d.d_RT = d.d_KT + R;
+  d.d_F = d.d_RT + R;
+  int d_temp = d.d_F + S;
+  // WL (LU precision): LU[nnz], ninv[S], x[S], P[n_pairs], ZERO, ONE, M temps, nu constants
+  d.L_LU = 0;
+  d.nnz_lu = nnz;
+  d.L_NINV = nnz;
+  d.L_X = nnz + S;
+  d.L_P = d.L_X + S;
+  d.L_ZERO = d.L_P + n_pairs;
+  const int L_ONE = d.L_ZERO + 1;
+  int L_temp = L_ONE + 1;
+  d.m_clear = nnz;
+
+  // ---- f program: f_i = sum_j nu_ij r_j, species-major, chunked
+  {
+    std::vector<std::vector<std::pair<double, int>>> by_species(S);
+    for (int j = 0; j < R; ++j)
+      for (auto &kv : nu[j]) by_species[kv.first].push_back({kv.second, j});
+    int n_temp = 0;
+    for (int i = 0; i < S; ++i) n_temp += (int)std::max<size_t>(1, (by_species[i].size() + CHUNK - 1) / CHUNK) - 1;
+    ConstTable ct;
+    ct.base = d_temp + n_temp;
+    std::vector<std::vector<std::pair<int, int>>> terms(S);
+    double flops = 0;
+    for (int i = 0; i < S; ++i)
+      for (auto &t : by_species[i]) {
+        terms[i].push_back({ct.get(t.first), d.d_RT + t.second});
+        flops += 2;
+      }
+    for (int j = 0; j < R; ++j) flops += rx[j].n_reac;
+    Scheduler sch(ct.base + (int)ct.vals.size() + 8);
+    int temp_next = d_temp;
+    for (int i = 0; i < S; ++i) add_sum(sch, d.d_F + i, true, terms[i], CHUNK, temp_next, d.d_ZERO, d.d_ONE);
+    m.f_prog = sch.finish();
+    m.flops_f = flops;
+    d.Wd_len = ct.base + (int)ct.vals.size();
+    m.d_consts_v = {1.0, 0.0};
+    m.d_consts_i = {d.d_ONE, d.d_ZERO};
+    for (size_t k = 0; k < ct.vals.size(); ++k) {
+      m.d_consts_v.push_back(ct.vals[k]);
+      m.d_consts_i.push_back(ct.base + (int)k);
+    }
+  }
+
+  // ---- pairs (reaction, reactant slot) and the M program
+  {
+    m.pair_rx.clear();
+    m.pair_other.clear();
+    std::vector<std::vector<std::pair<double, int>>> slot_terms(nnz);
+    int pidx = 0;
+    double flops = 0;
+    for (int j = 0; j < R; ++j)
+      for (int s = 0; s < rx[j].n_reac; ++s) {
+        int o[2] = {d.d_ONE, d.d_ONE};
+        int no = 0;
+        for (int s2 = 0; s2 < rx[j].n_reac; ++s2)
+          if (s2 != s) o[no++] = d.d_Y + rx[j].reac[s2];
+        m.pair_rx.push_back(j);
+        m.pair_other.push_back({o[0], o[1]});
+        flops += rx[j].n_reac;    // k~ times the other reactants, times -c
+        const int l = rx[j].reac[s];
+        for (auto &kv : nu[j]) {
+          const int sl = slot[m.pos[kv.first] * S + m.pos[l]];
+          slot_terms[sl].push_back({kv.second, pidx});
+        }
+        pidx++;
+      }
+    int n_temp = 0;
+    for (int k = 0; k < nnz; ++k)
+      n_temp += (int)std::max<size_t>(1, (slot_terms[k].size() + CHUNK - 1) / CHUNK) - 1;
+    ConstTable ct;
+    ct.base = L_temp + n_temp;
+    std::vector<std::vector<std::pair<int, int>>> terms(nnz);
+    for (int k = 0; k < nnz; ++k)
+      for (auto &t : slot_terms[k]) {
+        terms[k].push_back({ct.get(t.first), d.L_P + t.second});
+        flops += 2;
+      }
+    Scheduler sch(ct.base + (int)ct.vals.size() + 64);
+    int temp_next = L_temp;
+    for (int k = 0; k < nnz; ++k)
+      if (!terms[k].empty()) add_sum(sch, d.L_LU + k, false, terms[k], CHUNK, temp_next, d.L_ZERO, L_ONE);
+    m.m_prog = sch.finish();
+    m.flops_jac = flops;
+    d.WL_len = ct.base + (int)ct.vals.size();
+    m.L_consts_v = {0.0, 1.0};
+    m.L_consts_i = {d.L_ZERO, L_ONE};
+    for (size_t k = 0; k < ct.vals.size(); ++k) {
+      m.L_consts_v.push_back(ct.vals[k]);
+      m.L_consts_i.push_back(ct.base + (int)k);
+    }
+  }
+
+  // ---- LU program (right-looking; L stored negated, ninv_k = -1/u_kk)
+  {
+    Scheduler sch(d.WL_len + 8);
+    double flops = 0;
+    m.lu_diag.assign(S, 0);
+    for (int k = 0; k < S; ++k) m.lu_diag[k] = d.L_LU + slot[k * S + k];
+    for (int k = 0; k < S; ++k) {
+      const int dk = d.L_LU + slot[k * S + k];
+      const int nk = d.L_NINV + k;
+      sch.recip(nk, dk);
+      flops += 1;
+      std::vector<int> Lc, Ur;
+      for (int i = k + 1; i < S; ++i)
+        if (F[i * S + k]) Lc.push_back(i);
+      for (int j = k + 1; j < S; ++j)
+        if (F[k * S + j]) Ur.push_back(j);
+      for (int i : Lc) {
+        const int ik = d.L_LU + slot[i * S + k];
+        sch.fma(ik, ik, nk, d.L_ZERO);
+        flops += 1;
+      }
+      for (int i : Lc)
+        for (int j : Ur) {
+          const int ij = d.L_LU + slot[i * S + j];
+          sch.fma(ij, d.L_LU + slot[i * S + k], d.L_LU + slot[k * S + j], ij);
+          flops += 2;
+        }
+    }
+    m.lu_prog = sch.finish();
+    m.flops_lu = flops;
+  }
+
+  // ---- forward (x_i += (-l_ik) x_k) and backward (x_k = x_k / u_kk; x_i -= u_ik x_k) programs
+  {
+    Scheduler f(d.WL_len + 8), b(d.WL_len + 8);
+    double flops = 0;
+    for (int k = 0; k < S; ++k)
+      for (int i = k + 1; i < S; ++i)
+        if (F[i * S + k]) {
+          f.fma(d.L_X + i, d.L_LU + slot[i * S + k], d.L_X + k, d.L_X + i);
+          flops += 2;
+        }
+    for (int k = S - 1; k >= 0; --k) {
+      b.fma(d.L_X + k, d.L_NINV + k, d.L_X + k, d.L_ZERO);   // -ninv * x = x / u_kk
+      flops += 1;
+      for (int i = 0; i < k; ++i)
+        if (F[i * S + k]) {
+          b.fma(d.L_X + i, d.L_LU + slot[i * S + k], d.L_X + k, d.L_X + i);
+          flops += 2;
+        }
+    }
+    m.fwd_prog = f.finish();
+    m.bwd_prog = b.finish();
+    m.flops_solve = flops;
+  }
+  if (d.WL_len > 0x7ffe || d.Wd_len > 0x7ffe) { msg = "mechanism too large for 15-bit work indices"; return CHEM_EINVAL; }
+  return 0;
+}
+
+namespace {
+
+template <typename T>
+int put(Mechanism &m, const std::vector<T> &v, const T **dst, std::string &msg) {
+  *dst = nullptr;
+  if (v.empty()) return 0;
+  void *p = nullptr;
+  if (cudaMalloc(&p, v.size() * sizeof(T)) != cudaSuccess) { msg = "cudaMalloc failed for mechanism tables"; return CHEM_ENOMEM; }
+  m.allocations.push_back(p);
+  if (cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) { msg = "cudaMemcpy of mechanism tables failed"; return CHEM_ECUDA; }
+  *dst = (const T *)p;
+  return 0;
+}
+
+int put_prog(Mechanism &m, const HostProgram &hp, ProgramDev &pd, std::string &msg) {
+  std::vector<ushort4> v(hp.ops.size());
+  for (size_t i = 0; i < v.size(); ++i) v[i] = make_ushort4(hp.ops[i].t, hp.ops[i].a, hp.ops[i].b, hp.ops[i].c);
+  pd.n_pass = hp.n_pass();
+  return put(m, v, &pd.ops, msg);
+}
+
+// polynomial coefficients (in eta) of R(eta)_{jm} = prod_{l<m} (l - j eta)/(l+1)
+void r_poly(int j, int mm, double *c /* QMAX+1 */) {
+  for (int p = 0; p <= QMAX; ++p) c[p] = 0.0;
+  c[0] = 1.0;
+  for (int l = 0; l < mm; ++l) {
+    double n[QMAX + 1] = {0};
+    for (int p = 0; p <= QMAX; ++p) {
+      n[p] += c[p] * (double)l / (double)(l + 1);
+      if (p + 1 <= QMAX) n[p + 1] += -c[p] * (double)j / (double)(l + 1);
+    }
+    for (int p = 0; p <= QMAX; ++p) c[p] = n[p];
+  }
+}
+
+}  // namespace
+
+int upload_mechanism(Mechanism &m, std::string &msg) {
+  MechDev &d = m.dev;
+  const int S = m.S, R = m.R;
+  cudaGetDevice(&m.device);
+  std::vector<int> kind(R), nreac(R), phot(R);
+  std::vector<double> A(R), Ea(R), B(R), J(R);
+  std::vector<ushort4> slots(R);
+  int ip = 0;
+  for (int j = 0; j < R; ++j) {
+    const chem_reaction &r = m.rx[j];
+    kind[j] = r.kind;
+    nreac[j] = r.n_reac;
+    phot[j] = r.kind == CHEM_PHOTOLYSIS ? ip++ : -1;
+    A[j] = r.A;
+    Ea[j] = r.Ea_over_R;
+    B[j] = r.B;
+    J[j] = r.J;
+    uint16_t sl[3] = {(uint16_t)d.d_ONE, (uint16_t)d.d_ONE, (uint16_t)d.d_ONE};
+    for (int s = 0; s < r.n_reac; ++s) sl[s] = (uint16_t)(d.d_Y + r.reac[s]);
+    slots[j] = make_ushort4(sl[0], sl[1], sl[2], 0);
+  }
+  std::vector<ushort2> po(m.pair_other.size());
+  for (size_t k = 0; k < po.size(); ++k) po[k] = make_ushort2((uint16_t)m.pair_other[k].first, (uint16_t)m.pair_other[k].second);
+  std::vector<double> thr2(7 * GRID_N), thr3(7 * GRID_N), g(GRID_N);
+  for (int p = 0; p < 7; ++p)
+    for (int i = GRID_IMIN; i <= GRID_IMAX; ++i) {
+      thr2[p * GRID_N + i - GRID_IMIN] = 1.0 / (2.0 * exp2((double)i * (double)(p + 1) / 8.0));
+      thr3[p * GRID_N + i - GRID_IMIN] = 1.0 / (3.0 * exp2((double)i * (double)(p + 1) / 8.0));
+    }
+  for (int i = GRID_IMIN; i <= GRID_IMAX; ++i) g[i - GRID_IMIN] = exp2((double)i / 8.0);
+  int rc = 0;
+  if ((rc = put(m, kind, &d.rx_kind, msg)) || (rc = put(m, nreac, &d.rx_nreac, msg)) ||
+      (rc = put(m, phot, &d.rx_phot, msg)) || (rc = put(m, A, &d.rx_A, msg)) ||
+      (rc = put(m, Ea, &d.rx_Ea, msg)) || (rc = put(m, B, &d.rx_B, msg)) || (rc = put(m, J, &d.rx_J, msg)) ||
+      (rc = put(m, slots, &d.rx_slots, msg)) || (rc = put(m, m.pair_rx, &d.pair_rx, msg)) ||
+      (rc = put(m, po, &d.pair_other, msg)) || (rc = put(m, m.pos, &d.sp_pos, msg)) ||
+      (rc = put(m, m.lu_diag, &d.lu_diag, msg)) || (rc = put(m, m.d_consts_v, &d.d_const_val, msg)) ||
+      (rc = put(m, m.d_consts_i, &d.d_const_idx, msg)) || (rc = put(m, m.L_consts_v, &d.L_const_val, msg)) ||
+      (rc = put(m, m.L_consts_i, &d.L_const_idx, msg)) || (rc = put(m, thr2, &d.grid_thr2, msg)) ||
+      (rc = put(m, thr3, &d.grid_thr3, msg)) || (rc = put(m, g, &d.grid_g, msg)) ||
+      (rc = put_prog(m, m.f_prog, d.f_prog, msg)) || (rc = put_prog(m, m.m_prog, d.m_prog, msg)) ||
+      (rc = put_prog(m, m.lu_prog, d.lu_prog, msg)) || (rc = put_prog(m, m.fwd_prog, d.fwd_prog, msg)) ||
+      (rc = put_prog(m, m.bwd_prog, d.bwd_prog, msg))) {
+    free_mechanism(m);
+    return rc;
+  }
+  d.d_nconst = (int)m.d_consts_v.size();
+  d.L_nconst = (int)m.L_consts_v.size();
+  // T(eta) = U R(eta), U = R(1): coefficients of each entry as a polynomial in eta
+  std::vector<double> coef(QMAX * QMAX * (QMAX + 1), 0.0);
+  for (int i = 1; i <= QMAX; ++i)
+    for (int mm = 1; mm <= QMAX; ++mm) {
+      double *acc = &coef[((i - 1) * QMAX + (mm - 1)) * (QMAX + 1)];
+      for (int j = 1; j <= QMAX; ++j) {
+        double u[QMAX + 1], r[QMAX + 1];
+        r_poly(i, j, u);          // U_{ij} = R(1)_{ij}: the polynomial at eta = 1
+        double uij = 0.0;
+        for (int p = 0; p <= QMAX; ++p) uij += u[p];
+        r_poly(j, mm, r);
+        for (int p = 0; p <= QMAX; ++p) acc[p] += uij * r[p];
+      }
+    }
+  if ((rc = put(m, coef, &d.rescale_coef, msg))) {
+    free_mechanism(m);
+    return rc;
+  }
+  if (set_constants() != cudaSuccess) {
+    free_mechanism(m);
+    msg = "could not set solver constants on the device";
+    return CHEM_ECUDA;
+  }
+  (void)S;
+  return 0;
+}
+
+void free_mechanism(Mechanism &m) {
+  for (void *p : m.allocations) cudaFree(p);
+  m.allocations.clear();
+}
+
+}  // namespace chemgpu

@@ -1,0 +1,178 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances: the FP64 path must match the oracle within a relative error of
+1e-6 on every species above 1e-10 mol/mol.  Both sides run the same written
+integrator; rounding-order differences (FMA contraction, warp reductions,
+exp/pow last bits, sparse vs dense LU) are ~1e-15 relative per operation, far
+below that bound, unless a borderline accept/converge decision flips.  Such
+cells are counted (their step counts differ) and must still agree within the
+integration tolerance.  The FP32-LU path must match the FP64 oracle within
+10*rtol relative above the same floor: the Newton residual and the error test
+stay in FP64, so only the corrector's convergence path changes.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2501_00011_gb300 import synth  # noqa: E402
+
+FLOOR = 1e-10
+REL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def cg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_00011_gb300 import build, chemgpu
+    build.build()
+    torch.cuda.init()
+    chemgpu.load()
+    return chemgpu
+
+
+@pytest.fixture(scope="module")
+def mechs(cg):
+    return {"small": cg.Mechanism(synth.mechanism_small()), "tropo": cg.Mechanism(synth.mechanism_tropo())}
+
+
+def _rel_err(y, yo, floor=FLOOR):
+    mask = np.abs(yo) > floor
+    return np.abs(y - yo)[mask] / np.abs(yo)[mask]
+
+
+def _compare(y, st, yo, so, rel=REL, max_flip_frac=0.02, tol_flip=None):
+    assert np.array_equal(st["status"], so["status"]), (st["status"], so["status"])
+    ok = so["status"] == 0
+    same = (st["steps"] == so["steps"]) & (st["newton_iters"] == so["newton_iters"])
+    flips = ok & ~same
+    err_same = _rel_err(y[:, ok & same], yo[:, ok & same])
+    assert err_same.size == 0 or err_same.max() <= rel, err_same.max()
+    assert flips.sum() <= max(1, max_flip_frac * ok.sum()), flips.sum()
+    if flips.any() and tol_flip is not None:
+        assert _rel_err(y[:, flips], yo[:, flips]).max() <= tol_flip
+    return err_same.max() if err_same.size else 0.0, int(flips.sum())
+
+
+# ---------------------------------------------------------------- kernel level
+
+@pytest.mark.parametrize("name", ["small", "tropo"])
+def test_deriv_matches_oracle(oracle_lib, cg, mechs, name):
+    m = mechs[name]
+    cells = synth.random_cells(m.n_species, 70, T_range=(220, 310), P_range=(2e4, 1e5), seed=5)
+    c = cg.Cells(m, cells.n_cells)
+    c.set_state(cells.T, cells.P, cells.y)
+    ytest = synth.random_cells(m.n_species, 70, seed=6).y
+    f = c.eval_deriv(ytest)
+    om = oracle_lib.OracleMechanism(m.synth)
+    for k in range(cells.n_cells):
+        kt = oracle_lib.rate_constants(om, cells.T[k], cells.P[k])
+        fo = oracle_lib.deriv(om, kt, ytest[:, k])
+        J = oracle_lib.jacobian(om, kt, ytest[:, k])
+        scale = np.abs(J) @ np.abs(ytest[:, k]) + 1e-300       # size of the terms summed into f_i
+        assert np.all(np.abs(f[:, k] - fo) <= 1e-13 * scale)
+
+
+@pytest.mark.parametrize("name", ["small", "tropo"])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_newton_solve_matches_dense(oracle_lib, cg, mechs, name, prec):
+    m = mechs[name]
+    C = 40
+    cells = synth.random_cells(m.n_species, C, T_range=(220, 310), P_range=(2e4, 1e5), seed=8)
+    c = cg.Cells(m, C, lu_precision=prec)
+    c.set_state(cells.T, cells.P, cells.y)
+    rng = np.random.default_rng(9)
+    b = rng.standard_normal((m.n_species, C))
+    om = oracle_lib.OracleMechanism(m.synth)
+    tol = 1e-9 if prec == 64 else 2e-4
+    for cc in (1e-3, 1.0, 30.0):
+        x = c.eval_newton_solve(cc, cells.y, b)
+        for k in range(C):
+            kt = oracle_lib.rate_constants(om, cells.T[k], cells.P[k])
+            Mk = np.eye(m.n_species) - cc * oracle_lib.jacobian(om, kt, cells.y[:, k])
+            xr = np.linalg.solve(Mk, b[:, k])
+            # backward error of the GPU solution in the matrix norm
+            res = np.linalg.norm(Mk @ x[:, k] - b[:, k], np.inf)
+            assert res <= tol * (np.linalg.norm(Mk, np.inf) * np.linalg.norm(xr, np.inf) + np.linalg.norm(b[:, k], np.inf))
+
+
+# ---------------------------------------------------------------- full solve
+
+def test_solve_small_workload(oracle_lib, cg, mechs):
+    wl = synth.workload_small()
+    y, st = cg.solve(mechs["small"], wl.cells, wl.dt, wl.rtol, wl.atol)
+    yo, so = oracle_lib.solve_cells(wl.mech, wl.cells, wl.dt, wl.rtol, wl.atol)
+    _compare(y, st, yo, so, tol_flip=100 * wl.rtol)
+
+
+@pytest.mark.parametrize("driver", ["plain", "persistent"])
+def test_solve_tropo_subset(oracle_lib, cg, mechs, driver):
+    # 301 cells: several blocks and waves with a ragged tail
+    wl = synth.workload_tropo(301)
+    y, st = cg.solve(mechs["tropo"], wl.cells, wl.dt, wl.rtol, wl.atol, driver=driver)
+    yo, so = oracle_lib.solve_cells(wl.mech, wl.cells, wl.dt, wl.rtol, wl.atol)
+    err, flips = _compare(y, st, yo, so, tol_flip=100 * wl.rtol)
+    print(f"tropo 301 cells ({driver}): max rel err {err:.2e}, decision flips {flips}")
+
+
+def test_drivers_agree_bitwise(cg, mechs):
+    wl = synth.workload_tropo(97)
+    ya, sa = cg.solve(mechs["tropo"], wl.cells, wl.dt, wl.rtol, wl.atol, driver="plain")
+    yb, sb = cg.solve(mechs["tropo"], wl.cells, wl.dt, wl.rtol, wl.atol, driver="persistent", cells_per_block=3)
+    assert np.array_equal(ya, yb) and np.array_equal(sa, sb)
+
+
+def test_fp32_lu_within_bound(oracle_lib, cg, mechs):
+    wl = synth.workload_tropo(200)
+    y, st = cg.solve(mechs["tropo"], wl.cells, wl.dt, wl.rtol, wl.atol, lu_precision=32)
+    yo, so = oracle_lib.solve_cells(wl.mech, wl.cells, wl.dt, wl.rtol, wl.atol)
+    assert np.all(st["status"] == 0)
+    err = _rel_err(y, yo)
+    assert err.max() <= 10 * wl.rtol, err.max()
+    print(f"fp32 LU: max rel err vs FP64 oracle {err.max():.2e}; Newton iterations "
+          f"{st['newton_iters'].sum() / so['newton_iters'].sum():.3f}x the oracle's")
+
+
+def test_per_cell_photolysis(oracle_lib, cg, mechs):
+    wl = synth.workload_batching(150)
+    y, st = cg.solve(mechs["tropo"], wl.cells, wl.dt, wl.rtol, wl.atol)
+    yo, so = oracle_lib.solve_cells(wl.mech, wl.cells, wl.dt, wl.rtol, wl.atol)
+    _compare(y, st, yo, so, tol_flip=100 * wl.rtol)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_empty_and_single_cell(oracle_lib, cg, mechs):
+    wl = synth.workload_tropo(1)
+    c0 = cg.Cells(mechs["tropo"], 0)
+    c0.set_state(np.zeros(0), np.zeros(0), np.zeros((72, 0)))
+    c0.solve_step(600.0)
+    assert c0.get_state().shape == (72, 0)
+    y, st = cg.solve(mechs["tropo"], wl.cells, wl.dt, wl.rtol, wl.atol)
+    yo, so = oracle_lib.solve_cells(wl.mech, wl.cells, wl.dt, wl.rtol, wl.atol)
+    _compare(y, st, yo, so, tol_flip=100 * wl.rtol)
+
+
+def test_bad_inputs_and_step_cap(oracle_lib, cg, mechs):
+    wl = synth.workload_tropo(6)
+    cells = synth.subset(wl.cells, np.arange(6))
+    cells.T[1] = np.nan
+    cells.P[2] = -1.0
+    cells.y[5, 3] = np.inf
+    y, st = cg.solve(mechs["tropo"], cells, wl.dt, wl.rtol, wl.atol, max_steps=3)
+    yo, so = oracle_lib.solve_cells(wl.mech, cells, wl.dt, wl.rtol, wl.atol, max_steps=3)
+    assert st["status"].tolist() == so["status"].tolist() == [1, 6, 6, 6, 1, 1]
+    np.testing.assert_array_equal(y[:, [0, 4, 5]], cells.y[:, [0, 4, 5]])
+
+
+def test_api_errors(cg, mechs):
+    with pytest.raises(cg.ChemError):
+        cg.Cells(mechs["tropo"], 4, rtol=-1.0)
+    c = cg.Cells(mechs["tropo"], 4)
+    with pytest.raises(cg.ChemError):
+        c.solve_step(600.0)          # before set_state
+    bad = synth.mechanism_from_list(2, [dict(reac=[0], prod=[5], A=1.0)])
+    with pytest.raises(cg.ChemError):
+        cg.Mechanism(bad)
