@@ -41,9 +41,17 @@ def _dist():
     return ws, rank, local
 
 
-def _workload():
+FORMS = {   # name: (LU precision, driver)
+    "plain64": (64, "plain"),
+    "persistent64": (64, "persistent"),
+    "plain32": (32, "plain"),
+    "chosen": (32, "persistent"),
+}
+
+
+def _workload(n_cells=N_CELLS):
     from paper_2501_00011_gb300 import synth
-    return synth.workload_tropo(N_CELLS)
+    return synth.workload_tropo(n_cells)
 
 
 class ClockSampler:
@@ -154,7 +162,7 @@ def run_gpu(args):
     libbuild.build()
     from paper_2501_00011_gb300 import chemgpu
 
-    wl = _workload()
+    wl = _workload(args.cells)
     mech = chemgpu.Mechanism(wl.mech)
     info = mech.info()
     C, S = wl.cells.n_cells, wl.mech.n_species
@@ -189,11 +197,17 @@ def run_gpu(args):
         cells.close()
         return ms, st
 
+    forms = args.forms.split(",")
     barrier()
+    res = {}
     with ClockSampler(local) as clk:
-        ms_plain, st_plain = time_form(64, "plain", args.steps, args.warmup)
-        ms_chosen, st_chosen = time_form(32, "persistent", args.steps, args.warmup)
+        for name in forms:
+            res[name] = time_form(*FORMS[name], args.steps, args.warmup)
     clocks = clk.summary()
+    if args.no_e2e:          # profiling runs: timed kernels only, no report line
+        return 0
+    ms_plain, st_plain = res["plain64"]
+    ms_chosen, st_chosen = res["chosen"]
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     T_h = torch.from_numpy(wl.cells.T).pin_memory()
@@ -284,6 +298,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=3000)
     ap.add_argument("--ref-sample", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", type=int, default=N_CELLS, help="cells per GPU (the benchmark uses 10,000)")
+    ap.add_argument("--forms", default="plain64,chosen", help="comma list of " + ",".join(FORMS))
+    ap.add_argument("--no-e2e", action="store_true", help="profiling: run the timed forms only, print nothing")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

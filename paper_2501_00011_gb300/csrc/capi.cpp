@@ -140,7 +140,18 @@ int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *o
   const int wmax = max_warps_per_block(mech->m.dev, o.lu_precision);
   if (wmax < 1) return fail(CHEM_EINVAL, "mechanism working set does not fit in shared memory");
   if (o.cells_per_block > wmax) return fail(CHEM_EINVAL, "cells_per_block exceeds the shared-memory limit");
-  if (o.cells_per_block == 0) o.cells_per_block = (o.driver == CHEM_DRIVER_PERSISTENT) ? wmax : 1;
+  if (o.cells_per_block == 0) {
+    // largest number of resident cells per SM; ties go to the larger block
+    // (persistent: fewer queue pops per table stage) or to one warp (plain:
+    // blocks retire independently)
+    int best_w = 1, best_cells = 0;
+    for (int w = 1; w <= wmax; ++w) {
+      const int cells = w * occupancy(mech->m.dev, o.lu_precision, w);
+      const bool better = cells > best_cells || (cells == best_cells && o.driver == CHEM_DRIVER_PERSISTENT);
+      if (better) { best_cells = cells; best_w = w; }
+    }
+    o.cells_per_block = best_w;
+  }
 
   chem_cells *c = new (std::nothrow) chem_cells();
   if (!c) return fail(CHEM_ENOMEM, "host allocation failed");

@@ -125,6 +125,8 @@ size_t smem_per_cell(const MechDev &m, int lu_precision);
 cudaError_t set_constants();   // gamma_m, 1/gamma_m into constant memory of the current device
 cudaError_t launch_solve(const MechDev &m, const CellsDev &c, const LaunchCfg &cfg, cudaStream_t stream);
 int max_warps_per_block(const MechDev &m, int lu_precision);
+// resident blocks per SM of the solve kernel for a block of warps_per_block cells
+int occupancy(const MechDev &m, int lu_precision, int warps_per_block);
 // diagnostic: mode 0 out = f(y); mode 1 out = (I - c J(y))^{-1} b   (all [S][C] device arrays)
 cudaError_t launch_probe(const MechDev &M, const CellsDev &C, int lu_precision, int mode, double c, const double *y,
                          const double *b, double *out, cudaStream_t stream);

@@ -217,26 +217,23 @@ __device__ __forceinline__ void rescale(double (&D)[NROW][KS], int q, double eta
 #pragma unroll
     for (int p = QMAX - 1; p >= 0; --p) tv = fma(tv, eta, __ldg(cp + p));
   }
-  double nd[QMAX][KS];
+  // in place, rows ascending: row i reads only rows m >= i, still unchanged
 #pragma unroll
   for (int i = 1; i <= QMAX; ++i) {
     if (i > q) break;
+    double nd[KS];
 #pragma unroll
-    for (int k = 0; k < KS; ++k) nd[i - 1][k] = 0.0;
+    for (int k = 0; k < KS; ++k) nd[k] = 0.0;
 #pragma unroll
     for (int mm = 1; mm <= QMAX; ++mm) {
       if (mm > q) break;
       if (mm < i) continue;
       const double t = __shfl_sync(FULL, tv, (i - 1) * QMAX + (mm - 1));
 #pragma unroll
-      for (int k = 0; k < KS; ++k) nd[i - 1][k] = fma(t, D[mm][k], nd[i - 1][k]);
+      for (int k = 0; k < KS; ++k) nd[k] = fma(t, D[mm][k], nd[k]);
     }
-  }
 #pragma unroll
-  for (int i = 1; i <= QMAX; ++i) {
-    if (i > q) break;
-#pragma unroll
-    for (int k = 0; k < KS; ++k) D[i][k] = nd[i - 1][k];
+    for (int k = 0; k < KS; ++k) D[i][k] = nd[k];
   }
 }
 
@@ -649,16 +646,31 @@ cudaError_t launch_probe_t(const MechDev &M, const CellsDev &C, const SolveParam
 }
 
 template <typename T, int KS>
-cudaError_t launch_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int blocks, cudaStream_t stream) {
-  const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
+cudaError_t configure_t(size_t smem) {
   static int configured_bytes[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 64 && configured_bytes[dev] < (int)smem) {
-    cudaError_t e = cudaFuncSetAttribute(solve_kernel<T, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured_bytes[dev] = (int)smem;
-  }
+  if (dev < 64 && configured_bytes[dev] >= (int)smem) return cudaSuccess;
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaError_t e = cudaFuncSetAttribute(solve_kernel<T, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess && dev < 64) configured_bytes[dev] = optin;
+  return e;
+}
+
+template <typename T, int KS>
+int occupancy_t(int warps_per_block, size_t smem) {
+  if (configure_t<T, KS>(smem) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, solve_kernel<T, KS>, warps_per_block * WARP, smem) != cudaSuccess) return 0;
+  return n;
+}
+
+template <typename T, int KS>
+cudaError_t launch_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int blocks, cudaStream_t stream) {
+  const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
+  cudaError_t e = configure_t<T, KS>(smem);
+  if (e != cudaSuccess) return e;
   solve_kernel<T, KS><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, P);
   return cudaGetLastError();
 }
@@ -691,6 +703,18 @@ cudaError_t set_constants() {
   cudaError_t e = cudaMemcpyToSymbol(c_gam, gam, sizeof(gam));
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_igam, igam, sizeof(igam));
+}
+
+int occupancy(const MechDev &M, int lu_precision, int warps_per_block) {
+  const size_t smem = smem_per_cell(M, lu_precision) * (size_t)warps_per_block;
+  const bool f32 = lu_precision == 32;
+  switch ((M.S + WARP - 1) / WARP) {
+    case 1: return f32 ? occupancy_t<float, 1>(warps_per_block, smem) : occupancy_t<double, 1>(warps_per_block, smem);
+    case 2: return f32 ? occupancy_t<float, 2>(warps_per_block, smem) : occupancy_t<double, 2>(warps_per_block, smem);
+    case 3: return f32 ? occupancy_t<float, 3>(warps_per_block, smem) : occupancy_t<double, 3>(warps_per_block, smem);
+    case 4: return f32 ? occupancy_t<float, 4>(warps_per_block, smem) : occupancy_t<double, 4>(warps_per_block, smem);
+    default: return 0;
+  }
 }
 
 cudaError_t launch_probe(const MechDev &M, const CellsDev &C, int lu_precision, int mode, double c, const double *y,
@@ -733,7 +757,9 @@ cudaError_t launch_solve(const MechDev &M, const CellsDev &C, const LaunchCfg &c
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   int blocks;
   if (cfg.driver == CHEM_DRIVER_PERSISTENT) {
-    blocks = n_sm * (cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : 1);
+    int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : occupancy(M, cfg.lu_precision, cfg.warps_per_block);
+    if (bps < 1) bps = 1;
+    blocks = n_sm * bps;
     const int64_t need = (C.n_cells + P.warps_per_block - 1) / P.warps_per_block;
     if (blocks > need) blocks = (int)need;
   } else {
