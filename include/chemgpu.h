@@ -185,6 +185,33 @@ int chem_eval_deriv(chem_cells *cells, const double *y, double *f, int32_t mem, 
 int chem_eval_newton_solve(chem_cells *cells, double c, const double *y, const double *b, double *x,
                            int32_t mem, void *stream);
 
+/* Solve without any allocation by the library.
+ *
+ * For callers that must not allocate device memory once they are running: a
+ * host model under its own memory manager or a fixed device-memory budget,
+ * or a time loop that must never grow the device footprint after start-up.
+ * Create the mechanism at start-up (that allocates), then call this entry
+ * point with caller-owned DEVICE buffers: T[n_cells], P[n_cells],
+ * y[n_species][n_cells] (integrated in place over [0, dt], as
+ * chem_solve_step does), stats[n_cells] (written), and optionally
+ * J[n_photolysis][n_cells] and theta[n_reactions] (NULL: mechanism J,
+ * theta = 0).  opts NULL = defaults; the driver is always the persistent work
+ * queue.  The paper has no counterpart of this entry point.
+ *
+ * The work-queue counter lives in a 256-byte static device array inside the
+ * library (held by every GPU that loads the library until the process
+ * exits); the call clears it on stream before the launch and calls no
+ * cudaMalloc/cudaFree.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls on a device share its one counter: calls whose
+ * work overlaps on that GPU (e.g. launched on two streams) race and must be
+ * serialised by the caller.  n_cells beyond
+ * CHEM_NOALLOC_MAX_CELLS is rejected with CHEM_EINVAL. */
+#define CHEM_NOALLOC_MAX_CELLS 2147483647LL
+int chem_solve_step_noalloc(const chem_mech *mech, int64_t n_cells, const double *T, const double *P,
+                            const double *J, const double *theta, double *y, chem_cell_stats *stats,
+                            double dt, const chem_opts *opts, void *stream);
+
 /* Thread-local description of the last error ("" if none). */
 const char *chem_last_error(void);
 

@@ -28,7 +28,7 @@ EXPORTS = ["chem_opts_default", "chem_mechanism_create", "chem_mechanism_destroy
            "chem_mechanism_info", "chem_mechanism_structure", "chem_cells_create",
            "chem_cells_destroy", "chem_cells_set_state", "chem_cells_set_photolysis",
            "chem_cells_set_theta", "chem_solve_step", "chem_get_state", "chem_get_stats",
-           "chem_eval_deriv", "chem_eval_newton_solve", "chem_last_error"]
+           "chem_eval_deriv", "chem_eval_newton_solve", "chem_solve_step_noalloc", "chem_last_error"]
 
 
 class Reaction(ct.Structure):
@@ -92,6 +92,7 @@ def load(path: str | None = None):
         L.chem_get_stats.argtypes = [V, V, ct.c_int32, V]
         L.chem_eval_deriv.argtypes = [V, V, V, ct.c_int32, V]
         L.chem_eval_newton_solve.argtypes = [V, ct.c_double, V, V, V, ct.c_int32, V]
+        L.chem_solve_step_noalloc.argtypes = [V, ct.c_int64, V, V, V, V, V, V, ct.c_double, V, V]
         L.chem_last_error.restype = ct.c_char_p
         for name in EXPORTS:
             if name not in ("chem_opts_default", "chem_mechanism_destroy", "chem_cells_destroy",

@@ -9,10 +9,6 @@
 
 using namespace chemgpu;
 
-struct chem_mech {
-  Mechanism m;
-};
-
 struct chem_cells {
   const chem_mech *mech = nullptr;
   int64_t n = 0;
@@ -47,6 +43,8 @@ int check_mem(int32_t mem) {
 }
 
 }  // namespace
+
+void chemgpu::set_last_error(const std::string &msg) { g_err = msg; }
 
 extern "C" {
 

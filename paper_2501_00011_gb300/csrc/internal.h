@@ -131,4 +131,12 @@ int occupancy(const MechDev &m, int lu_precision, int warps_per_block);
 cudaError_t launch_probe(const MechDev &M, const CellsDev &C, int lu_precision, int mode, double c, const double *y,
                          const double *b, double *out, cudaStream_t stream);
 
+// sets the thread-local message returned by chem_last_error()
+void set_last_error(const std::string &msg);
+
 }  // namespace chemgpu
+
+// opaque handle of include/chemgpu.h
+struct chem_mech {
+  chemgpu::Mechanism m;
+};
