@@ -15,7 +15,7 @@ struct chem_cells {
   chem_opts opts{};
   double *T = nullptr, *P = nullptr, *y = nullptr, *J = nullptr, *theta = nullptr;
   chem_cell_stats *stats = nullptr;
-  int *queue = nullptr;
+  int *queue = nullptr;   // [0..1] work counter, [2] staging fallbacks
   bool have_state = false, use_J = false, use_theta = false;
   int device = 0;
 };
@@ -135,21 +135,11 @@ int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *o
   if (o.lu_precision != 64 && o.lu_precision != 32) return fail(CHEM_EINVAL, "lu_precision must be 64 or 32");
   if (o.driver != CHEM_DRIVER_PLAIN && o.driver != CHEM_DRIVER_PERSISTENT) return fail(CHEM_EINVAL, "bad driver");
   if (o.cells_per_block < 0 || o.cells_per_block > MAX_WARPS_PER_BLOCK || o.blocks_per_sm < 0) return fail(CHEM_EINVAL, "bad launch shape");
-  const int wmax = max_warps_per_block(mech->m.dev, o.lu_precision);
+  const int wmax = max_warps_per_block(mech->m.dev, o.lu_precision, o.driver);
   if (wmax < 1) return fail(CHEM_EINVAL, "mechanism working set does not fit in shared memory");
   if (o.cells_per_block > wmax) return fail(CHEM_EINVAL, "cells_per_block exceeds the shared-memory limit");
-  if (o.cells_per_block == 0) {
-    // largest number of resident cells per SM; ties go to the larger block
-    // (persistent: fewer queue pops per table stage) or to one warp (plain:
-    // blocks retire independently)
-    int best_w = 1, best_cells = 0;
-    for (int w = 1; w <= wmax; ++w) {
-      const int cells = w * occupancy(mech->m.dev, o.lu_precision, w);
-      const bool better = cells > best_cells || (cells == best_cells && o.driver == CHEM_DRIVER_PERSISTENT);
-      if (better) { best_cells = cells; best_w = w; }
-    }
-    o.cells_per_block = best_w;
-  }
+  if (o.cells_per_block == 0) o.cells_per_block = best_warps_per_block(mech->m.dev, o.lu_precision, o.driver);
+  if (o.cells_per_block < 1) return fail(CHEM_EINVAL, "no launch shape fits on this device");
 
   chem_cells *c = new (std::nothrow) chem_cells();
   if (!c) return fail(CHEM_ENOMEM, "host allocation failed");
@@ -164,13 +154,14 @@ int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *o
       (e = cudaMalloc(&c->P, n * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&c->y, n * S * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&c->stats, n * sizeof(chem_cell_stats))) != cudaSuccess ||
-      (e = cudaMalloc(&c->queue, 2 * sizeof(long long))) != cudaSuccess ||
+      (e = cudaMalloc(&c->queue, 4 * sizeof(long long))) != cudaSuccess ||
       (e = cudaMalloc(&c->theta, (R > 0 ? R : 1) * sizeof(double))) != cudaSuccess ||
       (mech->m.n_phot > 0 && (e = cudaMalloc(&c->J, n * mech->m.n_phot * sizeof(double))) != cudaSuccess)) {
     chem_cells_destroy(c);
     return fail(CHEM_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
   }
-  if ((e = cudaMemset(c->stats, 0, n * sizeof(chem_cell_stats))) != cudaSuccess) {
+  if ((e = cudaMemset(c->stats, 0, n * sizeof(chem_cell_stats))) != cudaSuccess ||
+      (e = cudaMemset(c->queue, 0, 4 * sizeof(long long))) != cudaSuccess) {
     chem_cells_destroy(c);
     return cuda_fail(e, "cudaMemset");
   }
@@ -247,6 +238,7 @@ int chem_solve_step(chem_cells *c, double dt, void *stream) {
   cd.y = c->y;
   cd.stats = c->stats;
   cd.queue = nullptr;
+  cd.error = c->queue + 4;
   if (c->opts.driver == CHEM_DRIVER_PERSISTENT) {
     cudaError_t e = cudaMemsetAsync(c->queue, 0, sizeof(long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
@@ -303,6 +295,7 @@ CellsDev cells_dev(chem_cells *c) {
   cd.y = c->y;
   cd.stats = c->stats;
   cd.queue = nullptr;
+  cd.error = c->queue + 4;
   return cd;
 }
 

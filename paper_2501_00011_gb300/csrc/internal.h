@@ -18,55 +18,64 @@ constexpr int GRID_IMIN = -26;      // step-factor grid g_i = 2^(i/8)
 constexpr int GRID_IMAX = 26;
 constexpr int GRID_N = GRID_IMAX - GRID_IMIN + 1;
 constexpr int WARP = 32;
-constexpr int MAX_WARPS_PER_BLOCK = 8;   // cells per block (history and vectors live in registers)
+constexpr int MAX_WARPS_PER_BLOCK = 12;  // cells per block (history and vectors live in registers)
 
 // A warp program is a sequence of passes of exactly 32 op slots; lane l runs
 // slot l of every pass and the warp synchronises between passes.  The
 // scheduler guarantees that no location written in a pass is read or written
 // by another op of the same pass, so the passes run without intra-pass races.
+// On the host an op holds element indices:
 //   FMA op:    W[t] = fma(W[a], W[b], W[c])      (NEG program: fma(-W[a], W[b], W[c]))
 //   RECIP op:  W[t & 0x7fff] = -1 / W[a]         (t has bit 15 set)
 //   empty:     t == 0xffff
+// On the device the same op holds BYTE offsets into the cell's work array,
+// empty slots become a harmless FMA into a dummy slot, and every slot of a
+// RECIP pass (empty ones included) carries c == 0xffff, so the pass kind is
+// warp-uniform and no slot needs a branch.
 struct Op {
   uint16_t t, a, b, c;
 };
 constexpr uint16_t OP_EMPTY = 0xffff;
 constexpr uint16_t OP_RECIP = 0x8000;
+constexpr uint16_t DEV_RECIP = 0xffff;     // device marker in .w of RECIP passes
 
-struct ProgramDev {
-  const ushort4 *ops;   // n_pass * 32 entries
-  int n_pass;
+// Tables read by every warp of every cell, packed into one 16-byte-aligned
+// blob per LU precision so that a block can stage them into shared memory
+// with one bulk copy.  Byte offsets of each section within the blob:
+struct TableOffsets {
+  int f_ops, fwd_ops, bwd_ops;     // ushort4 programs (f on Wd, fwd/bwd on WL)
+  int rx_slots;                    // uint2 [R]: byte offsets into Wd of the reactants' y
+  int pair_rx;                     // int [n_pairs]
+  int pair_other;                  // uint32 [n_pairs]: two 16-bit byte offsets into Wd
+  int lu_diag;                     // int [S]: byte offsets into WL of the pivot diagonal
+  int dconst_off, dconst_val;      // int [d_nconst] byte offsets into Wd, double values
+  int Lconst_off, Lconst_val;      // int [L_nconst] byte offsets into WL, double values
+  int thr2, thr3, g;               // step-factor grid, double [7][GRID_N] x2 and [GRID_N]
+  int bytes;                       // total, a multiple of 16
 };
 
 // Everything a solve kernel needs about a mechanism; passed by value.
 struct MechDev {
   int S, R, max_reac, n_phot, n_pairs;
-  // rate constants
+  // rate constants (read once per cell)
   const int *rx_kind;      // [R]
   const int *rx_nreac;     // [R]
   const int *rx_phot;      // [R] index among photolysis reactions, or -1
   const double *rx_A, *rx_Ea, *rx_B, *rx_J;
-  // f(y): reactant slots per reaction in Wd index space (missing -> Wd ONE)
-  const ushort4 *rx_slots; // [R] x=reac0 y=reac1 z=reac2 (Wd indices of y)
-  // Jacobian partials: one per (reaction, reactant slot)
-  const int *pair_rx;      // [n_pairs]
-  const ushort2 *pair_other;   // [n_pairs] Wd indices of the other reactants' y (ONE if none)
   // species permutation: position of species s in the pivot order
   const int *sp_pos;       // [S]
-  // per-cell double array Wd
-  int Wd_len, d_Y, d_KT, d_RT, d_F, d_ONE, d_ZERO;
-  // per-cell LU-precision array WL
-  int WL_len, L_LU, L_NINV, L_X, L_P, L_ZERO, nnz_lu;
-  const int *lu_diag;      // [S] WL index of the pivot-order diagonal entries
-  // constant slots to initialise in each cell's arrays
-  const double *d_const_val; const int *d_const_idx; int d_nconst;
-  const double *L_const_val; const int *L_const_idx; int L_nconst;
-  // LU slots that are diagonal entries of M (set to 1 before the J terms)
-  // and the number of WL entries to clear before forming M ([0, m_clear))
-  int m_clear;
-  ProgramDev f_prog, m_prog, lu_prog, fwd_prog, bwd_prog;
-  // step-factor grid: thr[p][i] for bias 2 (p = 0..6) and bias 3, and g[i]
-  const double *grid_thr2, *grid_thr3, *grid_g;
+  // per-cell double array Wd (element indices)
+  int Wd_len, d_Y, d_KT, d_RT, d_F, d_ONE, d_ZERO, d_DUMMY;
+  // per-cell LU-precision array WL (element indices)
+  int WL_len, L_LU, L_NINV, L_X, L_P, L_ZERO, L_DUMMY, nnz_lu;
+  int d_nconst, L_nconst;
+  int m_clear;             // WL entries [0, m_clear) are cleared before forming M
+  int f_npass, fwd_npass, bwd_npass, m_npass, lu_npass;
+  // staged tables: blob[0] for an FP64 LU, blob[1] for an FP32 LU (global memory)
+  const unsigned char *blob[2];
+  TableOffsets tab;
+  // programs streamed from global memory, per LU precision (byte-offset ops)
+  const ushort4 *m_ops[2], *lu_ops[2];
   // history rescale T(eta)_{im} = sum_p coef[(i-1)*QMAX + m-1][p] eta^p,
   // i, m = 1..QMAX, p = 0..QMAX
   const double *rescale_coef;
@@ -89,8 +98,9 @@ struct Mechanism {
   std::vector<double> d_consts_v, L_consts_v;
   std::vector<int> d_consts_i, L_consts_i;
   std::vector<int> pair_rx;
-  std::vector<std::pair<int, int>> pair_other;
-  std::vector<int> lu_diag;
+  std::vector<std::pair<int, int>> pair_other;   // Wd element indices
+  std::vector<int> lu_diag;                      // WL element indices
+  std::vector<int> rx_slot_idx;                  // [R][3] Wd element indices of the reactants' y
   std::vector<chem_reaction> rx;
   MechDev dev{};                     // device pointers filled in upload()
   std::vector<void *> allocations;   // device buffers owned
@@ -110,6 +120,7 @@ struct CellsDev {
   double *y;                    // [S][C] in/out
   chem_cell_stats *stats;       // [C]
   int *queue;                   // persistent driver work counter (may be null)
+  int *error;                   // counts blocks whose table staging fell back to plain loads (may be null)
 };
 
 struct LaunchCfg {
@@ -122,11 +133,14 @@ struct LaunchCfg {
 };
 
 size_t smem_per_cell(const MechDev &m, int lu_precision);
+size_t staged_bytes(const MechDev &m, int driver);   // tables staged per block by the driver
 cudaError_t set_constants();   // gamma_m, 1/gamma_m into constant memory of the current device
 cudaError_t launch_solve(const MechDev &m, const CellsDev &c, const LaunchCfg &cfg, cudaStream_t stream);
-int max_warps_per_block(const MechDev &m, int lu_precision);
+int max_warps_per_block(const MechDev &m, int lu_precision, int driver);
 // resident blocks per SM of the solve kernel for a block of warps_per_block cells
-int occupancy(const MechDev &m, int lu_precision, int warps_per_block);
+int occupancy(const MechDev &m, int lu_precision, int driver, int warps_per_block);
+// cells per block that maximises resident cells per SM (0 if nothing fits)
+int best_warps_per_block(const MechDev &m, int lu_precision, int driver);
 // diagnostic: mode 0 out = f(y); mode 1 out = (I - c J(y))^{-1} b   (all [S][C] device arrays)
 cudaError_t launch_probe(const MechDev &M, const CellsDev &C, int lu_precision, int mode, double c, const double *y,
                          const double *b, double *out, cudaStream_t stream);

@@ -15,13 +15,19 @@
 //
 // FP64 on GB300 issues one warp instruction per 16 SM cycles whether 1 or 32
 // lanes are active, so the sparse work is packed into 32-wide passes by the
-// host scheduler and scalar control is kept to few instructions.
+// host scheduler.  The persistent driver stages the tables every warp reads
+// all the time (f and triangular-solve programs, reaction slot tables,
+// constants, step-factor grid) into shared memory once per block with a TMA
+// bulk copy; the large M and LU programs stream from L2 with a deep prefetch.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "internal.h"
 
 namespace chemgpu {
+
+__constant__ double c_gam[QMAX + 2];
+__constant__ double c_igam[QMAX + 2];
 
 namespace {
 
@@ -31,6 +37,9 @@ constexpr double CRDOWN = 0.3, RDIV = 2.0, NLSCOEF = 0.1, DGMAX = 0.3, THRESH = 
 constexpr int MSBP = 20, MXNEF = 7, MXNCF = 10;
 constexpr double ETA_CF = 0.25, ETA_MXF = 0.2, ETA_CST_SAFETY = 0.9, ETA_CST_MIN = 0.1, STRETCH = 1e-3;
 constexpr double K_BOLTZMANN = 1.380649e-23;
+constexpr int PF_GLOBAL = 8;            // passes prefetched ahead when ops come from L2
+constexpr int PF_SHARED = 2;            // ... and from shared memory
+constexpr long TMA_WAIT_LIMIT = 1L << 22;
 
 struct SolveParams {
   double rtol, atol, dt;
@@ -38,6 +47,8 @@ struct SolveParams {
   int cell_bytes;      // shared memory per warp
   int wd_pad;          // Wd length rounded so WL starts 16-byte aligned
   int warps_per_block;
+  int prec;            // 0: FP64 LU, 1: FP32 LU
+  int tab_bytes;       // staged table bytes at the start of shared memory (0 if not staged)
 };
 
 // Newton-Raphson refinement of the hardware reciprocal approximation:
@@ -54,36 +65,55 @@ __device__ __forceinline__ double recip_nr(double x) {
 __device__ __forceinline__ double lu_recip(double x) { return recip_nr(x); }
 __device__ __forceinline__ float lu_recip(float x) { return __frcp_rn(x); }
 
-__device__ __forceinline__ ushort4 ld_op(const ushort4 *p) {
-  const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
-  return make_ushort4((unsigned short)(v.x & 0xffff), (unsigned short)(v.x >> 16),
-                      (unsigned short)(v.y & 0xffff), (unsigned short)(v.y >> 16));
+template <bool SMEM>
+__device__ __forceinline__ uint2 ld_op(const ushort4 *p) {
+  if (SMEM) return *reinterpret_cast<const uint2 *>(p);
+  return __ldg(reinterpret_cast<const uint2 *>(p));
 }
 
-// Run a warp program over the work array W (see internal.h for the op forms).
-template <typename T, bool NEG>
-__device__ __forceinline__ void run_prog(const ProgramDev pr, T *__restrict__ W, const int lane) {
-  const int np = pr.n_pass;
-  const ushort4 *ops = pr.ops + lane;
-  constexpr int PF = 4;   // passes prefetched ahead
-  const ushort4 empty = make_ushort4(OP_EMPTY, 0, 0, 0);
-  ushort4 buf[PF];
+template <typename T>
+__device__ __forceinline__ T &at(unsigned char *base, unsigned off) {
+  return *reinterpret_cast<T *>(base + off);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory accesses by 32-bit shared address (the work arrays always live in shared memory)
+__device__ __forceinline__ double lds(double *, uint32_t a) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ float lds(float *, uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts(uint32_t a, double v) { asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory"); }
+__device__ __forceinline__ void sts(uint32_t a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory"); }
+
+// Run a warp program (byte-offset ops, see internal.h) over the work array W.
+template <typename T, bool NEG, bool SMEM, int PF>
+__device__ __forceinline__ void run_ops(const ushort4 *ops, const int np, T *W, const int lane) {
+  const uint32_t wb = smem_addr(W);
+  T *const tag = nullptr;
+  ops += lane;
+  uint2 buf[PF];   // packed ops: x = t | a << 16, y = b | c << 16
 #pragma unroll
-  for (int i = 0; i < PF; ++i) buf[i] = (i < np) ? ld_op(ops + i * WARP) : empty;
+  for (int i = 0; i < PF; ++i) buf[i] = (i < np) ? ld_op<SMEM>(ops + i * WARP) : make_uint2(0, 0);
   for (int p0 = 0; p0 < np; p0 += PF) {
 #pragma unroll
     for (int i = 0; i < PF; ++i) {
       const int p = p0 + i;
       if (p >= np) break;
-      const ushort4 op = buf[i];
-      buf[i] = (p + PF < np) ? ld_op(ops + (size_t)(p + PF) * WARP) : empty;
-      if (op.x != OP_EMPTY) {
-        if (op.x & OP_RECIP) {
-          W[op.x & 0x7fff] = -lu_recip(W[op.y]);
-        } else {
-          const T a = W[op.y], b = W[op.z], c = W[op.w];
-          W[op.x] = NEG ? fma(-a, b, c) : fma(a, b, c);
-        }
+      const uint2 op = buf[i];
+      if (p + PF < np) buf[i] = ld_op<SMEM>(ops + (size_t)(p + PF) * WARP);
+      const uint32_t ot = op.x & 0xffff, oa = op.x >> 16, ob = op.y & 0xffff, oc = op.y >> 16;
+      if (oc == DEV_RECIP) {
+        sts(wb + ot, -lu_recip(lds(tag, wb + oa)));
+      } else {
+        const T a = lds(tag, wb + oa), b = lds(tag, wb + ob), c = lds(tag, wb + oc);
+        sts(wb + ot, NEG ? fma(-a, b, c) : fma(a, b, c));
       }
       __syncwarp();
     }
@@ -104,25 +134,66 @@ __device__ __forceinline__ double warp_min(double v) {
 // Largest grid factor g_i with err <= thr[p][i] (thr decreasing in i), else g_min.
 __device__ __forceinline__ double grid_eta(const double *thr, const double *g, double err, int p, int lane) {
   const double *tp = thr + p * GRID_N;
-  const bool ok0 = err <= __ldg(tp + lane);
-  const bool ok1 = (lane + WARP < GRID_N) && err <= __ldg(tp + lane + WARP);
+  const bool ok0 = err <= tp[lane];
+  const bool ok1 = (lane + WARP < GRID_N) && err <= tp[lane + WARP];
   const int cnt = __popc(__ballot_sync(FULL, ok0)) + __popc(__ballot_sync(FULL, ok1));
-  return __ldg(g + (cnt > 0 ? cnt - 1 : 0));
+  return g[cnt > 0 ? cnt - 1 : 0];
 }
 
-template <typename T, int KS>
+// ------------------------------------------------------------- TMA staging
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// bounded wait for phase `parity` of the barrier; false if the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long limit) {
+  for (long it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Table base of one block: the staged copy in shared memory or the blob in
+// global memory; section offsets come from the kernel parameter M.tab.
+struct Tabs {
+  const unsigned char *base;
+};
+template <typename X>
+__device__ __forceinline__ const X *tab(const Tabs &tb, int off) {
+  return reinterpret_cast<const X *>(tb.base + off);
+}
+
+template <typename T, int KS, bool STAGED>
 struct Cell {
   const MechDev &M;
   const SolveParams &P;
+  const Tabs &tb;
   double *Wd;
   T *WL;
   int lane;
   int pos[KS];        // pivot position of this lane's species
   bool own[KS];       // species index < S
-  double Sd;      // number of species as a double (norm divisor)
+  double Sd;          // number of species as a double (norm divisor)
 
-  __device__ Cell(const MechDev &m, const SolveParams &p, double *wd, T *wl, int l)
-      : M(m), P(p), Wd(wd), WL(wl), lane(l) {
+  __device__ __forceinline__ Cell(const MechDev &m, const SolveParams &p, const Tabs &t, double *wd, T *wl, int l)
+      : M(m), P(p), tb(t), Wd(wd), WL(wl), lane(l) {
 #pragma unroll
     for (int k = 0; k < KS; ++k) {
       const int s = lane + WARP * k;
@@ -132,7 +203,14 @@ struct Cell {
     Sd = (double)M.S;
   }
 
-  __device__ double wrms(const double (&v)[KS], const double (&w)[KS]) const {
+  __device__ __forceinline__ void init_constants() {
+    unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
+    unsigned char *wl = reinterpret_cast<unsigned char *>(WL);
+    for (int k = lane; k < M.d_nconst; k += WARP) at<double>(wd, tab<int>(tb, M.tab.dconst_off)[k]) = tab<double>(tb, M.tab.dconst_val)[k];
+    for (int k = lane; k < M.L_nconst; k += WARP) at<T>(wl, tab<int>(tb, M.tab.Lconst_off)[k]) = (T)tab<double>(tb, M.tab.Lconst_val)[k];
+  }
+
+  __device__ __forceinline__ double wrms(const double (&v)[KS], const double (&w)[KS]) const {
     double s = 0.0;
 #pragma unroll
     for (int k = 0; k < KS; ++k)
@@ -144,61 +222,64 @@ struct Cell {
     return sqrt(s / Sd);
   }
 
-  __device__ void weights(const double (&y)[KS], double (&w)[KS]) const {
+  __device__ __forceinline__ void weights(const double (&y)[KS], double (&w)[KS]) const {
 #pragma unroll
     for (int k = 0; k < KS; ++k) w[k] = own[k] ? 1.0 / (P.rtol * fabs(y[k]) + P.atol) : 0.0;
   }
 
   // a2: f(y) into registers
-  __device__ void eval_f(const double (&y)[KS], double (&f)[KS]) {
+  __device__ __forceinline__ void eval_f(const double (&y)[KS], double (&f)[KS]) {
 #pragma unroll
     for (int k = 0; k < KS; ++k)
       if (own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
     __syncwarp();
+    unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
     for (int j = lane; j < M.R; j += WARP) {
-      const uint2 sl = __ldg(reinterpret_cast<const uint2 *>(M.rx_slots) + j);
-      double r = Wd[M.d_KT + j] * Wd[sl.x & 0xffff];
-      if (M.max_reac > 1) r *= Wd[sl.x >> 16];
-      if (M.max_reac > 2) r *= Wd[sl.y & 0xffff];
+      const uint2 sl = tab<uint2>(tb, M.tab.rx_slots)[j];
+      double r = Wd[M.d_KT + j] * at<double>(wd, sl.x & 0xffff);
+      if (M.max_reac > 1) r *= at<double>(wd, sl.x >> 16);
+      if (M.max_reac > 2) r *= at<double>(wd, sl.y & 0xffff);
       Wd[M.d_RT + j] = r;
     }
     __syncwarp();
-    run_prog<double, false>(M.f_prog, Wd, lane);
+    run_ops<double, false, STAGED, STAGED ? PF_SHARED : PF_GLOBAL>(tab<ushort4>(tb, M.tab.f_ops), M.f_npass, Wd, lane);
 #pragma unroll
     for (int k = 0; k < KS; ++k) f[k] = own[k] ? Wd[M.d_F + lane + WARP * k] : 0.0;
     __syncwarp();
   }
 
   // a3-a5: M = I - c J(y) in the LU slots, then factor
-  __device__ void form_and_factor(double c, const double (&y)[KS]) {
+  __device__ __forceinline__ void form_and_factor(double c, const double (&y)[KS]) {
 #pragma unroll
     for (int k = 0; k < KS; ++k)
       if (own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
     for (int i = lane; i < M.m_clear; i += WARP) WL[i] = (T)0;
     __syncwarp();
-    for (int k = lane; k < M.S; k += WARP) WL[__ldg(M.lu_diag + k)] = (T)1;
+    unsigned char *wl = reinterpret_cast<unsigned char *>(WL);
+    unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
+    for (int k = lane; k < M.S; k += WARP) at<T>(wl, tab<int>(tb, M.tab.lu_diag)[k]) = (T)1;
     const double mc = -c;
     for (int pr = lane; pr < M.n_pairs; pr += WARP) {
-      const int j = __ldg(M.pair_rx + pr);
-      const unsigned o = __ldg(reinterpret_cast<const unsigned *>(M.pair_other) + pr);
+      const int j = tab<int>(tb, M.tab.pair_rx)[pr];
+      const unsigned o = tab<unsigned>(tb, M.tab.pair_other)[pr];
       double p = mc * Wd[M.d_KT + j];
-      if (M.max_reac > 1) p *= Wd[o & 0xffff];
-      if (M.max_reac > 2) p *= Wd[o >> 16];
+      if (M.max_reac > 1) p *= at<double>(wd, o & 0xffff);
+      if (M.max_reac > 2) p *= at<double>(wd, o >> 16);
       WL[M.L_P + pr] = (T)p;
     }
     __syncwarp();
-    run_prog<T, false>(M.m_prog, WL, lane);
-    run_prog<T, false>(M.lu_prog, WL, lane);
+    run_ops<T, false, false, PF_GLOBAL>(M.m_ops[P.prec], M.m_npass, WL, lane);
+    run_ops<T, false, false, PF_GLOBAL>(M.lu_ops[P.prec], M.lu_npass, WL, lane);
   }
 
   // a5: x = M^{-1} b with the factored M
-  __device__ void solve(const double (&b)[KS], double (&x)[KS]) {
+  __device__ __forceinline__ void solve(const double (&b)[KS], double (&x)[KS]) {
 #pragma unroll
     for (int k = 0; k < KS; ++k)
       if (own[k]) WL[M.L_X + pos[k]] = (T)b[k];
     __syncwarp();
-    run_prog<T, false>(M.fwd_prog, WL, lane);
-    run_prog<T, true>(M.bwd_prog, WL, lane);
+    run_ops<T, false, STAGED, STAGED ? PF_SHARED : PF_GLOBAL>(tab<ushort4>(tb, M.tab.fwd_ops), M.fwd_npass, WL, lane);
+    run_ops<T, true, STAGED, STAGED ? PF_SHARED : PF_GLOBAL>(tab<ushort4>(tb, M.tab.bwd_ops), M.bwd_npass, WL, lane);
 #pragma unroll
     for (int k = 0; k < KS; ++k) x[k] = own[k] ? (double)WL[M.L_X + pos[k]] : 0.0;
     __syncwarp();
@@ -237,24 +318,50 @@ __device__ __forceinline__ void rescale(double (&D)[NROW][KS], int q, double eta
   }
 }
 
+// Row access with a runtime row index.  Written as a switch with constant
+// row numbers: a loop of "if (m == r)" selects gets canonicalised into a
+// dynamically indexed access, which moves the whole history into local memory.
 template <int KS>
 __device__ __forceinline__ void get_row(const double (&D)[NROW][KS], int r, double (&out)[KS]) {
-#pragma unroll
-  for (int k = 0; k < KS; ++k) out[k] = 0.0;
-#pragma unroll
-  for (int m = 0; m < NROW; ++m)
-    if (m == r) {
-#pragma unroll
-      for (int k = 0; k < KS; ++k) out[k] = D[m][k];
-    }
+#define CHEM_ROW_CASE(R_)                                 \
+  case R_:                                               \
+    _Pragma("unroll") for (int k = 0; k < KS; ++k) out[k] = D[R_][k]; \
+    break;
+  switch (r) {
+    CHEM_ROW_CASE(0) CHEM_ROW_CASE(1) CHEM_ROW_CASE(2) CHEM_ROW_CASE(3)
+    CHEM_ROW_CASE(4) CHEM_ROW_CASE(5) CHEM_ROW_CASE(6) CHEM_ROW_CASE(7)
+    default:
+      _Pragma("unroll") for (int k = 0; k < KS; ++k) out[k] = 0.0;
+  }
+#undef CHEM_ROW_CASE
 }
 
+// Accepted step at order q: D_{q+2} = d - D_{q+1}, D_{q+1} = d, then
+// D_m += D_{m+1} for m = q .. 0.
+template <int KS>
+__device__ __forceinline__ void accept_update(double (&D)[NROW][KS], int q, const double (&d)[KS]) {
+#define CHEM_UPD_CASE(Q_)                                                      \
+  case Q_:                                                                    \
+    _Pragma("unroll") for (int k = 0; k < KS; ++k) {                          \
+      D[Q_ + 2][k] = d[k] - D[Q_ + 1][k];                                     \
+      D[Q_ + 1][k] = d[k];                                                    \
+    }                                                                         \
+    _Pragma("unroll") for (int m = Q_; m >= 0; --m)                           \
+      _Pragma("unroll") for (int k = 0; k < KS; ++k) D[m][k] += D[m + 1][k];  \
+    break;
+  switch (q) {
+    CHEM_UPD_CASE(1) CHEM_UPD_CASE(2) CHEM_UPD_CASE(3) CHEM_UPD_CASE(4) CHEM_UPD_CASE(5)
+    default:
+      break;
+  }
+#undef CHEM_UPD_CASE
+}
 
 // Inputs of one cell: y0 into registers, a1 rate constants into Wd[KT].
 // Returns true (warp-uniform) if any input or rate constant is not finite or
 // T, P are not positive.
 template <int KS>
-__device__ bool load_cell(const MechDev &M, const CellsDev &C, double *Wd, const int lane, const int64_t cell,
+__device__ __forceinline__ bool load_cell(const MechDev &M, const CellsDev &C, double *Wd, const int lane, const int64_t cell,
                           const bool (&own)[KS], double (&y0)[KS]) {
   const int64_t NC = C.n_cells;
   const int R = M.R;
@@ -286,18 +393,15 @@ __device__ bool load_cell(const MechDev &M, const CellsDev &C, double *Wd, const
   return bad;
 }
 
-template <typename T, int KS>
-__device__ void solve_cell(const MechDev &M, const CellsDev &C, const SolveParams &P, double *Wd, T *WL,
-                           const int lane, const int64_t cell, const double *gam, const double *igam) {
-  const int R = M.R;
+template <typename T, int KS, bool STAGED>
+__device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, const SolveParams &P, const Tabs &tb, double *Wd,
+                           T *WL, const int lane, const int64_t cell) {
   const int64_t NC = C.n_cells;
   chem_cell_stats st = {};
   int status = CHEM_CELL_OK;
 
-  for (int k = lane; k < M.d_nconst; k += WARP) Wd[__ldg(M.d_const_idx + k)] = __ldg(M.d_const_val + k);
-  for (int k = lane; k < M.L_nconst; k += WARP) WL[__ldg(M.L_const_idx + k)] = (T)__ldg(M.L_const_val + k);
-
-  Cell<T, KS> cl(M, P, Wd, WL, lane);
+  Cell<T, KS, STAGED> cl(M, P, tb, Wd, WL, lane);
+  cl.init_constants();
   double y0[KS];
   const bool bad = load_cell<KS>(M, C, Wd, lane, cell, cl.own, y0);
 
@@ -356,7 +460,8 @@ __device__ void solve_cell(const MechDev &M, const CellsDev &C, const SolveParam
       }
       if (!last && t + h == t) { status = CHEM_CELL_H_TOO_SMALL; break; }
 
-      const double c = h * igam[q];
+      const double iq = c_igam[q];
+      const double c = h * iq;
 #pragma unroll
       for (int k = 0; k < KS; ++k) {
         ypred[k] = D[0][k];
@@ -365,14 +470,15 @@ __device__ void solve_cell(const MechDev &M, const CellsDev &C, const SolveParam
 #pragma unroll
       for (int m = 1; m <= QMAX; ++m) {
         if (m > q) break;
+        const double gm = c_gam[m];
 #pragma unroll
         for (int k = 0; k < KS; ++k) {
           ypred[k] += D[m][k];
-          psi[k] = fma(gam[m], D[m][k], psi[k]);
+          psi[k] = fma(gm, D[m][k], psi[k]);
         }
       }
 #pragma unroll
-      for (int k = 0; k < KS; ++k) psi[k] *= igam[q];
+      for (int k = 0; k < KS; ++k) psi[k] *= iq;
 
       int fresh = 0;
       if (!have_M || force_M || fabs(c / cM - 1.0) > DGMAX || n_since_M >= MSBP) {
@@ -476,7 +582,7 @@ __device__ void solve_cell(const MechDev &M, const CellsDev &C, const SolveParam
         st.rejects++;
         nef++;
         if (nef >= MXNEF) { status = CHEM_CELL_ERR_FAIL; break; }
-        double eta = grid_eta(M.grid_thr2, M.grid_g, err, q, lane);
+        double eta = grid_eta(tab<double>(tb, M.tab.thr2), tab<double>(tb, M.tab.g), err, q, lane);
         if (nef >= 2 && eta > ETA_MXF) eta = ETA_MXF;
         if (nef >= 3 && q > 1) q -= 1;
         rescale<KS>(D, q, eta, M.rescale_coef, lane);
@@ -491,46 +597,25 @@ __device__ void solve_cell(const MechDev &M, const CellsDev &C, const SolveParam
       n_since_M++;
       nef = 0;
       ncf = 0;
-      {
-        double dq1[KS];
-        get_row<KS>(D, q + 1, dq1);
-#pragma unroll
-        for (int m = 2; m < NROW; ++m)
-          if (m == q + 2) {
-#pragma unroll
-            for (int k = 0; k < KS; ++k) D[m][k] = d[k] - dq1[k];
-          }
-#pragma unroll
-        for (int m = 1; m < NROW; ++m)
-          if (m == q + 1) {
-#pragma unroll
-            for (int k = 0; k < KS; ++k) D[m][k] = d[k];
-          }
-#pragma unroll
-        for (int m = QMAX; m >= 0; --m) {
-          if (m > q) continue;
-#pragma unroll
-          for (int k = 0; k < KS; ++k) D[m][k] += D[m + 1][k];
-        }
-      }
+      accept_update<KS>(D, q, d);
       if (last) break;
       n_eq++;
 
-      double eta = grid_eta(M.grid_thr2, M.grid_g, err, q, lane);
+      double eta = grid_eta(tab<double>(tb, M.tab.thr2), tab<double>(tb, M.tab.g), err, q, lane);
       int qn = q;
       if (n_eq >= q + 1) {
         if (q > 1) {
           double row[KS];
           get_row<KS>(D, q, row);
           const double e = cl.wrms(row, w) / (double)q;
-          const double em = grid_eta(M.grid_thr2, M.grid_g, e, q - 1, lane);
+          const double em = grid_eta(tab<double>(tb, M.tab.thr2), tab<double>(tb, M.tab.g), e, q - 1, lane);
           if (em > eta) { eta = em; qn = q - 1; }
         }
         if (q < qmax) {
           double row[KS];
           get_row<KS>(D, q + 2, row);
           const double e = cl.wrms(row, w) / (double)(q + 2);
-          const double ep = grid_eta(M.grid_thr3, M.grid_g, e, q + 1, lane);
+          const double ep = grid_eta(tab<double>(tb, M.tab.thr3), tab<double>(tb, M.tab.g), e, q + 1, lane);
           if (ep > eta) { eta = ep; qn = q + 1; }
         }
       }
@@ -566,36 +651,61 @@ __device__ void solve_cell(const MechDev &M, const CellsDev &C, const SolveParam
   __syncwarp();
 }
 
-__constant__ double c_gam[QMAX + 2];
-__constant__ double c_igam[QMAX + 2];
+// Stage the table blob into the first `bytes` of shared memory with one TMA
+// bulk copy.  The wait is bounded; if it runs out the block copies the blob
+// with ordinary loads instead (a late bulk copy writes the same bytes) and
+// counts the event in *err.
+__device__ bool stage_tables(const unsigned char *blob, int bytes, unsigned char *smem, uint64_t *bar, int *err) {
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, (uint32_t)bytes);
+    tma_load_1d(smem, blob, (uint32_t)bytes, bar);
+  }
+  const bool ok = __syncthreads_and(mbar_wait(bar, 0, TMA_WAIT_LIMIT));
+  if (!ok) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(blob);
+    uint4 *dst = reinterpret_cast<uint4 *>(smem);
+    for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    if (threadIdx.x == 0 && err) atomicAdd(err, 1);
+  }
+  return ok;
+}
 
-template <typename T, int KS>
+template <typename T, int KS, bool STAGED>
 __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const MechDev M, const CellsDev C, const SolveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t tma_bar;
   const int lane = threadIdx.x & (WARP - 1);
   const int warp = threadIdx.x / WARP;
-  double *Wd = reinterpret_cast<double *>(smem + (size_t)warp * P.cell_bytes);
-  T *WL = reinterpret_cast<T *>(Wd + P.wd_pad);
-  double gam[QMAX + 2], igam[QMAX + 2];
-#pragma unroll
-  for (int m = 0; m < QMAX + 2; ++m) {
-    gam[m] = c_gam[m];
-    igam[m] = c_igam[m];
+  Tabs tb;
+  bool staged_ok = true;
+  if (STAGED) {
+    staged_ok = stage_tables(M.blob[P.prec], P.tab_bytes, smem, &tma_bar, C.error);
+    tb.base = smem;
+  } else {
+    tb.base = M.blob[P.prec];
   }
+  double *Wd = reinterpret_cast<double *>(smem + P.tab_bytes + (size_t)warp * P.cell_bytes);
+  T *WL = reinterpret_cast<T *>(Wd + P.wd_pad);
   if (C.queue) {
     for (;;) {
       long long cell = 0;
       if (lane == 0) cell = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(C.queue), 1ull);
       cell = __shfl_sync(FULL, cell, 0);
       if (cell >= C.n_cells) break;
-      solve_cell<T, KS>(M, C, P, Wd, WL, lane, cell, gam, igam);
+      solve_cell<T, KS, STAGED>(M, C, P, tb, Wd, WL, lane, cell);
     }
   } else {
     const int64_t cell = (int64_t)blockIdx.x * P.warps_per_block + warp;
-    if (cell < C.n_cells) solve_cell<T, KS>(M, C, P, Wd, WL, lane, cell, gam, igam);
+    if (cell < C.n_cells) solve_cell<T, KS, STAGED>(M, C, P, tb, Wd, WL, lane, cell);
+  }
+  if (STAGED && !staged_ok) {
+    __syncthreads();
+    mbar_wait(&tma_bar, 0, TMA_WAIT_LIMIT);   // let a late bulk copy land before the block exits
   }
 }
-
 
 // Diagnostic: per cell, f(y) (mode 0) or x = (I - c J(y))^{-1} b (mode 1),
 // using the same device routines as the solve.
@@ -608,11 +718,12 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) probe_kernel(const
   const int warp = threadIdx.x / WARP;
   const int64_t cell = (int64_t)blockIdx.x * P.warps_per_block + warp;
   if (cell >= C.n_cells) return;
+  Tabs tb;
+  tb.base = M.blob[P.prec];
   double *Wd = reinterpret_cast<double *>(smem + (size_t)warp * P.cell_bytes);
   T *WL = reinterpret_cast<T *>(Wd + P.wd_pad);
-  for (int k = lane; k < M.d_nconst; k += WARP) Wd[__ldg(M.d_const_idx + k)] = __ldg(M.d_const_val + k);
-  for (int k = lane; k < M.L_nconst; k += WARP) WL[__ldg(M.L_const_idx + k)] = (T)__ldg(M.L_const_val + k);
-  Cell<T, KS> cl(M, P, Wd, WL, lane);
+  Cell<T, KS, false> cl(M, P, tb, Wd, WL, lane);
+  cl.init_constants();
   double y0[KS];
   load_cell<KS>(M, C, Wd, lane, cell, cl.own, y0);
   const int64_t NC = C.n_cells;
@@ -638,42 +749,75 @@ template <typename T, int KS>
 cudaError_t launch_probe_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int mode, double c,
                            const double *y, const double *b, double *out, cudaStream_t stream) {
   const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
-  cudaError_t e = cudaFuncSetAttribute(probe_kernel<T, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaError_t e = cudaFuncSetAttribute(probe_kernel<T, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e != cudaSuccess) return e;
   const int blocks = (int)((C.n_cells + P.warps_per_block - 1) / P.warps_per_block);
   probe_kernel<T, KS><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, P, mode, c, y, b, out);
   return cudaGetLastError();
 }
 
-template <typename T, int KS>
-cudaError_t configure_t(size_t smem) {
-  static int configured_bytes[64] = {0};
+template <typename T, int KS, bool STAGED>
+cudaError_t configure_t() {
+  static bool configured[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 64 && configured_bytes[dev] >= (int)smem) return cudaSuccess;
+  if (dev < 64 && configured[dev]) return cudaSuccess;
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaError_t e = cudaFuncSetAttribute(solve_kernel<T, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  if (e == cudaSuccess && dev < 64) configured_bytes[dev] = optin;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, solve_kernel<T, KS, STAGED>);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(solve_kernel<T, KS, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess && dev < 64) configured[dev] = true;
   return e;
 }
 
-template <typename T, int KS>
+template <typename T, int KS, bool STAGED>
 int occupancy_t(int warps_per_block, size_t smem) {
-  if (configure_t<T, KS>(smem) != cudaSuccess) return 0;
+  if (configure_t<T, KS, STAGED>() != cudaSuccess) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, solve_kernel<T, KS>, warps_per_block * WARP, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, solve_kernel<T, KS, STAGED>, warps_per_block * WARP, smem) !=
+      cudaSuccess)
+    return 0;
   return n;
 }
 
-template <typename T, int KS>
+template <typename T, int KS, bool STAGED>
 cudaError_t launch_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int blocks, cudaStream_t stream) {
-  const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
-  cudaError_t e = configure_t<T, KS>(smem);
+  const size_t smem = (size_t)P.tab_bytes + (size_t)P.cell_bytes * P.warps_per_block;
+  cudaError_t e = configure_t<T, KS, STAGED>();
   if (e != cudaSuccess) return e;
-  solve_kernel<T, KS><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, P);
+  solve_kernel<T, KS, STAGED><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, P);
   return cudaGetLastError();
 }
+
+template <typename T, bool STAGED>
+int occupancy_ks(const MechDev &M, int warps_per_block, size_t smem) {
+  switch ((M.S + WARP - 1) / WARP) {
+    case 1: return occupancy_t<T, 1, STAGED>(warps_per_block, smem);
+    case 2: return occupancy_t<T, 2, STAGED>(warps_per_block, smem);
+    case 3: return occupancy_t<T, 3, STAGED>(warps_per_block, smem);
+    case 4: return occupancy_t<T, 4, STAGED>(warps_per_block, smem);
+    default: return 0;
+  }
+}
+
+template <typename T, bool STAGED>
+cudaError_t launch_ks(const MechDev &M, const CellsDev &C, const SolveParams &P, int blocks, cudaStream_t stream) {
+  switch ((M.S + WARP - 1) / WARP) {
+    case 1: return launch_t<T, 1, STAGED>(M, C, P, blocks, stream);
+    case 2: return launch_t<T, 2, STAGED>(M, C, P, blocks, stream);
+    case 3: return launch_t<T, 3, STAGED>(M, C, P, blocks, stream);
+    case 4: return launch_t<T, 4, STAGED>(M, C, P, blocks, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool staged_driver(int driver) { return driver == CHEM_DRIVER_PERSISTENT; }
 
 }  // namespace
 
@@ -683,11 +827,14 @@ size_t smem_per_cell(const MechDev &m, int lu_precision) {
   return (wd + wl + 15) & ~(size_t)15;
 }
 
-int max_warps_per_block(const MechDev &m, int lu_precision) {
+size_t staged_bytes(const MechDev &m, int driver) { return staged_driver(driver) ? (size_t)m.tab.bytes : 0; }
+
+int max_warps_per_block(const MechDev &m, int lu_precision, int driver) {
   int dev = 0, smem_block = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const int w = (int)(smem_block / smem_per_cell(m, lu_precision));
+  const long avail = (long)smem_block - (long)staged_bytes(m, driver) - 64;
+  const int w = avail > 0 ? (int)(avail / (long)smem_per_cell(m, lu_precision)) : 0;
   return w < MAX_WARPS_PER_BLOCK ? w : MAX_WARPS_PER_BLOCK;
 }
 
@@ -705,16 +852,27 @@ cudaError_t set_constants() {
   return cudaMemcpyToSymbol(c_igam, igam, sizeof(igam));
 }
 
-int occupancy(const MechDev &M, int lu_precision, int warps_per_block) {
-  const size_t smem = smem_per_cell(M, lu_precision) * (size_t)warps_per_block;
+int occupancy(const MechDev &M, int lu_precision, int driver, int warps_per_block) {
+  const size_t smem = staged_bytes(M, driver) + smem_per_cell(M, lu_precision) * (size_t)warps_per_block;
   const bool f32 = lu_precision == 32;
-  switch ((M.S + WARP - 1) / WARP) {
-    case 1: return f32 ? occupancy_t<float, 1>(warps_per_block, smem) : occupancy_t<double, 1>(warps_per_block, smem);
-    case 2: return f32 ? occupancy_t<float, 2>(warps_per_block, smem) : occupancy_t<double, 2>(warps_per_block, smem);
-    case 3: return f32 ? occupancy_t<float, 3>(warps_per_block, smem) : occupancy_t<double, 3>(warps_per_block, smem);
-    case 4: return f32 ? occupancy_t<float, 4>(warps_per_block, smem) : occupancy_t<double, 4>(warps_per_block, smem);
-    default: return 0;
+  if (staged_driver(driver))
+    return f32 ? occupancy_ks<float, true>(M, warps_per_block, smem) : occupancy_ks<double, true>(M, warps_per_block, smem);
+  return f32 ? occupancy_ks<float, false>(M, warps_per_block, smem) : occupancy_ks<double, false>(M, warps_per_block, smem);
+}
+
+int best_warps_per_block(const MechDev &M, int lu_precision, int driver) {
+  const int wmax = max_warps_per_block(M, lu_precision, driver);
+  int best_w = 0, best_cells = 0;
+  for (int w = 1; w <= wmax; ++w) {
+    const int cells = w * occupancy(M, lu_precision, driver, w);
+    // most resident cells per SM; ties go to the larger block when the tables
+    // are staged per block, else to the smaller block (blocks retire independently)
+    if (cells > best_cells || (cells == best_cells && cells > 0 && staged_driver(driver))) {
+      best_cells = cells;
+      best_w = w;
+    }
   }
+  return best_w;
 }
 
 cudaError_t launch_probe(const MechDev &M, const CellsDev &C, int lu_precision, int mode, double c, const double *y,
@@ -724,21 +882,16 @@ cudaError_t launch_probe(const MechDev &M, const CellsDev &C, int lu_precision, 
   P.wd_pad = (M.Wd_len + 1) & ~1;
   P.cell_bytes = (int)smem_per_cell(M, lu_precision);
   P.warps_per_block = 1;
-  const int KS = (M.S + WARP - 1) / WARP;
+  P.prec = lu_precision == 32 ? 1 : 0;
+  P.tab_bytes = 0;
   const bool f32 = lu_precision == 32;
-#define CHEM_PROBE(KSV)                                                                       \
-  case KSV:                                                                                   \
-    return f32 ? launch_probe_t<float, KSV>(M, C, P, mode, c, y, b, out, stream)              \
-               : launch_probe_t<double, KSV>(M, C, P, mode, c, y, b, out, stream);
-  switch (KS) {
-    CHEM_PROBE(1)
-    CHEM_PROBE(2)
-    CHEM_PROBE(3)
-    CHEM_PROBE(4)
-    default:
-      return cudaErrorInvalidValue;
+  switch ((M.S + WARP - 1) / WARP) {
+    case 1: return f32 ? launch_probe_t<float, 1>(M, C, P, mode, c, y, b, out, stream) : launch_probe_t<double, 1>(M, C, P, mode, c, y, b, out, stream);
+    case 2: return f32 ? launch_probe_t<float, 2>(M, C, P, mode, c, y, b, out, stream) : launch_probe_t<double, 2>(M, C, P, mode, c, y, b, out, stream);
+    case 3: return f32 ? launch_probe_t<float, 3>(M, C, P, mode, c, y, b, out, stream) : launch_probe_t<double, 3>(M, C, P, mode, c, y, b, out, stream);
+    case 4: return f32 ? launch_probe_t<float, 4>(M, C, P, mode, c, y, b, out, stream) : launch_probe_t<double, 4>(M, C, P, mode, c, y, b, out, stream);
+    default: return cudaErrorInvalidValue;
   }
-#undef CHEM_PROBE
 }
 
 cudaError_t launch_solve(const MechDev &M, const CellsDev &C, const LaunchCfg &cfg, cudaStream_t stream) {
@@ -752,12 +905,15 @@ cudaError_t launch_solve(const MechDev &M, const CellsDev &C, const LaunchCfg &c
   P.wd_pad = (M.Wd_len + 1) & ~1;
   P.cell_bytes = (int)smem_per_cell(M, cfg.lu_precision);
   P.warps_per_block = cfg.warps_per_block;
+  P.prec = cfg.lu_precision == 32 ? 1 : 0;
+  const bool staged = staged_driver(cfg.driver);
+  P.tab_bytes = (int)staged_bytes(M, cfg.driver);
   int dev = 0, n_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   int blocks;
   if (cfg.driver == CHEM_DRIVER_PERSISTENT) {
-    int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : occupancy(M, cfg.lu_precision, cfg.warps_per_block);
+    int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : occupancy(M, cfg.lu_precision, cfg.driver, cfg.warps_per_block);
     if (bps < 1) bps = 1;
     blocks = n_sm * bps;
     const int64_t need = (C.n_cells + P.warps_per_block - 1) / P.warps_per_block;
@@ -765,21 +921,9 @@ cudaError_t launch_solve(const MechDev &M, const CellsDev &C, const LaunchCfg &c
   } else {
     blocks = (int)((C.n_cells + P.warps_per_block - 1) / P.warps_per_block);
   }
-  const int KS = (M.S + WARP - 1) / WARP;
   const bool f32 = cfg.lu_precision == 32;
-#define CHEM_LAUNCH(KSV)                                                               \
-  case KSV:                                                                            \
-    return f32 ? launch_t<float, KSV>(M, C, P, blocks, stream)                         \
-               : launch_t<double, KSV>(M, C, P, blocks, stream);
-  switch (KS) {
-    CHEM_LAUNCH(1)
-    CHEM_LAUNCH(2)
-    CHEM_LAUNCH(3)
-    CHEM_LAUNCH(4)
-    default:
-      return cudaErrorInvalidValue;
-  }
-#undef CHEM_LAUNCH
+  if (staged) return f32 ? launch_ks<float, true>(M, C, P, blocks, stream) : launch_ks<double, true>(M, C, P, blocks, stream);
+  return f32 ? launch_ks<float, false>(M, C, P, blocks, stream) : launch_ks<double, false>(M, C, P, blocks, stream);
 }
 
 }  // namespace chemgpu

@@ -242,7 +242,8 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
   d.L_P = d.L_X + S;
   d.L_ZERO = d.L_P + n_pairs;
   const int L_ONE = d.L_ZERO + 1;
-  int L_temp = L_ONE + 1;
+  const int L_NEG_ONE = L_ONE + 1;
+  int L_temp = L_NEG_ONE + 1;
   d.m_clear = nnz;
 
   // ---- f program: f_i = sum_j nu_ij r_j, species-major, chunked
@@ -317,8 +318,8 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
     m.m_prog = sch.finish();
     m.flops_jac = flops;
     d.WL_len = ct.base + (int)ct.vals.size();
-    m.L_consts_v = {0.0, 1.0};
-    m.L_consts_i = {d.L_ZERO, L_ONE};
+    m.L_consts_v = {0.0, 1.0, -1.0};
+    m.L_consts_i = {d.L_ZERO, L_ONE, L_NEG_ONE};
     for (size_t k = 0; k < ct.vals.size(); ++k) {
       m.L_consts_v.push_back(ct.vals[k]);
       m.L_consts_i.push_back(ct.base + (int)k);
@@ -357,7 +358,8 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
     m.flops_lu = flops;
   }
 
-  // ---- forward (x_i += (-l_ik) x_k) and backward (x_k = x_k / u_kk; x_i -= u_ik x_k) programs
+  // ---- forward (x_i += (-l_ik) x_k) and backward (x_k = x_k / u_kk; x_i -= u_ik x_k) programs,
+  // column-oriented: once x_k is final its column of updates is independent work
   {
     Scheduler f(d.WL_len + 8), b(d.WL_len + 8);
     double flops = 0;
@@ -380,7 +382,15 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
     m.bwd_prog = b.finish();
     m.flops_solve = flops;
   }
-  if (d.WL_len > 0x7ffe || d.Wd_len > 0x7ffe) { msg = "mechanism too large for 15-bit work indices"; return CHEM_EINVAL; }
+  d.d_DUMMY = d.Wd_len++;
+  d.L_DUMMY = d.WL_len++;
+  if ((size_t)d.WL_len * sizeof(double) > 0xfff0 || (size_t)d.Wd_len * sizeof(double) > 0xfff0) {
+    msg = "mechanism too large: the per-cell work arrays exceed the 16-bit byte offsets of the warp programs";
+    return CHEM_EINVAL;
+  }
+  m.rx_slot_idx.assign((size_t)R * 3, d.d_ONE);
+  for (int j = 0; j < R; ++j)
+    for (int s2 = 0; s2 < rx[j].n_reac; ++s2) m.rx_slot_idx[(size_t)j * 3 + s2] = d.d_Y + rx[j].reac[s2];
   return 0;
 }
 
@@ -398,11 +408,31 @@ int put(Mechanism &m, const std::vector<T> &v, const T **dst, std::string &msg) 
   return 0;
 }
 
-int put_prog(Mechanism &m, const HostProgram &hp, ProgramDev &pd, std::string &msg) {
+// Device form of a program: byte offsets (element index * elem), empty slots
+// as FMAs into the dummy slot, RECIP passes marked in every slot.
+std::vector<ushort4> device_ops(const HostProgram &hp, int elem, int dummy, int zero, int one) {
   std::vector<ushort4> v(hp.ops.size());
-  for (size_t i = 0; i < v.size(); ++i) v[i] = make_ushort4(hp.ops[i].t, hp.ops[i].a, hp.ops[i].b, hp.ops[i].c);
-  pd.n_pass = hp.n_pass();
-  return put(m, v, &pd.ops, msg);
+  const int np = hp.n_pass();
+  for (int p = 0; p < np; ++p) {
+    bool recip = false;
+    for (int l = 0; l < WARP; ++l) {
+      const Op &o = hp.ops[(size_t)p * WARP + l];
+      if (o.t != OP_EMPTY && (o.t & OP_RECIP)) recip = true;
+    }
+    for (int l = 0; l < WARP; ++l) {
+      const Op &o = hp.ops[(size_t)p * WARP + l];
+      ushort4 &d = v[(size_t)p * WARP + l];
+      if (o.t == OP_EMPTY) {
+        d = recip ? make_ushort4(dummy * elem, one * elem, 0, DEV_RECIP)
+                  : make_ushort4(dummy * elem, zero * elem, zero * elem, zero * elem);
+      } else if (recip) {
+        d = make_ushort4((o.t & 0x7fff) * elem, o.a * elem, 0, DEV_RECIP);
+      } else {
+        d = make_ushort4(o.t * elem, o.a * elem, o.b * elem, o.c * elem);
+      }
+    }
+  }
+  return v;
 }
 
 // polynomial coefficients (in eta) of R(eta)_{jm} = prod_{l<m} (l - j eta)/(l+1)
@@ -419,15 +449,26 @@ void r_poly(int j, int mm, double *c /* QMAX+1 */) {
   }
 }
 
+struct BlobWriter {
+  std::vector<unsigned char> buf;
+  template <typename T>
+  int add(const std::vector<T> &v) {
+    const int off = (int)buf.size();
+    const size_t n = v.size() * sizeof(T);
+    buf.resize(off + ((n + 15) & ~(size_t)15), 0);
+    if (n) std::memcpy(buf.data() + off, v.data(), n);
+    return off;
+  }
+};
+
 }  // namespace
 
 int upload_mechanism(Mechanism &m, std::string &msg) {
   MechDev &d = m.dev;
-  const int S = m.S, R = m.R;
+  const int R = m.R, S = m.S;
   cudaGetDevice(&m.device);
   std::vector<int> kind(R), nreac(R), phot(R);
   std::vector<double> A(R), Ea(R), B(R), J(R);
-  std::vector<ushort4> slots(R);
   int ip = 0;
   for (int j = 0; j < R; ++j) {
     const chem_reaction &r = m.rx[j];
@@ -438,12 +479,7 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
     Ea[j] = r.Ea_over_R;
     B[j] = r.B;
     J[j] = r.J;
-    uint16_t sl[3] = {(uint16_t)d.d_ONE, (uint16_t)d.d_ONE, (uint16_t)d.d_ONE};
-    for (int s = 0; s < r.n_reac; ++s) sl[s] = (uint16_t)(d.d_Y + r.reac[s]);
-    slots[j] = make_ushort4(sl[0], sl[1], sl[2], 0);
   }
-  std::vector<ushort2> po(m.pair_other.size());
-  for (size_t k = 0; k < po.size(); ++k) po[k] = make_ushort2((uint16_t)m.pair_other[k].first, (uint16_t)m.pair_other[k].second);
   std::vector<double> thr2(7 * GRID_N), thr3(7 * GRID_N), g(GRID_N);
   for (int p = 0; p < 7; ++p)
     for (int i = GRID_IMIN; i <= GRID_IMAX; ++i) {
@@ -451,24 +487,56 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
       thr3[p * GRID_N + i - GRID_IMIN] = 1.0 / (3.0 * exp2((double)i * (double)(p + 1) / 8.0));
     }
   for (int i = GRID_IMIN; i <= GRID_IMAX; ++i) g[i - GRID_IMIN] = exp2((double)i / 8.0);
-  int rc = 0;
-  if ((rc = put(m, kind, &d.rx_kind, msg)) || (rc = put(m, nreac, &d.rx_nreac, msg)) ||
-      (rc = put(m, phot, &d.rx_phot, msg)) || (rc = put(m, A, &d.rx_A, msg)) ||
-      (rc = put(m, Ea, &d.rx_Ea, msg)) || (rc = put(m, B, &d.rx_B, msg)) || (rc = put(m, J, &d.rx_J, msg)) ||
-      (rc = put(m, slots, &d.rx_slots, msg)) || (rc = put(m, m.pair_rx, &d.pair_rx, msg)) ||
-      (rc = put(m, po, &d.pair_other, msg)) || (rc = put(m, m.pos, &d.sp_pos, msg)) ||
-      (rc = put(m, m.lu_diag, &d.lu_diag, msg)) || (rc = put(m, m.d_consts_v, &d.d_const_val, msg)) ||
-      (rc = put(m, m.d_consts_i, &d.d_const_idx, msg)) || (rc = put(m, m.L_consts_v, &d.L_const_val, msg)) ||
-      (rc = put(m, m.L_consts_i, &d.L_const_idx, msg)) || (rc = put(m, thr2, &d.grid_thr2, msg)) ||
-      (rc = put(m, thr3, &d.grid_thr3, msg)) || (rc = put(m, g, &d.grid_g, msg)) ||
-      (rc = put_prog(m, m.f_prog, d.f_prog, msg)) || (rc = put_prog(m, m.m_prog, d.m_prog, msg)) ||
-      (rc = put_prog(m, m.lu_prog, d.lu_prog, msg)) || (rc = put_prog(m, m.fwd_prog, d.fwd_prog, msg)) ||
-      (rc = put_prog(m, m.bwd_prog, d.bwd_prog, msg))) {
-    free_mechanism(m);
-    return rc;
+
+  // the staged blobs, one per LU precision (identical section offsets)
+  for (int prec = 0; prec < 2; ++prec) {
+    const int el = prec == 0 ? 8 : 4;     // bytes per WL element
+    BlobWriter bw;
+    TableOffsets t;
+    t.f_ops = bw.add(device_ops(m.f_prog, 8, d.d_DUMMY, d.d_ZERO, d.d_ONE));
+    t.fwd_ops = bw.add(device_ops(m.fwd_prog, el, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1));
+    t.bwd_ops = bw.add(device_ops(m.bwd_prog, el, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1));
+    std::vector<uint2> slots(R);
+    for (int j = 0; j < R; ++j)
+      slots[j] = make_uint2((unsigned)(m.rx_slot_idx[j * 3] * 8) | ((unsigned)(m.rx_slot_idx[j * 3 + 1] * 8) << 16),
+                            (unsigned)(m.rx_slot_idx[j * 3 + 2] * 8));
+    t.rx_slots = bw.add(slots);
+    t.pair_rx = bw.add(m.pair_rx);
+    std::vector<unsigned> po(m.pair_other.size());
+    for (size_t k = 0; k < po.size(); ++k)
+      po[k] = (unsigned)(m.pair_other[k].first * 8) | ((unsigned)(m.pair_other[k].second * 8) << 16);
+    t.pair_other = bw.add(po);
+    std::vector<int> diag(S);
+    for (int k = 0; k < S; ++k) diag[k] = m.lu_diag[k] * el;
+    t.lu_diag = bw.add(diag);
+    std::vector<int> doff(m.d_consts_i.size()), loff(m.L_consts_i.size());
+    for (size_t k = 0; k < doff.size(); ++k) doff[k] = m.d_consts_i[k] * 8;
+    for (size_t k = 0; k < loff.size(); ++k) loff[k] = m.L_consts_i[k] * el;
+    t.dconst_off = bw.add(doff);
+    t.dconst_val = bw.add(m.d_consts_v);
+    t.Lconst_off = bw.add(loff);
+    t.Lconst_val = bw.add(m.L_consts_v);
+    t.thr2 = bw.add(thr2);
+    t.thr3 = bw.add(thr3);
+    t.g = bw.add(g);
+    t.bytes = (int)bw.buf.size();
+    d.tab = t;
+    int rc = put(m, bw.buf, &d.blob[prec], msg);
+    if (!rc) rc = put(m, device_ops(m.m_prog, el, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1), &d.m_ops[prec], msg);
+    if (!rc) rc = put(m, device_ops(m.lu_prog, el, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1), &d.lu_ops[prec], msg);
+    if (rc) {
+      free_mechanism(m);
+      return rc;
+    }
   }
+  d.f_npass = m.f_prog.n_pass();
+  d.fwd_npass = m.fwd_prog.n_pass();
+  d.bwd_npass = m.bwd_prog.n_pass();
+  d.m_npass = m.m_prog.n_pass();
+  d.lu_npass = m.lu_prog.n_pass();
   d.d_nconst = (int)m.d_consts_v.size();
   d.L_nconst = (int)m.L_consts_v.size();
+
   // T(eta) = U R(eta), U = R(1): coefficients of each entry as a polynomial in eta
   std::vector<double> coef(QMAX * QMAX * (QMAX + 1), 0.0);
   for (int i = 1; i <= QMAX; ++i)
@@ -483,7 +551,11 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
         for (int p = 0; p <= QMAX; ++p) acc[p] += uij * r[p];
       }
     }
-  if ((rc = put(m, coef, &d.rescale_coef, msg))) {
+  int rc = 0;
+  if ((rc = put(m, kind, &d.rx_kind, msg)) || (rc = put(m, nreac, &d.rx_nreac, msg)) ||
+      (rc = put(m, phot, &d.rx_phot, msg)) || (rc = put(m, A, &d.rx_A, msg)) ||
+      (rc = put(m, Ea, &d.rx_Ea, msg)) || (rc = put(m, B, &d.rx_B, msg)) || (rc = put(m, J, &d.rx_J, msg)) ||
+      (rc = put(m, m.pos, &d.sp_pos, msg)) || (rc = put(m, coef, &d.rescale_coef, msg))) {
     free_mechanism(m);
     return rc;
   }
@@ -492,7 +564,6 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
     msg = "could not set solver constants on the device";
     return CHEM_ECUDA;
   }
-  (void)S;
   return 0;
 }
 

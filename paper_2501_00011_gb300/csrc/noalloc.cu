@@ -23,8 +23,8 @@
 namespace chemgpu {
 namespace {
 
-// Scratch for the work-queue counter (one 64-bit word is used; the array is
-// 256 bytes so the counter sits alone in its cache line).
+// Scratch: word 0 is the work-queue counter, word 1 counts blocks whose table
+// staging fell back to plain loads; 256 bytes keep them alone in their line.
 constexpr int NOALLOC_SCRATCH_WORDS = 32;
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[NOALLOC_SCRATCH_WORDS];
 
@@ -75,17 +75,11 @@ extern "C" int chem_solve_step_noalloc(const chem_mech *mech, int64_t n_cells, c
     if (e != cudaSuccess || !p) return fail(CHEM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     g_scratch_addr[dev] = p;
   }
-  const int wmax = max_warps_per_block(mech->m.dev, o.lu_precision);
+  const int wmax = max_warps_per_block(mech->m.dev, o.lu_precision, CHEM_DRIVER_PERSISTENT);
   if (wmax < 1) return fail(CHEM_EINVAL, "mechanism working set does not fit in shared memory");
   if (o.cells_per_block > wmax) return fail(CHEM_EINVAL, "cells_per_block exceeds the shared-memory limit");
-  if (o.cells_per_block == 0) {
-    int best_w = 1, best_cells = 0;
-    for (int w = 1; w <= wmax; ++w) {
-      const int cells = w * occupancy(mech->m.dev, o.lu_precision, w);
-      if (cells >= best_cells) { best_cells = cells; best_w = w; }
-    }
-    o.cells_per_block = best_w;
-  }
+  if (o.cells_per_block == 0) o.cells_per_block = best_warps_per_block(mech->m.dev, o.lu_precision, CHEM_DRIVER_PERSISTENT);
+  if (o.cells_per_block < 1) return fail(CHEM_EINVAL, "no launch shape fits on this device");
 
   cudaStream_t s = (cudaStream_t)stream;
   // the counter must start at zero for every call
@@ -101,6 +95,7 @@ extern "C" int chem_solve_step_noalloc(const chem_mech *mech, int64_t n_cells, c
   cd.y = y;
   cd.stats = stats;
   cd.queue = reinterpret_cast<int *>(g_scratch_addr[dev]);
+  cd.error = reinterpret_cast<int *>(reinterpret_cast<unsigned long long *>(g_scratch_addr[dev]) + 1);
   LaunchCfg cfg;
   cfg.lu_precision = o.lu_precision;
   cfg.driver = CHEM_DRIVER_PERSISTENT;
