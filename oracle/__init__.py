@@ -98,7 +98,7 @@ def lib():
             if hasattr(L, "orc_adjoint"):
                 L.orc_adjoint.argtypes = [P, P, P, P, P, P, P]
                 L.orc_adjoint.restype = ct.c_int
-                L.orc_replay.argtypes = [P, P, P, P, ct.c_double, ct.c_int, P]
+                L.orc_replay.argtypes = [P, P, P, P, ct.c_double, ct.c_int, P, P]
                 L.orc_replay.restype = ct.c_int
                 L.orc_tangent.argtypes = [P, P, P, P, P, P, P]
                 L.orc_tangent.restype = ct.c_int
@@ -255,3 +255,63 @@ def solve_cells(mech, cells, dt, rtol, atol, max_order=5, max_steps=5000, theta=
     o = _opts(rtol, atol, max_order, max_steps)
     lib().orc_solve_cells(m.ref, C, _p(T), _p(P), _p(jp), _p(th), _p(y), float(dt), ct.byref(o), _p(st))
     return y, st
+
+
+def _tape_struct(tape: Tape):
+    arrs = (np.ascontiguousarray(tape.kind, np.int32), np.ascontiguousarray(tape.q, np.int32),
+            np.ascontiguousarray(tape.val, np.float64), np.ascontiguousarray(tape.y, np.float64))
+    n = arrs[0].size
+    return _Tape(n, n, 0, 0, *(a.ctypes.data for a in arrs)), arrs
+
+
+def integrate_steps(mech, kt, y0, dt, n_steps, rtol, atol, max_order=5, max_steps=5000, tape_cap=20000):
+    """n_steps consecutive solves of one cell; returns (y, [stats], concatenated Tape)."""
+    y = np.array(y0, np.float64)
+    stats, parts = [], []
+    for _ in range(n_steps):
+        y, st, tp = integrate(mech, kt, y, dt, rtol, atol, max_order=max_order, max_steps=max_steps,
+                              tape_cap=tape_cap)
+        stats.append(st)
+        parts.append(tp)
+    tape = Tape(np.concatenate([p.kind for p in parts]), np.concatenate([p.q for p in parts]),
+                np.concatenate([p.val for p in parts]), np.concatenate([p.y for p in parts]))
+    return y, stats, tape
+
+
+def replay(mech, kt, y0, tape: Tape, newton_tol=1e-15, maxit=30, keep_steps=False):
+    """The frozen-step map of a tape: y0 -> y_final (and y after every STEP event)."""
+    m = _mk(mech)
+    ts, keep = _tape_struct(tape)
+    y0 = np.ascontiguousarray(y0, np.float64)
+    out = np.empty(m.S)
+    ys = np.zeros((tape.kind.size, m.S)) if keep_steps else None
+    rc = lib().orc_replay(m.ref, _p(np.ascontiguousarray(kt, np.float64)), _p(y0), ct.byref(ts), float(newton_tol),
+                          int(maxit), _p(out), _p(ys))
+    if rc:
+        raise RuntimeError("replay: a step equation did not converge")
+    return (out, ys) if keep_steps else out
+
+
+def tangent(mech, kt, y0, tape: Tape, dy0, dtheta):
+    m = _mk(mech)
+    ts, keep = _tape_struct(tape)
+    out = np.empty(m.S)
+    rc = lib().orc_tangent(m.ref, _p(np.ascontiguousarray(kt, np.float64)), _p(np.ascontiguousarray(y0, np.float64)),
+                           ct.byref(ts), _p(np.ascontiguousarray(dy0, np.float64)),
+                           _p(np.ascontiguousarray(dtheta, np.float64)), _p(out))
+    if rc:
+        raise RuntimeError("tangent: a step equation did not converge")
+    return out
+
+
+def adjoint(mech, kt, y0, tape: Tape, lam_final):
+    """(dL/dy0, dL/dtheta) of the frozen-step map for dL/dy_final = lam_final."""
+    m = _mk(mech)
+    ts, keep = _tape_struct(tape)
+    ly0 = np.empty(m.S)
+    g = np.empty(m.R)
+    rc = lib().orc_adjoint(m.ref, _p(np.ascontiguousarray(kt, np.float64)), _p(np.ascontiguousarray(y0, np.float64)),
+                           ct.byref(ts), _p(np.ascontiguousarray(lam_final, np.float64)), _p(ly0), _p(g))
+    if rc:
+        raise RuntimeError("adjoint: a step equation did not converge")
+    return ly0, g

@@ -113,6 +113,17 @@ int orc_solve_cells(const orc_mech *m, int64_t n_cells, const double *T, const d
                     const double *jphot, const double *theta, double *y, double dt,
                     const orc_opts *o, orc_stats *st);
 
+/* adjoint.c: the frozen-step replay map of a tape, its tangent and adjoint.
+ * kt includes theta.  y_steps (optional) receives y after every STEP event
+ * ([tape n][S], other rows untouched).  Return 0, or 1 if a step equation did
+ * not converge / a matrix was exactly singular. */
+int orc_replay(const orc_mech *m, const double *kt, const double *y0, const orc_tape *tape, double newton_tol,
+               int maxit, double *y_out, double *y_steps);
+int orc_tangent(const orc_mech *m, const double *kt, const double *y0, const orc_tape *tape, const double *dy0,
+                const double *dtheta, double *dy_out);
+int orc_adjoint(const orc_mech *m, const double *kt, const double *y0, const orc_tape *tape,
+                const double *lam_final, double *lam_y0, double *g_theta);
+
 #ifdef __cplusplus
 }
 #endif

@@ -190,7 +190,7 @@ struct Cell {
   int lane;
   int pos[KS];        // pivot position of this lane's species
   bool own[KS];       // species index < S
-  double Sd;          // number of species as a double (norm divisor)
+  double invS;        // 1 / number of species (norm weight)
 
   __device__ __forceinline__ Cell(const MechDev &m, const SolveParams &p, const Tabs &t, double *wd, T *wl, int l)
       : M(m), P(p), tb(t), Wd(wd), WL(wl), lane(l) {
@@ -200,7 +200,7 @@ struct Cell {
       own[k] = s < M.S;
       pos[k] = own[k] ? __ldg(M.sp_pos + s) : 0;
     }
-    Sd = (double)M.S;
+    invS = 1.0 / (double)M.S;
   }
 
   __device__ __forceinline__ void init_constants() {
@@ -219,12 +219,12 @@ struct Cell {
         s = fma(t, t, s);
       }
     s = warp_sum(s);
-    return sqrt(s / Sd);
+    return sqrt(s * invS);
   }
 
   __device__ __forceinline__ void weights(const double (&y)[KS], double (&w)[KS]) const {
 #pragma unroll
-    for (int k = 0; k < KS; ++k) w[k] = own[k] ? 1.0 / (P.rtol * fabs(y[k]) + P.atol) : 0.0;
+    for (int k = 0; k < KS; ++k) w[k] = own[k] ? recip_nr(fma(P.rtol, fabs(y[k]), P.atol)) : 0.0;
   }
 
   // a2: f(y) into registers
@@ -555,7 +555,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
             }
           vs = warp_sum(vs);
           eta_c = warp_min(eta_c);
-          if (sqrt(vs / cl.Sd) <= tol) {
+          if (sqrt(vs * cl.invS) <= tol) {
 #pragma unroll
             for (int k = 0; k < KS; ++k)
               if (cl.own[k] && y[k] < 0.0) {
