@@ -44,6 +44,7 @@ extern "C" {
 #define CHEM_MAX_REAC 3
 #define CHEM_MAX_PROD 8
 #define CHEM_MAX_SPECIES 128
+#define CHEM_MAX_TAPE_ROWS (1 << 20)   /* largest chem_opts.tape_steps */
 
 /* error codes (negative returns) */
 #define CHEM_EINVAL (-1)   /* bad argument or mechanism table */
@@ -113,8 +114,10 @@ typedef struct {
   int32_t driver;                  /* CHEM_DRIVER_* */
   int32_t cells_per_block;         /* warps (= concurrent cells) per block; 0 = auto */
   int32_t blocks_per_sm;           /* persistent driver: resident blocks per SM; 0 = auto */
-  int32_t record_adjoint;          /* 1: record the step tape for chem_sensitivity */
-  int32_t tape_steps;              /* tape capacity in accepted steps per cell (0 = 400) */
+  int32_t record_adjoint;          /* 1: record the tape for chem_sensitivity (needs lu_precision 64) */
+  int32_t tape_steps;              /* tape rows per cell: states stored, one per solve, per
+                                      refactorisation and per accepted corrector iteration
+                                      (0 = 2000, at most CHEM_MAX_TAPE_ROWS); events 3x that + 64 */
 } chem_opts;
 
 typedef struct {
@@ -172,6 +175,40 @@ int chem_get_state(const chem_cells *cells, double *y, int32_t mem, void *stream
 /* Copy the per-cell statistics of the last solve (out[n_cells]); synchronises
  * stream when mem is CHEM_MEM_HOST. */
 int chem_get_stats(const chem_cells *cells, chem_cell_stats *out, int32_t mem, void *stream);
+
+/* Discrete adjoint (needs opts.record_adjoint).  Every solve_step since the
+ * last set_state recorded, per cell, everything that determined its result:
+ * the initial step, every history rescale, every accepted step with its order,
+ * its corrector iteration count and its projections onto y >= 0, and every
+ * refactorisation of the iteration matrix, with the states f and J were
+ * evaluated at.  For L = sum_{i,c} dL_dy[i][c] * y[i][c] (y the current state)
+ * this returns dL_dtheta[n_reactions] (theta: the log multipliers of
+ * chem_cells_set_theta, shared by all cells; the sum over cells) and
+ * dL_dy0[n_species][n_cells] (the state at set_state).  It is the exact
+ * adjoint of the computation the solve made, with its controls frozen: the
+ * recorded step sizes, orders, iteration counts and projections, and the
+ * iteration matrices M = I - c_M J(y_J) held constant (the paper's CVODE
+ * BDF/Newton integration is the map being differentiated; the adjoint itself
+ * has no counterpart in the paper).  One warp per cell walks its tape in
+ * reverse through transposed sparse LU solves.  Inputs in `mem` space,
+ * asynchronous copies on `stream`, then synchronises stream.  Returns 0, a
+ * negative error, or the number of cells whose tape overflowed or whose
+ * forward solve failed (their dL_dy0 is 0 and they add nothing to
+ * dL_dtheta). */
+int chem_sensitivity(chem_cells *cells, const double *dL_dy, double *dL_dtheta, double *dL_dy0, int32_t mem,
+                     void *stream);
+/* The recorded tape of one cell, in host arrays of `capacity` events: kind
+ * 0 = INIT (val h0), 1 = RESCALE (q order, val eta), 2 = STEP (q order, val
+ * c = h/gamma_q), 3 = PROJECT (q the species the next STEP projects onto 0),
+ * 4 = REFACTOR (q its row, val c_M), 5 = ITER (q the iteration of the next
+ * STEP).  INIT, REFACTOR and ITER events own one row each, in event order:
+ * the state at the start of the solve, y_J, and the iterate f was evaluated
+ * at; rows (may be NULL) receives them, [n_rows][n_species].  *n_events and
+ * *n_rows receive the lengths; nothing else is copied if capacity < n_events
+ * (rows must hold n_rows rows).  Synchronous.  Errors: CHEM_EINVAL,
+ * CHEM_ESTATE (no recording), CHEM_ECUDA. */
+int chem_get_tape(const chem_cells *cells, int64_t cell, int32_t *kind, int32_t *q, double *val, double *rows,
+                  int32_t capacity, int32_t *n_events, int32_t *n_rows);
 
 /* Diagnostics for kernel-level parity.  For every cell, with the cell's T, P,
  * photolysis rates and theta from the batch (set_state must have been

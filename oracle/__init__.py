@@ -98,7 +98,7 @@ def lib():
             if hasattr(L, "orc_adjoint"):
                 L.orc_adjoint.argtypes = [P, P, P, P, P, P, P]
                 L.orc_adjoint.restype = ct.c_int
-                L.orc_replay.argtypes = [P, P, P, P, ct.c_double, ct.c_int, P, P]
+                L.orc_replay.argtypes = [P, P, P, P, P, P, P]
                 L.orc_replay.restype = ct.c_int
                 L.orc_tangent.argtypes = [P, P, P, P, P, P, P]
                 L.orc_tangent.restype = ct.c_int
@@ -278,17 +278,21 @@ def integrate_steps(mech, kt, y0, dt, n_steps, rtol, atol, max_order=5, max_step
     return y, stats, tape
 
 
-def replay(mech, kt, y0, tape: Tape, newton_tol=1e-15, maxit=30, keep_steps=False):
-    """The frozen-step map of a tape: y0 -> y_final (and y after every STEP event)."""
+def replay(mech, kt, y0, tape: Tape, keep_steps=False, kt_M=None):
+    """The frozen-control map of a tape: y0 -> y_final (and y after every STEP event).
+
+    The iteration matrices are formed with the rate constants kt_M (default kt):
+    pass the recorded run's constants to perturb kt with the matrices frozen."""
     m = _mk(mech)
     ts, keep = _tape_struct(tape)
     y0 = np.ascontiguousarray(y0, np.float64)
     out = np.empty(m.S)
     ys = np.zeros((tape.kind.size, m.S)) if keep_steps else None
-    rc = lib().orc_replay(m.ref, _p(np.ascontiguousarray(kt, np.float64)), _p(y0), ct.byref(ts), float(newton_tol),
-                          int(maxit), _p(out), _p(ys))
+    ktM = None if kt_M is None else np.ascontiguousarray(kt_M, np.float64)
+    kt = np.ascontiguousarray(kt, np.float64)
+    rc = lib().orc_replay(m.ref, _p(kt), _p(ktM), _p(y0), ct.byref(ts), _p(out), _p(ys))
     if rc:
-        raise RuntimeError("replay: a step equation did not converge")
+        raise RuntimeError("replay: singular or missing iteration matrix")
     return (out, ys) if keep_steps else out
 
 
@@ -296,22 +300,23 @@ def tangent(mech, kt, y0, tape: Tape, dy0, dtheta):
     m = _mk(mech)
     ts, keep = _tape_struct(tape)
     out = np.empty(m.S)
-    rc = lib().orc_tangent(m.ref, _p(np.ascontiguousarray(kt, np.float64)), _p(np.ascontiguousarray(y0, np.float64)),
-                           ct.byref(ts), _p(np.ascontiguousarray(dy0, np.float64)),
-                           _p(np.ascontiguousarray(dtheta, np.float64)), _p(out))
+    # contiguous copies held in locals: they must outlive the call
+    kt, y0, dy0, dtheta = (np.ascontiguousarray(a, np.float64) for a in (kt, y0, dy0, dtheta))
+    rc = lib().orc_tangent(m.ref, _p(kt), _p(y0), ct.byref(ts), _p(dy0), _p(dtheta), _p(out))
     if rc:
-        raise RuntimeError("tangent: a step equation did not converge")
+        raise RuntimeError("tangent: singular or missing iteration matrix")
     return out
 
 
 def adjoint(mech, kt, y0, tape: Tape, lam_final):
-    """(dL/dy0, dL/dtheta) of the frozen-step map for dL/dy_final = lam_final."""
+    """(dL/dy0, dL/dtheta) of the frozen-control map for dL/dy_final = lam_final."""
     m = _mk(mech)
     ts, keep = _tape_struct(tape)
     ly0 = np.empty(m.S)
     g = np.empty(m.R)
-    rc = lib().orc_adjoint(m.ref, _p(np.ascontiguousarray(kt, np.float64)), _p(np.ascontiguousarray(y0, np.float64)),
-                           ct.byref(ts), _p(np.ascontiguousarray(lam_final, np.float64)), _p(ly0), _p(g))
+    # contiguous copies held in locals: they must outlive the call
+    kt, y0, lam_final = (np.ascontiguousarray(a, np.float64) for a in (kt, y0, lam_final))
+    rc = lib().orc_adjoint(m.ref, _p(kt), _p(y0), ct.byref(ts), _p(lam_final), _p(ly0), _p(g))
     if rc:
-        raise RuntimeError("adjoint: a step equation did not converge")
+        raise RuntimeError("adjoint: singular or missing iteration matrix")
     return ly0, g

@@ -1,34 +1,45 @@
 /*
- * adjoint.c -- tangent and discrete adjoint of the frozen-step BDF map, for
- * the oracle.  TEST INFRASTRUCTURE ONLY (see oracle.h).
+ * adjoint.c -- the frozen-control map of a tape, its tangent and its discrete
+ * adjoint, for the oracle.  TEST INFRASTRUCTURE ONLY (see oracle.h).
  *
- * The map.  An integration leaves a tape of the operations that changed the
- * backward-difference history D (orc_tape): INIT (D_0 = y, D_1 = h0 f(y), the
- * rest 0), RESCALE (order q, factor eta: D_{1..q} <- T(eta) D_{1..q}) and
- * accepted STEP (order q, c = h / gamma_q).  The replay map y0 -> y_final
- * re-applies these operations with the step sizes and orders frozen, solving
- * each step equation
- *     d = c f(y_pred + d) - psi,   y_pred = sum_{m<=q} D_m,
- *     psi = (1/gamma_q) sum_{m=1..q} gamma_m D_m
- * exactly (Newton with a fresh Jacobian to rounding level) and without the
- * y >= 0 projection, then updating D_{q+2} = d - D_{q+1}, D_{q+1} = d,
- * D_m += D_{m+1} (m = q..0).  A tape may hold several consecutive solves:
- * every INIT restarts the history from the current D_0.
+ * The map.  An integration leaves a tape (orc_tape) of everything that
+ * determined its result.  The frozen-control map (y0, theta) -> y_final
+ * recomputes that result with every control decision of the integrator held
+ * fixed (step sizes, orders, the number of corrector iterations, the
+ * iteration matrices, the projections):
+ *   INIT      D_0 = y (the current state), D_1 = h0 f(y), higher rows 0;
+ *   RESCALE   D_{1..q} <- T(eta) D_{1..q}  (history rescale at order q);
+ *   REFACTOR  M = I - c_M J(y_J) with y_J the RECORDED state and the rate
+ *             constants of the recorded run: the iteration matrix is a
+ *             preconditioner, a constant of the map (it depends neither on y0
+ *             nor on theta);
+ *   ITER      counts the corrector iterations K of the next STEP;
+ *   PROJECT   marks a species that the next STEP projects onto y = 0;
+ *   STEP      (q, c): y_pred = sum_{m<=q} D_m, psi = (1/gamma_q) sum_{m=1..q}
+ *             gamma_m D_m, d_0 = 0 and K modified-Newton iterations
+ *                 d_{k+1} = d_k + s M^{-1} (c f(y_pred + d_k) - psi - d_k),
+ *             s = 1 if c == c_M else 2/(1 + c/c_M); projected species then
+ *             get d_i = -y_pred_i (y_i = 0); the history is updated with
+ *             D_{q+2} = d - D_{q+1}, D_{q+1} = d, D_m += D_{m+1} (m = q..0).
+ * With the recorded inputs this is the integrator's own arithmetic, so the map
+ * reproduces its result exactly; the adjoint below is the exact adjoint of the
+ * map.  A tape may hold several consecutive solves: every INIT restarts the
+ * history from the current D_0.
  *
  * Sensitivities are taken with respect to y0 and to theta, the per-reaction
  * log multipliers of the rate constants (k~_j -> k~_j e^{theta_j}), at the
  * theta already folded into kt; d r_j / d theta_j = r_j.
  *
- * The adjoint of one STEP (lambda' the adjoint of D after it): the step
- * writes D'_m = sum_{i=m..q} D_i + d (m <= q), D'_{q+1} = d,
- * D'_{q+2} = d - D_{q+1}; so
- *     lambda_d = lambda'_{q+2} + lambda'_{q+1} + sum_{m<=q} lambda'_m,
- *     lambda_i = sum_{m<=i} lambda'_m (i <= q), lambda_{q+1} = -lambda'_{q+2},
- *     lambda_{q+2} = 0, higher rows unchanged;
- * and through the implicit step equation (I - cJ) dd = c J dy_pred
- * + c F_theta dtheta - dpsi, with mu = (I - cJ)^{-T} lambda_d:
- *     lambda_i += c J^T mu (i <= q),  lambda_i -= (gamma_i/gamma_q) mu (1 <= i <= q),
- *     dL/dtheta_j += c r_j(y) (nu_j . mu).
+ * Adjoint of a STEP (lambda' the adjoint of D after it):
+ *   lambda_d = lambda'_{q+2} + lambda'_{q+1} + sum_{m<=q} lambda'_m;
+ *   lambda_i = sum_{m<=i} lambda'_m (i <= q), lambda_{q+1} = -lambda'_{q+2},
+ *   lambda_{q+2} = 0;
+ *   projected i: lambda_ypred,i = -lambda_d,i and lambda_d,i = 0;
+ *   for k = K-1..0, with g = s M^{-T} lambda_d and y_k = y_pred + d_k:
+ *     lambda_ypred += c J(y_k)^T g,  lambda_psi -= g,
+ *     lambda_d += c J(y_k)^T g - g,  dL/dtheta_j += c r_j(y_k) (nu_j . g);
+ *   lambda_i += lambda_ypred (i <= q),
+ *   lambda_i += (gamma_i/gamma_q) lambda_psi (1 <= i <= q).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -37,6 +48,8 @@
 #include "oracle.h"
 
 #define NROW (ORC_QMAX + 3)
+
+enum { EV_INIT = 0, EV_RESCALE = 1, EV_STEP = 2, EV_PROJECT = 3, EV_REFACTOR = 4, EV_ITER = 5 };
 
 static double gamma_m(int m) {
   double g = 0.0;
@@ -82,63 +95,48 @@ static void matvec(int S, const double *A, const double *x, double *y, int trans
   }
 }
 
-/* x = (I - c J)^{-1} b, or its transpose; J dense [S*S] */
-static int solve_shifted(int S, double c, const double *J, const double *b, double *x, int transpose) {
-  double *M = (double *)malloc(sizeof(double) * S * S);
-  int32_t *piv = (int32_t *)malloc(sizeof(int32_t) * S);
+/* the iteration matrix of a REFACTOR event, M = I - c_M J(y_J), as dense LUs
+ * of M and of M^T */
+typedef struct {
+  double *LU, *LUT;
+  int32_t *piv, *pivT;
+  double cM;
+} iter_matrix;
+
+static void im_alloc(iter_matrix *im, int S) {
+  im->LU = (double *)malloc(sizeof(double) * S * S);
+  im->LUT = (double *)malloc(sizeof(double) * S * S);
+  im->piv = (int32_t *)malloc(sizeof(int32_t) * S);
+  im->pivT = (int32_t *)malloc(sizeof(int32_t) * S);
+  im->cM = 0.0;
+}
+static void im_free(iter_matrix *im) { free(im->LU); free(im->LUT); free(im->piv); free(im->pivT); }
+
+/* forms M the way the integrator does; returns nonzero for an exactly singular M */
+static int im_form(iter_matrix *im, const orc_mech *m, const double *kt, const double *yJ, double cM) {
+  const int S = m->n_species;
+  orc_jacobian(m, kt, yJ, im->LU);
+  for (int i = 0; i < S * S; ++i) im->LU[i] = -cM * im->LU[i];
+  for (int i = 0; i < S; ++i) im->LU[i * S + i] += 1.0;
   for (int i = 0; i < S; ++i)
-    for (int k = 0; k < S; ++k) {
-      const double jv = transpose ? J[k * S + i] : J[i * S + k];
-      M[i * S + k] = (i == k ? 1.0 : 0.0) - c * jv;
-    }
-  int rc = orc_lu_factor(S, M, piv);
-  if (rc == 0) {
-    memcpy(x, b, sizeof(double) * S);
-    orc_lu_solve(S, M, piv, x);
-  }
-  free(M);
-  free(piv);
-  return rc;
+    for (int k = 0; k < S; ++k) im->LUT[i * S + k] = im->LU[k * S + i];
+  im->cM = cM;
+  const int a = orc_lu_factor(S, im->LU, im->piv);
+  const int b = orc_lu_factor(S, im->LUT, im->pivT);
+  return a != 0 || b != 0;
 }
 
-static double maxabs(int S, const double *v) {
-  double m = 0.0;
-  for (int i = 0; i < S; ++i)
-    if (fabs(v[i]) > m) m = fabs(v[i]);
-  return m;
-}
-
-/* exact solution of one step equation; d in/out (start value), y out */
-static int step_solve(const orc_mech *m, const double *kt, int S, double c, const double *ypred, const double *psi,
-                      double *d, double *y, double newton_tol, int maxit) {
-  double *f = (double *)malloc(sizeof(double) * S);
-  double *F = (double *)malloc(sizeof(double) * S);
-  double *dx = (double *)malloc(sizeof(double) * S);
-  double *J = (double *)malloc(sizeof(double) * S * S);
-  int rc = 1;
-  for (int it = 0; it < maxit; ++it) {
-    for (int i = 0; i < S; ++i) y[i] = ypred[i] + d[i];
-    orc_deriv(m, kt, y, f);
-    for (int i = 0; i < S; ++i) F[i] = c * f[i] - psi[i] - d[i];
-    orc_jacobian(m, kt, y, J);
-    if (solve_shifted(S, c, J, F, dx, 0)) break;
-    for (int i = 0; i < S; ++i) d[i] += dx[i];
-    if (maxabs(S, dx) <= newton_tol * (maxabs(S, y) + 1e-300)) { rc = 0; break; }
-  }
-  for (int i = 0; i < S; ++i) y[i] = ypred[i] + d[i];
-  free(f); free(F); free(dx); free(J);
-  return rc;
-}
-
+/* y_pred and psi of a step at order q, summed in the integrator's order */
 static void predict(int S, int q, const double *D, double *ypred, double *psi) {
   const double igq = 1.0 / gamma_m(q);
   for (int i = 0; i < S; ++i) {
-    double s = D[i], p = 0.0;
-    for (int k = 1; k <= q; ++k) {
-      s += D[(size_t)k * S + i];
-      p += gamma_m(k) * D[(size_t)k * S + i];
-    }
+    double s = D[i];
+    for (int k = 1; k <= q; ++k) s += D[(size_t)k * S + i];
     ypred[i] = s;
+  }
+  for (int i = 0; i < S; ++i) {
+    double p = 0.0;
+    for (int k = 1; k <= q; ++k) p += gamma_m(k) * D[(size_t)k * S + i];
     psi[i] = p * igq;
   }
 }
@@ -152,209 +150,243 @@ static void history_update(int S, int q, double *D, const double *d) {
     for (int i = 0; i < S; ++i) D[(size_t)k * S + i] += D[(size_t)(k + 1) * S + i];
 }
 
-/* the rescale matrix T(eta) (q x q, rows/cols 1..q) as orc_rescale applies it */
-static void rescale_T(int S, int q, double eta, double T[ORC_QMAX][ORC_QMAX]) {
-  /* apply orc_rescale to unit vectors: column mm of T = rescale(e_mm) */
-  double *D = (double *)calloc((size_t)(q + 1), sizeof(double));
-  (void)S;
+/* the rescale matrix T(eta) on rows 1..q, read off orc_rescale column by column */
+static void rescale_T(int q, double eta, double T[ORC_QMAX][ORC_QMAX]) {
+  double D[ORC_QMAX + 1];
   for (int mm = 0; mm < q; ++mm) {
-    memset(D, 0, sizeof(double) * (q + 1));
+    memset(D, 0, sizeof(D));
     D[mm + 1] = 1.0;
     orc_rescale(1, q, eta, D);
     for (int i = 0; i < q; ++i) T[i][mm] = D[i + 1];
   }
-  free(D);
 }
 
-int orc_replay(const orc_mech *m, const double *kt, const double *y0, const orc_tape *tp, double newton_tol,
-               int maxit, double *y_out, double *y_steps) {
-  const int S = m->n_species;
-  double *D = (double *)calloc((size_t)NROW * S, sizeof(double));
-  double *ypred = (double *)malloc(sizeof(double) * S), *psi = (double *)malloc(sizeof(double) * S);
-  double *d = (double *)malloc(sizeof(double) * S), *y = (double *)malloc(sizeof(double) * S);
-  double *f = (double *)malloc(sizeof(double) * S);
-  int rc = 0;
-  memcpy(D, y0, sizeof(double) * S);
-  for (int e = 0; e < tp->n; ++e) {
-    const int kind = tp->kind[e], q = tp->q[e];
-    const double val = tp->val[e];
-    if (kind == 0) {               /* INIT: restart the history from the current y */
-      for (int r = 1; r < NROW; ++r)
-        for (int i = 0; i < S; ++i) D[(size_t)r * S + i] = 0.0;
-      orc_deriv(m, kt, D, f);
-      for (int i = 0; i < S; ++i) D[S + i] = val * f[i];
-    } else if (kind == 1) {
-      orc_rescale(S, q, val, D);
-    } else {
-      predict(S, q, D, ypred, psi);
-      for (int i = 0; i < S; ++i) d[i] = 0.0;
-      if (step_solve(m, kt, S, val, ypred, psi, d, y, newton_tol, maxit)) rc = 1;
-      history_update(S, q, D, d);
-      if (y_steps) memcpy(y_steps + (size_t)e * S, D, sizeof(double) * S);
-    }
-  }
-  memcpy(y_out, D, sizeof(double) * S);
-  free(D); free(ypred); free(psi); free(d); free(y); free(f);
-  return rc;
-}
+static double step_scale(double c, double cM) { return (c == cM) ? 1.0 : 2.0 / (1.0 + c / cM); }
 
-int orc_tangent(const orc_mech *m, const double *kt, const double *y0, const orc_tape *tp, const double *dy0,
-                const double *dtheta, double *dy_out) {
+/*
+ * One walk of the map; iteration matrices are formed with the rate constants
+ * ktM, the map's arithmetic uses kt.  With dy0 non-NULL it also carries the tangent dD
+ * (dtheta then non-NULL too).  iters (optional) receives every corrector
+ * iterate y_k in tape order ([number of ITER events][S]); yinit the state at
+ * every INIT ([tape n][S]); y_steps y after every STEP ([tape n][S]).
+ */
+static int walk(const orc_mech *m, const double *kt, const double *ktM, const double *y0, const orc_tape *tp,
+                const double *dy0,
+                const double *dtheta, double *y_out, double *dy_out, double *iters, double *yinit,
+                double *y_steps) {
   const int S = m->n_species, R = m->n_reactions;
+  const int tan = dy0 != NULL;
   double *D = (double *)calloc((size_t)NROW * S, sizeof(double));
   double *dD = (double *)calloc((size_t)NROW * S, sizeof(double));
   double *ypred = (double *)malloc(sizeof(double) * S), *psi = (double *)malloc(sizeof(double) * S);
   double *dyp = (double *)malloc(sizeof(double) * S), *dpsi = (double *)malloc(sizeof(double) * S);
-  double *d = (double *)malloc(sizeof(double) * S), *y = (double *)malloc(sizeof(double) * S);
-  double *dd = (double *)malloc(sizeof(double) * S), *b = (double *)malloc(sizeof(double) * S);
-  double *f = (double *)malloc(sizeof(double) * S), *tmp = (double *)malloc(sizeof(double) * S);
-  double *J = (double *)malloc(sizeof(double) * S * S), *r = (double *)malloc(sizeof(double) * (R > 0 ? R : 1));
-  int rc = 0;
+  double *d = (double *)malloc(sizeof(double) * S), *dd = (double *)malloc(sizeof(double) * S);
+  double *y = (double *)malloc(sizeof(double) * S), *dyv = (double *)malloc(sizeof(double) * S);
+  double *f = (double *)malloc(sizeof(double) * S), *rr = (double *)malloc(sizeof(double) * S);
+  double *tmp = (double *)malloc(sizeof(double) * S), *b = (double *)malloc(sizeof(double) * S);
+  double *J = (double *)malloc(sizeof(double) * S * S);
+  double *r = (double *)malloc(sizeof(double) * (R > 0 ? R : 1));
+  int *mask = (int *)calloc((size_t)S, sizeof(int));
+  iter_matrix im;
+  im_alloc(&im, S);
+  int K = 0, rc = 0, have_M = 0;
+  long row = 0;
   memcpy(D, y0, sizeof(double) * S);
-  memcpy(dD, dy0, sizeof(double) * S);
+  if (tan) memcpy(dD, dy0, sizeof(double) * S);
   for (int e = 0; e < tp->n; ++e) {
     const int kind = tp->kind[e], q = tp->q[e];
     const double val = tp->val[e];
-    if (kind == 0) {
-      for (int row = 1; row < NROW; ++row)
-        for (int i = 0; i < S; ++i) D[(size_t)row * S + i] = dD[(size_t)row * S + i] = 0.0;
+    if (kind == EV_INIT) {
+      if (yinit) memcpy(yinit + (size_t)e * S, D, sizeof(double) * S);
+      for (size_t i = S; i < (size_t)NROW * S; ++i) D[i] = dD[i] = 0.0;
       orc_deriv(m, kt, D, f);
-      orc_jacobian(m, kt, D, J);
-      rates(m, kt, D, r);
-      matvec(S, J, dD, tmp, 0);
-      ftheta_times(m, r, dtheta, b);
+      if (tan) {
+        orc_jacobian(m, kt, D, J);
+        rates(m, kt, D, r);
+        matvec(S, J, dD, tmp, 0);
+        ftheta_times(m, r, dtheta, b);
+      }
       for (int i = 0; i < S; ++i) {
         D[S + i] = val * f[i];
-        dD[S + i] = val * (tmp[i] + b[i]);
+        if (tan) dD[S + i] = val * (tmp[i] + b[i]);
       }
-    } else if (kind == 1) {
+    } else if (kind == EV_RESCALE) {
       orc_rescale(S, q, val, D);
-      orc_rescale(S, q, val, dD);
-    } else {
-      const double c = val;
+      if (tan) orc_rescale(S, q, val, dD);
+    } else if (kind == EV_REFACTOR) {
+      if (im_form(&im, m, ktM, tp->y + (size_t)e * S, val)) rc = 1;
+      have_M = 1;
+    } else if (kind == EV_ITER) {
+      K++;
+    } else if (kind == EV_PROJECT) {
+      mask[q] = 1;
+    } else if (kind == EV_STEP) {
+      if (!have_M) { rc = 1; break; }
+      const double c = val, s = step_scale(c, im.cM);
       predict(S, q, D, ypred, psi);
-      predict(S, q, dD, dyp, dpsi);
-      for (int i = 0; i < S; ++i) d[i] = 0.0;
-      if (step_solve(m, kt, S, c, ypred, psi, d, y, 1e-15, 30)) rc = 1;
-      orc_jacobian(m, kt, y, J);
-      rates(m, kt, y, r);
-      /* (I - cJ) dd = c J dy_pred + c F_theta dtheta - dpsi */
-      matvec(S, J, dyp, tmp, 0);
-      ftheta_times(m, r, dtheta, b);
-      for (int i = 0; i < S; ++i) b[i] = c * tmp[i] + c * b[i] - dpsi[i];
-      if (solve_shifted(S, c, J, b, dd, 0)) rc = 1;
+      if (tan) predict(S, q, dD, dyp, dpsi);
+      for (int i = 0; i < S; ++i) d[i] = dd[i] = 0.0;
+      for (int k = 0; k < K; ++k) {
+        for (int i = 0; i < S; ++i) y[i] = ypred[i] + d[i];
+        if (iters) memcpy(iters + (size_t)(row + k) * S, y, sizeof(double) * S);
+        orc_deriv(m, kt, y, f);
+        for (int i = 0; i < S; ++i) rr[i] = c * f[i] - psi[i] - d[i];
+        orc_lu_solve(S, im.LU, im.piv, rr);
+        if (tan) {
+          for (int i = 0; i < S; ++i) dyv[i] = dyp[i] + dd[i];
+          orc_jacobian(m, kt, y, J);
+          rates(m, kt, y, r);
+          matvec(S, J, dyv, tmp, 0);
+          ftheta_times(m, r, dtheta, b);
+          for (int i = 0; i < S; ++i) b[i] = c * (tmp[i] + b[i]) - dpsi[i] - dd[i];
+          orc_lu_solve(S, im.LU, im.piv, b);
+        }
+        for (int i = 0; i < S; ++i) {
+          if (s != 1.0) rr[i] *= s;
+          d[i] += rr[i];
+          if (tan) dd[i] += s * b[i];
+        }
+      }
+      row += K;
+      for (int i = 0; i < S; ++i)
+        if (mask[i]) {
+          d[i] -= ypred[i] + d[i];
+          if (tan) dd[i] = -dyp[i];
+        }
       history_update(S, q, D, d);
-      history_update(S, q, dD, dd);
+      if (tan) history_update(S, q, dD, dd);
+      if (y_steps) memcpy(y_steps + (size_t)e * S, D, sizeof(double) * S);
+      memset(mask, 0, sizeof(int) * S);
+      K = 0;
     }
   }
-  memcpy(dy_out, dD, sizeof(double) * S);
-  free(D); free(dD); free(ypred); free(psi); free(dyp); free(dpsi); free(d); free(y); free(dd); free(b);
-  free(f); free(tmp); free(J); free(r);
+  if (y_out) memcpy(y_out, D, sizeof(double) * S);
+  if (dy_out) memcpy(dy_out, dD, sizeof(double) * S);
+  im_free(&im);
+  free(D); free(dD); free(ypred); free(psi); free(dyp); free(dpsi); free(d); free(dd); free(y); free(dyv);
+  free(f); free(rr); free(tmp); free(b); free(J); free(r); free(mask);
   return rc;
+}
+
+int orc_replay(const orc_mech *m, const double *kt, const double *kt_M, const double *y0, const orc_tape *tp,
+               double *y_out, double *y_steps) {
+  return walk(m, kt, kt_M ? kt_M : kt, y0, tp, NULL, NULL, y_out, NULL, NULL, NULL, y_steps);
+}
+
+int orc_tangent(const orc_mech *m, const double *kt, const double *y0, const orc_tape *tp, const double *dy0,
+                const double *dtheta, double *dy_out) {
+  return walk(m, kt, kt, y0, tp, dy0, dtheta, NULL, dy_out, NULL, NULL, NULL);
 }
 
 int orc_adjoint(const orc_mech *m, const double *kt, const double *y0, const orc_tape *tp, const double *lam_final,
                 double *lam_y0, double *g_theta) {
   const int S = m->n_species, R = m->n_reactions, n = tp->n;
-  double *ys = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * S);
-  double *yinit = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * S);   /* y at each INIT */
-  double *yend = (double *)malloc(sizeof(double) * S);
+  long n_rows = 0;
+  for (int e = 0; e < n; ++e) n_rows += tp->kind[e] == EV_ITER;
+  double *iters = (double *)malloc(sizeof(double) * (size_t)(n_rows > 0 ? n_rows : 1) * S);
+  double *yinit = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * S);
   double *L = (double *)calloc((size_t)NROW * S, sizeof(double));
-  double *nl = (double *)calloc((size_t)NROW * S, sizeof(double));
-  double *lamd = (double *)malloc(sizeof(double) * S), *mu = (double *)malloc(sizeof(double) * S);
+  double *lamd = (double *)malloc(sizeof(double) * S), *g = (double *)malloc(sizeof(double) * S);
+  double *lyp = (double *)malloc(sizeof(double) * S), *lpsi = (double *)malloc(sizeof(double) * S);
   double *tmp = (double *)malloc(sizeof(double) * S), *J = (double *)malloc(sizeof(double) * S * S);
-  double *r = (double *)malloc(sizeof(double) * (R > 0 ? R : 1)), *nm = (double *)malloc(sizeof(double) * (R > 0 ? R : 1));
-  int rc = 0;
-
-  /* forward replay, keeping y after every STEP and at every INIT */
-  {
-    double *D = (double *)calloc((size_t)NROW * S, sizeof(double));
-    double *ypred = (double *)malloc(sizeof(double) * S), *psi = (double *)malloc(sizeof(double) * S);
-    double *d = (double *)malloc(sizeof(double) * S), *y = (double *)malloc(sizeof(double) * S);
-    memcpy(D, y0, sizeof(double) * S);
-    for (int e = 0; e < n; ++e) {
-      const int kind = tp->kind[e], q = tp->q[e];
-      const double val = tp->val[e];
-      if (kind == 0) {
-        memcpy(yinit + (size_t)e * S, D, sizeof(double) * S);
-        for (int row = 1; row < NROW; ++row)
-          for (int i = 0; i < S; ++i) D[(size_t)row * S + i] = 0.0;
-        orc_deriv(m, kt, D, tmp);
-        for (int i = 0; i < S; ++i) D[S + i] = val * tmp[i];
-      } else if (kind == 1) {
-        orc_rescale(S, q, val, D);
-      } else {
-        predict(S, q, D, ypred, psi);
-        for (int i = 0; i < S; ++i) d[i] = 0.0;
-        if (step_solve(m, kt, S, val, ypred, psi, d, y, 1e-15, 30)) rc = 1;
-        history_update(S, q, D, d);
-        memcpy(ys + (size_t)e * S, D, sizeof(double) * S);
-      }
-    }
-    memcpy(yend, D, sizeof(double) * S);
-    free(D); free(ypred); free(psi); free(d); free(y);
-  }
-  (void)yend;
+  double *r = (double *)malloc(sizeof(double) * (R > 0 ? R : 1));
+  double *nm = (double *)malloc(sizeof(double) * (R > 0 ? R : 1));
+  int *mask = (int *)calloc((size_t)S, sizeof(int));
+  iter_matrix im;
+  im_alloc(&im, S);
+  int im_event = -1;
+  int rc = walk(m, kt, kt, y0, tp, NULL, NULL, NULL, NULL, iters, yinit, NULL);
 
   for (int j = 0; j < R; ++j) g_theta[j] = 0.0;
   memcpy(L, lam_final, sizeof(double) * S);
-  for (int e = n - 1; e >= 0; --e) {
+  long row = n_rows;               /* iterates of the STEPs not yet visited: rows [0, row) */
+  for (int e = n - 1; e >= 0 && rc == 0; --e) {
     const int kind = tp->kind[e], q = tp->q[e];
     const double val = tp->val[e];
-    if (kind == 2) {
-      const double c = val, igq = 1.0 / gamma_m(q);
-      const double *y = ys + (size_t)e * S;
-      for (int i = 0; i < S; ++i) {
-        double s = L[(size_t)(q + 2) * S + i] + L[(size_t)(q + 1) * S + i];
-        for (int k = 0; k <= q; ++k) s += L[(size_t)k * S + i];
-        lamd[i] = s;
+    if (kind == EV_STEP) {
+      /* the step's projections and iteration count precede it */
+      memset(mask, 0, sizeof(int) * S);
+      int K = 0, e2 = e - 1;
+      for (; e2 >= 0 && (tp->kind[e2] == EV_PROJECT || tp->kind[e2] == EV_ITER); --e2) {
+        if (tp->kind[e2] == EV_PROJECT) mask[tp->q[e2]] = 1;
+        else K++;
       }
-      memcpy(nl, L, sizeof(double) * NROW * S);
+      /* the iteration matrix in force: the last REFACTOR before the step */
+      int er = e2;
+      while (er >= 0 && tp->kind[er] != EV_REFACTOR) --er;
+      if (er < 0) { rc = 1; break; }
+      if (er != im_event) {
+        if (im_form(&im, m, kt, tp->y + (size_t)er * S, tp->val[er])) rc = 1;
+        im_event = er;
+      }
+      const double c = val, s = step_scale(c, im.cM), igq = 1.0 / gamma_m(q);
+      row -= K;
+      /* history update, then projection */
       for (int i = 0; i < S; ++i) {
-        nl[(size_t)(q + 1) * S + i] = -L[(size_t)(q + 2) * S + i];
-        nl[(size_t)(q + 2) * S + i] = 0.0;
         double acc = 0.0;
         for (int k = 0; k <= q; ++k) {
           acc += L[(size_t)k * S + i];
-          nl[(size_t)k * S + i] = acc;
+          L[(size_t)k * S + i] = acc;
+        }
+        lamd[i] = L[(size_t)(q + 2) * S + i] + L[(size_t)(q + 1) * S + i] + acc;
+        L[(size_t)(q + 1) * S + i] = -L[(size_t)(q + 2) * S + i];
+        L[(size_t)(q + 2) * S + i] = 0.0;
+        lyp[i] = 0.0;
+        lpsi[i] = 0.0;
+        if (mask[i]) {
+          lyp[i] = -lamd[i];
+          lamd[i] = 0.0;
         }
       }
-      orc_jacobian(m, kt, y, J);
-      if (solve_shifted(S, c, J, lamd, mu, 1)) rc = 1;
-      matvec(S, J, mu, tmp, 1);                 /* J^T mu */
-      for (int i = 0; i < S; ++i) {
-        for (int k = 0; k <= q; ++k) nl[(size_t)k * S + i] += c * tmp[i];
-        for (int k = 1; k <= q; ++k) nl[(size_t)k * S + i] -= gamma_m(k) * igq * mu[i];
+      /* the K corrector iterations, last first */
+      for (int k = K - 1; k >= 0; --k) {
+        const double *yk = iters + (size_t)(row + k) * S;
+        memcpy(g, lamd, sizeof(double) * S);
+        orc_lu_solve(S, im.LUT, im.pivT, g);
+        for (int i = 0; i < S; ++i) g[i] *= s;
+        orc_jacobian(m, kt, yk, J);
+        matvec(S, J, g, tmp, 1);
+        rates(m, kt, yk, r);
+        nu_dot(m, g, nm);
+        for (int j = 0; j < R; ++j) g_theta[j] += c * r[j] * nm[j];
+        for (int i = 0; i < S; ++i) {
+          lamd[i] += c * tmp[i] - g[i];
+          lyp[i] += c * tmp[i];
+          lpsi[i] -= g[i];
+        }
       }
-      rates(m, kt, y, r);
-      nu_dot(m, mu, nm);
-      for (int j = 0; j < R; ++j) g_theta[j] += c * r[j] * nm[j];
-      memcpy(L, nl, sizeof(double) * NROW * S);
-    } else if (kind == 1) {
+      for (int i = 0; i < S; ++i) {
+        for (int k = 0; k <= q; ++k) L[(size_t)k * S + i] += lyp[i];
+        for (int k = 1; k <= q; ++k) L[(size_t)k * S + i] += gamma_m(k) * igq * lpsi[i];
+      }
+    } else if (kind == EV_RESCALE) {
       double T[ORC_QMAX][ORC_QMAX];
-      rescale_T(S, q, val, T);
+      rescale_T(q, val, T);
       for (int i = 0; i < S; ++i) {
         double in[ORC_QMAX];
         for (int k = 0; k < q; ++k) in[k] = L[(size_t)(k + 1) * S + i];
         for (int mm = 0; mm < q; ++mm) {
-          double s = 0.0;
-          for (int k = 0; k < q; ++k) s += T[k][mm] * in[k];
-          L[(size_t)(mm + 1) * S + i] = s;
+          double s2 = 0.0;
+          for (int k = 0; k < q; ++k) s2 += T[k][mm] * in[k];
+          L[(size_t)(mm + 1) * S + i] = s2;
         }
       }
-    } else {
-      /* INIT: D_0 = y, D_1 = h0 f(y), higher rows reset */
+    } else if (kind == EV_INIT) {
+      /* D_0 = y, D_1 = h0 f(y), higher rows reset */
       const double *y = yinit + (size_t)e * S;
       orc_jacobian(m, kt, y, J);
-      matvec(S, J, L + S, tmp, 1);              /* J^T lambda_1 */
+      matvec(S, J, L + S, tmp, 1);
       rates(m, kt, y, r);
       nu_dot(m, L + S, nm);
       for (int j = 0; j < R; ++j) g_theta[j] += val * r[j] * nm[j];
       for (int i = 0; i < S; ++i) L[i] += val * tmp[i];
       for (size_t i = S; i < (size_t)NROW * S; ++i) L[i] = 0.0;
     }
+    /* ITER, PROJECT and REFACTOR are consumed by their STEP */
   }
   memcpy(lam_y0, L, sizeof(double) * S);
-  free(ys); free(yinit); free(yend); free(L); free(nl); free(lamd); free(mu); free(tmp); free(J); free(r); free(nm);
+  im_free(&im);
+  free(iters); free(yinit); free(L); free(lamd); free(g); free(lyp); free(lpsi); free(tmp); free(J); free(r);
+  free(nm); free(mask);
   return rc;
 }

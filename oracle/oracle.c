@@ -294,6 +294,10 @@ int orc_integrate(const orc_mech *m, const double *kt, double *y0, double dt, co
   tape_push(tape, S, 0 /*INIT*/, q, h, y0);
 
   const long n_fixed = fixed ? lround(dt / h) : 0;
+  int *projected = (int *)malloc(sizeof(int) * S);   /* species projected onto y = 0 in this attempt */
+  int n_projected = 0;
+  double *iters = (double *)malloc(sizeof(double) * (size_t)(NEWTON_MAXITER + 64) * S);  /* iterates of the attempt */
+  int n_iters = 0;
   int n_eq = 0, have_M = 0, force_M = 0, n_since_M = 0, nef = 0, ncf = 0, last = 0;
   double cM = 0.0, rho = 1.0;
   int status = ORC_OK;
@@ -346,6 +350,7 @@ int orc_integrate(const orc_mech *m, const double *kt, double *y0, double dt, co
       rho = 1.0;
       fresh = 1;
       st->jac_evals++;
+      tape_push(tape, S, 4 /*REFACTOR*/, 0, c, ypred);
     }
     force_M = 0;
     const double scale = (c == cM) ? 1.0 : 2.0 / (1.0 + c / cM);
@@ -356,7 +361,10 @@ int orc_integrate(const orc_mech *m, const double *kt, double *y0, double dt, co
     for (int i = 0; i < S; ++i) { d[i] = 0.0; y[i] = ypred[i]; }
     double del = 0.0, del_prev = 0.0;
     int conv = 0;
+    n_iters = 0;
     for (int it = 0; it < maxit; ++it) {
+      if (it < NEWTON_MAXITER + 64) memcpy(iters + (size_t)it * S, y, sizeof(double) * S);
+      n_iters = it + 1;
       orc_deriv(m, kt, y, f);
       st->f_evals++;
       for (int i = 0; i < S; ++i) dy[i] = c * f[i] - psi[i] - d[i];
@@ -402,10 +410,11 @@ int orc_integrate(const orc_mech *m, const double *kt, double *y0, double dt, co
           const double r = (D[i] > 0.0) ? D[i] / (D[i] - y[i]) : 0.0;
           if (r < eta_c) eta_c = r;
         }
+      n_projected = 0;
       if (nv > 0) {
         if (sqrt(vs / (double)S) <= tol) {
           for (int i = 0; i < S; ++i)
-            if (y[i] < 0.0) { d[i] -= y[i]; y[i] = 0.0; }
+            if (y[i] < 0.0) { d[i] -= y[i]; y[i] = 0.0; projected[n_projected++] = i; }
         } else {
           st->rejects++;
           nef++;
@@ -449,6 +458,9 @@ int orc_integrate(const orc_mech *m, const double *kt, double *y0, double dt, co
     }
     for (int k = q; k >= 0; --k)
       for (int i = 0; i < S; ++i) D[(size_t)k * S + i] += D[(size_t)(k + 1) * S + i];
+    for (int k = 0; k < n_iters && k < NEWTON_MAXITER + 64; ++k) tape_push(tape, S, 5 /*ITER*/, k, 0.0, iters + (size_t)k * S);
+    for (int k = 0; k < n_projected; ++k) tape_push(tape, S, 3 /*PROJECT*/, projected[k], 0.0, NULL);
+    n_projected = 0;
     tape_push(tape, S, 2 /*STEP*/, q, c, D);
     if (fixed && o->y_hist) memcpy(o->y_hist + (size_t)(st->steps - 1) * S, D, sizeof(double) * S);
     if (last) break;
@@ -490,6 +502,8 @@ int orc_integrate(const orc_mech *m, const double *kt, double *y0, double dt, co
   st->final_h = h;
 
   free(D); free(ypred); free(y); free(d); free(psi); free(w); free(f); free(dy); free(M); free(piv);
+  free(projected);
+  free(iters);
   return status;
 }
 

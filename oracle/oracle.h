@@ -78,9 +78,12 @@ typedef struct {
   double final_h;
 } orc_stats;
 
-/* Tape of one cell's integration: the sequence of operations that changed the
- * history array, in order.  kind 0 = INIT (val = h0, y = y0), 1 = RESCALE
- * (q, val = eta), 2 = accepted STEP (q, val = c = h/gamma_q, y = accepted y).
+/* Tape of one cell's integration: the operations that determined its result,
+ * in order.  kind 0 = INIT (val = h0, y = y0); 1 = RESCALE of the history
+ * (q, val = eta); 2 = accepted STEP (q, val = c = h/gamma_q, y = accepted y);
+ * 3 = PROJECT (q = a species the following STEP projected onto y = 0);
+ * 4 = REFACTOR (val = c_M, y = the state J was evaluated at: M = I - c_M J(y));
+ * 5 = ITER (y = a Newton iterate of the following STEP, in order).
  * Arrays are sized by the caller (cap events; y is [cap][S]). */
 typedef struct {
   int32_t cap, n, overflow, pad;
@@ -113,12 +116,17 @@ int orc_solve_cells(const orc_mech *m, int64_t n_cells, const double *T, const d
                     const double *jphot, const double *theta, double *y, double dt,
                     const orc_opts *o, orc_stats *st);
 
-/* adjoint.c: the frozen-step replay map of a tape, its tangent and adjoint.
- * kt includes theta.  y_steps (optional) receives y after every STEP event
- * ([tape n][S], other rows untouched).  Return 0, or 1 if a step equation did
- * not converge / a matrix was exactly singular. */
-int orc_replay(const orc_mech *m, const double *kt, const double *y0, const orc_tape *tape, double newton_tol,
-               int maxit, double *y_out, double *y_steps);
+/* adjoint.c: the frozen-control map of a tape (every control decision of the
+ * integrator held fixed: step sizes, orders, corrector iteration counts,
+ * iteration matrices formed from the recorded states, projections), its
+ * tangent and its discrete adjoint.  kt includes theta.  orc_replay forms the
+ * iteration matrices with kt_M (NULL: kt), so that a perturbed kt can be
+ * replayed against the matrices of the recorded run.  y_steps (optional)
+ * receives y after every STEP event ([tape n][S], other rows untouched).
+ * Return 0, or 1 if an iteration matrix was exactly singular or a STEP had no
+ * iteration matrix before it. */
+int orc_replay(const orc_mech *m, const double *kt, const double *kt_M, const double *y0, const orc_tape *tape,
+               double *y_out, double *y_steps);
 int orc_tangent(const orc_mech *m, const double *kt, const double *y0, const orc_tape *tape, const double *dy0,
                 const double *dtheta, double *dy_out);
 int orc_adjoint(const orc_mech *m, const double *kt, const double *y0, const orc_tape *tape,

@@ -28,7 +28,8 @@ EXPORTS = ["chem_opts_default", "chem_mechanism_create", "chem_mechanism_destroy
            "chem_mechanism_info", "chem_mechanism_structure", "chem_cells_create",
            "chem_cells_destroy", "chem_cells_set_state", "chem_cells_set_photolysis",
            "chem_cells_set_theta", "chem_solve_step", "chem_get_state", "chem_get_stats",
-           "chem_eval_deriv", "chem_eval_newton_solve", "chem_solve_step_noalloc", "chem_last_error"]
+           "chem_eval_deriv", "chem_eval_newton_solve", "chem_solve_step_noalloc", "chem_sensitivity",
+           "chem_get_tape", "chem_last_error"]
 
 
 class Reaction(ct.Structure):
@@ -93,6 +94,8 @@ def load(path: str | None = None):
         L.chem_eval_deriv.argtypes = [V, V, V, ct.c_int32, V]
         L.chem_eval_newton_solve.argtypes = [V, ct.c_double, V, V, V, ct.c_int32, V]
         L.chem_solve_step_noalloc.argtypes = [V, ct.c_int64, V, V, V, V, V, V, ct.c_double, V, V]
+        L.chem_sensitivity.argtypes = [V, V, V, V, ct.c_int32, V]
+        L.chem_get_tape.argtypes = [V, ct.c_int64, V, V, V, V, ct.c_int32, V, V]
         L.chem_last_error.restype = ct.c_char_p
         for name in EXPORTS:
             if name not in ("chem_opts_default", "chem_mechanism_destroy", "chem_cells_destroy",
@@ -275,6 +278,35 @@ class Cells:
                "chem_eval_newton_solve")
         return x
 
+    def sensitivity(self, dL_dy, dL_dtheta=None, dL_dy0=None, stream=None):
+        """(dL/dtheta [R], dL/dy0 [S, C], n_bad) for L = sum dL_dy * y."""
+        R = self.mech.n_reactions
+        dy = dL_dy
+        if dL_dtheta is None:
+            dL_dtheta = np.zeros(R)
+        if dL_dy0 is None:
+            dL_dy0 = np.zeros((self.mech.n_species, self.n_cells))
+        (pa, ma, k1), (pt, mt, k2), (p0, m0, k3) = _ptr(dy), _ptr(dL_dtheta), _ptr(dL_dy0)
+        if not (ma == mt == m0):
+            raise ChemError("dL_dy, dL_dtheta and dL_dy0 must all be on the host or all on the device")
+        n_bad = _check(load().chem_sensitivity(self._h, pa, pt, p0, ma, _stream_ptr(stream)), "chem_sensitivity")
+        return dL_dtheta, dL_dy0, n_bad
+
+    def get_tape(self, cell: int):
+        """(kind, q, val, rows) of one cell's recorded tape; rows [n_rows, S] belong,
+        in order, to the INIT, REFACTOR and ITER events."""
+        n, nr = ct.c_int32(0), ct.c_int32(0)
+        _check(load().chem_get_tape(self._h, int(cell), None, None, None, None, 0, ct.byref(n), ct.byref(nr)),
+               "chem_get_tape")
+        kind = np.zeros(n.value, np.int32)
+        q = np.zeros(n.value, np.int32)
+        val = np.zeros(n.value)
+        rows = np.zeros((nr.value, self.mech.n_species))
+        _check(load().chem_get_tape(self._h, int(cell), ct.c_void_p(kind.ctypes.data), ct.c_void_p(q.ctypes.data),
+                                    ct.c_void_p(val.ctypes.data), ct.c_void_p(rows.ctypes.data), n.value,
+                                    ct.byref(n), ct.byref(nr)), "chem_get_tape")
+        return kind, q, val, rows
+
     def close(self):
         if getattr(self, "_h", None):
             load().chem_cells_destroy(self._h)
@@ -301,3 +333,47 @@ def solve(mech: Mechanism, cells: synth.Cells, dt: float, rtol: float, atol: flo
         return y, c.get_stats()
     finally:
         c.close()
+
+
+def _autograd_function():
+    import torch
+
+    class ChemSolveFn(torch.autograd.Function):
+        """y_final = solve(theta, y0) over n_steps solve_step calls; backward runs the
+        discrete adjoint (chem_sensitivity).  theta [R] and y0 [S, C] are float64
+        tensors on the batch's device; T, P [C] likewise."""
+
+        @staticmethod
+        def forward(ctx, theta, y0, cells, T, P, dt, n_steps):
+            cells.set_theta(theta.detach().contiguous())
+            cells.set_state(T, P, y0.detach().contiguous())
+            for _ in range(int(n_steps)):
+                cells.solve_step(dt)
+            y = torch.empty_like(y0)
+            cells.get_state(out=y)
+            ctx.cells = cells
+            ctx.R = theta.numel()
+            return y
+
+        @staticmethod
+        def backward(ctx, gy):
+            import torch as _t
+            gth = _t.zeros(ctx.R, dtype=_t.float64, device=gy.device)
+            gy0 = _t.zeros_like(gy)
+            _, _, n_bad = ctx.cells.sensitivity(gy.contiguous(), gth, gy0)
+            if n_bad:
+                raise ChemError(f"{n_bad} cells have no sensitivity (tape overflow or failed solve)")
+            return gth, gy0, None, None, None, None, None
+
+    return ChemSolveFn
+
+
+_FN = None
+
+
+def solve_with_grad(cells: Cells, theta, y0, T, P, dt: float, n_steps: int = 1):
+    """Differentiable multi-cell solve (cells must be created with record_adjoint=True)."""
+    global _FN
+    if _FN is None:
+        _FN = _autograd_function()
+    return _FN.apply(theta, y0, cells, T, P, dt, n_steps)

@@ -4,6 +4,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -18,6 +19,11 @@ struct chem_cells {
   int *queue = nullptr;   // [0..1] work counter, [2] staging fallbacks
   bool have_state = false, use_J = false, use_theta = false;
   int device = 0;
+  // adjoint (record_adjoint)
+  int *tape_kq = nullptr, *tape_n = nullptr, *tape_bad = nullptr, *tape_rows = nullptr;
+  double *tape_val = nullptr;
+  int tape_cap = 0, row_cap = 0;
+  double *ytape = nullptr, *gcell = nullptr, *dLdy = nullptr, *dLdy0 = nullptr, *dLdtheta = nullptr;
 };
 
 namespace {
@@ -140,6 +146,10 @@ int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *o
   if (o.cells_per_block > wmax) return fail(CHEM_EINVAL, "cells_per_block exceeds the shared-memory limit");
   if (o.cells_per_block == 0) o.cells_per_block = best_warps_per_block(mech->m.dev, o.lu_precision, o.driver);
   if (o.cells_per_block < 1) return fail(CHEM_EINVAL, "no launch shape fits on this device");
+  if (o.record_adjoint && o.lu_precision != 64)
+    return fail(CHEM_EINVAL, "record_adjoint needs lu_precision 64 (the adjoint differentiates the FP64 iteration)");
+  if (o.record_adjoint && (o.tape_steps < 0 || o.tape_steps > CHEM_MAX_TAPE_ROWS))
+    return fail(CHEM_EINVAL, "tape_steps out of range");
 
   chem_cells *c = new (std::nothrow) chem_cells();
   if (!c) return fail(CHEM_ENOMEM, "host allocation failed");
@@ -160,6 +170,30 @@ int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *o
     chem_cells_destroy(c);
     return fail(CHEM_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
   }
+  if (o.record_adjoint) {
+    c->row_cap = o.tape_steps > 0 ? o.tape_steps : 2000;
+    c->tape_cap = 3 * c->row_cap + 64;
+    const size_t E = (size_t)c->tape_cap, RC = (size_t)c->row_cap;
+    if ((e = cudaMalloc(&c->tape_kq, n * E * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&c->tape_val, n * E * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&c->tape_n, n * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&c->tape_rows, n * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&c->tape_bad, n * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&c->ytape, n * RC * S * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&c->gcell, n * (R > 0 ? R : 1) * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&c->dLdy, n * S * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&c->dLdy0, n * S * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&c->dLdtheta, (R > 0 ? R : 1) * sizeof(double))) != cudaSuccess) {
+      chem_cells_destroy(c);
+      return fail(CHEM_ENOMEM, std::string("cudaMalloc of the adjoint tape failed: ") + cudaGetErrorString(e));
+    }
+    if ((e = cudaMemset(c->tape_n, 0, n * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(c->tape_rows, 0, n * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(c->tape_bad, 0, n * sizeof(int))) != cudaSuccess) {
+      chem_cells_destroy(c);
+      return cuda_fail(e, "cudaMemset");
+    }
+  }
   if ((e = cudaMemset(c->stats, 0, n * sizeof(chem_cell_stats))) != cudaSuccess ||
       (e = cudaMemset(c->queue, 0, 4 * sizeof(long long))) != cudaSuccess) {
     chem_cells_destroy(c);
@@ -178,6 +212,16 @@ void chem_cells_destroy(chem_cells *c) {
   cudaFree(c->theta);
   cudaFree(c->stats);
   cudaFree(c->queue);
+  cudaFree(c->tape_kq);
+  cudaFree(c->tape_val);
+  cudaFree(c->tape_n);
+  cudaFree(c->tape_rows);
+  cudaFree(c->tape_bad);
+  cudaFree(c->ytape);
+  cudaFree(c->gcell);
+  cudaFree(c->dLdy);
+  cudaFree(c->dLdy0);
+  cudaFree(c->dLdtheta);
   delete c;
 }
 
@@ -192,6 +236,12 @@ int chem_cells_set_state(chem_cells *c, const double *T, const double *P, const 
   if ((e = cudaMemcpyAsync(c->T, T, n * sizeof(double), kind_in(mem), s)) != cudaSuccess) return cuda_fail(e, "set_state T");
   if ((e = cudaMemcpyAsync(c->P, P, n * sizeof(double), kind_in(mem), s)) != cudaSuccess) return cuda_fail(e, "set_state P");
   if ((e = cudaMemcpyAsync(c->y, y, n * S * sizeof(double), kind_in(mem), s)) != cudaSuccess) return cuda_fail(e, "set_state y");
+  if (c->tape_n) {   // a new state starts a new tape
+    if ((e = cudaMemsetAsync(c->tape_n, 0, n * sizeof(int), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->tape_rows, 0, n * sizeof(int), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->tape_bad, 0, n * sizeof(int), s)) != cudaSuccess)
+      return cuda_fail(e, "set_state tape reset");
+  }
   c->have_state = true;
   return 0;
 }
@@ -229,7 +279,7 @@ int chem_solve_step(chem_cells *c, double dt, void *stream) {
   if (!c->have_state) return fail(CHEM_ESTATE, "solve_step before set_state");
   if (c->n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
-  CellsDev cd;
+  CellsDev cd{};
   cd.n_cells = c->n;
   cd.T = c->T;
   cd.P = c->P;
@@ -239,6 +289,14 @@ int chem_solve_step(chem_cells *c, double dt, void *stream) {
   cd.stats = c->stats;
   cd.queue = nullptr;
   cd.error = c->queue + 4;
+  cd.tape_kq = c->tape_kq;
+  cd.ytape = c->ytape;
+  cd.tape_val = c->tape_val;
+  cd.tape_n = c->tape_n;
+  cd.tape_rows = c->tape_rows;
+  cd.tape_bad = c->tape_bad;
+  cd.tape_cap = c->tape_cap;
+  cd.row_cap = c->row_cap;
   if (c->opts.driver == CHEM_DRIVER_PERSISTENT) {
     cudaError_t e = cudaMemsetAsync(c->queue, 0, sizeof(long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
@@ -286,7 +344,7 @@ int chem_get_stats(const chem_cells *c, chem_cell_stats *out, int32_t mem, void 
 namespace {
 
 CellsDev cells_dev(chem_cells *c) {
-  CellsDev cd;
+  CellsDev cd{};
   cd.n_cells = c->n;
   cd.T = c->T;
   cd.P = c->P;
@@ -296,6 +354,13 @@ CellsDev cells_dev(chem_cells *c) {
   cd.stats = c->stats;
   cd.queue = nullptr;
   cd.error = c->queue + 4;
+  cd.tape_kq = nullptr;
+  cd.ytape = nullptr;
+  cd.tape_val = nullptr;
+  cd.tape_n = nullptr;
+  cd.tape_rows = nullptr;
+  cd.tape_bad = nullptr;
+  cd.tape_cap = cd.row_cap = 0;
   return cd;
 }
 
@@ -341,6 +406,88 @@ int chem_eval_deriv(chem_cells *c, const double *y, double *f, int32_t mem, void
 int chem_eval_newton_solve(chem_cells *c, double cc, const double *y, const double *b, double *x, int32_t mem,
                            void *stream) {
   return probe(c, 1, cc, y, b, x, mem, stream);
+}
+
+int chem_sensitivity(chem_cells *c, const double *dL_dy, double *dL_dtheta, double *dL_dy0, int32_t mem, void *stream) {
+  g_err.clear();
+  if (!c || !dL_dy || !dL_dtheta || !dL_dy0) return fail(CHEM_EINVAL, "NULL argument");
+  if (int rc = check_mem(mem)) return rc;
+  if (!c->tape_n) return fail(CHEM_ESTATE, "the batch was created without record_adjoint");
+  if (!c->have_state) return fail(CHEM_ESTATE, "sensitivity before set_state");
+  const size_t n = (size_t)c->n, S = (size_t)c->mech->m.S, R = (size_t)c->mech->m.R;
+  if (n == 0) {
+    if (mem == CHEM_MEM_HOST) std::memset(dL_dtheta, 0, R * sizeof(double));
+    else cudaMemsetAsync(dL_dtheta, 0, R * sizeof(double), (cudaStream_t)stream);
+    return 0;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(c->dLdy, dL_dy, n * S * sizeof(double), kind_in(mem), s)) != cudaSuccess)
+    return cuda_fail(e, "sensitivity copy-in");
+  CellsDev cd{};
+  cd.n_cells = c->n;
+  cd.T = c->T;
+  cd.P = c->P;
+  cd.J = c->use_J ? c->J : nullptr;
+  cd.theta = c->use_theta ? c->theta : nullptr;
+  cd.y = c->y;
+  cd.stats = c->stats;
+  cd.queue = nullptr;
+  cd.error = nullptr;
+  cd.tape_kq = c->tape_kq;
+  cd.ytape = c->ytape;
+  cd.tape_val = c->tape_val;
+  cd.tape_n = c->tape_n;
+  cd.tape_rows = c->tape_rows;
+  cd.tape_bad = c->tape_bad;
+  cd.tape_cap = c->tape_cap;
+  cd.row_cap = c->row_cap;
+  AdjDev ad;
+  ad.dLdy = c->dLdy;
+  ad.dLdy0 = c->dLdy0;
+  ad.gcell = c->gcell;
+  ad.dLdtheta = c->dLdtheta;
+  if ((e = launch_adjoint(c->mech->m.dev, cd, ad, s)) != cudaSuccess) return cuda_fail(e, "adjoint kernels");
+  if ((e = cudaMemcpyAsync(dL_dy0, c->dLdy0, n * S * sizeof(double), kind_out(mem), s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(dL_dtheta, c->dLdtheta, R * sizeof(double), kind_out(mem), s)) != cudaSuccess)
+    return cuda_fail(e, "sensitivity copy-out");
+  std::vector<int> bad(n);
+  if ((e = cudaMemcpyAsync(bad.data(), c->tape_bad, n * sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_fail(e, "sensitivity sync");
+  int n_bad = 0;
+  for (int v : bad) n_bad += v != 0;
+  return n_bad;
+}
+
+int chem_get_tape(const chem_cells *c, int64_t cell, int32_t *kind, int32_t *q, double *val, double *rows,
+                  int32_t capacity, int32_t *n_events, int32_t *n_rows) {
+  g_err.clear();
+  if (!c || !n_events || !n_rows) return fail(CHEM_EINVAL, "NULL argument");
+  if (!c->tape_n) return fail(CHEM_ESTATE, "the batch was created without record_adjoint");
+  if (cell < 0 || cell >= c->n) return fail(CHEM_EINVAL, "cell index out of range");
+  int n = 0, nr = 0;
+  cudaError_t e;
+  if ((e = cudaMemcpy(&n, c->tape_n + cell, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(&nr, c->tape_rows + cell, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "get_tape");
+  *n_events = n;
+  *n_rows = nr;
+  if (capacity < n || !kind || !q || !val) return 0;
+  std::vector<int> kq(n);
+  if ((e = cudaMemcpy(kq.data(), c->tape_kq + cell * (int64_t)c->tape_cap, n * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(val, c->tape_val + cell * (int64_t)c->tape_cap, n * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "get_tape");
+  const size_t S = (size_t)c->mech->m.S;
+  if (rows && nr > 0 &&
+      (e = cudaMemcpy(rows, c->ytape + cell * (int64_t)c->row_cap * S, (size_t)nr * S * sizeof(double),
+                      cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "get_tape rows");
+  for (int i = 0; i < n; ++i) {
+    kind[i] = kq[i] & 0xff;
+    q[i] = kq[i] >> 8;
+  }
+  return 0;
 }
 
 }  // extern "C"

@@ -19,6 +19,7 @@ constexpr int GRID_IMAX = 26;
 constexpr int GRID_N = GRID_IMAX - GRID_IMIN + 1;
 constexpr int WARP = 32;
 constexpr int MAX_WARPS_PER_BLOCK = 12;  // cells per block (history and vectors live in registers)
+constexpr int ADJ_WARPS_PER_BLOCK = 4;   // cells per block of the adjoint kernel
 
 // A warp program is a sequence of passes of exactly 32 op slots; lane l runs
 // slot l of every pass and the warp synchronises between passes.  The
@@ -79,6 +80,15 @@ struct MechDev {
   // history rescale T(eta)_{im} = sum_p coef[(i-1)*QMAX + m-1][p] eta^p,
   // i, m = 1..QMAX, p = 0..QMAX
   const double *rescale_coef;
+  // ---- discrete adjoint (FP64): Wd extended by mu[S], nm[R] = nu_j . mu,
+  // pp[n_pairs] = dr_j/dy_l, jtm[S] = J^T mu, g[R] (theta gradient), temps, constants
+  int Wda_len, a_MU, a_NM, a_PP, a_JTM, a_G;
+  int a_nconst;
+  const int *a_const_off;          // byte offsets into the extended Wd
+  const double *a_const_val;
+  const ushort4 *nudot_ops, *jt_ops;    // programs on the extended Wd
+  const ushort4 *fwdT_ops, *bwdT_ops;   // U^T and L^T solves on WL (FP64 byte offsets)
+  int nudot_npass, jt_npass, fwdT_npass, bwdT_npass;
 };
 
 struct HostProgram {
@@ -93,6 +103,9 @@ struct Mechanism {
   std::vector<int> pos;              // pivot position of each species
   std::vector<uint8_t> fill;         // S*S in pivot order
   HostProgram f_prog, m_prog, lu_prog, fwd_prog, bwd_prog;
+  HostProgram nudot_prog, jt_prog, fwdT_prog, bwdT_prog;   // adjoint
+  std::vector<double> a_consts_v;
+  std::vector<int> a_consts_i;
   double flops_f = 0, flops_jac = 0, flops_lu = 0, flops_solve = 0;
   // host copies of the small tables that upload_mechanism() sends to the device
   std::vector<double> d_consts_v, L_consts_v;
@@ -121,6 +134,33 @@ struct CellsDev {
   chem_cell_stats *stats;       // [C]
   int *queue;                   // persistent driver work counter (may be null)
   int *error;                   // counts blocks whose table staging fell back to plain loads (may be null)
+  // adjoint tape (tape_n null: not recording).  Per cell e < tape_cap events,
+  // kq = kind | q << 8, val:
+  //   0 INIT      val h0,   row y at the start of the solve
+  //   1 RESCALE   q order,  val eta
+  //   2 STEP      q order,  val c = h/gamma_q (accepted step)
+  //   3 PROJECT   q species projected onto y = 0 by the next STEP
+  //   4 REFACTOR  q its row index, val c_M; row y_J (M = I - c_M J(y_J))
+  //   5 ITER      q iteration k of the next STEP; row y_k, the iterate it
+  //               evaluated f at
+  // Rows are numbered in event order over the INIT, REFACTOR and ITER events.
+  int *tape_kq;
+  double *tape_val;
+  double *ytape;                // [C][row_cap][S] rows
+  int *tape_n;                  // [C] events so far (kept across solve_step calls)
+  int *tape_bad;                // [C] nonzero: overflow or a failed solve, no sensitivity
+  int *tape_rows;               // [C] rows so far
+  int tape_cap, row_cap;
+};
+
+enum TapeKind { EV_INIT = 0, EV_RESCALE = 1, EV_STEP = 2, EV_PROJECT = 3, EV_REFACTOR = 4, EV_ITER = 5 };
+
+// Buffers of chem_sensitivity (device, owned by the batch).
+struct AdjDev {
+  const double *dLdy;           // [S][C]
+  double *dLdy0;                // [S][C]
+  double *gcell;                // [R][C] per-cell theta gradients
+  double *dLdtheta;             // [R]
 };
 
 struct LaunchCfg {
@@ -144,6 +184,9 @@ int best_warps_per_block(const MechDev &m, int lu_precision, int driver);
 // diagnostic: mode 0 out = f(y); mode 1 out = (I - c J(y))^{-1} b   (all [S][C] device arrays)
 cudaError_t launch_probe(const MechDev &M, const CellsDev &C, int lu_precision, int mode, double c, const double *y,
                          const double *b, double *out, cudaStream_t stream);
+
+// discrete adjoint: replay (exact steps, y rows), backward sweep, theta reduction
+cudaError_t launch_adjoint(const MechDev &m, const CellsDev &c, const AdjDev &a, cudaStream_t stream);
 
 // sets the thread-local message returned by chem_last_error()
 void set_last_error(const std::string &msg);

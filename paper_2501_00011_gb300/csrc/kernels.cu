@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace chemgpu {
@@ -393,7 +395,94 @@ __device__ __forceinline__ bool load_cell(const MechDev &M, const CellsDev &C, d
   return bad;
 }
 
-template <typename T, int KS, bool STAGED>
+// Event tape of one cell for the discrete adjoint (event kinds and rows as
+// CellsDev documents them).  Every lane keeps the counters; lane 0 writes the
+// events, each lane its own species of a row.  With ON false every method is
+// empty and the solve kernel carries no recording state.
+template <int KS, bool ON>
+struct Recorder {
+  const CellsDev &C;
+  int64_t cell;
+  double *yrows;        // this cell's rows
+  int n, rows, S;
+  bool on, over;   // on == ON
+  __device__ __forceinline__ Recorder(const CellsDev &c, int64_t cl, int s)
+      : C(c), cell(cl), yrows(nullptr), n(0), rows(0), S(s), on(ON), over(false) {
+    if (ON) {
+      n = C.tape_n[cell];
+      rows = C.tape_rows[cell];
+      yrows = C.ytape + cell * (int64_t)C.row_cap * s;
+    }
+  }
+  __device__ __forceinline__ void event(int kind, int q, double val, int lane) {
+    if (lane == 0) {
+      const int64_t i = cell * (int64_t)C.tape_cap + n;
+      C.tape_kq[i] = kind | (q << 8);
+      C.tape_val[i] = val;
+    }
+    n++;
+  }
+  __device__ __forceinline__ void write_row(int r, const double (&y)[KS], int lane) {
+#pragma unroll
+    for (int k = 0; k < KS; ++k)
+      if (lane + WARP * k < S) yrows[(int64_t)r * S + lane + WARP * k] = y[k];
+  }
+  // an event without a row (RESCALE, STEP, PROJECT)
+  __device__ __forceinline__ void push(int kind, int q, double val, int lane) {
+    if (!ON) return;
+    if (n >= C.tape_cap) {
+      over = true;
+      return;
+    }
+    event(kind, q, val, lane);
+  }
+  // an event with a row (INIT, REFACTOR); a REFACTOR's q is its row index
+  __device__ __forceinline__ void push_row(int kind, int q, double val, const double (&y)[KS], int lane) {
+    if (!ON) return;
+    if (n >= C.tape_cap || rows >= C.row_cap) {
+      over = true;
+      return;
+    }
+    write_row(rows, y, lane);
+    event(kind, kind == EV_REFACTOR ? rows : q, val, lane);
+    rows++;
+  }
+  // iterate it of the current attempt, kept only if the step is accepted
+  __device__ __forceinline__ void iterate(int it, const double (&y)[KS], int lane) {
+    if (ON && rows + it < C.row_cap) write_row(rows + it, y, lane);
+  }
+  // acceptance: the attempt's K iterates become ITER events
+  __device__ __forceinline__ void accept_iters(int K, int lane) {
+    if (!ON) return;
+    if (n + K > C.tape_cap || rows + K > C.row_cap) {
+      over = true;
+      return;
+    }
+    for (int k = 0; k < K; ++k) event(EV_ITER, k, 0.0, lane);
+    rows += K;
+  }
+  // acceptance: the species the attempt projected onto y = 0, ascending
+  __device__ __forceinline__ void accept_projections(const unsigned (&pm)[KS], int lane) {
+    if (!ON) return;
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      unsigned b = pm[k];
+      while (b) {
+        const int l = __ffs(b) - 1;
+        b &= b - 1;
+        push(EV_PROJECT, l + WARP * k, 0.0, lane);
+      }
+    }
+  }
+  __device__ __forceinline__ void finish(bool failed, int lane) {
+    if (!ON || lane != 0) return;
+    C.tape_n[cell] = n;
+    C.tape_rows[cell] = rows;
+    if (over || failed) C.tape_bad[cell] = 1;
+  }
+};
+
+template <typename T, int KS, bool STAGED, bool REC>
 __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, const SolveParams &P, const Tabs &tb, double *Wd,
                            T *WL, const int lane, const int64_t cell) {
   const int64_t NC = C.n_cells;
@@ -404,6 +493,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
   cl.init_constants();
   double y0[KS];
   const bool bad = load_cell<KS>(M, C, Wd, lane, cell, cl.own, y0);
+  Recorder<KS, REC> rec(C, cell, M.S);
 
   const double dt = P.dt;
   int q = 1;
@@ -439,6 +529,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
       D[0][k] = y0[k];
       D[1][k] = h * f0[k];
     }
+    rec.push_row(EV_INIT, q, h, y0, lane);
 
     double t = 0.0, cM = 0.0, rho = 1.0;
     int n_eq = 0, have_M = 0, force_M = 0, n_since_M = 0, nef = 0, ncf = 0, last = 0;
@@ -451,6 +542,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
         const double hn = dt - t;
         if (hn != h) {
           rescale<KS>(D, q, hn / h, M.rescale_coef, lane);
+          rec.push(EV_RESCALE, q, hn / h, lane);
           h = hn;
           n_eq = 0;
         }
@@ -489,6 +581,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
         rho = 1.0;
         fresh = 1;
         st.jac_evals++;
+        rec.push_row(EV_REFACTOR, 0, c, ypred, lane);
       }
       force_M = 0;
       const double scale = (c == cM) ? 1.0 : 2.0 / (1.0 + c / cM);
@@ -501,7 +594,10 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
       }
       double del = 0.0, del_prev = 0.0;
       int conv = 0;
+      int n_it = 0;
       for (int it = 0; it < NEWTON_MAXITER; ++it) {
+        rec.iterate(it, y, lane);
+        n_it = it + 1;
         cl.eval_f(y, f);
         st.f_evals++;
 #pragma unroll
@@ -532,6 +628,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
           force_M = 1;
         } else {
           rescale<KS>(D, q, ETA_CF, M.rescale_coef, lane);
+          rec.push(EV_RESCALE, q, ETA_CF, lane);
           h *= ETA_CF;
           n_eq = 0;
         }
@@ -539,6 +636,9 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
       }
 
       // inequality constraint y >= 0
+      unsigned pm[KS];          // species projected onto y = 0 (ballot per register slot)
+#pragma unroll
+      for (int k = 0; k < KS; ++k) pm[k] = 0u;
       {
         bool neg = false;
 #pragma unroll
@@ -557,11 +657,14 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
           eta_c = warp_min(eta_c);
           if (sqrt(vs * cl.invS) <= tol) {
 #pragma unroll
-            for (int k = 0; k < KS; ++k)
-              if (cl.own[k] && y[k] < 0.0) {
+            for (int k = 0; k < KS; ++k) {
+              const bool p = cl.own[k] && y[k] < 0.0;
+              if (p) {
                 d[k] -= y[k];
                 y[k] = 0.0;
               }
+              if (REC) pm[k] = __ballot_sync(FULL, p);
+            }
           } else {
             st.rejects++;
             nef++;
@@ -569,6 +672,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
             double eta = ETA_CST_SAFETY * eta_c;
             if (eta < ETA_CST_MIN) eta = ETA_CST_MIN;
             rescale<KS>(D, q, eta, M.rescale_coef, lane);
+            rec.push(EV_RESCALE, q, eta, lane);
             h *= eta;
             n_eq = 0;
             continue;
@@ -586,6 +690,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
         if (nef >= 2 && eta > ETA_MXF) eta = ETA_MXF;
         if (nef >= 3 && q > 1) q -= 1;
         rescale<KS>(D, q, eta, M.rescale_coef, lane);
+        rec.push(EV_RESCALE, q, eta, lane);
         h *= eta;
         n_eq = 0;
         continue;
@@ -598,6 +703,9 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
       nef = 0;
       ncf = 0;
       accept_update<KS>(D, q, d);
+      rec.accept_iters(n_it, lane);
+      rec.accept_projections(pm, lane);
+      rec.push(EV_STEP, q, c, lane);
       if (last) break;
       n_eq++;
 
@@ -622,6 +730,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
       if (eta >= THRESH) {
         q = qn;
         rescale<KS>(D, q, eta, M.rescale_coef, lane);
+        rec.push(EV_RESCALE, q, eta, lane);
         h *= eta;
         n_eq = 0;
       }
@@ -642,6 +751,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
         if (cl.own[k]) C.y[(int64_t)(lane + WARP * k) * NC + cell] = D[0][k];
     }
   }
+  rec.finish(status != CHEM_CELL_OK, lane);
   if (lane == 0) {
     st.status = status;
     st.final_order = q;
@@ -673,7 +783,7 @@ __device__ bool stage_tables(const unsigned char *blob, int bytes, unsigned char
   return ok;
 }
 
-template <typename T, int KS, bool STAGED>
+template <typename T, int KS, bool STAGED, bool REC>
 __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const MechDev M, const CellsDev C, const SolveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t tma_bar;
@@ -695,11 +805,11 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const
       if (lane == 0) cell = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(C.queue), 1ull);
       cell = __shfl_sync(FULL, cell, 0);
       if (cell >= C.n_cells) break;
-      solve_cell<T, KS, STAGED>(M, C, P, tb, Wd, WL, lane, cell);
+      solve_cell<T, KS, STAGED, REC>(M, C, P, tb, Wd, WL, lane, cell);
     }
   } else {
     const int64_t cell = (int64_t)blockIdx.x * P.warps_per_block + warp;
-    if (cell < C.n_cells) solve_cell<T, KS, STAGED>(M, C, P, tb, Wd, WL, lane, cell);
+    if (cell < C.n_cells) solve_cell<T, KS, STAGED, REC>(M, C, P, tb, Wd, WL, lane, cell);
   }
   if (STAGED && !staged_ok) {
     __syncthreads();
@@ -759,7 +869,7 @@ cudaError_t launch_probe_t(const MechDev &M, const CellsDev &C, const SolveParam
   return cudaGetLastError();
 }
 
-template <typename T, int KS, bool STAGED>
+template <typename T, int KS, bool STAGED, bool REC>
 cudaError_t configure_t() {
   static bool configured[64] = {false};
   int dev = 0;
@@ -768,9 +878,9 @@ cudaError_t configure_t() {
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, solve_kernel<T, KS, STAGED>);
+  cudaError_t e = cudaFuncGetAttributes(&fa, solve_kernel<T, KS, STAGED, REC>);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(solve_kernel<T, KS, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(solve_kernel<T, KS, STAGED, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            optin - (int)fa.sharedSizeBytes);
   if (e == cudaSuccess && dev < 64) configured[dev] = true;
   return e;
@@ -778,21 +888,33 @@ cudaError_t configure_t() {
 
 template <typename T, int KS, bool STAGED>
 int occupancy_t(int warps_per_block, size_t smem) {
-  if (configure_t<T, KS, STAGED>() != cudaSuccess) return 0;
+  if (configure_t<T, KS, STAGED, false>() != cudaSuccess) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, solve_kernel<T, KS, STAGED>, warps_per_block * WARP, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, solve_kernel<T, KS, STAGED, false>, warps_per_block * WARP, smem) !=
       cudaSuccess)
     return 0;
   return n;
 }
 
+template <typename T, int KS, bool STAGED, bool REC>
+cudaError_t launch_rec_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int blocks, cudaStream_t stream) {
+  const size_t smem = (size_t)P.tab_bytes + (size_t)P.cell_bytes * P.warps_per_block;
+  cudaError_t e = configure_t<T, KS, STAGED, REC>();
+  if (e != cudaSuccess) return e;
+  solve_kernel<T, KS, STAGED, REC><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, P);
+  return cudaGetLastError();
+}
+
+// The recording kernel exists for the FP64 iteration only (the adjoint
+// differentiates FP64 LU solves).
 template <typename T, int KS, bool STAGED>
 cudaError_t launch_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int blocks, cudaStream_t stream) {
-  const size_t smem = (size_t)P.tab_bytes + (size_t)P.cell_bytes * P.warps_per_block;
-  cudaError_t e = configure_t<T, KS, STAGED>();
-  if (e != cudaSuccess) return e;
-  solve_kernel<T, KS, STAGED><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, P);
-  return cudaGetLastError();
+  if constexpr (std::is_same<T, double>::value) {
+    if (C.tape_n) return launch_rec_t<T, KS, STAGED, true>(M, C, P, blocks, stream);
+  } else {
+    if (C.tape_n) return cudaErrorInvalidValue;
+  }
+  return launch_rec_t<T, KS, STAGED, false>(M, C, P, blocks, stream);
 }
 
 template <typename T, bool STAGED>
@@ -815,6 +937,309 @@ cudaError_t launch_ks(const MechDev &M, const CellsDev &C, const SolveParams &P,
     case 4: return launch_t<T, 4, STAGED>(M, C, P, blocks, stream);
     default: return cudaErrorInvalidValue;
   }
+}
+
+
+// ============================================================== discrete adjoint
+// The exact adjoint of the forward solve with its controls frozen (Background:
+// CVODE's BDF/Newton integration is the map being differentiated).  The
+// forward records, per cell, every operation on the BDF history and the
+// states the corrector evaluated f and J at (REFACTOR and ITER rows), so the
+// backward needs no re-solve: one warp per cell walks the tape in reverse
+// carrying the adjoints lambda of the history rows D_0..D_7 in registers.
+//   STEP      lambda_d from the history update; projected species pass
+//             their lambda_d to lambda_ypred with a minus sign;
+//   ITER k    g = s M^{-T} lambda_d (the LU of the REFACTOR in force, then
+//             U^T and L^T solves), J(y_k)^T g and nu_j . g by pass programs
+//             on the extended Wd array: lambda_d += c J^T g - g,
+//             lambda_ypred += c J^T g, lambda_psi -= g,
+//             dL/dtheta_j += c r_j(y_k) (nu_j . g); after k = 0 lambda_ypred
+//             and lambda_psi fold into lambda_0..q;
+//   RESCALE   lambda_{1..q} <- T(eta)^T lambda_{1..q};
+//   INIT      D_1 = h0 f(y) folds into lambda_0, higher rows reset.
+// M = I - c_M J(y_J) is a constant of the map (the recorded y_J and the
+// forward's rate constants); the backward re-forms and re-factors it from the
+// REFACTOR row each time the walk enters another REFACTOR's range.
+
+// lambda_{1..q} <- T(eta)^T lambda_{1..q}: lambda'_m = sum_{i<=m} T_im lambda_i
+template <int KS>
+__device__ __forceinline__ void rescale_adjoint(double (&L)[NROW][KS], int q, double eta, const double *coef, int lane) {
+  double tv = 0.0;
+  if (lane < QMAX * QMAX) {
+    const double *cp = coef + lane * (QMAX + 1);
+    tv = __ldg(cp + QMAX);
+#pragma unroll
+    for (int p = QMAX - 1; p >= 0; --p) tv = fma(tv, eta, __ldg(cp + p));
+  }
+  // m descending: row m reads rows i <= m, still unchanged
+#pragma unroll
+  for (int mm = QMAX; mm >= 1; --mm) {
+    if (mm > q) continue;
+    double nl[KS];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) nl[k] = 0.0;
+#pragma unroll
+    for (int i = 1; i <= QMAX; ++i) {
+      if (i > mm) continue;
+      const double t = __shfl_sync(FULL, tv, (i - 1) * QMAX + (mm - 1));
+#pragma unroll
+      for (int k = 0; k < KS; ++k) nl[k] = fma(t, L[i][k], nl[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < KS; ++k) L[mm][k] = nl[k];
+  }
+}
+
+// Adjoint of an accepted STEP at order q (before the implicit part):
+// lambda_d = lambda_{q+2} + lambda_{q+1} + sum_{m<=q} lambda_m; lambda_i (i<=q)
+// = prefix sums, lambda_{q+1} = -lambda_{q+2}, lambda_{q+2} = 0.
+template <int KS>
+__device__ __forceinline__ void step_adjoint_linear(double (&L)[NROW][KS], int q, double (&lamd)[KS]) {
+#define CHEM_ADJ_CASE(Q_)                                                           \
+  case Q_:                                                                         \
+    _Pragma("unroll") for (int k = 0; k < KS; ++k) {                               \
+      double acc = 0.0;                                                            \
+      _Pragma("unroll") for (int m = 0; m <= Q_; ++m) {                            \
+        acc += L[m][k];                                                            \
+        L[m][k] = acc;                                                             \
+      }                                                                            \
+      lamd[k] = L[Q_ + 2][k] + L[Q_ + 1][k] + acc;                                 \
+      L[Q_ + 1][k] = -L[Q_ + 2][k];                                                \
+      L[Q_ + 2][k] = 0.0;                                                          \
+    }                                                                              \
+    break;
+  switch (q) {
+    CHEM_ADJ_CASE(1) CHEM_ADJ_CASE(2) CHEM_ADJ_CASE(3) CHEM_ADJ_CASE(4) CHEM_ADJ_CASE(5)
+    default:
+      break;
+  }
+#undef CHEM_ADJ_CASE
+}
+
+// rates RT and partials PP = dr_j/dy_l at the y stored in Wd[Y]
+template <int KS>
+__device__ __forceinline__ void rates_partials(const MechDev &M, const Tabs &tb, double *Wd, int lane) {
+  unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
+  for (int j = lane; j < M.R; j += WARP) {
+    const uint2 sl = tab<uint2>(tb, M.tab.rx_slots)[j];
+    double r = Wd[M.d_KT + j] * at<double>(wd, sl.x & 0xffff);
+    if (M.max_reac > 1) r *= at<double>(wd, sl.x >> 16);
+    if (M.max_reac > 2) r *= at<double>(wd, sl.y & 0xffff);
+    Wd[M.d_RT + j] = r;
+  }
+  for (int pr = lane; pr < M.n_pairs; pr += WARP) {
+    const int j = tab<int>(tb, M.tab.pair_rx)[pr];
+    const unsigned o = tab<unsigned>(tb, M.tab.pair_other)[pr];
+    double p = Wd[M.d_KT + j];
+    if (M.max_reac > 1) p *= at<double>(wd, o & 0xffff);
+    if (M.max_reac > 2) p *= at<double>(wd, o >> 16);
+    Wd[M.a_PP + pr] = p;
+  }
+  __syncwarp();
+}
+
+// Wd[MU] = v; runs nu.mu and J^T mu programs; theta gradient += scale * r_j * (nu_j . v); out = J^T v
+template <int KS>
+__device__ __forceinline__ void jt_and_theta(const MechDev &M, double *Wd, const bool (&own)[KS], const double (&v)[KS],
+                                             double scale, double (&out)[KS], int lane) {
+#pragma unroll
+  for (int k = 0; k < KS; ++k)
+    if (own[k]) Wd[M.a_MU + lane + WARP * k] = v[k];
+  __syncwarp();
+  run_ops<double, false, false, PF_GLOBAL>(M.nudot_ops, M.nudot_npass, Wd, lane);
+  run_ops<double, false, false, PF_GLOBAL>(M.jt_ops, M.jt_npass, Wd, lane);
+  for (int j = lane; j < M.R; j += WARP) Wd[M.a_G + j] = fma(scale * Wd[M.d_RT + j], Wd[M.a_NM + j], Wd[M.a_G + j]);
+#pragma unroll
+  for (int k = 0; k < KS; ++k) out[k] = own[k] ? Wd[M.a_JTM + lane + WARP * k] : 0.0;
+  __syncwarp();
+}
+
+template <int KS>
+__device__ __forceinline__ void read_row(const double *yt, int r, int S, const bool (&own)[KS], int lane, double (&y)[KS]) {
+#pragma unroll
+  for (int k = 0; k < KS; ++k) y[k] = own[k] ? yt[(int64_t)r * S + lane + WARP * k] : 0.0;
+}
+
+template <int KS>
+__device__ void backward_cell(const MechDev &M, const CellsDev &C, const AdjDev &A, const SolveParams &P, const Tabs &tb,
+                              double *Wd, double *WL, const int lane, const int64_t cell) {
+  const int64_t NC = C.n_cells;
+  Cell<double, KS, false> cl(M, P, tb, Wd, WL, lane);
+  cl.init_constants();
+  unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
+  for (int k = lane; k < M.a_nconst; k += WARP) at<double>(wd, __ldg(M.a_const_off + k)) = __ldg(M.a_const_val + k);
+  for (int j = lane; j < M.R; j += WARP) Wd[M.a_G + j] = 0.0;
+  double y0[KS];
+  load_cell<KS>(M, C, Wd, lane, cell, cl.own, y0);   // rate constants
+  double L[NROW][KS];
+#pragma unroll
+  for (int m = 0; m < NROW; ++m)
+#pragma unroll
+    for (int k = 0; k < KS; ++k) L[m][k] = 0.0;
+#pragma unroll
+  for (int k = 0; k < KS; ++k) L[0][k] = cl.own[k] ? A.dLdy[(int64_t)(lane + WARP * k) * NC + cell] : 0.0;
+
+  const int n = C.tape_n[cell];
+  const int *kqs = C.tape_kq + cell * (int64_t)C.tape_cap;
+  const double *vals = C.tape_val + cell * (int64_t)C.tape_cap;
+  const double *yt = C.ytape + cell * (int64_t)C.row_cap * M.S;
+  int row = C.tape_rows[cell];     // rows of the events before the walk position
+  int er = n - 1;                  // the last REFACTOR before the walk position
+  while (er >= 0 && (__ldg(kqs + er) & 0xff) != EV_REFACTOR) --er;
+  int m_event = -1;                // the REFACTOR whose LU is in WL
+  double lamd[KS], lyp[KS], lpsi[KS];
+#pragma unroll
+  for (int k = 0; k < KS; ++k) lamd[k] = lyp[k] = lpsi[k] = 0.0;
+  int sq = 1;
+  double sc = 0.0, ss = 1.0;
+  bool bad = false;
+
+  for (int e = n - 1; e >= 0; --e) {
+    const int kq = __ldg(kqs + e);
+    const double val = __ldg(vals + e);
+    const int kind = kq & 0xff, q = kq >> 8;
+    if (kind == EV_RESCALE) {
+      rescale_adjoint<KS>(L, q, val, M.rescale_coef, lane);
+    } else if (kind == EV_STEP) {
+      step_adjoint_linear<KS>(L, q, lamd);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) lyp[k] = lpsi[k] = 0.0;
+      sq = q;
+      sc = val;
+      while (er >= e) {
+        --er;
+        while (er >= 0 && (__ldg(kqs + er) & 0xff) != EV_REFACTOR) --er;
+      }
+      if (er < 0) {
+        bad = true;
+        break;
+      }
+      const double cM = __ldg(vals + er);
+      if (er != m_event) {
+        double yJ[KS];
+        read_row<KS>(yt, __ldg(kqs + er) >> 8, M.S, cl.own, lane, yJ);
+        cl.form_and_factor(cM, yJ);
+        m_event = er;
+      }
+      ss = (sc == cM) ? 1.0 : 2.0 / (1.0 + sc / cM);
+    } else if (kind == EV_PROJECT) {
+#pragma unroll
+      for (int k = 0; k < KS; ++k)
+        if (q == lane + WARP * k) {
+          lyp[k] = -lamd[k];
+          lamd[k] = 0.0;
+        }
+    } else if (kind == EV_ITER) {
+      if (--row < 0) {
+        bad = true;
+        break;
+      }
+      double y[KS], g[KS], jtg[KS];
+      read_row<KS>(yt, row, M.S, cl.own, lane, y);
+#pragma unroll
+      for (int k = 0; k < KS; ++k)
+        if (cl.own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
+      __syncwarp();
+      rates_partials<KS>(M, tb, Wd, lane);
+      // g = s M^{-T} lambda_d
+#pragma unroll
+      for (int k = 0; k < KS; ++k)
+        if (cl.own[k]) WL[M.L_X + cl.pos[k]] = lamd[k];
+      __syncwarp();
+      run_ops<double, true, false, PF_GLOBAL>(M.fwdT_ops, M.fwdT_npass, WL, lane);
+      run_ops<double, false, false, PF_GLOBAL>(M.bwdT_ops, M.bwdT_npass, WL, lane);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) g[k] = cl.own[k] ? ss * WL[M.L_X + cl.pos[k]] : 0.0;
+      __syncwarp();
+      jt_and_theta<KS>(M, Wd, cl.own, g, sc, jtg, lane);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const double cj = sc * jtg[k];
+        lamd[k] += cj - g[k];
+        lyp[k] += cj;
+        lpsi[k] -= g[k];
+      }
+      if (q == 0) {
+        // the predictor: y_pred = sum_{m<=q} D_m, psi = (1/gamma_q) sum gamma_m D_m
+        const double iq = c_igam[sq];
+#pragma unroll
+        for (int m = 0; m <= QMAX; ++m) {
+          if (m > sq) continue;
+          const double gm = (m >= 1) ? c_gam[m] * iq : 0.0;
+#pragma unroll
+          for (int k = 0; k < KS; ++k) L[m][k] += fma(gm, lpsi[k], lyp[k]);
+        }
+      }
+    } else if (kind == EV_REFACTOR) {
+      --row;
+    } else if (kind == EV_INIT) {
+      // D_0 = y, D_1 = h0 f(y), higher rows reset
+      if (--row < 0) {
+        bad = true;
+        break;
+      }
+      double y[KS], jtl[KS], l1[KS];
+      read_row<KS>(yt, row, M.S, cl.own, lane, y);
+#pragma unroll
+      for (int k = 0; k < KS; ++k)
+        if (cl.own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
+      __syncwarp();
+      rates_partials<KS>(M, tb, Wd, lane);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) l1[k] = L[1][k];
+      jt_and_theta<KS>(M, Wd, cl.own, l1, val, jtl, lane);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) L[0][k] = fma(val, jtl[k], L[0][k]);
+#pragma unroll
+      for (int m = 1; m < NROW; ++m)
+#pragma unroll
+        for (int k = 0; k < KS; ++k) L[m][k] = 0.0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KS; ++k)
+    if (cl.own[k]) A.dLdy0[(int64_t)(lane + WARP * k) * NC + cell] = bad ? 0.0 : L[0][k];
+  for (int j = lane; j < M.R; j += WARP) A.gcell[(int64_t)j * NC + cell] = bad ? 0.0 : Wd[M.a_G + j];
+  if (bad && lane == 0) C.tape_bad[cell] = 1;
+}
+
+template <int KS>
+__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) adjoint_kernel(const MechDev M, const CellsDev C, const AdjDev A,
+                                                                    const SolveParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & (WARP - 1);
+  const int warp = threadIdx.x / WARP;
+  const int64_t cell = (int64_t)blockIdx.x * P.warps_per_block + warp;
+  if (cell >= C.n_cells) return;
+  Tabs tb;
+  tb.base = M.blob[0];
+  double *Wd = reinterpret_cast<double *>(smem + (size_t)warp * P.cell_bytes);
+  double *WL = Wd + P.wd_pad;
+  if (C.tape_bad[cell]) {
+    for (int i = lane; i < M.S; i += WARP) A.dLdy0[(int64_t)i * C.n_cells + cell] = 0.0;
+    for (int j = lane; j < M.R; j += WARP) A.gcell[(int64_t)j * C.n_cells + cell] = 0.0;
+    return;
+  }
+  backward_cell<KS>(M, C, A, P, tb, Wd, WL, lane, cell);
+}
+
+// dL/dtheta_j = sum over cells of the per-cell gradients, in cell order
+__global__ void theta_reduce_kernel(const double *gcell, int64_t n_cells, int R, double *out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= R) return;
+  double s = 0.0;
+  for (int64_t c = 0; c < n_cells; ++c) s += gcell[(int64_t)j * n_cells + c];
+  out[j] = s;
+}
+
+template <int KS>
+cudaError_t launch_adj_t(const MechDev &M, const CellsDev &C, const AdjDev &A, const SolveParams &P, cudaStream_t stream) {
+  const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
+  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int blocks = (int)((C.n_cells + P.warps_per_block - 1) / P.warps_per_block);
+  adjoint_kernel<KS><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, A, P);
+  return cudaGetLastError();
 }
 
 bool staged_driver(int driver) { return driver == CHEM_DRIVER_PERSISTENT; }
@@ -924,6 +1349,34 @@ cudaError_t launch_solve(const MechDev &M, const CellsDev &C, const LaunchCfg &c
   const bool f32 = cfg.lu_precision == 32;
   if (staged) return f32 ? launch_ks<float, true>(M, C, P, blocks, stream) : launch_ks<double, true>(M, C, P, blocks, stream);
   return f32 ? launch_ks<float, false>(M, C, P, blocks, stream) : launch_ks<double, false>(M, C, P, blocks, stream);
+}
+
+cudaError_t launch_adjoint(const MechDev &M, const CellsDev &C, const AdjDev &A, cudaStream_t stream) {
+  if (C.n_cells <= 0) return cudaSuccess;
+  SolveParams P{};
+  P.wd_pad = (M.Wda_len + 1) & ~1;
+  P.cell_bytes = (int)(((size_t)P.wd_pad * sizeof(double) + (size_t)M.WL_len * sizeof(double) + 15) & ~(size_t)15);
+  P.prec = 0;
+  P.tab_bytes = 0;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // several cells per block, as many as shared memory allows up to the cap
+  int w = optin / P.cell_bytes;
+  if (w > ADJ_WARPS_PER_BLOCK) w = ADJ_WARPS_PER_BLOCK;
+  if (w < 1) return cudaErrorInvalidValue;
+  P.warps_per_block = w;
+  cudaError_t e = cudaSuccess;
+  switch ((M.S + WARP - 1) / WARP) {
+    case 1: e = launch_adj_t<1>(M, C, A, P, stream); break;
+    case 2: e = launch_adj_t<2>(M, C, A, P, stream); break;
+    case 3: e = launch_adj_t<3>(M, C, A, P, stream); break;
+    case 4: e = launch_adj_t<4>(M, C, A, P, stream); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  theta_reduce_kernel<<<(M.R + 127) / 128, 128, 0, stream>>>(A.gcell, C.n_cells, M.R, A.dLdtheta);
+  return cudaGetLastError();
 }
 
 }  // namespace chemgpu

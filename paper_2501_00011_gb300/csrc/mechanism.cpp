@@ -384,6 +384,67 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
   }
   d.d_DUMMY = d.Wd_len++;
   d.L_DUMMY = d.WL_len++;
+
+  // ---- discrete adjoint: programs on Wd extended past the forward layout
+  // (the forward prefix keeps y, ONE, ZERO and k~ where the forward tables
+  // expect them) and the transposed triangular solves on WL.
+  {
+    d.a_MU = d.Wd_len;
+    d.a_NM = d.a_MU + S;
+    d.a_PP = d.a_NM + R;
+    d.a_JTM = d.a_PP + n_pairs;
+    d.a_G = d.a_JTM + S;
+    int temp0 = d.a_G + R;
+    // nu_j . mu for every reaction, and J^T mu for every species
+    std::vector<std::vector<std::pair<double, int>>> nd_terms(R);   // (nu, species)
+    for (int j = 0; j < R; ++j)
+      for (auto &kv : nu[j]) nd_terms[j].push_back({kv.second, kv.first});
+    std::vector<std::vector<std::pair<int, int>>> jt_terms(S);      // (pair, reaction)
+    {
+      int pidx = 0;
+      for (int j = 0; j < R; ++j)
+        for (int s2 = 0; s2 < rx[j].n_reac; ++s2) jt_terms[rx[j].reac[s2]].push_back({pidx++, j});
+    }
+    int n_temp = 0;
+    for (int j = 0; j < R; ++j) n_temp += (int)std::max<size_t>(1, (nd_terms[j].size() + CHUNK - 1) / CHUNK) - 1;
+    for (int l = 0; l < S; ++l) n_temp += (int)std::max<size_t>(1, (jt_terms[l].size() + CHUNK - 1) / CHUNK) - 1;
+    ConstTable ct;
+    ct.base = temp0 + n_temp;
+    Scheduler a(ct.base + 64 + 2 * R), b(ct.base + 64 + 2 * R);
+    int temp_next = temp0;
+    for (int j = 0; j < R; ++j) {
+      std::vector<std::pair<int, int>> terms;
+      for (auto &t : nd_terms[j]) terms.push_back({ct.get(t.first), d.a_MU + t.second});
+      add_sum(a, d.a_NM + j, true, terms, CHUNK, temp_next, d.d_ZERO, d.d_ONE);
+    }
+    for (int l = 0; l < S; ++l) {
+      std::vector<std::pair<int, int>> terms;
+      for (auto &t : jt_terms[l]) terms.push_back({d.a_PP + t.first, d.a_NM + t.second});
+      add_sum(b, d.a_JTM + l, true, terms, CHUNK, temp_next, d.d_ZERO, d.d_ONE);
+    }
+    m.nudot_prog = a.finish();
+    m.jt_prog = b.finish();
+    d.Wda_len = ct.base + (int)ct.vals.size();
+    m.a_consts_v = ct.vals;
+    m.a_consts_i.clear();
+    for (size_t k = 0; k < ct.vals.size(); ++k) m.a_consts_i.push_back(ct.base + (int)k);
+    if ((size_t)d.Wda_len * sizeof(double) > 0xfff0) {
+      msg = "mechanism too large for the adjoint's 16-bit byte offsets";
+      return CHEM_EINVAL;
+    }
+    // M^T = U^T L^T: solve U^T z = b (lower, diagonal u_kk), then L^T x = z (unit upper, L stored negated)
+    Scheduler f(d.WL_len + 8), g(d.WL_len + 8);
+    for (int k = 0; k < S; ++k) {
+      f.fma(d.L_X + k, d.L_NINV + k, d.L_X + k, d.L_ZERO);           // NEG: -ninv * z = z / u_kk
+      for (int j = k + 1; j < S; ++j)
+        if (F[k * S + j]) f.fma(d.L_X + j, d.L_LU + slot[k * S + j], d.L_X + k, d.L_X + j);   // z_j -= u_kj z_k
+    }
+    for (int k = S - 1; k >= 0; --k)
+      for (int i = 0; i < k; ++i)
+        if (F[k * S + i]) g.fma(d.L_X + i, d.L_LU + slot[k * S + i], d.L_X + k, d.L_X + i);   // x_i += (-l_ki) x_k
+    m.fwdT_prog = f.finish();
+    m.bwdT_prog = g.finish();
+  }
   if ((size_t)d.WL_len * sizeof(double) > 0xfff0 || (size_t)d.Wd_len * sizeof(double) > 0xfff0) {
     msg = "mechanism too large: the per-cell work arrays exceed the 16-bit byte offsets of the warp programs";
     return CHEM_EINVAL;
@@ -528,6 +589,24 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
       free_mechanism(m);
       return rc;
     }
+  }
+  {
+    int rc = 0;
+    std::vector<int> aoff(m.a_consts_i.size());
+    for (size_t k = 0; k < aoff.size(); ++k) aoff[k] = m.a_consts_i[k] * 8;
+    if ((rc = put(m, aoff, &d.a_const_off, msg)) || (rc = put(m, m.a_consts_v, &d.a_const_val, msg)) ||
+        (rc = put(m, device_ops(m.nudot_prog, 8, d.d_DUMMY, d.d_ZERO, d.d_ONE), &d.nudot_ops, msg)) ||
+        (rc = put(m, device_ops(m.jt_prog, 8, d.d_DUMMY, d.d_ZERO, d.d_ONE), &d.jt_ops, msg)) ||
+        (rc = put(m, device_ops(m.fwdT_prog, 8, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1), &d.fwdT_ops, msg)) ||
+        (rc = put(m, device_ops(m.bwdT_prog, 8, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1), &d.bwdT_ops, msg))) {
+      free_mechanism(m);
+      return rc;
+    }
+    d.a_nconst = (int)m.a_consts_v.size();
+    d.nudot_npass = m.nudot_prog.n_pass();
+    d.jt_npass = m.jt_prog.n_pass();
+    d.fwdT_npass = m.fwdT_prog.n_pass();
+    d.bwdT_npass = m.bwdT_prog.n_pass();
   }
   d.f_npass = m.f_prog.n_pass();
   d.fwd_npass = m.fwd_prog.n_pass();

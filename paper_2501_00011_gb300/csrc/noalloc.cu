@@ -86,7 +86,7 @@ extern "C" int chem_solve_step_noalloc(const chem_mech *mech, int64_t n_cells, c
   e = cudaMemsetAsync(g_scratch_addr[dev], 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return fail(CHEM_ECUDA, std::string("scratch reset: ") + cudaGetErrorString(e));
 
-  CellsDev cd;
+  CellsDev cd{};
   cd.n_cells = n_cells;
   cd.T = T;
   cd.P = P;

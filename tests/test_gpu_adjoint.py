@@ -1,0 +1,151 @@
+"""GPU discrete adjoint against the oracle adjoint and finite differences.
+
+The GPU's own recorded tape (step sizes, orders, iteration counts,
+projections, and the states its iteration matrices and iterates were
+evaluated at) is read back and given to the oracle, so both differentiate
+the same frozen-control map.  The oracle replays that map: it must reproduce
+the GPU's final state to rounding (1e-9 relative: the GPU's sparse LU and the
+oracle's dense pivoted LU round differently).  The GPU's dL/dy0 and
+dL/dtheta must match the oracle adjoint to 1e-8 relative, and central
+differences (step 1e-6) of the oracle's replay must match the GPU gradient
+to 1e-5 relative, the differentiation bar of the workload.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2501_00011_gb300 import synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def cg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_00011_gb300 import build, chemgpu
+    build.build()
+    torch.cuda.init()
+    chemgpu.load()
+    return chemgpu
+
+
+def _tape_for(oracle_lib, kind, q, val, rows):
+    """The GPU tape in the oracle's layout: one state per event (rows go, in
+    order, to the INIT, REFACTOR and ITER events; the others get zeros)."""
+    has_row = (kind == 0) | (kind == 4) | (kind == 5)
+    assert has_row.sum() == rows.shape[0]
+    y = np.zeros((kind.size, rows.shape[1]))
+    y[has_row] = rows
+    return oracle_lib.Tape(kind.astype(np.int32), q.astype(np.int32), val.astype(np.float64), y)
+
+
+def _run(cg, wl, n_cells, n_steps):
+    m = cg.Mechanism(wl.mech)
+    cells = synth.subset(wl.cells, np.arange(n_cells))
+    c = cg.Cells(m, n_cells, rtol=wl.rtol, atol=wl.atol, record_adjoint=True)
+    c.set_state(cells.T, cells.P, cells.y)
+    for _ in range(n_steps):
+        c.solve_step(wl.dt)
+    w = synth.loss_weights(wl.mech.n_species, n_cells)
+    gth, gy0, n_bad = c.sensitivity(w)
+    assert n_bad == 0
+    return m, c, cells, w, gth, gy0
+
+
+@pytest.mark.parametrize("name,n_steps", [("small", 2), ("tropo", 4)])
+def test_gpu_adjoint_matches_oracle_adjoint(oracle_lib, cg, name, n_steps):
+    wl = synth.workload_small() if name == "small" else synth.workload_adjoint(12)
+    n_cells = 6
+    m, c, cells, w, gth, gy0 = _run(cg, wl, n_cells, n_steps)
+    g_sum = np.zeros(wl.mech.n_reactions)
+    y_gpu = c.get_state()
+    for k in range(n_cells):
+        kind, q, val, rows = c.get_tape(k)
+        assert (kind == 0).sum() == n_steps
+        assert np.all(np.isin(kind, [0, 1, 2, 3, 4, 5]))
+        tape = _tape_for(oracle_lib, kind, q, val, rows)
+        kt = oracle_lib.rate_constants(wl.mech, cells.T[k], cells.P[k])
+        yr = oracle_lib.replay(wl.mech, kt, cells.y[:, k], tape)
+        big = np.abs(y_gpu[:, k]) > 1e-10 * np.abs(y_gpu[:, k]).max()
+        assert np.all(np.abs(yr - y_gpu[:, k])[big] <= 1e-9 * np.abs(y_gpu[:, k])[big]), k
+        ly0, g = oracle_lib.adjoint(wl.mech, kt, cells.y[:, k], tape, w[:, k])
+        g_sum += g
+        scale = np.abs(ly0).max()
+        assert np.all(np.abs(gy0[:, k] - ly0) <= 1e-8 * np.abs(ly0) + 1e-12 * scale), k
+    scale = np.abs(g_sum).max()
+    assert np.all(np.abs(gth - g_sum) <= 1e-8 * np.abs(g_sum) + 1e-12 * scale)
+
+
+def test_gpu_adjoint_matches_finite_differences(oracle_lib, cg):
+    wl = synth.workload_adjoint(8)
+    n_cells, n_steps = 3, 4
+    m, c, cells, w, gth, gy0 = _run(cg, wl, n_cells, n_steps)
+    rng = np.random.default_rng(11)
+    eps = 1e-6
+    tapes = [_tape_for(oracle_lib, *c.get_tape(k)) for k in range(n_cells)]
+    kts = [oracle_lib.rate_constants(wl.mech, cells.T[k], cells.P[k]) for k in range(n_cells)]
+
+    def loss(theta, dy0=None):
+        # the iteration matrices stay those of the recorded run (kt_M)
+        tot = 0.0
+        for k in range(n_cells):
+            kt = oracle_lib.rate_constants(wl.mech, cells.T[k], cells.P[k], theta=theta)
+            y0 = cells.y[:, k] if dy0 is None else cells.y[:, k] + dy0[:, k]
+            tot += w[:, k] @ oracle_lib.replay(wl.mech, kt, y0, tapes[k], kt_M=kts[k])
+        return tot
+
+    R = wl.mech.n_reactions
+    for _ in range(2):
+        v = rng.standard_normal(R)
+        fd = (loss(eps * v) - loss(-eps * v)) / (2 * eps)
+        assert abs(fd - gth @ v) <= 1e-5 * (np.abs(gth) @ np.abs(v))
+        u = rng.standard_normal(cells.y.shape) * cells.y
+        fd = (loss(np.zeros(R), eps * u) - loss(np.zeros(R), -eps * u)) / (2 * eps)
+        assert abs(fd - np.sum(gy0 * u)) <= 1e-5 * np.sum(np.abs(gy0 * u))
+
+
+def test_autograd_function_matches_sensitivity(cg):
+    wl = synth.workload_adjoint(16)
+    dev = torch.device("cuda")
+    m = cg.Mechanism(wl.mech)
+    c = cg.Cells(m, 16, rtol=wl.rtol, atol=wl.atol, record_adjoint=True)
+    theta = torch.zeros(wl.mech.n_reactions, dtype=torch.float64, device=dev, requires_grad=True)
+    y0 = torch.from_numpy(wl.cells.y[:, :16].copy()).to(dev).requires_grad_(True)
+    T = torch.from_numpy(wl.cells.T[:16].copy()).to(dev)
+    P = torch.from_numpy(wl.cells.P[:16].copy()).to(dev)
+    w = torch.from_numpy(synth.loss_weights(wl.mech.n_species, 16)).to(dev)
+    y = cg.solve_with_grad(c, theta, y0, T, P, wl.dt, 2)
+    (w * y).sum().backward()
+    gth, gy0, n_bad = c.sensitivity(w.cpu().numpy())
+    assert n_bad == 0
+    np.testing.assert_allclose(theta.grad.cpu().numpy(), gth, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(y0.grad.cpu().numpy(), gy0, rtol=1e-12, atol=0)
+
+
+def test_tape_overflow_is_reported(cg):
+    wl = synth.workload_adjoint(4)
+    m = cg.Mechanism(wl.mech)
+    c = cg.Cells(m, 4, rtol=wl.rtol, atol=wl.atol, record_adjoint=True, tape_steps=8)
+    c.set_state(wl.cells.T[:4], wl.cells.P[:4], wl.cells.y[:, :4])
+    c.solve_step(wl.dt)
+    gth, gy0, n_bad = c.sensitivity(np.ones((wl.mech.n_species, 4)))
+    assert n_bad == 4
+    assert np.all(gy0 == 0.0) and np.all(gth == 0.0)
+
+
+def test_recording_needs_fp64_lu(cg):
+    wl = synth.workload_adjoint(4)
+    m = cg.Mechanism(wl.mech)
+    with pytest.raises(cg.ChemError):
+        cg.Cells(m, 4, record_adjoint=True, lu_precision=32)
+
+
+def test_sensitivity_requires_recording(cg):
+    wl = synth.workload_adjoint(4)
+    m = cg.Mechanism(wl.mech)
+    c = cg.Cells(m, 4)
+    c.set_state(wl.cells.T[:4], wl.cells.P[:4], wl.cells.y[:, :4])
+    c.solve_step(wl.dt)
+    with pytest.raises(cg.ChemError):
+        c.sensitivity(np.ones((wl.mech.n_species, 4)))
