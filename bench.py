@@ -9,8 +9,10 @@ error and step control, all in one kernel).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Prints one JSON line (rank 0).  Multi-GPU runs are weak scaling: every rank
-solves its own 10,000 cells; there is no collective on the data path.
+Prints one JSON line (rank 0).  Multi-GPU runs are weak scaling: rank r solves
+its contiguous shard (10,000 cells) of a global batch of N x 10,000 cells; the
+forward solve has no collective, the adjoint measurement adds one sum of the
+theta gradient over ranks.
 """
 from __future__ import annotations
 
@@ -32,6 +34,35 @@ UNIT = "cells/s"
 N_CELLS = 10_000
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 FP64_PEAK_NOMINAL = 152 * 2070e6 * 2 * 2   # SMs x clock x 2 FP64 FMA lanes/SM/clk x 2 flops
+PROFILE = os.path.join(ROOT, "profiles", "solve_kernel_fp64_persistent_tropo10k.md")
+KERNEL_SOURCES = ("paper_2501_00011_gb300/csrc/kernels.cu", "paper_2501_00011_gb300/csrc/internal.h",
+                  "paper_2501_00011_gb300/csrc/mechanism.cpp")
+
+
+def _kernel_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of the headline kernel from the committed ncu
+    summary, or None when the summary is missing or the kernel sources have
+    changed since it was taken."""
+    try:
+        vals = {}
+        for line in open(PROFILE):
+            if ":" in line and line.split(":", 1)[0].strip() in ("dram_bytes_per_launch", "source_sha256"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+        if vals.get("source_sha256") != _kernel_sha():
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def _dist():
@@ -162,7 +193,12 @@ def run_gpu(args):
     libbuild.build()
     from paper_2501_00011_gb300 import chemgpu
 
-    wl = _workload(args.cells)
+    # rank r solves its contiguous shard of a global batch of ws x cells
+    from paper_2501_00011_gb300 import shard, synth
+    wl = _workload(args.cells * ws)
+    if ws > 1:
+        b, e = shard.cell_range(wl.cells.n_cells, rank, ws)
+        wl.cells = synth.subset(wl.cells, np.arange(b, e))
     mech = chemgpu.Mechanism(wl.mech)
     info = mech.info()
     C, S = wl.cells.n_cells, wl.mech.n_species
@@ -177,6 +213,76 @@ def run_gpu(args):
         if ws > 1:
             import torch.distributed as dist
             dist.barrier()
+
+    def time_extras(chemgpu, mech, dev, stream, flush, barrier):
+        """The batching form (50,000 cells, six 600 s steps as one captured graph,
+        autotuned launch shape) and the adjoint form (2,048 cells, four steps
+        forward with the tape, then the sensitivity)."""
+        from paper_2501_00011_gb300 import synth
+        out = {}
+        wl3 = synth.workload_batching(args.batch_cells)
+        n3 = wl3.cells.n_cells
+        c3 = chemgpu.Cells(mech, n3, rtol=wl3.rtol, atol=wl3.atol, driver="persistent")
+        T3, P3 = torch.from_numpy(wl3.cells.T).to(dev), torch.from_numpy(wl3.cells.P).to(dev)
+        y3, J3 = torch.from_numpy(wl3.cells.y).to(dev), torch.from_numpy(wl3.cells.J).to(dev)
+        c3.set_state(T3, P3, y3, stream=stream)
+        c3.set_photolysis(J3, stream=stream)
+        w, b = c3.autotune(wl3.dt)
+        c3.solve_steps(wl3.dt, wl3.n_steps, stream=stream)          # warm-up (captures the graph)
+        barrier()
+        ms = []
+        for k in range(2):
+            c3.set_state(T3, P3, y3, stream=stream)
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c3.solve_steps(wl3.dt, wl3.n_steps, stream=stream)
+            e1.record(stream)
+            barrier()
+            ms.append(e0.elapsed_time(e1))
+        st3 = c3.get_stats(stream=stream)
+        c3.close()
+        t3 = min(ms)
+        out["batching_50k"] = {
+            "value": n3 * wl3.n_steps / (t3 / 1e3), "unit": "cells/s (cell-steps per second)",
+            "ms_per_graph": t3, "cells": n3, "steps_per_graph": wl3.n_steps,
+            "form": "persistent work queue, 6 x 600 s steps captured in one CUDA graph, per-cell photolysis, FP64",
+            "autotuned": {"cells_per_block": w, "blocks_per_sm": b},
+            "integrator_steps_last_600s": {"min": int(st3["steps"].min()), "median": float(np.median(st3["steps"])),
+                                           "max": int(st3["steps"].max())},
+            "cells_ok": int(np.sum(st3["status"] == 0))}
+        wl5 = synth.workload_adjoint(args.adjoint_cells)
+        n5 = wl5.cells.n_cells
+        c5 = chemgpu.Cells(mech, n5, rtol=wl5.rtol, atol=wl5.atol, driver="persistent", record_adjoint=True)
+        T5, P5 = torch.from_numpy(wl5.cells.T).to(dev), torch.from_numpy(wl5.cells.P).to(dev)
+        y5 = torch.from_numpy(wl5.cells.y).to(dev)
+        w5 = torch.from_numpy(synth.loss_weights(wl5.mech.n_species, n5)).to(dev)
+        gth = torch.zeros(wl5.mech.n_reactions, dtype=torch.float64, device=dev)
+        gy0 = torch.zeros_like(y5)
+        fwd, bwd = [], []
+        for rep in range(3):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            flush.fill_(float(rep))
+            e[0].record(stream)
+            c5.set_state(T5, P5, y5, stream=stream)
+            for _ in range(wl5.n_steps):
+                c5.solve_step(wl5.dt, stream=stream)
+            e[1].record(stream)
+            _, _, n_bad = c5.sensitivity(w5, gth, gy0, stream=stream)
+            if ws > 1:                    # the one exchange: dL/dtheta summed over ranks in rank order
+                gth = shard.reduce_theta_grad(gth)
+            e[2].record(stream)
+            barrier()
+            if rep > 0:
+                fwd.append(e[0].elapsed_time(e[1]))
+                bwd.append(e[1].elapsed_time(e[2]))
+        c5.close()
+        tf, tb = min(fwd), min(bwd)
+        out["adjoint_2k"] = {
+            "value": n5 / ((tf + tb) / 1e3), "unit": "cells/s (4-step forward with tape + discrete adjoint)",
+            "forward_ms": tf, "backward_ms": tb, "cells": n5, "steps": wl5.n_steps, "cells_bad": n_bad,
+            "form": "persistent forward recording the tape; one warp per cell backward through transposed sparse LU"}
+        return out
 
     def time_form(lu_precision, driver, steps, warmup):
         cells = chemgpu.Cells(mech, C, rtol=wl.rtol, atol=wl.atol, lu_precision=lu_precision, driver=driver)
@@ -203,6 +309,7 @@ def run_gpu(args):
     with ClockSampler(local) as clk:
         for name in forms:
             res[name] = time_form(*FORMS[name], args.steps, args.warmup)
+        extras = {} if (args.no_e2e or args.no_extras) else time_extras(chemgpu, mech, dev, stream, flush, barrier)
     clocks = clk.summary()
     if args.no_e2e:          # profiling runs: timed kernels only, no report line
         return 0
@@ -256,6 +363,14 @@ def run_gpu(args):
                      + np.sum(st["solves"]) * info["flops_solve"])
     kernel_ms = statistics.mean(ms_head)
     achieved = flops(st_head) / (kernel_ms / 1e3)
+    hbm_peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            hbm_peak = float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        hbm_peak = 6800.0
+    hbm_bytes = C * (2 * S * 8 + 2 * 8 + 48)     # y in and out, T and P, per-cell statistics
+    hbm_achieved = hbm_bytes / (kernel_ms / 1e3) / 1e9
     if rank == 0:
         cpu_rate, cpu_el = (None, None)
         if not args.no_cpu_baseline:
@@ -278,13 +393,18 @@ def run_gpu(args):
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(C * (S + 2) * 8),
                     "d2h_bytes_per_step": int(C * S * 8), "form": "persistent FP64, pinned host buffers through the C ABI"},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_NOMINAL, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_NOMINAL, "traffic": _profiled_traffic(),
                          "kernel": "solve_kernel<double,3,staged> (FP64 pipe)",
                          "note": "peak = 152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM x 2 flops (derived); "
-                                 "algorithmic FP64 flops from per-cell counters"},
+                                 "algorithmic FP64 flops from per-cell counters; traffic = ncu DRAM bytes per launch "
+                                 "(null when the kernel changed since the capture)"},
+            "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
+                    "bytes_per_cell": hbm_bytes // C, "note": "algorithmic HBM bytes of the same kernel; "
+                    "peak = measured copy bandwidth; does not bind"},
             "gpu_launches": args.steps,
             "clocks": clocks,
         }
+        line.update(extras)
         if cpu_rate is not None:
             line["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": f"first {args.cpu_sample} of the {C} cells, single thread, {cpu_el:.1f} s"}
@@ -307,6 +427,9 @@ def main():
     ap.add_argument("--cells", type=int, default=N_CELLS, help="cells per GPU (the benchmark uses 10,000)")
     ap.add_argument("--forms", default="persistent64,plain64,chosen", help="comma list of " + ",".join(FORMS))
     ap.add_argument("--no-e2e", action="store_true", help="profiling: run the timed forms only, print nothing")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batching and adjoint measurements")
+    ap.add_argument("--batch-cells", type=int, default=50_000, help="cells of the batching measurement")
+    ap.add_argument("--adjoint-cells", type=int, default=2_048, help="cells of the adjoint measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

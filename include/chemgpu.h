@@ -45,6 +45,8 @@ extern "C" {
 #define CHEM_MAX_PROD 8
 #define CHEM_MAX_SPECIES 128
 #define CHEM_MAX_TAPE_ROWS (1 << 20)   /* largest chem_opts.tape_steps */
+#define CHEM_MAX_GRAPH_STEPS 4096      /* largest n_steps of chem_solve_steps */
+#define CHEM_AUTOTUNE_SAMPLE 16384     /* default sample of chem_autotune */
 
 /* error codes (negative returns) */
 #define CHEM_EINVAL (-1)   /* bad argument or mechanism table */
@@ -168,6 +170,26 @@ int chem_cells_set_theta(chem_cells *cells, const double *theta, int32_t mem, vo
  * afresh and the new state replaces the old.  Asynchronous; per-cell outcomes
  * are read with chem_get_stats.  Errors: CHEM_EINVAL, CHEM_ESTATE, CHEM_ECUDA. */
 int chem_solve_step(chem_cells *cells, double dt, void *stream);
+/* n_steps consecutive chem_solve_step calls of dt (1..CHEM_MAX_GRAPH_STEPS) as
+ * one CUDA graph launch on stream: the per-step queue resets and solve
+ * kernels are captured once, on an internal stream, and the graph is re-used
+ * while n_steps, dt, the launch shape and the photolysis/theta sources
+ * (per-cell or mechanism J, theta set or not) stay the same; any change
+ * re-captures it.  The inputs it reads (T, P, y, J, theta) are the batch's
+ * own buffers, so set_state / set_photolysis / set_theta between launches
+ * take effect.  Results are identical to n_steps chem_solve_step calls.
+ * Asynchronous.  Errors: CHEM_EINVAL, CHEM_ESTATE, CHEM_ECUDA. */
+int chem_solve_steps(chem_cells *cells, double dt, int32_t n_steps, void *stream);
+/* Choose the launch shape of the batch by measurement: every cells-per-block
+ * w the shared memory allows and, for the persistent driver, every resident
+ * block count 1..occupancy(w) is timed (CUDA events, best of two) on a scratch
+ * copy of the first n_sample cells (0: min(n_cells, CHEM_AUTOTUNE_SAMPLE))
+ * integrated over dt; the fastest shape becomes the batch's cells_per_block /
+ * blocks_per_sm and is written to the outputs (each may be NULL).  The
+ * batch's state is not touched.  Needs set_state.  Allocates scratch and
+ * synchronises.  Errors: CHEM_EINVAL, CHEM_ESTATE, CHEM_ENOMEM, CHEM_ECUDA. */
+int chem_autotune(chem_cells *cells, double dt, int64_t n_sample, int32_t *cells_per_block,
+                  int32_t *blocks_per_sm);
 
 /* Copy the state y[n_species][n_cells] out (synchronises stream when mem is
  * CHEM_MEM_HOST). */

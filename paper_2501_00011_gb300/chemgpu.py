@@ -27,7 +27,8 @@ STATUS = {0: "OK", 1: "MAX_STEPS", 2: "H_TOO_SMALL", 3: "ERR_FAIL", 4: "CONV_FAI
 EXPORTS = ["chem_opts_default", "chem_mechanism_create", "chem_mechanism_destroy",
            "chem_mechanism_info", "chem_mechanism_structure", "chem_cells_create",
            "chem_cells_destroy", "chem_cells_set_state", "chem_cells_set_photolysis",
-           "chem_cells_set_theta", "chem_solve_step", "chem_get_state", "chem_get_stats",
+           "chem_cells_set_theta", "chem_solve_step", "chem_solve_steps", "chem_autotune",
+           "chem_get_state", "chem_get_stats",
            "chem_eval_deriv", "chem_eval_newton_solve", "chem_solve_step_noalloc", "chem_sensitivity",
            "chem_get_tape", "chem_last_error"]
 
@@ -95,6 +96,8 @@ def load(path: str | None = None):
         L.chem_eval_newton_solve.argtypes = [V, ct.c_double, V, V, V, ct.c_int32, V]
         L.chem_solve_step_noalloc.argtypes = [V, ct.c_int64, V, V, V, V, V, V, ct.c_double, V, V]
         L.chem_sensitivity.argtypes = [V, V, V, V, ct.c_int32, V]
+        L.chem_solve_steps.argtypes = [V, ct.c_double, ct.c_int32, V]
+        L.chem_autotune.argtypes = [V, ct.c_double, ct.c_int64, V, V]
         L.chem_get_tape.argtypes = [V, ct.c_int64, V, V, V, V, ct.c_int32, V, V]
         L.chem_last_error.restype = ct.c_char_p
         for name in EXPORTS:
@@ -244,6 +247,16 @@ class Cells:
     def solve_step(self, dt: float, stream=None):
         _check(load().chem_solve_step(self._h, float(dt), _stream_ptr(stream)), "chem_solve_step")
 
+    def solve_steps(self, dt: float, n_steps: int, stream=None):
+        """n_steps consecutive steps of dt as one captured CUDA graph launch."""
+        _check(load().chem_solve_steps(self._h, float(dt), int(n_steps), _stream_ptr(stream)), "chem_solve_steps")
+
+    def autotune(self, dt: float, n_sample: int = 0):
+        """Measure launch shapes on a sample of the current state; returns (cells_per_block, blocks_per_sm)."""
+        w, b = ct.c_int32(0), ct.c_int32(0)
+        _check(load().chem_autotune(self._h, float(dt), int(n_sample), ct.byref(w), ct.byref(b)), "chem_autotune")
+        return w.value, b.value
+
     def get_state(self, out=None, stream=None):
         """Returns y [S, C]; into `out` (tensor/array) if given, else a new numpy array."""
         if out is None:
@@ -341,29 +354,65 @@ def _autograd_function():
     class ChemSolveFn(torch.autograd.Function):
         """y_final = solve(theta, y0) over n_steps solve_step calls; backward runs the
         discrete adjoint (chem_sensitivity).  theta [R] and y0 [S, C] are float64
-        tensors on the batch's device; T, P [C] likewise."""
+        tensors on the batch's device; T, P [C] likewise.
+
+        Step checkpointing: the forward keeps the state after every step
+        (S x C doubles each).  The backward differentiates the whole recorded
+        tape when it fits; when it does not (a cell's tape overflowed) or when
+        checkpoint=True, it re-runs the steps one at a time from the kept
+        states, last first, each with a fresh tape, and chains the adjoint
+        through them: the tape then only has to hold one step.  The batch must
+        not be used otherwise between the forward and the backward."""
 
         @staticmethod
-        def forward(ctx, theta, y0, cells, T, P, dt, n_steps):
-            cells.set_theta(theta.detach().contiguous())
-            cells.set_state(T, P, y0.detach().contiguous())
-            for _ in range(int(n_steps)):
-                cells.solve_step(dt)
-            y = torch.empty_like(y0)
-            cells.get_state(out=y)
-            ctx.cells = cells
+        def forward(ctx, theta, y0, cells, T, P, dt, n_steps, checkpoint):
+            n_steps = int(n_steps)
+            th = theta.detach().contiguous()
+            cells.set_theta(th)
+            states = [y0.detach().contiguous()]
+            if checkpoint:
+                # one tape per step: start every step afresh from the kept state
+                for k in range(n_steps):
+                    cells.set_state(T, P, states[-1])
+                    cells.solve_step(dt)
+                    states.append(cells.get_state(out=torch.empty_like(y0)))
+            else:
+                cells.set_state(T, P, states[0])
+                for k in range(n_steps):
+                    cells.solve_step(dt)
+                    states.append(cells.get_state(out=torch.empty_like(y0)))
+            ctx.cells, ctx.T, ctx.P, ctx.dt, ctx.theta = cells, T, P, dt, th
+            ctx.states, ctx.per_step = states, bool(checkpoint)
             ctx.R = theta.numel()
-            return y
+            return states[-1].clone()
 
         @staticmethod
         def backward(ctx, gy):
             import torch as _t
+            c = ctx.cells
+            c.set_theta(ctx.theta)          # the backward evaluates rates with the forward's theta
             gth = _t.zeros(ctx.R, dtype=_t.float64, device=gy.device)
-            gy0 = _t.zeros_like(gy)
-            _, _, n_bad = ctx.cells.sensitivity(gy.contiguous(), gth, gy0)
-            if n_bad:
-                raise ChemError(f"{n_bad} cells have no sensitivity (tape overflow or failed solve)")
-            return gth, gy0, None, None, None, None, None
+            lam = gy.contiguous()
+            n_steps = len(ctx.states) - 1
+            if not ctx.per_step:
+                gy0 = _t.zeros_like(gy)
+                _, _, n_bad = c.sensitivity(lam, gth, gy0)
+                if n_bad == 0:
+                    return gth, gy0, None, None, None, None, None, None
+            # re-run step k from its kept state (the last step's tape is current
+            # in per-step mode), then carry lambda back through it
+            g_k = _t.empty_like(gth)
+            for k in range(n_steps - 1, -1, -1):
+                if not (ctx.per_step and k == n_steps - 1):
+                    c.set_state(ctx.T, ctx.P, ctx.states[k])
+                    c.solve_step(ctx.dt)
+                lam_prev = _t.empty_like(lam)
+                _, _, n_bad = c.sensitivity(lam, g_k, lam_prev)
+                if n_bad:
+                    raise ChemError(f"{n_bad} cells have no sensitivity for step {k} (tape overflow or failed solve)")
+                gth += g_k
+                lam = lam_prev
+            return gth, lam, None, None, None, None, None, None
 
     return ChemSolveFn
 
@@ -371,9 +420,13 @@ def _autograd_function():
 _FN = None
 
 
-def solve_with_grad(cells: Cells, theta, y0, T, P, dt: float, n_steps: int = 1):
-    """Differentiable multi-cell solve (cells must be created with record_adjoint=True)."""
+def solve_with_grad(cells: Cells, theta, y0, T, P, dt: float, n_steps: int = 1, checkpoint: bool = False):
+    """Differentiable multi-cell solve (cells must be created with record_adjoint=True).
+
+    checkpoint=True records one step at a time (the tape holds one step; the
+    backward re-runs steps from kept states); otherwise the backward falls back
+    to that only when the whole tape overflowed."""
     global _FN
     if _FN is None:
         _FN = _autograd_function()
-    return _FN.apply(theta, y0, cells, T, P, dt, n_steps)
+    return _FN.apply(theta, y0, cells, T, P, dt, n_steps, checkpoint)

@@ -23,6 +23,12 @@ struct chem_cells {
   int *tape_kq = nullptr, *tape_n = nullptr, *tape_bad = nullptr, *tape_rows = nullptr;
   double *tape_val = nullptr;
   int tape_cap = 0, row_cap = 0;
+  // chem_solve_steps: the captured graph and what it was captured for
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0, graph_w = 0, graph_bps = 0;
+  double graph_dt = 0.0;
+  bool graph_J = false, graph_theta = false;
   double *ytape = nullptr, *gcell = nullptr, *dLdy = nullptr, *dLdy0 = nullptr, *dLdtheta = nullptr;
 };
 
@@ -205,6 +211,8 @@ int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *o
 
 void chem_cells_destroy(chem_cells *c) {
   if (!c) return;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   cudaFree(c->T);
   cudaFree(c->P);
   cudaFree(c->y);
@@ -272,13 +280,11 @@ int chem_cells_set_theta(chem_cells *c, const double *theta, int32_t mem, void *
   return 0;
 }
 
-int chem_solve_step(chem_cells *c, double dt, void *stream) {
-  g_err.clear();
-  if (!c) return fail(CHEM_EINVAL, "NULL argument");
-  if (!(dt > 0.0) || !(dt < 1e300)) return fail(CHEM_EINVAL, "dt must be positive and finite");
-  if (!c->have_state) return fail(CHEM_ESTATE, "solve_step before set_state");
-  if (c->n == 0) return 0;
-  cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+CellsDev solve_dev(chem_cells *c) {
   CellsDev cd{};
   cd.n_cells = c->n;
   cd.T = c->T;
@@ -297,23 +303,196 @@ int chem_solve_step(chem_cells *c, double dt, void *stream) {
   cd.tape_bad = c->tape_bad;
   cd.tape_cap = c->tape_cap;
   cd.row_cap = c->row_cap;
+  return cd;
+}
+
+LaunchCfg launch_cfg(const chem_opts &o, double dt) {
+  LaunchCfg cfg;
+  cfg.lu_precision = o.lu_precision;
+  cfg.driver = o.driver;
+  cfg.warps_per_block = o.cells_per_block;
+  cfg.blocks_per_sm = o.blocks_per_sm;
+  cfg.rtol = o.rtol;
+  cfg.atol = o.atol;
+  cfg.dt = dt;
+  cfg.max_order = o.max_order;
+  cfg.max_steps = o.max_steps;
+  return cfg;
+}
+
+// One solve of every cell on stream s: queue reset (persistent driver) and
+// the solve kernel.  Stream-ordered calls only, so it can be captured.
+cudaError_t enqueue_solve(chem_cells *c, double dt, cudaStream_t s) {
+  CellsDev cd = solve_dev(c);
   if (c->opts.driver == CHEM_DRIVER_PERSISTENT) {
     cudaError_t e = cudaMemsetAsync(c->queue, 0, sizeof(long long), s);
-    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+    if (e != cudaSuccess) return e;
     cd.queue = c->queue;
   }
-  LaunchCfg cfg;
-  cfg.lu_precision = c->opts.lu_precision;
-  cfg.driver = c->opts.driver;
-  cfg.warps_per_block = c->opts.cells_per_block;
-  cfg.blocks_per_sm = c->opts.blocks_per_sm;
-  cfg.rtol = c->opts.rtol;
-  cfg.atol = c->opts.atol;
-  cfg.dt = dt;
-  cfg.max_order = c->opts.max_order;
-  cfg.max_steps = c->opts.max_steps;
-  cudaError_t e = launch_solve(c->mech->m.dev, cd, cfg, s);
+  return launch_solve(c->mech->m.dev, cd, launch_cfg(c->opts, dt), s);
+}
+
+int check_solve_args(chem_cells *c, double dt) {
+  if (!c) return fail(CHEM_EINVAL, "NULL argument");
+  if (!(dt > 0.0) || !(dt < 1e300)) return fail(CHEM_EINVAL, "dt must be positive and finite");
+  if (!c->have_state) return fail(CHEM_ESTATE, "solve before set_state");
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int chem_solve_step(chem_cells *c, double dt, void *stream) {
+  g_err.clear();
+  if (int rc = check_solve_args(c, dt)) return rc;
+  if (c->n == 0) return 0;
+  cudaError_t e = enqueue_solve(c, dt, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
+  return 0;
+}
+
+int chem_solve_steps(chem_cells *c, double dt, int32_t n_steps, void *stream) {
+  g_err.clear();
+  if (int rc = check_solve_args(c, dt)) return rc;
+  if (n_steps < 1 || n_steps > CHEM_MAX_GRAPH_STEPS) return fail(CHEM_EINVAL, "n_steps out of range");
+  if (c->n == 0) return 0;
+  cudaError_t e;
+  const bool same = c->graph && c->graph_steps == n_steps && c->graph_dt == dt &&
+                    c->graph_w == c->opts.cells_per_block && c->graph_bps == c->opts.blocks_per_sm &&
+                    c->graph_J == c->use_J && c->graph_theta == c->use_theta;
+  if (!same) {
+    if (c->graph) {
+      cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+    }
+    if (!c->capture_stream && (e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "capture stream");
+    // relaxed mode: the launch path may query and set kernel attributes while capturing
+    if ((e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+      return cuda_fail(e, "begin capture");
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < n_steps && le == cudaSuccess; ++k) le = enqueue_solve(c, dt, c->capture_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->capture_stream, &g);
+    if (le != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(le, "capture of the solve steps");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->graph = nullptr;
+      return cuda_fail(e, "graph instantiate");
+    }
+    c->graph_steps = n_steps;
+    c->graph_dt = dt;
+    c->graph_w = c->opts.cells_per_block;
+    c->graph_bps = c->opts.blocks_per_sm;
+    c->graph_J = c->use_J;
+    c->graph_theta = c->use_theta;
+  }
+  if ((e = cudaGraphLaunch(c->graph, (cudaStream_t)stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
+  return 0;
+}
+
+int chem_autotune(chem_cells *c, double dt, int64_t n_sample, int32_t *cells_per_block, int32_t *blocks_per_sm) {
+  g_err.clear();
+  if (int rc = check_solve_args(c, dt)) return rc;
+  if (n_sample < 0) return fail(CHEM_EINVAL, "n_sample must be >= 0");
+  if (c->n == 0) return 0;
+  const int64_t ns = (n_sample == 0 || n_sample > c->n) ? (c->n < CHEM_AUTOTUNE_SAMPLE ? c->n : CHEM_AUTOTUNE_SAMPLE) : n_sample;
+  const MechDev &M = c->mech->m.dev;
+  const size_t S = (size_t)M.S, NP = (size_t)M.n_phot;
+  const int prec = c->opts.lu_precision, drv = c->opts.driver;
+  // scratch copy of the first ns cells with stride ns
+  double *T = nullptr, *P = nullptr, *y = nullptr, *y0 = nullptr, *J = nullptr;
+  chem_cell_stats *st = nullptr;
+  long long *q = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t s = nullptr;
+  int rc = 0;
+  cudaError_t e;
+  auto cleanup = [&]() {
+    cudaFree(T); cudaFree(P); cudaFree(y); cudaFree(y0); cudaFree(J); cudaFree(st); cudaFree(q);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+  };
+  if ((e = cudaMalloc(&T, ns * sizeof(double))) != cudaSuccess || (e = cudaMalloc(&P, ns * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&y, ns * S * sizeof(double))) != cudaSuccess || (e = cudaMalloc(&y0, ns * S * sizeof(double))) != cudaSuccess ||
+      (c->use_J && NP > 0 && (e = cudaMalloc(&J, ns * NP * sizeof(double))) != cudaSuccess) ||
+      (e = cudaMalloc(&st, ns * sizeof(chem_cell_stats))) != cudaSuccess ||
+      (e = cudaMalloc(&q, 4 * sizeof(long long))) != cudaSuccess) {
+    cleanup();
+    return fail(CHEM_ENOMEM, std::string("autotune scratch: ") + cudaGetErrorString(e));
+  }
+  if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess || (e = cudaEventCreate(&e0)) != cudaSuccess ||
+      (e = cudaEventCreate(&e1)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(T, c->T, ns * sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(P, c->P, ns * sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpy2DAsync(y0, ns * sizeof(double), c->y, c->n * sizeof(double), ns * sizeof(double), S,
+                             cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+      (J && (e = cudaMemcpy2DAsync(J, ns * sizeof(double), c->J, c->n * sizeof(double), ns * sizeof(double), NP,
+                                   cudaMemcpyDeviceToDevice, s)) != cudaSuccess) ||
+      (e = cudaMemsetAsync(q, 0, 4 * sizeof(long long), s)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "autotune setup");
+  }
+  CellsDev cd{};
+  cd.n_cells = ns;
+  cd.T = T;
+  cd.P = P;
+  cd.J = J;
+  cd.theta = c->use_theta ? c->theta : nullptr;
+  cd.y = y;
+  cd.stats = st;
+  cd.error = reinterpret_cast<int *>(q + 2);
+  const int wmax = max_warps_per_block(M, prec, drv);
+  float best = 0.0f;
+  int best_w = 0, best_b = 0;
+  for (int w = 1; w <= wmax && rc == 0; ++w) {
+    const int occ = occupancy(M, prec, drv, w);
+    if (occ < 1) continue;
+    const int nb = drv == CHEM_DRIVER_PERSISTENT ? occ : 1;
+    for (int b = 1; b <= nb && rc == 0; ++b) {
+      LaunchCfg cfg = launch_cfg(c->opts, dt);
+      cfg.warps_per_block = w;
+      cfg.blocks_per_sm = drv == CHEM_DRIVER_PERSISTENT ? b : 0;
+      float t_min = 0.0f;
+      for (int rep = 0; rep < 2; ++rep) {
+        if ((e = cudaMemcpyAsync(y, y0, ns * S * sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) break;
+        cd.queue = nullptr;
+        if (drv == CHEM_DRIVER_PERSISTENT) {
+          if ((e = cudaMemsetAsync(q, 0, sizeof(long long), s)) != cudaSuccess) break;
+          cd.queue = reinterpret_cast<int *>(q);
+        }
+        float ms = 0.0f;
+        if ((e = cudaEventRecord(e0, s)) != cudaSuccess || (e = launch_solve(M, cd, cfg, s)) != cudaSuccess ||
+            (e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+          break;
+        if (rep == 0 || ms < t_min) t_min = ms;
+      }
+      if (e != cudaSuccess) {
+        rc = cuda_fail(e, "autotune trial");
+        break;
+      }
+      if (best_w == 0 || t_min < best) {
+        best = t_min;
+        best_w = w;
+        best_b = cfg.blocks_per_sm;
+      }
+    }
+  }
+  cleanup();
+  if (rc) return rc;
+  if (best_w == 0) return fail(CHEM_EINVAL, "no launch shape fits on this device");
+  c->opts.cells_per_block = best_w;
+  c->opts.blocks_per_sm = best_b;
+  if (cells_per_block) *cells_per_block = best_w;
+  if (blocks_per_sm) *blocks_per_sm = best_b;
   return 0;
 }
 

@@ -123,6 +123,37 @@ def test_autograd_function_matches_sensitivity(cg):
     np.testing.assert_allclose(y0.grad.cpu().numpy(), gy0, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("mode", ["checkpoint", "overflow_fallback"])
+def test_step_checkpointing_matches_full_tape(cg, mode):
+    # per-step recording (forced, or the automatic fallback after a tape
+    # overflow) chains the adjoint through re-run steps: same gradients as
+    # one tape over all steps, up to the order of the theta sums
+    wl = synth.workload_adjoint(16)
+    dev = torch.device("cuda")
+    m = cg.Mechanism(wl.mech)
+    T = torch.from_numpy(wl.cells.T[:16].copy()).to(dev)
+    P = torch.from_numpy(wl.cells.P[:16].copy()).to(dev)
+    w = torch.from_numpy(synth.loss_weights(wl.mech.n_species, 16)).to(dev)
+    grads = []
+    for kind in ("full", mode):
+        tape = 400 if kind == "overflow_fallback" else 0
+        c = cg.Cells(m, 16, rtol=wl.rtol, atol=wl.atol, record_adjoint=True, tape_steps=tape)
+        theta = torch.zeros(wl.mech.n_reactions, dtype=torch.float64, device=dev, requires_grad=True)
+        y0 = torch.from_numpy(wl.cells.y[:, :16].copy()).to(dev).requires_grad_(True)
+        y = cg.solve_with_grad(c, theta, y0, T, P, wl.dt, wl.n_steps, checkpoint=(kind == "checkpoint"))
+        (w * y).sum().backward()
+        grads.append((y.detach().cpu().numpy(), theta.grad.cpu().numpy(), y0.grad.cpu().numpy()))
+        if kind == "overflow_fallback":
+            c.set_state(T, P, y0.detach())
+            for _ in range(wl.n_steps):
+                c.solve_step(wl.dt)
+            assert c.sensitivity(w.cpu().numpy())[2] > 0      # the whole tape does not fit
+    (ya, ga, ha), (yb, gb, hb) = grads
+    assert np.array_equal(ya, yb)
+    np.testing.assert_allclose(gb, ga, rtol=1e-11, atol=1e-14 * np.abs(ga).max())
+    np.testing.assert_allclose(hb, ha, rtol=1e-11, atol=1e-14 * np.abs(ha).max())
+
+
 def test_tape_overflow_is_reported(cg):
     wl = synth.workload_adjoint(4)
     m = cg.Mechanism(wl.mech)
