@@ -114,7 +114,9 @@ typedef struct {
   int32_t max_steps;               /* default 5000 */
   int32_t lu_precision;            /* 64 (default) or 32: LU factor/solve in FP32 */
   int32_t driver;                  /* CHEM_DRIVER_* */
-  int32_t cells_per_block;         /* warps (= concurrent cells) per block; 0 = auto */
+  int32_t cells_per_block;         /* warps (= concurrent cells) per block; 0 = auto: 1 for the
+                                      plain driver, the most resident cells per SM for the
+                                      persistent one (chem_autotune measures instead) */
   int32_t blocks_per_sm;           /* persistent driver: resident blocks per SM; 0 = auto */
   int32_t record_adjoint;          /* 1: record the tape for chem_sensitivity (needs lu_precision 64) */
   int32_t tape_steps;              /* tape rows per cell: states stored, one per solve, per

@@ -400,7 +400,9 @@ def _autograd_function():
                 if n_bad == 0:
                     return gth, gy0, None, None, None, None, None, None
             # re-run step k from its kept state (the last step's tape is current
-            # in per-step mode), then carry lambda back through it
+            # in per-step mode), then carry lambda back through it; a failed
+            # whole-tape attempt above has written partial sums into gth
+            gth.zero_()
             g_k = _t.empty_like(gth)
             for k in range(n_steps - 1, -1, -1):
                 if not (ctx.per_step and k == n_steps - 1):

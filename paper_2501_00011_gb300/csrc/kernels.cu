@@ -39,8 +39,6 @@ constexpr double CRDOWN = 0.3, RDIV = 2.0, NLSCOEF = 0.1, DGMAX = 0.3, THRESH = 
 constexpr int MSBP = 20, MXNEF = 7, MXNCF = 10;
 constexpr double ETA_CF = 0.25, ETA_MXF = 0.2, ETA_CST_SAFETY = 0.9, ETA_CST_MIN = 0.1, STRETCH = 1e-3;
 constexpr double K_BOLTZMANN = 1.380649e-23;
-constexpr int PF_GLOBAL = 8;            // passes prefetched ahead when ops come from L2
-constexpr int PF_SHARED = 2;            // ... and from shared memory
 constexpr long TMA_WAIT_LIMIT = 1L << 22;
 
 struct SolveParams {
@@ -94,31 +92,30 @@ __device__ __forceinline__ float lds(float *, uint32_t a) {
 __device__ __forceinline__ void sts(uint32_t a, double v) { asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory"); }
 __device__ __forceinline__ void sts(uint32_t a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory"); }
 
-// Run a warp program (byte-offset ops, see internal.h) over the work array W.
-template <typename T, bool NEG, bool SMEM, int PF>
+// Run a warp program (byte-offset ops, see internal.h) over the work array W,
+// the next pass's op prefetched.  The loop is deliberately not unrolled and
+// prefetches one pass only: the solve kernel is bound by instruction fetch as
+// much as by latency, and deeper prefetch (unrolled copies of the pass body at
+// every call site) measured 17% slower on the persistent driver and 33% on the
+// plain one.  Calls out of line measured slower still (register save/restore).
+template <typename T, bool NEG, bool SMEM>
 __device__ __forceinline__ void run_ops(const ushort4 *ops, const int np, T *W, const int lane) {
   const uint32_t wb = smem_addr(W);
   T *const tag = nullptr;
   ops += lane;
-  uint2 buf[PF];   // packed ops: x = t | a << 16, y = b | c << 16
-#pragma unroll
-  for (int i = 0; i < PF; ++i) buf[i] = (i < np) ? ld_op<SMEM>(ops + i * WARP) : make_uint2(0, 0);
-  for (int p0 = 0; p0 < np; p0 += PF) {
-#pragma unroll
-    for (int i = 0; i < PF; ++i) {
-      const int p = p0 + i;
-      if (p >= np) break;
-      const uint2 op = buf[i];
-      if (p + PF < np) buf[i] = ld_op<SMEM>(ops + (size_t)(p + PF) * WARP);
-      const uint32_t ot = op.x & 0xffff, oa = op.x >> 16, ob = op.y & 0xffff, oc = op.y >> 16;
-      if (oc == DEV_RECIP) {
-        sts(wb + ot, -lu_recip(lds(tag, wb + oa)));
-      } else {
-        const T a = lds(tag, wb + oa), b = lds(tag, wb + ob), c = lds(tag, wb + oc);
-        sts(wb + ot, NEG ? fma(-a, b, c) : fma(a, b, c));
-      }
-      __syncwarp();
+  uint2 next = np > 0 ? ld_op<SMEM>(ops) : make_uint2(0, 0);   // packed: x = t | a << 16, y = b | c << 16
+#pragma unroll 1
+  for (int p = 0; p < np; ++p) {
+    const uint2 op = next;
+    if (p + 1 < np) next = ld_op<SMEM>(ops + (size_t)(p + 1) * WARP);
+    const uint32_t ot = op.x & 0xffff, oa = op.x >> 16, ob = op.y & 0xffff, oc = op.y >> 16;
+    if (oc == DEV_RECIP) {
+      sts(wb + ot, -lu_recip(lds(tag, wb + oa)));
+    } else {
+      const T a = lds(tag, wb + oa), b = lds(tag, wb + ob), c = lds(tag, wb + oc);
+      sts(wb + ot, NEG ? fma(-a, b, c) : fma(a, b, c));
     }
+    __syncwarp();
   }
 }
 
@@ -182,6 +179,57 @@ __device__ __forceinline__ const X *tab(const Tabs &tb, int off) {
   return reinterpret_cast<const X *>(tb.base + off);
 }
 
+// Phase bodies that touch only the cell's shared-memory arrays and the tables.
+
+// a2: r_j = k~_j prod y, then f = the f program, from y in Wd[Y]
+template <bool STAGED>
+__device__ __forceinline__ void f_core(const MechDev &M, const unsigned char *tbase, double *Wd, const int lane) {
+  unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
+  const uint2 *slots = reinterpret_cast<const uint2 *>(tbase + M.tab.rx_slots);
+  for (int j = lane; j < M.R; j += WARP) {
+    const uint2 sl = slots[j];
+    double r = Wd[M.d_KT + j] * at<double>(wd, sl.x & 0xffff);
+    if (M.max_reac > 1) r *= at<double>(wd, sl.x >> 16);
+    if (M.max_reac > 2) r *= at<double>(wd, sl.y & 0xffff);
+    Wd[M.d_RT + j] = r;
+  }
+  __syncwarp();
+  run_ops<double, false, STAGED>(reinterpret_cast<const ushort4 *>(tbase + M.tab.f_ops), M.f_npass, Wd, lane);
+}
+
+// a3-a5: M = I - c J(y) in the LU slots from y in Wd[Y], then factor
+template <typename T>
+__device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *tbase, const int prec, double *Wd, T *WL,
+                                      const double c, const int lane) {
+  for (int i = lane; i < M.m_clear; i += WARP) WL[i] = (T)0;
+  __syncwarp();
+  unsigned char *wl = reinterpret_cast<unsigned char *>(WL);
+  unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
+  const int *diag = reinterpret_cast<const int *>(tbase + M.tab.lu_diag);
+  const int *prx = reinterpret_cast<const int *>(tbase + M.tab.pair_rx);
+  const unsigned *pother = reinterpret_cast<const unsigned *>(tbase + M.tab.pair_other);
+  for (int k = lane; k < M.S; k += WARP) at<T>(wl, diag[k]) = (T)1;
+  const double mc = -c;
+  for (int pr = lane; pr < M.n_pairs; pr += WARP) {
+    const int j = prx[pr];
+    const unsigned o = pother[pr];
+    double p = mc * Wd[M.d_KT + j];
+    if (M.max_reac > 1) p *= at<double>(wd, o & 0xffff);
+    if (M.max_reac > 2) p *= at<double>(wd, o >> 16);
+    WL[M.L_P + pr] = (T)p;
+  }
+  __syncwarp();
+  run_ops<T, false, false>(M.m_ops[prec], M.m_npass, WL, lane);
+  run_ops<T, false, false>(M.lu_ops[prec], M.lu_npass, WL, lane);
+}
+
+// a5: forward and backward substitution on the vector in WL[X]
+template <typename T, bool STAGED>
+__device__ __forceinline__ void solve_core(const MechDev &M, const unsigned char *tbase, T *WL, const int lane) {
+  run_ops<T, false, STAGED>(reinterpret_cast<const ushort4 *>(tbase + M.tab.fwd_ops), M.fwd_npass, WL, lane);
+  run_ops<T, true, STAGED>(reinterpret_cast<const ushort4 *>(tbase + M.tab.bwd_ops), M.bwd_npass, WL, lane);
+}
+
 template <typename T, int KS, bool STAGED>
 struct Cell {
   const MechDev &M;
@@ -235,16 +283,7 @@ struct Cell {
     for (int k = 0; k < KS; ++k)
       if (own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
     __syncwarp();
-    unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
-    for (int j = lane; j < M.R; j += WARP) {
-      const uint2 sl = tab<uint2>(tb, M.tab.rx_slots)[j];
-      double r = Wd[M.d_KT + j] * at<double>(wd, sl.x & 0xffff);
-      if (M.max_reac > 1) r *= at<double>(wd, sl.x >> 16);
-      if (M.max_reac > 2) r *= at<double>(wd, sl.y & 0xffff);
-      Wd[M.d_RT + j] = r;
-    }
-    __syncwarp();
-    run_ops<double, false, STAGED, STAGED ? PF_SHARED : PF_GLOBAL>(tab<ushort4>(tb, M.tab.f_ops), M.f_npass, Wd, lane);
+    f_core<STAGED>(M, tb.base, Wd, lane);
 #pragma unroll
     for (int k = 0; k < KS; ++k) f[k] = own[k] ? Wd[M.d_F + lane + WARP * k] : 0.0;
     __syncwarp();
@@ -255,23 +294,7 @@ struct Cell {
 #pragma unroll
     for (int k = 0; k < KS; ++k)
       if (own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
-    for (int i = lane; i < M.m_clear; i += WARP) WL[i] = (T)0;
-    __syncwarp();
-    unsigned char *wl = reinterpret_cast<unsigned char *>(WL);
-    unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
-    for (int k = lane; k < M.S; k += WARP) at<T>(wl, tab<int>(tb, M.tab.lu_diag)[k]) = (T)1;
-    const double mc = -c;
-    for (int pr = lane; pr < M.n_pairs; pr += WARP) {
-      const int j = tab<int>(tb, M.tab.pair_rx)[pr];
-      const unsigned o = tab<unsigned>(tb, M.tab.pair_other)[pr];
-      double p = mc * Wd[M.d_KT + j];
-      if (M.max_reac > 1) p *= at<double>(wd, o & 0xffff);
-      if (M.max_reac > 2) p *= at<double>(wd, o >> 16);
-      WL[M.L_P + pr] = (T)p;
-    }
-    __syncwarp();
-    run_ops<T, false, false, PF_GLOBAL>(M.m_ops[P.prec], M.m_npass, WL, lane);
-    run_ops<T, false, false, PF_GLOBAL>(M.lu_ops[P.prec], M.lu_npass, WL, lane);
+    mlu_core<T>(M, tb.base, P.prec, Wd, WL, c, lane);
   }
 
   // a5: x = M^{-1} b with the factored M
@@ -280,8 +303,7 @@ struct Cell {
     for (int k = 0; k < KS; ++k)
       if (own[k]) WL[M.L_X + pos[k]] = (T)b[k];
     __syncwarp();
-    run_ops<T, false, STAGED, STAGED ? PF_SHARED : PF_GLOBAL>(tab<ushort4>(tb, M.tab.fwd_ops), M.fwd_npass, WL, lane);
-    run_ops<T, true, STAGED, STAGED ? PF_SHARED : PF_GLOBAL>(tab<ushort4>(tb, M.tab.bwd_ops), M.bwd_npass, WL, lane);
+    solve_core<T, STAGED>(M, tb.base, WL, lane);
 #pragma unroll
     for (int k = 0; k < KS; ++k) x[k] = own[k] ? (double)WL[M.L_X + pos[k]] : 0.0;
     __syncwarp();
@@ -784,7 +806,7 @@ __device__ bool stage_tables(const unsigned char *blob, int bytes, unsigned char
 }
 
 template <typename T, int KS, bool STAGED, bool REC>
-__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const MechDev M, const CellsDev C, const SolveParams P) {
+__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const __grid_constant__ MechDev M, const CellsDev C, const SolveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t tma_bar;
   const int lane = threadIdx.x & (WARP - 1);
@@ -820,7 +842,7 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const
 // Diagnostic: per cell, f(y) (mode 0) or x = (I - c J(y))^{-1} b (mode 1),
 // using the same device routines as the solve.
 template <typename T, int KS>
-__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) probe_kernel(const MechDev M, const CellsDev C, const SolveParams P,
+__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) probe_kernel(const __grid_constant__ MechDev M, const CellsDev C, const SolveParams P,
                                                                   int mode, double c, const double *yin, const double *bin,
                                                                   double *out) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1046,8 +1068,8 @@ __device__ __forceinline__ void jt_and_theta(const MechDev &M, double *Wd, const
   for (int k = 0; k < KS; ++k)
     if (own[k]) Wd[M.a_MU + lane + WARP * k] = v[k];
   __syncwarp();
-  run_ops<double, false, false, PF_GLOBAL>(M.nudot_ops, M.nudot_npass, Wd, lane);
-  run_ops<double, false, false, PF_GLOBAL>(M.jt_ops, M.jt_npass, Wd, lane);
+  run_ops<double, false, false>(M.nudot_ops, M.nudot_npass, Wd, lane);
+  run_ops<double, false, false>(M.jt_ops, M.jt_npass, Wd, lane);
   for (int j = lane; j < M.R; j += WARP) Wd[M.a_G + j] = fma(scale * Wd[M.d_RT + j], Wd[M.a_NM + j], Wd[M.a_G + j]);
 #pragma unroll
   for (int k = 0; k < KS; ++k) out[k] = own[k] ? Wd[M.a_JTM + lane + WARP * k] : 0.0;
@@ -1146,8 +1168,8 @@ __device__ void backward_cell(const MechDev &M, const CellsDev &C, const AdjDev 
       for (int k = 0; k < KS; ++k)
         if (cl.own[k]) WL[M.L_X + cl.pos[k]] = lamd[k];
       __syncwarp();
-      run_ops<double, true, false, PF_GLOBAL>(M.fwdT_ops, M.fwdT_npass, WL, lane);
-      run_ops<double, false, false, PF_GLOBAL>(M.bwdT_ops, M.bwdT_npass, WL, lane);
+      run_ops<double, true, false>(M.fwdT_ops, M.fwdT_npass, WL, lane);
+      run_ops<double, false, false>(M.bwdT_ops, M.bwdT_npass, WL, lane);
 #pragma unroll
       for (int k = 0; k < KS; ++k) g[k] = cl.own[k] ? ss * WL[M.L_X + cl.pos[k]] : 0.0;
       __syncwarp();
@@ -1204,7 +1226,7 @@ __device__ void backward_cell(const MechDev &M, const CellsDev &C, const AdjDev 
 }
 
 template <int KS>
-__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) adjoint_kernel(const MechDev M, const CellsDev C, const AdjDev A,
+__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) adjoint_kernel(const __grid_constant__ MechDev M, const CellsDev C, const AdjDev A,
                                                                     const SolveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & (WARP - 1);
@@ -1287,12 +1309,17 @@ int occupancy(const MechDev &M, int lu_precision, int driver, int warps_per_bloc
 
 int best_warps_per_block(const MechDev &M, int lu_precision, int driver) {
   const int wmax = max_warps_per_block(M, lu_precision, driver);
+  // The plain driver runs one cell per block: a block retires only when its
+  // slowest cell does, and that tail costs more than the odd extra resident
+  // cell a larger block may fit (72/186, 10,000 cells: 49.6 ms at 1 cell per
+  // block against 64.1 ms at 11).
+  if (!staged_driver(driver)) return (wmax >= 1 && occupancy(M, lu_precision, driver, 1) >= 1) ? 1 : 0;
+  // The persistent driver stages the tables once per block: most resident
+  // cells per SM, ties to the larger block.
   int best_w = 0, best_cells = 0;
   for (int w = 1; w <= wmax; ++w) {
     const int cells = w * occupancy(M, lu_precision, driver, w);
-    // most resident cells per SM; ties go to the larger block when the tables
-    // are staged per block, else to the smaller block (blocks retire independently)
-    if (cells > best_cells || (cells == best_cells && cells > 0 && staged_driver(driver))) {
+    if (cells > 0 && cells >= best_cells) {
       best_cells = cells;
       best_w = w;
     }

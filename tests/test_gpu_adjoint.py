@@ -123,6 +123,23 @@ def test_autograd_function_matches_sensitivity(cg):
     np.testing.assert_allclose(y0.grad.cpu().numpy(), gy0, rtol=1e-12, atol=0)
 
 
+def _rows_needed(cg, m, wl, T, P, y0, n_steps):
+    """Largest tape (rows) any cell needs for all n_steps, and for any single step."""
+    c = cg.Cells(m, y0.shape[1], rtol=wl.rtol, atol=wl.atol, record_adjoint=True)
+    c.set_state(T, P, y0)
+    states = [y0]
+    for _ in range(n_steps):
+        c.solve_step(wl.dt)
+        states.append(c.get_state())
+    rows_all = max(c.get_tape(k)[3].shape[0] for k in range(y0.shape[1]))
+    rows_one = 0
+    for s in states[:-1]:
+        c.set_state(T, P, s)
+        c.solve_step(wl.dt)
+        rows_one = max(rows_one, max(c.get_tape(k)[3].shape[0] for k in range(y0.shape[1])))
+    return rows_all, rows_one
+
+
 @pytest.mark.parametrize("mode", ["checkpoint", "overflow_fallback"])
 def test_step_checkpointing_matches_full_tape(cg, mode):
     # per-step recording (forced, or the automatic fallback after a tape
@@ -134,9 +151,15 @@ def test_step_checkpointing_matches_full_tape(cg, mode):
     T = torch.from_numpy(wl.cells.T[:16].copy()).to(dev)
     P = torch.from_numpy(wl.cells.P[:16].copy()).to(dev)
     w = torch.from_numpy(synth.loss_weights(wl.mech.n_species, 16)).to(dev)
+    tape_small = 0
+    if mode == "overflow_fallback":
+        rows_all, rows_one = _rows_needed(cg, m, wl, wl.cells.T[:16], wl.cells.P[:16], wl.cells.y[:, :16].copy(),
+                                          wl.n_steps)
+        assert rows_one < rows_all
+        tape_small = rows_one          # holds any one step, not all of them
     grads = []
     for kind in ("full", mode):
-        tape = 400 if kind == "overflow_fallback" else 0
+        tape = tape_small if kind == "overflow_fallback" else 0
         c = cg.Cells(m, 16, rtol=wl.rtol, atol=wl.atol, record_adjoint=True, tape_steps=tape)
         theta = torch.zeros(wl.mech.n_reactions, dtype=torch.float64, device=dev, requires_grad=True)
         y0 = torch.from_numpy(wl.cells.y[:, :16].copy()).to(dev).requires_grad_(True)
