@@ -119,6 +119,48 @@ __device__ __forceinline__ void run_ops(const ushort4 *ops, const int np, T *W, 
   }
 }
 
+// The same interpreter for programs in global memory, with the ops streamed
+// RING passes ahead by cp.async into a ring of RING x 256 bytes of shared
+// memory (ring: 8-byte aligned shared address).  Each lane copies and reads
+// only its own op slots, so cp.async.wait_group alone orders them.
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <typename T, bool NEG, int RING>
+__device__ __forceinline__ void run_ops_ring(const ushort4 *ops, const int np, T *W, const int lane, const uint32_t ring) {
+  const uint32_t wb = smem_addr(W);
+  T *const tag = nullptr;
+  const uint2 *g = reinterpret_cast<const uint2 *>(ops) + lane;
+  const uint32_t rb = ring + 8u * lane;
+#pragma unroll 1
+  for (int i = 0; i < RING - 1; ++i) {
+    if (i < np) cp_async8(rb + 256u * i, g + (size_t)i * WARP);
+    cp_async_commit();
+  }
+#pragma unroll 1
+  for (int p = 0; p < np; ++p) {
+    const int q = p + RING - 1;
+    if (q < np) cp_async8(rb + 256u * (q % RING), g + (size_t)q * WARP);
+    cp_async_commit();
+    cp_async_wait<RING - 1>();          // pass p's group has landed
+    uint32_t ox, oy;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(ox), "=r"(oy) : "r"(rb + 256u * (p % RING)) : "memory");
+    const uint32_t ot = ox & 0xffff, oa = ox >> 16, ob = oy & 0xffff, oc = oy >> 16;
+    if (oc == DEV_RECIP) {
+      sts(wb + ot, -lu_recip(lds(tag, wb + oa)));
+    } else {
+      const T a = lds(tag, wb + oa), b = lds(tag, wb + ob), c = lds(tag, wb + oc);
+      sts(wb + ot, NEG ? fma(-a, b, c) : fma(a, b, c));
+    }
+    __syncwarp();
+  }
+  cp_async_wait<0>();                   // nothing in flight once the ring's memory is reused
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -220,14 +262,25 @@ __device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *
   }
   __syncwarp();
   run_ops<T, false, false>(M.m_ops[prec], M.m_npass, WL, lane);
-  run_ops<T, false, false>(M.lu_ops[prec], M.lu_npass, WL, lane);
+  // The pair products are dead once M is formed: their slots become the ring
+  // that streams the LU program (the largest, read from L2) ahead of use.
+  const uint32_t pb = smem_addr(WL + M.L_P);
+  const uint32_t rb = (pb + 7u) & ~7u;
+  const int cap = M.n_pairs * (int)sizeof(T) - (int)(rb - pb);
+  if (cap >= 8 * 256)
+    run_ops_ring<T, false, 8>(M.lu_ops[prec], M.lu_npass, WL, lane, rb);
+  else if (cap >= 4 * 256)
+    run_ops_ring<T, false, 4>(M.lu_ops[prec], M.lu_npass, WL, lane, rb);
+  else
+    run_ops<T, false, false>(M.lu_ops[prec], M.lu_npass, WL, lane);
 }
 
-// a5: forward and backward substitution on the vector in WL[X]
+// a5: forward and backward substitution with the LDU factors on the vector in
+// WL[X]; it leaves -x there (the programs run without negation).
 template <typename T, bool STAGED>
 __device__ __forceinline__ void solve_core(const MechDev &M, const unsigned char *tbase, T *WL, const int lane) {
   run_ops<T, false, STAGED>(reinterpret_cast<const ushort4 *>(tbase + M.tab.fwd_ops), M.fwd_npass, WL, lane);
-  run_ops<T, true, STAGED>(reinterpret_cast<const ushort4 *>(tbase + M.tab.bwd_ops), M.bwd_npass, WL, lane);
+  run_ops<T, false, STAGED>(reinterpret_cast<const ushort4 *>(tbase + M.tab.bwd_ops), M.bwd_npass, WL, lane);
 }
 
 template <typename T, int KS, bool STAGED>
@@ -305,7 +358,7 @@ struct Cell {
     __syncwarp();
     solve_core<T, STAGED>(M, tb.base, WL, lane);
 #pragma unroll
-    for (int k = 0; k < KS; ++k) x[k] = own[k] ? (double)WL[M.L_X + pos[k]] : 0.0;
+    for (int k = 0; k < KS; ++k) x[k] = own[k] ? -(double)WL[M.L_X + pos[k]] : 0.0;
     __syncwarp();
   }
 };
@@ -1168,10 +1221,10 @@ __device__ void backward_cell(const MechDev &M, const CellsDev &C, const AdjDev 
       for (int k = 0; k < KS; ++k)
         if (cl.own[k]) WL[M.L_X + cl.pos[k]] = lamd[k];
       __syncwarp();
-      run_ops<double, true, false>(M.fwdT_ops, M.fwdT_npass, WL, lane);
+      run_ops<double, false, false>(M.fwdT_ops, M.fwdT_npass, WL, lane);
       run_ops<double, false, false>(M.bwdT_ops, M.bwdT_npass, WL, lane);
 #pragma unroll
-      for (int k = 0; k < KS; ++k) g[k] = cl.own[k] ? ss * WL[M.L_X + cl.pos[k]] : 0.0;
+      for (int k = 0; k < KS; ++k) g[k] = cl.own[k] ? -ss * WL[M.L_X + cl.pos[k]] : 0.0;   // the programs leave -M^{-T} lambda
       __syncwarp();
       jt_and_theta<KS>(M, Wd, cl.own, g, sc, jtg, lane);
 #pragma unroll

@@ -97,6 +97,57 @@ void add_sum(Scheduler &s, int target, bool fresh, const std::vector<std::pair<i
   for (int t : temps) s.fma(target, ONE, t, target);
 }
 
+// Rows of a triangular solve: W[x_i] += sum W[coef] * W[x_k] over the row's
+// terms (coef, k), rows emitted in the given order so every source is final
+// first.  A row's terms are taken in the order their sources become final (the
+// scheduler's last write), in the row itself or, when that finishes the row
+// sooner, split with one temporary from a small pool that is folded in last.
+void emit_rows(Scheduler &s, const std::vector<int> &rows, const std::vector<std::vector<std::pair<int, int>>> &terms,
+               const std::vector<int> &xloc, int tmp0, int ntmp, int &tnext, int ZERO, int ONE) {
+  for (int i : rows) {
+    std::vector<std::pair<int, int>> tk = terms[i];
+    if (tk.empty()) continue;
+    const int x = xloc[i];
+    std::stable_sort(tk.begin(), tk.end(), [&](const std::pair<int, int> &a, const std::pair<int, int> &b) {
+      return s.lastw[xloc[a.second]] < s.lastw[xloc[b.second]];
+    });
+    // earliest completion with the row alone, and with the row plus a temporary
+    int t1 = s.lastw[x] + 1;
+    for (auto &t : tk) t1 = std::max(t1, s.lastw[xloc[t.second]] + 1) + 1;
+    int fx = s.lastw[x] + 1, ft = 0;
+    std::vector<int> where(tk.size());
+    bool used_t = false;
+    for (size_t q = 0; q < tk.size(); ++q) {
+      const int r = s.lastw[xloc[tk[q].second]] + 1;
+      const int ex = std::max(fx, r), et = std::max(ft, r);
+      if (et < ex) {
+        where[q] = 1;
+        ft = et + 1;
+        used_t = true;
+      } else {
+        where[q] = 0;
+        fx = ex + 1;
+      }
+    }
+    const int t2 = used_t ? std::max(fx, ft) + 1 : fx;
+    if (!used_t || t2 >= t1) {
+      for (auto &t : tk) s.fma(x, t.first, xloc[t.second], x);
+      continue;
+    }
+    const int tmp = tmp0 + (tnext++ % ntmp);
+    bool fresh = true;
+    for (size_t q = 0; q < tk.size(); ++q) {
+      if (where[q]) {
+        s.fma(tmp, tk[q].first, xloc[tk[q].second], fresh ? ZERO : tmp);
+        fresh = false;
+      } else {
+        s.fma(x, tk[q].first, xloc[tk[q].second], x);
+      }
+    }
+    s.fma(x, ONE, tmp, x);
+  }
+}
+
 std::vector<int> markowitz_order(int S, std::vector<uint8_t> B) {
   std::vector<int> order;
   std::vector<uint8_t> alive(S, 1);
@@ -140,6 +191,7 @@ struct ConstTable {
 };
 
 constexpr int CHUNK = 8;
+constexpr int NSTMP = 16;   // temporaries of the triangular solves
 
 }  // namespace
 
@@ -326,7 +378,8 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
     }
   }
 
-  // ---- LU program (right-looking; L stored negated, ninv_k = -1/u_kk)
+  // ---- LU program (right-looking, M = L D U'): L unit lower stored negated,
+  // ninv_k = -1/u_kk, U' unit upper stored negated (-u_kj/u_kk)
   {
     Scheduler sch(d.WL_len + 8);
     double flops = 0;
@@ -353,31 +406,44 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
           sch.fma(ij, d.L_LU + slot[i * S + k], d.L_LU + slot[k * S + j], ij);
           flops += 2;
         }
+      // U' = D^{-1} U: row k becomes -u_kj/u_kk once pivot k's updates have read it
+      // (not counted: the factorisation's algorithmic flops are those of plain LU)
+      for (int j : Ur) {
+        const int kj = d.L_LU + slot[k * S + j];
+        sch.fma(kj, kj, nk, d.L_ZERO);
+      }
     }
     m.lu_prog = sch.finish();
     m.flops_lu = flops;
   }
 
-  // ---- forward (x_i += (-l_ik) x_k) and backward (x_k = x_k / u_kk; x_i -= u_ik x_k) programs,
-  // column-oriented: once x_k is final its column of updates is independent work
+  // ---- solves with the LDU factors, both programs without negation:
+  // forward:  X = L^{-1} b, then X_k = ninv_k y_k = -(D^{-1} y)_k once every row
+  //           that reads y_k has;
+  // backward: V = -x from V_k = X_k + sum_{j>k} (-u'_kj) V_j (unit upper),
+  // so the solution is -X.  Row-oriented, see emit_rows.
+  std::vector<int> rows_up(S), rows_down(S), xloc(S);
+  for (int k = 0; k < S; ++k) {
+    rows_up[k] = k;
+    rows_down[k] = S - 1 - k;
+    xloc[k] = d.L_X + k;
+  }
+  const int L_STMP = d.WL_len;
+  d.WL_len += NSTMP;
   {
     Scheduler f(d.WL_len + 8), b(d.WL_len + 8);
+    std::vector<std::vector<std::pair<int, int>>> lt(S), ut(S);
     double flops = 0;
-    for (int k = 0; k < S; ++k)
-      for (int i = k + 1; i < S; ++i)
-        if (F[i * S + k]) {
-          f.fma(d.L_X + i, d.L_LU + slot[i * S + k], d.L_X + k, d.L_X + i);
-          flops += 2;
-        }
-    for (int k = S - 1; k >= 0; --k) {
-      b.fma(d.L_X + k, d.L_NINV + k, d.L_X + k, d.L_ZERO);   // -ninv * x = x / u_kk
-      flops += 1;
-      for (int i = 0; i < k; ++i)
-        if (F[i * S + k]) {
-          b.fma(d.L_X + i, d.L_LU + slot[i * S + k], d.L_X + k, d.L_X + i);
-          flops += 2;
-        }
-    }
+    for (int i = 0; i < S; ++i)
+      for (int k = 0; k < S; ++k) {
+        if (k < i && F[i * S + k]) lt[i].push_back({d.L_LU + slot[i * S + k], k});
+        if (k > i && F[i * S + k]) ut[i].push_back({d.L_LU + slot[i * S + k], k});
+      }
+    for (int i = 0; i < S; ++i) flops += 2.0 * (double)(lt[i].size() + ut[i].size()) + 1.0;
+    int tnext = 0;
+    emit_rows(f, rows_up, lt, xloc, L_STMP, NSTMP, tnext, d.L_ZERO, L_ONE);
+    for (int k = 0; k < S; ++k) f.fma(d.L_X + k, d.L_NINV + k, d.L_X + k, d.L_ZERO);
+    emit_rows(b, rows_down, ut, xloc, L_STMP, NSTMP, tnext, d.L_ZERO, L_ONE);
     m.fwd_prog = f.finish();
     m.bwd_prog = b.finish();
     m.flops_solve = flops;
@@ -432,16 +498,22 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
       msg = "mechanism too large for the adjoint's 16-bit byte offsets";
       return CHEM_EINVAL;
     }
-    // M^T = U^T L^T: solve U^T z = b (lower, diagonal u_kk), then L^T x = z (unit upper, L stored negated)
+    // M^T = U'^T D L^T: W = U'^{-T} b (unit lower, coefficients -u'_kj), X_k =
+    // ninv_k W_k = -(D^{-1} W)_k, then Q = -mu from Q_i = X_i + sum_{k>i} (-l_ki) Q_k
+    // (unit upper); mu = -X.  Both programs without negation.
     Scheduler f(d.WL_len + 8), g(d.WL_len + 8);
-    for (int k = 0; k < S; ++k) {
-      f.fma(d.L_X + k, d.L_NINV + k, d.L_X + k, d.L_ZERO);           // NEG: -ninv * z = z / u_kk
-      for (int j = k + 1; j < S; ++j)
-        if (F[k * S + j]) f.fma(d.L_X + j, d.L_LU + slot[k * S + j], d.L_X + k, d.L_X + j);   // z_j -= u_kj z_k
+    {
+      std::vector<std::vector<std::pair<int, int>>> uT(S), lT(S);
+      for (int k = 0; k < S; ++k)
+        for (int j = 0; j < S; ++j) {
+          if (j > k && F[k * S + j]) uT[j].push_back({d.L_LU + slot[k * S + j], k});
+          if (j < k && F[k * S + j]) lT[j].push_back({d.L_LU + slot[k * S + j], k});
+        }
+      int tnext = 0;
+      emit_rows(f, rows_up, uT, xloc, L_STMP, NSTMP, tnext, d.L_ZERO, L_ONE);
+      for (int k = 0; k < S; ++k) f.fma(d.L_X + k, d.L_NINV + k, d.L_X + k, d.L_ZERO);
+      emit_rows(g, rows_down, lT, xloc, L_STMP, NSTMP, tnext, d.L_ZERO, L_ONE);
     }
-    for (int k = S - 1; k >= 0; --k)
-      for (int i = 0; i < k; ++i)
-        if (F[k * S + i]) g.fma(d.L_X + i, d.L_LU + slot[k * S + i], d.L_X + k, d.L_X + i);   // x_i += (-l_ki) x_k
     m.fwdT_prog = f.finish();
     m.bwdT_prog = g.finish();
   }
