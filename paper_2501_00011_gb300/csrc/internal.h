@@ -52,6 +52,8 @@ struct TableOffsets {
   int dconst_off, dconst_val;      // int [d_nconst] byte offsets into Wd, double values
   int Lconst_off, Lconst_val;      // int [L_nconst] byte offsets into WL, double values
   int thr2, thr3, g;               // step-factor grid, double [7][GRID_N] x2 and [GRID_N]
+  int staged;                      // bytes of the prefix the persistent driver stages in shared
+                                   // memory (the programs and slots used every Newton iteration)
   int bytes;                       // total, a multiple of 16
 };
 
@@ -68,7 +70,7 @@ struct MechDev {
   // per-cell double array Wd (element indices)
   int Wd_len, d_Y, d_KT, d_RT, d_F, d_ONE, d_ZERO, d_DUMMY;
   // per-cell LU-precision array WL (element indices)
-  int WL_len, L_LU, L_NINV, L_X, L_P, L_ZERO, L_DUMMY, nnz_lu;
+  int WL_len, L_LU, L_X, L_P, L_ZERO, L_DUMMY, nnz_lu;
   int d_nconst, L_nconst;
   int m_clear;             // WL entries [0, m_clear) are cleared before forming M
   int f_npass, fwd_npass, bwd_npass, m_npass, lu_npass;

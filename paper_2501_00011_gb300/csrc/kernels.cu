@@ -211,14 +211,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
   return false;
 }
 
-// Table base of one block: the staged copy in shared memory or the blob in
-// global memory; section offsets come from the kernel parameter M.tab.
+// Table bases of one block: base holds the hot prefix (programs and slots used
+// every Newton iteration), staged in shared memory or the blob in global
+// memory; gbase is always the global blob (tables used once per cell, step or
+// refactorisation).  Section offsets come from the kernel parameter M.tab.
 struct Tabs {
   const unsigned char *base;
+  const unsigned char *gbase;
 };
 template <typename X>
 __device__ __forceinline__ const X *tab(const Tabs &tb, int off) {
   return reinterpret_cast<const X *>(tb.base + off);
+}
+template <typename X>
+__device__ __forceinline__ const X *gtab(const Tabs &tb, int off) {
+  return reinterpret_cast<const X *>(tb.gbase + off);
 }
 
 // Phase bodies that touch only the cell's shared-memory arrays and the tables.
@@ -241,15 +248,15 @@ __device__ __forceinline__ void f_core(const MechDev &M, const unsigned char *tb
 
 // a3-a5: M = I - c J(y) in the LU slots from y in Wd[Y], then factor
 template <typename T>
-__device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *tbase, const int prec, double *Wd, T *WL,
+__device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *gbase, const int prec, double *Wd, T *WL,
                                       const double c, const int lane) {
   for (int i = lane; i < M.m_clear; i += WARP) WL[i] = (T)0;
   __syncwarp();
   unsigned char *wl = reinterpret_cast<unsigned char *>(WL);
   unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
-  const int *diag = reinterpret_cast<const int *>(tbase + M.tab.lu_diag);
-  const int *prx = reinterpret_cast<const int *>(tbase + M.tab.pair_rx);
-  const unsigned *pother = reinterpret_cast<const unsigned *>(tbase + M.tab.pair_other);
+  const int *diag = reinterpret_cast<const int *>(gbase + M.tab.lu_diag);
+  const int *prx = reinterpret_cast<const int *>(gbase + M.tab.pair_rx);
+  const unsigned *pother = reinterpret_cast<const unsigned *>(gbase + M.tab.pair_other);
   for (int k = lane; k < M.S; k += WARP) at<T>(wl, diag[k]) = (T)1;
   const double mc = -c;
   for (int pr = lane; pr < M.n_pairs; pr += WARP) {
@@ -309,8 +316,8 @@ struct Cell {
   __device__ __forceinline__ void init_constants() {
     unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
     unsigned char *wl = reinterpret_cast<unsigned char *>(WL);
-    for (int k = lane; k < M.d_nconst; k += WARP) at<double>(wd, tab<int>(tb, M.tab.dconst_off)[k]) = tab<double>(tb, M.tab.dconst_val)[k];
-    for (int k = lane; k < M.L_nconst; k += WARP) at<T>(wl, tab<int>(tb, M.tab.Lconst_off)[k]) = (T)tab<double>(tb, M.tab.Lconst_val)[k];
+    for (int k = lane; k < M.d_nconst; k += WARP) at<double>(wd, gtab<int>(tb, M.tab.dconst_off)[k]) = gtab<double>(tb, M.tab.dconst_val)[k];
+    for (int k = lane; k < M.L_nconst; k += WARP) at<T>(wl, gtab<int>(tb, M.tab.Lconst_off)[k]) = (T)gtab<double>(tb, M.tab.Lconst_val)[k];
   }
 
   __device__ __forceinline__ double wrms(const double (&v)[KS], const double (&w)[KS]) const {
@@ -347,7 +354,7 @@ struct Cell {
 #pragma unroll
     for (int k = 0; k < KS; ++k)
       if (own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
-    mlu_core<T>(M, tb.base, P.prec, Wd, WL, c, lane);
+    mlu_core<T>(M, tb.gbase, P.prec, Wd, WL, c, lane);
   }
 
   // a5: x = M^{-1} b with the factored M
@@ -761,7 +768,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
         st.rejects++;
         nef++;
         if (nef >= MXNEF) { status = CHEM_CELL_ERR_FAIL; break; }
-        double eta = grid_eta(tab<double>(tb, M.tab.thr2), tab<double>(tb, M.tab.g), err, q, lane);
+        double eta = grid_eta(gtab<double>(tb, M.tab.thr2), gtab<double>(tb, M.tab.g), err, q, lane);
         if (nef >= 2 && eta > ETA_MXF) eta = ETA_MXF;
         if (nef >= 3 && q > 1) q -= 1;
         rescale<KS>(D, q, eta, M.rescale_coef, lane);
@@ -784,21 +791,21 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
       if (last) break;
       n_eq++;
 
-      double eta = grid_eta(tab<double>(tb, M.tab.thr2), tab<double>(tb, M.tab.g), err, q, lane);
+      double eta = grid_eta(gtab<double>(tb, M.tab.thr2), gtab<double>(tb, M.tab.g), err, q, lane);
       int qn = q;
       if (n_eq >= q + 1) {
         if (q > 1) {
           double row[KS];
           get_row<KS>(D, q, row);
           const double e = cl.wrms(row, w) / (double)q;
-          const double em = grid_eta(tab<double>(tb, M.tab.thr2), tab<double>(tb, M.tab.g), e, q - 1, lane);
+          const double em = grid_eta(gtab<double>(tb, M.tab.thr2), gtab<double>(tb, M.tab.g), e, q - 1, lane);
           if (em > eta) { eta = em; qn = q - 1; }
         }
         if (q < qmax) {
           double row[KS];
           get_row<KS>(D, q + 2, row);
           const double e = cl.wrms(row, w) / (double)(q + 2);
-          const double ep = grid_eta(tab<double>(tb, M.tab.thr3), tab<double>(tb, M.tab.g), e, q + 1, lane);
+          const double ep = grid_eta(gtab<double>(tb, M.tab.thr3), gtab<double>(tb, M.tab.g), e, q + 1, lane);
           if (ep > eta) { eta = ep; qn = q + 1; }
         }
       }
@@ -865,6 +872,7 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const
   const int lane = threadIdx.x & (WARP - 1);
   const int warp = threadIdx.x / WARP;
   Tabs tb;
+  tb.gbase = M.blob[P.prec];
   bool staged_ok = true;
   if (STAGED) {
     staged_ok = stage_tables(M.blob[P.prec], P.tab_bytes, smem, &tma_bar, C.error);
@@ -904,7 +912,7 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) probe_kernel(const
   const int64_t cell = (int64_t)blockIdx.x * P.warps_per_block + warp;
   if (cell >= C.n_cells) return;
   Tabs tb;
-  tb.base = M.blob[P.prec];
+  tb.base = tb.gbase = M.blob[P.prec];
   double *Wd = reinterpret_cast<double *>(smem + (size_t)warp * P.cell_bytes);
   T *WL = reinterpret_cast<T *>(Wd + P.wd_pad);
   Cell<T, KS, false> cl(M, P, tb, Wd, WL, lane);
@@ -1287,7 +1295,7 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) adjoint_kernel(con
   const int64_t cell = (int64_t)blockIdx.x * P.warps_per_block + warp;
   if (cell >= C.n_cells) return;
   Tabs tb;
-  tb.base = M.blob[0];
+  tb.base = tb.gbase = M.blob[0];
   double *Wd = reinterpret_cast<double *>(smem + (size_t)warp * P.cell_bytes);
   double *WL = Wd + P.wd_pad;
   if (C.tape_bad[cell]) {
@@ -1327,7 +1335,7 @@ size_t smem_per_cell(const MechDev &m, int lu_precision) {
   return (wd + wl + 15) & ~(size_t)15;
 }
 
-size_t staged_bytes(const MechDev &m, int driver) { return staged_driver(driver) ? (size_t)m.tab.bytes : 0; }
+size_t staged_bytes(const MechDev &m, int driver) { return staged_driver(driver) ? (size_t)m.tab.staged : 0; }
 
 int max_warps_per_block(const MechDev &m, int lu_precision, int driver) {
   int dev = 0, smem_block = 0;

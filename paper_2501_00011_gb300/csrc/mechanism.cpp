@@ -286,11 +286,11 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
   d.d_RT = d.d_KT + R;
   d.d_F = d.d_RT + R;
   int d_temp = d.d_F + S;
-  // WL (LU precision): LU[nnz], ninv[S], x[S], P[n_pairs], ZERO, ONE, M temps, nu constants
+  // WL (LU precision): LU[nnz] (-1/u_kk in the pivot slots once factored), x[S], P[n_pairs],
+  // ZERO, ONE, M temps, nu constants, solve temporaries
   d.L_LU = 0;
   d.nnz_lu = nnz;
-  d.L_NINV = nnz;
-  d.L_X = nnz + S;
+  d.L_X = nnz;
   d.L_P = d.L_X + S;
   d.L_ZERO = d.L_P + n_pairs;
   const int L_ONE = d.L_ZERO + 1;
@@ -379,7 +379,7 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
   }
 
   // ---- LU program (right-looking, M = L D U'): L unit lower stored negated,
-  // ninv_k = -1/u_kk, U' unit upper stored negated (-u_kj/u_kk)
+  // -1/u_kk in the pivot's own slot, U' unit upper stored negated (-u_kj/u_kk)
   {
     Scheduler sch(d.WL_len + 8);
     double flops = 0;
@@ -387,7 +387,7 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
     for (int k = 0; k < S; ++k) m.lu_diag[k] = d.L_LU + slot[k * S + k];
     for (int k = 0; k < S; ++k) {
       const int dk = d.L_LU + slot[k * S + k];
-      const int nk = d.L_NINV + k;
+      const int nk = dk;                // the reciprocal overwrites the pivot
       sch.recip(nk, dk);
       flops += 1;
       std::vector<int> Lc, Ur;
@@ -442,7 +442,7 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
     for (int i = 0; i < S; ++i) flops += 2.0 * (double)(lt[i].size() + ut[i].size()) + 1.0;
     int tnext = 0;
     emit_rows(f, rows_up, lt, xloc, L_STMP, NSTMP, tnext, d.L_ZERO, L_ONE);
-    for (int k = 0; k < S; ++k) f.fma(d.L_X + k, d.L_NINV + k, d.L_X + k, d.L_ZERO);
+    for (int k = 0; k < S; ++k) f.fma(d.L_X + k, d.L_LU + slot[k * S + k], d.L_X + k, d.L_ZERO);
     emit_rows(b, rows_down, ut, xloc, L_STMP, NSTMP, tnext, d.L_ZERO, L_ONE);
     m.fwd_prog = f.finish();
     m.bwd_prog = b.finish();
@@ -511,7 +511,7 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
         }
       int tnext = 0;
       emit_rows(f, rows_up, uT, xloc, L_STMP, NSTMP, tnext, d.L_ZERO, L_ONE);
-      for (int k = 0; k < S; ++k) f.fma(d.L_X + k, d.L_NINV + k, d.L_X + k, d.L_ZERO);
+      for (int k = 0; k < S; ++k) f.fma(d.L_X + k, d.L_LU + slot[k * S + k], d.L_X + k, d.L_ZERO);
       emit_rows(g, rows_down, lT, xloc, L_STMP, NSTMP, tnext, d.L_ZERO, L_ONE);
     }
     m.fwdT_prog = f.finish();
@@ -634,6 +634,7 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
       slots[j] = make_uint2((unsigned)(m.rx_slot_idx[j * 3] * 8) | ((unsigned)(m.rx_slot_idx[j * 3 + 1] * 8) << 16),
                             (unsigned)(m.rx_slot_idx[j * 3 + 2] * 8));
     t.rx_slots = bw.add(slots);
+    t.staged = (int)bw.buf.size();         // the rest is read from global memory
     t.pair_rx = bw.add(m.pair_rx);
     std::vector<unsigned> po(m.pair_other.size());
     for (size_t k = 0; k < po.size(); ++k)
