@@ -53,7 +53,8 @@ struct TableOffsets {
   int Lconst_off, Lconst_val;      // int [L_nconst] byte offsets into WL, double values
   int thr2, thr3, g;               // step-factor grid, double [7][GRID_N] x2 and [GRID_N]
   int staged;                      // bytes of the prefix the persistent driver stages in shared
-                                   // memory (the programs and slots used every Newton iteration)
+                                   // memory (programs and slots used every Newton iteration or
+                                   // refactorisation; constants and the grid stay in global memory)
   int bytes;                       // total, a multiple of 16
 };
 

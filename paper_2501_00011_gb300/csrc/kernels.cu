@@ -248,15 +248,15 @@ __device__ __forceinline__ void f_core(const MechDev &M, const unsigned char *tb
 
 // a3-a5: M = I - c J(y) in the LU slots from y in Wd[Y], then factor
 template <typename T>
-__device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *gbase, const int prec, double *Wd, T *WL,
+__device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *tbase, const int prec, double *Wd, T *WL,
                                       const double c, const int lane) {
   for (int i = lane; i < M.m_clear; i += WARP) WL[i] = (T)0;
   __syncwarp();
   unsigned char *wl = reinterpret_cast<unsigned char *>(WL);
   unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
-  const int *diag = reinterpret_cast<const int *>(gbase + M.tab.lu_diag);
-  const int *prx = reinterpret_cast<const int *>(gbase + M.tab.pair_rx);
-  const unsigned *pother = reinterpret_cast<const unsigned *>(gbase + M.tab.pair_other);
+  const int *diag = reinterpret_cast<const int *>(tbase + M.tab.lu_diag);
+  const int *prx = reinterpret_cast<const int *>(tbase + M.tab.pair_rx);
+  const unsigned *pother = reinterpret_cast<const unsigned *>(tbase + M.tab.pair_other);
   for (int k = lane; k < M.S; k += WARP) at<T>(wl, diag[k]) = (T)1;
   const double mc = -c;
   for (int pr = lane; pr < M.n_pairs; pr += WARP) {
@@ -268,9 +268,17 @@ __device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *
     WL[M.L_P + pr] = (T)p;
   }
   __syncwarp();
-  run_ops<T, false, false>(M.m_ops[prec], M.m_npass, WL, lane);
-  // The pair products are dead once M is formed: their slots become the ring
-  // that streams the LU program (the largest, read from L2) ahead of use.
+  // Both programs are read from L2, so their ops are streamed ahead through a
+  // ring in memory that is dead at the time: the rates and f slots of Wd
+  // while M is formed (f is not being evaluated), then the pair products,
+  // which are dead once M is formed, while it is factored.
+  const uint32_t wr = smem_addr(Wd + M.d_RT);            // 8-byte aligned (a double slot)
+  if ((M.R + M.S) * 8 >= 8 * 256)
+    run_ops_ring<T, false, 8>(M.m_ops[prec], M.m_npass, WL, lane, wr);
+  else if ((M.R + M.S) * 8 >= 4 * 256)
+    run_ops_ring<T, false, 4>(M.m_ops[prec], M.m_npass, WL, lane, wr);
+  else
+    run_ops<T, false, false>(M.m_ops[prec], M.m_npass, WL, lane);
   const uint32_t pb = smem_addr(WL + M.L_P);
   const uint32_t rb = (pb + 7u) & ~7u;
   const int cap = M.n_pairs * (int)sizeof(T) - (int)(rb - pb);
@@ -354,7 +362,7 @@ struct Cell {
 #pragma unroll
     for (int k = 0; k < KS; ++k)
       if (own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
-    mlu_core<T>(M, tb.gbase, P.prec, Wd, WL, c, lane);
+    mlu_core<T>(M, tb.base, P.prec, Wd, WL, c, lane);
   }
 
   // a5: x = M^{-1} b with the factored M

@@ -634,7 +634,6 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
       slots[j] = make_uint2((unsigned)(m.rx_slot_idx[j * 3] * 8) | ((unsigned)(m.rx_slot_idx[j * 3 + 1] * 8) << 16),
                             (unsigned)(m.rx_slot_idx[j * 3 + 2] * 8));
     t.rx_slots = bw.add(slots);
-    t.staged = (int)bw.buf.size();         // the rest is read from global memory
     t.pair_rx = bw.add(m.pair_rx);
     std::vector<unsigned> po(m.pair_other.size());
     for (size_t k = 0; k < po.size(); ++k)
@@ -643,6 +642,7 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
     std::vector<int> diag(S);
     for (int k = 0; k < S; ++k) diag[k] = m.lu_diag[k] * el;
     t.lu_diag = bw.add(diag);
+    t.staged = (int)bw.buf.size();         // the rest is read from global memory
     std::vector<int> doff(m.d_consts_i.size()), loff(m.L_consts_i.size());
     for (size_t k = 0; k < doff.size(); ++k) doff[k] = m.d_consts_i[k] * 8;
     for (size_t k = 0; k < loff.size(); ++k) loff[k] = m.L_consts_i[k] * el;
