@@ -184,8 +184,9 @@ def rescale(D, q: int, eta: float) -> np.ndarray:
     return D
 
 
-def grid_eta(err: float, p: int, bias: float) -> float:
-    return lib().orc_grid_eta(float(err), int(p), float(bias))
+def grid_eta(err2: float, p: int, bias: float) -> float:
+    """Step factor for the squared error estimate err2 (see orc_grid_eta)."""
+    return lib().orc_grid_eta(float(err2), int(p), float(bias))
 
 
 @dataclass

@@ -18,7 +18,7 @@
  *   STEP      (q, c): y_pred = sum_{m<=q} D_m, psi = (1/gamma_q) sum_{m=1..q}
  *             gamma_m D_m, d_0 = 0 and K modified-Newton iterations
  *                 d_{k+1} = d_k + s M^{-1} (c f(y_pred + d_k) - psi - d_k),
- *             s = 1 if c == c_M else 2/(1 + c/c_M); projected species then
+ *             s = 1 if c == c_M else 2/(1 + c (1/c_M)); projected species then
  *             get d_i = -y_pred_i (y_i = 0); the history is updated with
  *             D_{q+2} = d - D_{q+1}, D_{q+1} = d, D_m += D_{m+1} (m = q..0).
  * With the recorded inputs this is the integrator's own arithmetic, so the map
@@ -161,7 +161,7 @@ static void rescale_T(int q, double eta, double T[ORC_QMAX][ORC_QMAX]) {
   }
 }
 
-static double step_scale(double c, double cM) { return (c == cM) ? 1.0 : 2.0 / (1.0 + c / cM); }
+static double step_scale(double c, double cM) { return (c == cM) ? 1.0 : 2.0 / (1.0 + c * (1.0 / cM)); }
 
 /*
  * One walk of the map; iteration matrices are formed with the rate constants

@@ -106,8 +106,9 @@ int orc_lu_factor(int n, double *A, int32_t *piv);
 void orc_lu_solve(int n, const double *LU, const int32_t *piv, double *b);
 /* history rescale of differences D_1..D_q (rows of length S) for a step ratio eta */
 void orc_rescale(int S, int q, double eta, double *D);
-/* step-factor grid: largest grid factor g with bias*err*g^(p+1) <= 1 */
-double orc_grid_eta(double err, int p, double bias);
+/* step-factor grid: largest grid factor g with bias*err*g^(p+1) <= 1, tested on
+ * err2 = err^2 against 1/(bias^2 g^(2(p+1))) */
+double orc_grid_eta(double err2, int p, double bias);
 /* integrate one cell over [0, dt]; y is in/out (kept on failure); tape may be NULL */
 int orc_integrate(const orc_mech *m, const double *kt, double *y, double dt, const orc_opts *o,
                   orc_stats *st, orc_tape *tape);

@@ -51,7 +51,8 @@ struct TableOffsets {
   int lu_diag;                     // int [S]: byte offsets into WL of the pivot diagonal
   int dconst_off, dconst_val;      // int [d_nconst] byte offsets into Wd, double values
   int Lconst_off, Lconst_val;      // int [L_nconst] byte offsets into WL, double values
-  int thr2, thr3, g;               // step-factor grid, double [7][GRID_N] x2 and [GRID_N]
+  int thr2, thr3, g;               // step-factor grid: squared thresholds (biases 2 and 3),
+                                   // double [7][GRID_N] each, and the factors g_i, [GRID_N]
   int staged;                      // bytes of the prefix the persistent driver stages in shared
                                    // memory (programs and slots used every Newton iteration or
                                    // refactorisation; constants and the grid stay in global memory)

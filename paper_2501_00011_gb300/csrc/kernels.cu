@@ -30,6 +30,7 @@ namespace chemgpu {
 
 __constant__ double c_gam[QMAX + 2];
 __constant__ double c_igam[QMAX + 2];
+__constant__ double c_isq[QMAX + 3];    // 1/n^2: the squared error estimates' divisors
 
 namespace {
 
@@ -173,10 +174,12 @@ __device__ __forceinline__ double warp_min(double v) {
 }
 
 // Largest grid factor g_i with err <= thr[p][i] (thr decreasing in i), else g_min.
-__device__ __forceinline__ double grid_eta(const double *thr, const double *g, double err, int p, int lane) {
+// Largest step factor g_i of the grid 2^(i/8) whose squared threshold
+// 1/(bias^2 2^(i(p+1)/4)) (host table, row p) the squared error err2 meets.
+__device__ __forceinline__ double grid_eta(const double *thr, const double *g, double err2, int p, int lane) {
   const double *tp = thr + p * GRID_N;
-  const bool ok0 = err <= tp[lane];
-  const bool ok1 = (lane + WARP < GRID_N) && err <= tp[lane + WARP];
+  const bool ok0 = err2 <= tp[lane];
+  const bool ok1 = (lane + WARP < GRID_N) && err2 <= tp[lane + WARP];
   const int cnt = __popc(__ballot_sync(FULL, ok0)) + __popc(__ballot_sync(FULL, ok1));
   return g[cnt > 0 ? cnt - 1 : 0];
 }
@@ -338,6 +341,19 @@ struct Cell {
       }
     s = warp_sum(s);
     return sqrt(s * invS);
+  }
+
+  // squared norm (1/S) sum (v_i w_i)^2: the corrector, constraint and error
+  // tests compare squared norms with squared bounds (no square root)
+  __device__ __forceinline__ double norm2(const double (&v)[KS], const double (&w)[KS]) const {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < KS; ++k)
+      if (own[k]) {
+        const double t = v[k] * w[k];
+        s = fma(t, t, s);
+      }
+    return warp_sum(s) * invS;
   }
 
   __device__ __forceinline__ void weights(const double (&y)[KS], double (&w)[KS]) const {
@@ -621,7 +637,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
     }
     rec.push_row(EV_INIT, q, h, y0, lane);
 
-    double t = 0.0, cM = 0.0, rho = 1.0;
+    double t = 0.0, cM = 0.0, icM = 0.0, rho2 = 1.0;   // rho2: squared convergence-rate estimate
     int n_eq = 0, have_M = 0, force_M = 0, n_since_M = 0, nef = 0, ncf = 0, last = 0;
     const int qmax = P.max_order;
     double ypred[KS], psi[KS], d[KS], y[KS], x[KS];
@@ -663,26 +679,28 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
       for (int k = 0; k < KS; ++k) psi[k] *= iq;
 
       int fresh = 0;
-      if (!have_M || force_M || fabs(c / cM - 1.0) > DGMAX || n_since_M >= MSBP) {
+      if (!have_M || force_M || fabs(c * icM - 1.0) > DGMAX || n_since_M >= MSBP) {
         cl.form_and_factor(c, ypred);
         have_M = 1;
         cM = c;
+        icM = 1.0 / c;
         n_since_M = 0;
-        rho = 1.0;
+        rho2 = 1.0;
         fresh = 1;
         st.jac_evals++;
         rec.push_row(EV_REFACTOR, 0, c, ypred, lane);
       }
       force_M = 0;
-      const double scale = (c == cM) ? 1.0 : 2.0 / (1.0 + c / cM);
+      const double scale = (c == cM) ? 1.0 : 2.0 / (1.0 + c * icM);
       const double tol = NLSCOEF * (double)(q + 1);
+      const double tol2 = tol * tol;
 
 #pragma unroll
       for (int k = 0; k < KS; ++k) {
         d[k] = 0.0;
         y[k] = ypred[k];
       }
-      double del = 0.0, del_prev = 0.0;
+      double del2 = 0.0, del2_prev = 0.0;
       int conv = 0;
       int n_it = 0;
       for (int it = 0; it < NEWTON_MAXITER; ++it) {
@@ -698,17 +716,17 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
 #pragma unroll
           for (int k = 0; k < KS; ++k) x[k] *= scale;
         }
-        del = cl.wrms(x, w);
+        del2 = cl.norm2(x, w);
 #pragma unroll
         for (int k = 0; k < KS; ++k) {
           d[k] += x[k];
           y[k] = ypred[k] + d[k];
         }
         st.newton_iters++;
-        if (it > 0) rho = fmax(CRDOWN * rho, del / del_prev);
-        if (del * fmin(1.0, rho) <= tol) { conv = 1; break; }
-        if (it > 0 && del > RDIV * del_prev) break;
-        del_prev = del;
+        if (it > 0) rho2 = fmax(CRDOWN * CRDOWN * rho2, del2 / del2_prev);
+        if (del2 * fmin(1.0, rho2) <= tol2) { conv = 1; break; }
+        if (it > 0 && del2 > RDIV * RDIV * del2_prev) break;
+        del2_prev = del2;
       }
       if (!conv) {
         st.conv_fails++;
@@ -745,7 +763,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
             }
           vs = warp_sum(vs);
           eta_c = warp_min(eta_c);
-          if (sqrt(vs * cl.invS) <= tol) {
+          if (vs * cl.invS <= tol2) {
 #pragma unroll
             for (int k = 0; k < KS; ++k) {
               const bool p = cl.own[k] && y[k] < 0.0;
@@ -771,12 +789,12 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
       }
 
       // local error test
-      const double err = cl.wrms(d, w) / (double)(q + 1);
-      if (!(err <= 1.0)) {
+      const double err2 = cl.norm2(d, w) * c_isq[q + 1];     // (||d|| / (q+1))^2
+      if (!(err2 <= 1.0)) {
         st.rejects++;
         nef++;
         if (nef >= MXNEF) { status = CHEM_CELL_ERR_FAIL; break; }
-        double eta = grid_eta(gtab<double>(tb, M.tab.thr2), gtab<double>(tb, M.tab.g), err, q, lane);
+        double eta = grid_eta(gtab<double>(tb, M.tab.thr2), gtab<double>(tb, M.tab.g), err2, q, lane);
         if (nef >= 2 && eta > ETA_MXF) eta = ETA_MXF;
         if (nef >= 3 && q > 1) q -= 1;
         rescale<KS>(D, q, eta, M.rescale_coef, lane);
@@ -799,21 +817,21 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
       if (last) break;
       n_eq++;
 
-      double eta = grid_eta(gtab<double>(tb, M.tab.thr2), gtab<double>(tb, M.tab.g), err, q, lane);
+      double eta = grid_eta(gtab<double>(tb, M.tab.thr2), gtab<double>(tb, M.tab.g), err2, q, lane);
       int qn = q;
       if (n_eq >= q + 1) {
         if (q > 1) {
           double row[KS];
           get_row<KS>(D, q, row);
-          const double e = cl.wrms(row, w) / (double)q;
-          const double em = grid_eta(gtab<double>(tb, M.tab.thr2), gtab<double>(tb, M.tab.g), e, q - 1, lane);
+          const double e2 = cl.norm2(row, w) * c_isq[q];
+          const double em = grid_eta(gtab<double>(tb, M.tab.thr2), gtab<double>(tb, M.tab.g), e2, q - 1, lane);
           if (em > eta) { eta = em; qn = q - 1; }
         }
         if (q < qmax) {
           double row[KS];
           get_row<KS>(D, q + 2, row);
-          const double e = cl.wrms(row, w) / (double)(q + 2);
-          const double ep = grid_eta(gtab<double>(tb, M.tab.thr3), gtab<double>(tb, M.tab.g), e, q + 1, lane);
+          const double e2 = cl.norm2(row, w) * c_isq[q + 2];
+          const double ep = grid_eta(gtab<double>(tb, M.tab.thr3), gtab<double>(tb, M.tab.g), e2, q + 1, lane);
           if (ep > eta) { eta = ep; qn = q + 1; }
         }
       }
@@ -1212,7 +1230,7 @@ __device__ void backward_cell(const MechDev &M, const CellsDev &C, const AdjDev 
         cl.form_and_factor(cM, yJ);
         m_event = er;
       }
-      ss = (sc == cM) ? 1.0 : 2.0 / (1.0 + sc / cM);
+      ss = (sc == cM) ? 1.0 : 2.0 / (1.0 + sc * (1.0 / cM));   // as the forward formed it
     } else if (kind == EV_PROJECT) {
 #pragma unroll
       for (int k = 0; k < KS; ++k)
@@ -1363,8 +1381,12 @@ cudaError_t set_constants() {
     gam[k] = g;
     igam[k] = 1.0 / g;
   }
+  double isq[QMAX + 3];
+  isq[0] = 0.0;
+  for (int n = 1; n <= QMAX + 2; ++n) isq[n] = 1.0 / (double)(n * n);
   cudaError_t e = cudaMemcpyToSymbol(c_gam, gam, sizeof(gam));
   if (e != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_isq, isq, sizeof(isq))) != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_igam, igam, sizeof(igam));
 }
 

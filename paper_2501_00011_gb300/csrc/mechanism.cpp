@@ -616,8 +616,9 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
   std::vector<double> thr2(7 * GRID_N), thr3(7 * GRID_N), g(GRID_N);
   for (int p = 0; p < 7; ++p)
     for (int i = GRID_IMIN; i <= GRID_IMAX; ++i) {
-      thr2[p * GRID_N + i - GRID_IMIN] = 1.0 / (2.0 * exp2((double)i * (double)(p + 1) / 8.0));
-      thr3[p * GRID_N + i - GRID_IMIN] = 1.0 / (3.0 * exp2((double)i * (double)(p + 1) / 8.0));
+      // squared thresholds 1/(bias^2 2^(i(p+1)/4)): the kernel tests squared error estimates
+      thr2[p * GRID_N + i - GRID_IMIN] = 1.0 / (2.0 * 2.0 * exp2((double)i * (double)(p + 1) / 4.0));
+      thr3[p * GRID_N + i - GRID_IMIN] = 1.0 / (3.0 * 3.0 * exp2((double)i * (double)(p + 1) / 4.0));
     }
   for (int i = GRID_IMIN; i <= GRID_IMAX; ++i) g[i - GRID_IMIN] = exp2((double)i / 8.0);
 

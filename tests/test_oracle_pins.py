@@ -162,11 +162,13 @@ def test_rescale_reproduces_polynomial_interpolation(oracle_lib, q, eta):
 
 
 def test_grid_eta_definition(oracle_lib):
+    # the oracle takes the squared error estimate; the chosen factor is the
+    # largest grid value with bias * err * eta^(p+1) <= 1
     g = [2.0 ** (i / 8.0) for i in range(-26, 27)]
     for err in (0.0, 1e-9, 1e-3, 0.05, 0.3, 1.0, 2.0, 1e3):
         for p in range(1, 7):
             for bias in (2.0, 3.0):
-                eta = oracle_lib.grid_eta(err, p, bias)
+                eta = oracle_lib.grid_eta(err * err, p, bias)
                 i = int(round(8 * math.log2(eta)))
                 assert eta == pytest.approx(g[i + 26], rel=1e-15)
                 ok = bias * err * eta ** (p + 1) <= 1.0 * (1 + 1e-12)
