@@ -17,6 +17,7 @@ struct chem_cells {
   double *T = nullptr, *P = nullptr, *y = nullptr, *J = nullptr, *theta = nullptr;
   chem_cell_stats *stats = nullptr;
   int *queue = nullptr;   // [0..1] work counter, [2] staging fallbacks
+  int *order = nullptr, *order_bucket = nullptr, *order_hist = nullptr;   // persistent driver: queue order
   bool have_state = false, use_J = false, use_theta = false;
   int device = 0;
   // adjoint (record_adjoint)
@@ -176,6 +177,13 @@ int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *o
     chem_cells_destroy(c);
     return fail(CHEM_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
   }
+  if (o.driver == CHEM_DRIVER_PERSISTENT &&
+      ((e = cudaMalloc(&c->order, n * sizeof(int))) != cudaSuccess ||
+       (e = cudaMalloc(&c->order_bucket, n * sizeof(int))) != cudaSuccess ||
+       (e = cudaMalloc(&c->order_hist, 2 * ORDER_BUCKETS * sizeof(int))) != cudaSuccess)) {
+    chem_cells_destroy(c);
+    return fail(CHEM_ENOMEM, std::string("cudaMalloc of the queue order failed: ") + cudaGetErrorString(e));
+  }
   if (o.record_adjoint) {
     c->row_cap = o.tape_steps > 0 ? o.tape_steps : 2000;
     c->tape_cap = 3 * c->row_cap + 64;
@@ -220,6 +228,9 @@ void chem_cells_destroy(chem_cells *c) {
   cudaFree(c->theta);
   cudaFree(c->stats);
   cudaFree(c->queue);
+  cudaFree(c->order);
+  cudaFree(c->order_bucket);
+  cudaFree(c->order_hist);
   cudaFree(c->tape_kq);
   cudaFree(c->tape_val);
   cudaFree(c->tape_n);
@@ -328,6 +339,11 @@ cudaError_t enqueue_solve(chem_cells *c, double dt, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(c->queue, 0, sizeof(long long), s);
     if (e != cudaSuccess) return e;
     cd.queue = c->queue;
+    // stiffest cells first, so the longest solves do not start last
+    if ((e = launch_order(c->mech->m.dev, cd, c->opts.rtol, c->opts.atol, c->order_bucket, c->order_hist, c->order, s)) !=
+        cudaSuccess)
+      return e;
+    cd.order = c->order;
   }
   return launch_solve(c->mech->m.dev, cd, launch_cfg(c->opts, dt), s);
 }

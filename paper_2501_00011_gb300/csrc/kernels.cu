@@ -41,6 +41,7 @@ constexpr int MSBP = 20, MXNEF = 7, MXNCF = 10;
 constexpr double ETA_CF = 0.25, ETA_MXF = 0.2, ETA_CST_SAFETY = 0.9, ETA_CST_MIN = 0.1, STRETCH = 1e-3;
 constexpr double K_BOLTZMANN = 1.380649e-23;
 constexpr long TMA_WAIT_LIMIT = 1L << 22;
+constexpr int ORDER_WARPS = 8;          // cells per block of the queue-order kernel
 
 struct SolveParams {
   double rtol, atol, dt;
@@ -914,6 +915,7 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const
       if (lane == 0) cell = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(C.queue), 1ull);
       cell = __shfl_sync(FULL, cell, 0);
       if (cell >= C.n_cells) break;
+      if (C.order) cell = __ldg(C.order + cell);
       solve_cell<T, KS, STAGED, REC>(M, C, P, tb, Wd, WL, lane, cell);
     }
   } else {
@@ -1351,6 +1353,82 @@ cudaError_t launch_adj_t(const MechDev &M, const CellsDev &C, const AdjDev &A, c
   return cudaGetLastError();
 }
 
+// ----------------------------------------------------------- queue order
+// One warp per cell computes a cost key; the queue then hands out the most
+// expensive cells first, so that the slowest solves do not start last (with a
+// few cells per warp, one late expensive cell otherwise holds a whole SM).
+// The key is the cell's cost in the previous solve of the batch (the f
+// evaluations, solves, factorisations and steps of its statistics, weighted
+// by their FP64 work), and for a batch's first solve the stiffness ratio
+// ||f(y0)|| / ||y0|| in the weighted norm (the integrator's initial step is
+// h0 ~ ||y0|| / ||f(y0)||), which takes the rate constants and one f.
+template <int KS>
+__global__ void __launch_bounds__(ORDER_WARPS * WARP) order_keys_kernel(const __grid_constant__ MechDev M, const CellsDev C,
+                                                                          const SolveParams P, int *bucket, int *hist) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & (WARP - 1);
+  const int warp = threadIdx.x / WARP;
+  const int64_t cell = (int64_t)blockIdx.x * ORDER_WARPS + warp;
+  if (cell >= C.n_cells) return;
+  Tabs tb;
+  tb.base = tb.gbase = M.blob[0];
+  double *Wd = reinterpret_cast<double *>(smem + (size_t)warp * P.cell_bytes);
+  double l;                                  // log2 of the key, larger first
+  const chem_cell_stats prev = C.stats[cell];
+  if (prev.steps > 0) {
+    l = log2(65.0 * prev.f_evals + 100.0 * prev.solves + 560.0 * prev.jac_evals + 150.0 * prev.steps);
+  } else {
+    Cell<double, KS, false> cl(M, P, tb, Wd, nullptr, lane);
+    unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
+    for (int k = lane; k < M.d_nconst; k += WARP) at<double>(wd, gtab<int>(tb, M.tab.dconst_off)[k]) = gtab<double>(tb, M.tab.dconst_val)[k];
+    double y0[KS], w[KS], f0[KS];
+    const bool bad = load_cell<KS>(M, C, Wd, lane, cell, cl.own, y0);
+    l = -1e9;                                // bad inputs last
+    if (!bad) {
+      cl.weights(y0, w);
+      cl.eval_f(y0, f0);
+      const double d0 = cl.wrms(y0, w), d1 = cl.wrms(f0, w);
+      const double r = d1 / fmax(d0, 1e-5);
+      if (r > 0.0 && isfinite(r)) l = log2(r);
+    }
+  }
+  // 4 buckets per octave of the key, largest first
+  const int k = (int)fmin(fmax(floor(4.0 * l), -127.0), 127.0);
+  const int b = 127 - k;                     // 0 .. 254
+  if (lane == 0) {
+    bucket[cell] = b;
+    atomicAdd(hist + b, 1);
+  }
+}
+
+// exclusive prefix sum of the bucket counts into the scatter cursors
+__global__ void order_scan_kernel(int *hist) {
+  if (threadIdx.x != 0) return;
+  int acc = 0;
+  for (int b = 0; b < ORDER_BUCKETS; ++b) {
+    const int n = hist[b];
+    hist[ORDER_BUCKETS + b] = acc;
+    acc += n;
+  }
+}
+
+__global__ void order_scatter_kernel(const int *bucket, int *hist, int *order, int64_t n) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int pos = atomicAdd(hist + ORDER_BUCKETS + bucket[c], 1);
+  order[pos] = (int)c;
+}
+
+template <int KS>
+cudaError_t launch_order_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int *bucket, int *hist, cudaStream_t s) {
+  const size_t smem = (size_t)P.cell_bytes * ORDER_WARPS;
+  cudaError_t e = cudaFuncSetAttribute(order_keys_kernel<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (C.n_cells + ORDER_WARPS - 1) / ORDER_WARPS;
+  order_keys_kernel<KS><<<(unsigned)blocks, ORDER_WARPS * WARP, smem, s>>>(M, C, P, bucket, hist);
+  return cudaGetLastError();
+}
+
 bool staged_driver(int driver) { return driver == CHEM_DRIVER_PERSISTENT; }
 
 }  // namespace
@@ -1494,6 +1572,31 @@ cudaError_t launch_adjoint(const MechDev &M, const CellsDev &C, const AdjDev &A,
   }
   if (e != cudaSuccess) return e;
   theta_reduce_kernel<<<(M.R + 127) / 128, 128, 0, stream>>>(A.gcell, C.n_cells, M.R, A.dLdtheta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order(const MechDev &M, const CellsDev &C, double rtol, double atol, int *bucket, int *hist,
+                         int *order, cudaStream_t stream) {
+  if (C.n_cells <= 0) return cudaSuccess;
+  SolveParams P{};
+  P.rtol = rtol;
+  P.atol = atol;
+  P.wd_pad = (M.Wd_len + 1) & ~1;
+  P.cell_bytes = (int)(((size_t)P.wd_pad * sizeof(double) + 15) & ~(size_t)15);
+  P.warps_per_block = ORDER_WARPS;
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * ORDER_BUCKETS, stream);
+  if (e != cudaSuccess) return e;
+  switch ((M.S + WARP - 1) / WARP) {
+    case 1: e = launch_order_t<1>(M, C, P, bucket, hist, stream); break;
+    case 2: e = launch_order_t<2>(M, C, P, bucket, hist, stream); break;
+    case 3: e = launch_order_t<3>(M, C, P, bucket, hist, stream); break;
+    case 4: e = launch_order_t<4>(M, C, P, bucket, hist, stream); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  order_scan_kernel<<<1, 32, 0, stream>>>(hist);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  order_scatter_kernel<<<(unsigned)((C.n_cells + 255) / 256), 256, 0, stream>>>(bucket, hist, order, C.n_cells);
   return cudaGetLastError();
 }
 
