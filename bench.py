@@ -251,6 +251,37 @@ def run_gpu(args):
             "integrator_steps_last_600s": {"min": int(st3["steps"].min()), "median": float(np.median(st3["steps"])),
                                            "max": int(st3["steps"].max())},
             "cells_ok": int(np.sum(st3["status"] == 0))}
+        # f(y) alone by three kernel designs on the 10,000-cell state, rate constants precomputed:
+        # this library's gather and the paper's reaction-parallel atomic design (AoS / SoA reaction data)
+        cd = chemgpu.Cells(mech, C, rtol=wl.rtol, atol=wl.atol)
+        cd.set_state(T_d, P_d, y0_d, stream=stream)
+        f_out = torch.empty_like(y0_d)
+        designs = {}
+        names = {chemgpu.DERIV_GATHER: "gather_warp_per_cell", chemgpu.DERIV_ATOMIC_AOS: "atomic_reaction_parallel_aos",
+                 chemgpu.DERIV_ATOMIC_SOA: "atomic_reaction_parallel_soa"}
+        for dsg, nm in names.items():
+            cd.eval_deriv_design(dsg, y0_d, out=f_out, stream=stream)      # first call also forms the rate constants
+            ts = []
+            for k in range(10):
+                flush.fill_(float(k))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                cd.eval_deriv_design(dsg, y0_d, out=f_out, stream=stream)
+                e1.record(stream)
+                barrier()
+                ts.append(e0.elapsed_time(e1))
+            t = statistics.median(ts)
+            designs[nm] = {"ms": t, "cells_per_s": C / (t / 1e3),
+                           "hbm_gbs": C * (2 * S + wl.mech.n_reactions) * 8 / (t / 1e3) / 1e9}
+        cd.close()
+        g = designs["gather_warp_per_cell"]["ms"]
+        for nm in designs:
+            designs[nm]["vs_gather"] = g / designs[nm]["ms"]
+        out["derivative_designs"] = {
+            "cells": C, "designs": designs,
+            "note": "f(y) only, rate constants precomputed; median of 10 launches with L2 flushed between; "
+                    "hbm_gbs counts y and k~ read and f written once per cell (the atomic designs re-read y "
+                    "per reaction and add through L2)"}
         wl5 = synth.workload_adjoint(args.adjoint_cells)
         n5 = wl5.cells.n_cells
         c5 = chemgpu.Cells(mech, n5, rtol=wl5.rtol, atol=wl5.atol, driver="persistent", record_adjoint=True)

@@ -237,6 +237,25 @@ int chem_sensitivity(chem_cells *cells, const double *dL_dy, double *dL_dtheta, 
 int chem_get_tape(const chem_cells *cells, int64_t cell, int32_t *kind, int32_t *q, double *val, double *rows,
                   int32_t capacity, int32_t *n_events, int32_t *n_rows);
 
+/* Designs of the derivative f(y) for chem_eval_deriv_design. */
+#define CHEM_DERIV_GATHER 0       /* this library's: one warp per cell, the compiled f program, no atomics */
+#define CHEM_DERIV_ATOMIC_AOS 1   /* the paper's: one thread per reaction and cell, FP64 atomic adds into f,
+                                     reaction data as an array of structures */
+#define CHEM_DERIV_ATOMIC_SOA 2   /* the same with the reaction data as a structure of arrays */
+
+/* Derivative only, for comparing kernel designs (the paper's Implementations
+ * section describes its GPU Derivative: a thread per reaction and cell adding
+ * to f with atomic operations; it has no counterpart of the gather design).
+ * f[n_species][n_cells] = f(y) for y[n_species][n_cells] (cell unit stride,
+ * `mem` space) with the batch's rate constants k~[n_reactions][n_cells],
+ * computed on the GPU on the first call after set_state, set_photolysis or
+ * set_theta and kept in a buffer the batch allocates then (8 * n_reactions *
+ * n_cells bytes).  The atomic designs sum in an unspecified order (results
+ * agree to rounding); the gather design is deterministic.  Asynchronous for
+ * device memory; synchronises for host memory.  Errors: CHEM_EINVAL (design,
+ * NULL), CHEM_ESTATE (before set_state), CHEM_ENOMEM, CHEM_ECUDA. */
+int chem_eval_deriv_design(chem_cells *cells, int32_t design, const double *y, double *f, int32_t mem, void *stream);
+
 /* Diagnostics for kernel-level parity.  For every cell, with the cell's T, P,
  * photolysis rates and theta from the batch (set_state must have been
  * called), evaluate on the GPU with the same device routines the solve uses:

@@ -29,8 +29,11 @@ EXPORTS = ["chem_opts_default", "chem_mechanism_create", "chem_mechanism_destroy
            "chem_cells_destroy", "chem_cells_set_state", "chem_cells_set_photolysis",
            "chem_cells_set_theta", "chem_solve_step", "chem_solve_steps", "chem_autotune",
            "chem_get_state", "chem_get_stats",
-           "chem_eval_deriv", "chem_eval_newton_solve", "chem_solve_step_noalloc", "chem_sensitivity",
+           "chem_eval_deriv", "chem_eval_newton_solve", "chem_eval_deriv_design", "chem_solve_step_noalloc", "chem_sensitivity",
            "chem_get_tape", "chem_last_error"]
+
+
+DERIV_GATHER, DERIV_ATOMIC_AOS, DERIV_ATOMIC_SOA = 0, 1, 2
 
 
 class Reaction(ct.Structure):
@@ -94,6 +97,7 @@ def load(path: str | None = None):
         L.chem_get_stats.argtypes = [V, V, ct.c_int32, V]
         L.chem_eval_deriv.argtypes = [V, V, V, ct.c_int32, V]
         L.chem_eval_newton_solve.argtypes = [V, ct.c_double, V, V, V, ct.c_int32, V]
+        L.chem_eval_deriv_design.argtypes = [V, ct.c_int32, V, V, ct.c_int32, V]
         L.chem_solve_step_noalloc.argtypes = [V, ct.c_int64, V, V, V, V, V, V, ct.c_double, V, V]
         L.chem_sensitivity.argtypes = [V, V, V, V, ct.c_int32, V]
         L.chem_solve_steps.argtypes = [V, ct.c_double, ct.c_int32, V]
@@ -290,6 +294,17 @@ class Cells:
                                              ct.c_void_p(x.ctypes.data), MEM_HOST, _stream_ptr(stream)),
                "chem_eval_newton_solve")
         return x
+
+    def eval_deriv_design(self, design: int, y, out=None, stream=None):
+        """f(y) [S, C] by one of the DERIV_* kernel designs (rate constants cached per state)."""
+        if out is None:
+            out = np.empty((self.mech.n_species, self.n_cells)) if isinstance(y, np.ndarray) else y.new_empty(y.shape)
+        (py, my, k1), (po, mo, k2) = _ptr(y), _ptr(out)
+        if my != mo:
+            raise ChemError("y and out must both be on the host or both on the device")
+        _check(load().chem_eval_deriv_design(self._h, int(design), py, po, my, _stream_ptr(stream)),
+               "chem_eval_deriv_design")
+        return out
 
     def sensitivity(self, dL_dy, dL_dtheta=None, dL_dy0=None, stream=None):
         """(dL/dtheta [R], dL/dy0 [S, C], n_bad) for L = sum dL_dy * y."""

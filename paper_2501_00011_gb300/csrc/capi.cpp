@@ -18,6 +18,8 @@ struct chem_cells {
   chem_cell_stats *stats = nullptr;
   int *queue = nullptr;   // [0..1] work counter, [2] staging fallbacks
   int *order = nullptr, *order_bucket = nullptr, *order_hist = nullptr;   // persistent driver: queue order
+  double *kt = nullptr;       // chem_eval_deriv_design: rate constants [R][C], allocated on first use
+  bool kt_valid = false;      // ... and current for the batch's T, P, photolysis and theta
   bool have_state = false, use_J = false, use_theta = false;
   int device = 0;
   // adjoint (record_adjoint)
@@ -231,6 +233,7 @@ void chem_cells_destroy(chem_cells *c) {
   cudaFree(c->order);
   cudaFree(c->order_bucket);
   cudaFree(c->order_hist);
+  cudaFree(c->kt);
   cudaFree(c->tape_kq);
   cudaFree(c->tape_val);
   cudaFree(c->tape_n);
@@ -247,6 +250,7 @@ void chem_cells_destroy(chem_cells *c) {
 int chem_cells_set_state(chem_cells *c, const double *T, const double *P, const double *y, int32_t mem, void *stream) {
   g_err.clear();
   if (!c || !T || !P || !y) return fail(CHEM_EINVAL, "NULL argument");
+  c->kt_valid = false;
   if (int rc = check_mem(mem)) return rc;
   if (c->n == 0) { c->have_state = true; return 0; }
   cudaStream_t s = (cudaStream_t)stream;
@@ -268,6 +272,7 @@ int chem_cells_set_state(chem_cells *c, const double *T, const double *P, const 
 int chem_cells_set_photolysis(chem_cells *c, const double *J, int32_t mem, void *stream) {
   g_err.clear();
   if (!c) return fail(CHEM_EINVAL, "NULL argument");
+  c->kt_valid = false;
   if (!J) { c->use_J = false; return 0; }
   if (int rc = check_mem(mem)) return rc;
   const size_t np = (size_t)c->mech->m.n_phot;
@@ -281,6 +286,7 @@ int chem_cells_set_photolysis(chem_cells *c, const double *J, int32_t mem, void 
 int chem_cells_set_theta(chem_cells *c, const double *theta, int32_t mem, void *stream) {
   g_err.clear();
   if (!c) return fail(CHEM_EINVAL, "NULL argument");
+  c->kt_valid = false;
   if (!theta) { c->use_theta = false; return 0; }
   if (int rc = check_mem(mem)) return rc;
   const size_t R = (size_t)c->mech->m.R;
@@ -601,6 +607,47 @@ int chem_eval_deriv(chem_cells *c, const double *y, double *f, int32_t mem, void
 int chem_eval_newton_solve(chem_cells *c, double cc, const double *y, const double *b, double *x, int32_t mem,
                            void *stream) {
   return probe(c, 1, cc, y, b, x, mem, stream);
+}
+
+int chem_eval_deriv_design(chem_cells *c, int32_t design, const double *y, double *f, int32_t mem, void *stream) {
+  g_err.clear();
+  if (!c || !y || !f) return fail(CHEM_EINVAL, "NULL argument");
+  if (design != CHEM_DERIV_GATHER && design != CHEM_DERIV_ATOMIC_AOS && design != CHEM_DERIV_ATOMIC_SOA)
+    return fail(CHEM_EINVAL, "unknown derivative design");
+  if (int rc = check_mem(mem)) return rc;
+  if (!c->have_state) return fail(CHEM_ESTATE, "derivative before set_state");
+  if (c->n == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  const MechDev &M = c->mech->m.dev;
+  cudaError_t e;
+  if (!c->kt && (e = cudaMalloc(&c->kt, (size_t)c->n * (M.R > 0 ? M.R : 1) * sizeof(double))) != cudaSuccess) {
+    c->kt = nullptr;
+    return fail(CHEM_ENOMEM, std::string("cudaMalloc of the rate constants failed: ") + cudaGetErrorString(e));
+  }
+  if (!c->kt_valid) {
+    if ((e = launch_rates(M, cells_dev(c), c->kt, s)) != cudaSuccess) return cuda_fail(e, "rate constants");
+    c->kt_valid = true;
+  }
+  const size_t bytes = (size_t)c->n * M.S * sizeof(double);
+  const double *dy = y;
+  double *df = f, *tmp = nullptr;
+  if (mem == CHEM_MEM_HOST) {
+    if ((e = cudaMalloc(&tmp, 2 * bytes)) != cudaSuccess) return fail(CHEM_ENOMEM, "cudaMalloc for derivative scratch");
+    if ((e = cudaMemcpyAsync(tmp, y, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+      cudaFree(tmp);
+      return cuda_fail(e, "derivative copy-in");
+    }
+    dy = tmp;
+    df = tmp + bytes / sizeof(double);
+  }
+  e = launch_deriv_design(M, cells_dev(c), design, c->kt, dy, df, s);
+  if (e == cudaSuccess && mem == CHEM_MEM_HOST) {
+    e = cudaMemcpyAsync(f, df, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "derivative kernels");
+  return 0;
 }
 
 int chem_sensitivity(chem_cells *c, const double *dL_dy, double *dL_dtheta, double *dL_dy0, int32_t mem, void *stream) {

@@ -67,6 +67,12 @@ struct MechDev {
   const int *rx_nreac;     // [R]
   const int *rx_phot;      // [R] index among photolysis reactions, or -1
   const double *rx_A, *rx_Ea, *rx_B, *rx_J;
+  // reaction data for the derivative-design comparison (chem_eval_deriv_design):
+  // the caller's records as uploaded (array of structures), and the same as
+  // structure of arrays: reactants [R][3], product counts [R], products and yields [R][8]
+  const chem_reaction *rx_aos;
+  const int *rx_reac, *rx_nprod, *rx_prod;
+  const double *rx_yld;
   // species permutation: position of species s in the pivot order
   const int *sp_pos;       // [S]
   // per-cell double array Wd (element indices)
@@ -200,6 +206,14 @@ cudaError_t launch_probe(const MechDev &M, const CellsDev &C, int lu_precision, 
 
 // discrete adjoint: replay (exact steps, y rows), backward sweep, theta reduction
 cudaError_t launch_adjoint(const MechDev &m, const CellsDev &c, const AdjDev &a, cudaStream_t stream);
+// deriv.cu: derivative-only kernels for comparing designs.  kt[R][C] rate
+// constants of the batch (launch_rates fills it); y, f [S][C] on the device.
+cudaError_t launch_rates(const MechDev &m, const CellsDev &c, double *kt, cudaStream_t stream);
+cudaError_t launch_deriv_design(const MechDev &m, const CellsDev &c, int design, const double *kt, const double *y,
+                                double *f, cudaStream_t stream);
+// kernels.cu: the gather design (one warp per cell, the compiled f program)
+cudaError_t launch_deriv_gather(const MechDev &m, const CellsDev &c, const double *kt, const double *y, double *f,
+                                cudaStream_t stream);
 
 // sets the thread-local message returned by chem_last_error()
 void set_last_error(const std::string &msg);

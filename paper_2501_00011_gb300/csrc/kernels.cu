@@ -25,6 +25,7 @@
 #include <type_traits>
 
 #include "internal.h"
+#include "device_common.cuh"
 
 namespace chemgpu {
 
@@ -39,7 +40,6 @@ constexpr int NEWTON_MAXITER = 3;
 constexpr double CRDOWN = 0.3, RDIV = 2.0, NLSCOEF = 0.1, DGMAX = 0.3, THRESH = 1.5;
 constexpr int MSBP = 20, MXNEF = 7, MXNCF = 10;
 constexpr double ETA_CF = 0.25, ETA_MXF = 0.2, ETA_CST_SAFETY = 0.9, ETA_CST_MIN = 0.1, STRETCH = 1e-3;
-constexpr double K_BOLTZMANN = 1.380649e-23;
 constexpr long TMA_WAIT_LIMIT = 1L << 22;
 constexpr int ORDER_WARPS = 8;          // cells per block of the queue-order kernel
 
@@ -482,17 +482,9 @@ __device__ __forceinline__ bool load_cell(const MechDev &M, const CellsDev &C, d
     if (own[k] && !isfinite(y0[k])) bad = true;
   }
   if (!__any_sync(FULL, bad)) {
-    const double n_air = Pc / (K_BOLTZMANN * Tc) * 1e-6;
+    const double n_air = air_number_density(Tc, Pc);
     for (int j = lane; j < R; j += WARP) {
-      double kj;
-      if (__ldg(M.rx_kind + j) == CHEM_PHOTOLYSIS) {
-        kj = C.J ? C.J[(int64_t)__ldg(M.rx_phot + j) * NC + cell] : __ldg(M.rx_J + j);
-      } else {
-        kj = __ldg(M.rx_A + j) * exp(-__ldg(M.rx_Ea + j) / Tc) * pow(Tc / 300.0, __ldg(M.rx_B + j));
-        const int nr = __ldg(M.rx_nreac + j);
-        for (int r = 1; r < nr; ++r) kj *= n_air;
-      }
-      if (C.theta) kj *= exp(C.theta[j]);
+      const double kj = rate_constant(M, C, j, cell, Tc, n_air);
       Wd[M.d_KT + j] = kj;
       if (!isfinite(kj)) bad = true;
     }
@@ -966,14 +958,30 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) probe_kernel(const
     if (cl.own[k]) out[(int64_t)(lane + WARP * k) * NC + cell] = r[k];
 }
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum,
+// once per device and kernel: a host call at every launch would sit between
+// the launches on the timeline.
+template <auto Kernel>
+cudaError_t allow_max_smem() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && done[dev]) return cudaSuccess;
+  int optin = 0;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, Kernel)) != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess && dev < 64) done[dev] = true;
+  return e;
+}
+
 template <typename T, int KS>
 cudaError_t launch_probe_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int mode, double c,
                            const double *y, const double *b, double *out, cudaStream_t stream) {
   const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaError_t e = cudaFuncSetAttribute(probe_kernel<T, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaError_t e = allow_max_smem<probe_kernel<T, KS>>();
   if (e != cudaSuccess) return e;
   const int blocks = (int)((C.n_cells + P.warps_per_block - 1) / P.warps_per_block);
   probe_kernel<T, KS><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, P, mode, c, y, b, out);
@@ -1346,7 +1354,7 @@ __global__ void theta_reduce_kernel(const double *gcell, int64_t n_cells, int R,
 template <int KS>
 cudaError_t launch_adj_t(const MechDev &M, const CellsDev &C, const AdjDev &A, const SolveParams &P, cudaStream_t stream) {
   const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
-  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem<adjoint_kernel<KS>>();
   if (e != cudaSuccess) return e;
   const int blocks = (int)((C.n_cells + P.warps_per_block - 1) / P.warps_per_block);
   adjoint_kernel<KS><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, A, P);
@@ -1422,11 +1430,58 @@ __global__ void order_scatter_kernel(const int *bucket, int *hist, int *order, i
 template <int KS>
 cudaError_t launch_order_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int *bucket, int *hist, cudaStream_t s) {
   const size_t smem = (size_t)P.cell_bytes * ORDER_WARPS;
-  cudaError_t e = cudaFuncSetAttribute(order_keys_kernel<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem<order_keys_kernel<KS>>();
   if (e != cudaSuccess) return e;
   const int64_t blocks = (C.n_cells + ORDER_WARPS - 1) / ORDER_WARPS;
   order_keys_kernel<KS><<<(unsigned)blocks, ORDER_WARPS * WARP, smem, s>>>(M, C, P, bucket, hist);
   return cudaGetLastError();
+}
+
+// ----------------------------------------------------- derivative only
+// a2 for every cell with the rate constants given (kt[R][C]): a block of
+// GATHER_CELLS cells copies the hot table prefix into shared memory, reads its
+// y and k~ tiles with the cells fastest (coalesced), transposes them into the
+// cells' Wd slices, runs the rates and the f program one warp per cell, and
+// writes f back the same way.
+constexpr int GATHER_CELLS = 16;
+
+template <int KS>
+__global__ void __launch_bounds__(GATHER_CELLS * WARP) deriv_gather_kernel(const __grid_constant__ MechDev M, const int64_t NC,
+                                                                             const double *kt, const double *y, double *f,
+                                                                             const int cell_doubles) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  // the hot table prefix (f program, reactant slots), then the cells' slices
+  const int tb = M.tab.staged;
+  for (int i = threadIdx.x; i < tb / 16; i += blockDim.x)
+    reinterpret_cast<uint4 *>(smem)[i] = __ldg(reinterpret_cast<const uint4 *>(M.blob[0]) + i);
+  double *sm = reinterpret_cast<double *>(smem + tb);
+  const int lane = threadIdx.x & (WARP - 1);
+  const int warp = threadIdx.x / WARP;
+  const int64_t c0 = (int64_t)blockIdx.x * GATHER_CELLS;
+  const int nb = (int)((NC - c0) < GATHER_CELLS ? (NC - c0) : GATHER_CELLS);    // cells of this block
+  // tiles in: element (row, cell) -> slice of cell, slot row
+  for (int i = threadIdx.x; i < M.S * GATHER_CELLS; i += blockDim.x) {
+    const int r = i / GATHER_CELLS, cl = i % GATHER_CELLS;
+    if (cl < nb) sm[(size_t)cl * cell_doubles + M.d_Y + r] = y[(int64_t)r * NC + c0 + cl];
+  }
+  for (int i = threadIdx.x; i < M.R * GATHER_CELLS; i += blockDim.x) {
+    const int r = i / GATHER_CELLS, cl = i % GATHER_CELLS;
+    if (cl < nb) sm[(size_t)cl * cell_doubles + M.d_KT + r] = kt[(int64_t)r * NC + c0 + cl];
+  }
+  if (warp < nb) {
+    double *Wd = sm + (size_t)warp * cell_doubles;
+    unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
+    const unsigned char *gb = M.blob[0];
+    for (int k = lane; k < M.d_nconst; k += WARP)
+      at<double>(wd, reinterpret_cast<const int *>(gb + M.tab.dconst_off)[k]) = reinterpret_cast<const double *>(gb + M.tab.dconst_val)[k];
+  }
+  __syncthreads();
+  if (warp < nb) f_core<true>(M, smem, sm + (size_t)warp * cell_doubles, lane);
+  __syncthreads();
+  for (int i = threadIdx.x; i < M.S * GATHER_CELLS; i += blockDim.x) {
+    const int r = i / GATHER_CELLS, cl = i % GATHER_CELLS;
+    if (cl < nb) f[(int64_t)r * NC + c0 + cl] = sm[(size_t)cl * cell_doubles + M.d_F + r];
+  }
 }
 
 bool staged_driver(int driver) { return driver == CHEM_DRIVER_PERSISTENT; }
@@ -1572,6 +1627,27 @@ cudaError_t launch_adjoint(const MechDev &M, const CellsDev &C, const AdjDev &A,
   }
   if (e != cudaSuccess) return e;
   theta_reduce_kernel<<<(M.R + 127) / 128, 128, 0, stream>>>(A.gcell, C.n_cells, M.R, A.dLdtheta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deriv_gather(const MechDev &M, const CellsDev &C, const double *kt, const double *y, double *f,
+                                cudaStream_t stream) {
+  if (C.n_cells <= 0) return cudaSuccess;
+  const int cell_doubles = (M.Wd_len + 1) & ~1;
+  const size_t smem = (size_t)M.tab.staged + (size_t)cell_doubles * sizeof(double) * GATHER_CELLS;
+  cudaError_t e;
+  const unsigned blocks = (unsigned)((C.n_cells + GATHER_CELLS - 1) / GATHER_CELLS);
+  switch ((M.S + WARP - 1) / WARP) {
+#define CHEM_GATHER_CASE(K_)                                                                                      \
+    case K_:                                                                                                      \
+      if ((e = allow_max_smem<deriv_gather_kernel<K_>>()) != cudaSuccess) return e;                          \
+      deriv_gather_kernel<K_><<<blocks, GATHER_CELLS * WARP, smem, stream>>>(M, C.n_cells, kt, y, f, cell_doubles); \
+      break;
+    CHEM_GATHER_CASE(1) CHEM_GATHER_CASE(2) CHEM_GATHER_CASE(3) CHEM_GATHER_CASE(4)
+#undef CHEM_GATHER_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

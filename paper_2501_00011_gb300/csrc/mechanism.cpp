@@ -712,6 +712,27 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
     free_mechanism(m);
     return rc;
   }
+  {
+    // reaction data of the derivative-design comparison: the records as given
+    // (array of structures) and the same as separate arrays
+    std::vector<int> reac((size_t)R * CHEM_MAX_REAC, 0), nprod(R), prod((size_t)R * CHEM_MAX_PROD, 0);
+    std::vector<double> yld((size_t)R * CHEM_MAX_PROD, 0.0);
+    for (int j = 0; j < R; ++j) {
+      const chem_reaction &r = m.rx[j];
+      for (int s = 0; s < r.n_reac; ++s) reac[(size_t)j * CHEM_MAX_REAC + s] = r.reac[s];
+      nprod[j] = r.n_prod;
+      for (int q = 0; q < r.n_prod; ++q) {
+        prod[(size_t)j * CHEM_MAX_PROD + q] = r.prod[q];
+        yld[(size_t)j * CHEM_MAX_PROD + q] = r.yield[q];
+      }
+    }
+    if ((rc = put(m, m.rx, &d.rx_aos, msg)) || (rc = put(m, reac, &d.rx_reac, msg)) ||
+        (rc = put(m, nprod, &d.rx_nprod, msg)) || (rc = put(m, prod, &d.rx_prod, msg)) ||
+        (rc = put(m, yld, &d.rx_yld, msg))) {
+      free_mechanism(m);
+      return rc;
+    }
+  }
   if (set_constants() != cudaSuccess) {
     free_mechanism(m);
     msg = "could not set solver constants on the device";

@@ -51,6 +51,35 @@ def test_deriv_matches_oracle(oracle_lib, cg, mechs, name):
 
 
 @pytest.mark.parametrize("name", ["small", "tropo"])
+@pytest.mark.parametrize("design", [0, 1, 2])
+def test_deriv_designs_match_oracle(oracle_lib, cg, mechs, name, design):
+    # the gather design and the paper's reaction-parallel atomic design (both
+    # reaction-data layouts) on 333 cells (a ragged last block), per-cell photolysis
+    m = mechs[name]
+    cells = synth.random_cells(m.n_species, 333, T_range=(200, 320), P_range=(2e4, 1e5), seed=12)
+    c = cg.Cells(m, cells.n_cells)
+    c.set_state(cells.T, cells.P, cells.y)
+    n_phot = int(np.sum(m.synth.kind == 1))
+    jp = np.abs(np.random.default_rng(13).standard_normal((n_phot, cells.n_cells))) * 1e-3
+    c.set_photolysis(jp)
+    ytest = synth.random_cells(m.n_species, cells.n_cells, seed=14).y
+    f = c.eval_deriv_design(design, ytest)
+    om = oracle_lib.OracleMechanism(m.synth)
+    for k in range(cells.n_cells):
+        kt = oracle_lib.rate_constants(om, cells.T[k], cells.P[k], jphot=jp[:, k])
+        fo = oracle_lib.deriv(om, kt, ytest[:, k])
+        scale = np.abs(oracle_lib.jacobian(om, kt, ytest[:, k])) @ np.abs(ytest[:, k]) + 1e-300
+        assert np.all(np.abs(f[:, k] - fo) <= 1e-13 * scale), k
+    # the cached rate constants follow set_theta
+    th = np.linspace(-0.5, 0.5, m.n_reactions)
+    c.set_theta(th)
+    f2 = c.eval_deriv_design(design, ytest)
+    kt = oracle_lib.rate_constants(om, cells.T[0], cells.P[0], jphot=jp[:, 0], theta=th)
+    fo = oracle_lib.deriv(om, kt, ytest[:, 0])
+    assert np.allclose(f2[:, 0], fo, rtol=1e-12, atol=1e-12 * np.abs(fo).max())
+
+
+@pytest.mark.parametrize("name", ["small", "tropo"])
 @pytest.mark.parametrize("prec", [64, 32])
 def test_newton_solve_matches_dense(oracle_lib, cg, mechs, name, prec):
     m = mechs[name]
