@@ -125,6 +125,14 @@ typedef struct {
   int32_t tape_steps;              /* tape rows per cell: states stored, one per solve, per
                                       refactorisation and per accepted corrector iteration
                                       (0 = 2000, at most CHEM_MAX_TAPE_ROWS); events 3x that + 64 */
+  int32_t couple_cells;            /* 1 (default): every cell integrated on its own.  G > 1: the
+                                      paper's multi-cell system (Implementations, Multi-cells): cells
+                                      integrated in groups of G consecutive cells, each group one ODE
+                                      system with shared step size, order and Newton iterations and
+                                      one WRMS norm over all its species (the linear systems stay
+                                      block-diagonal, one block per cell).  FP64 only, no adjoint;
+                                      cells_per_block must be a multiple of G (0: the largest that
+                                      fits); a CUDA block holds whole groups. */
 } chem_opts;
 
 typedef struct {

@@ -321,3 +321,49 @@ def adjoint(mech, kt, y0, tape: Tape, lam_final):
     if rc:
         raise RuntimeError("adjoint: singular or missing iteration matrix")
     return ly0, g
+
+
+# ---------------------------------------------------------------- coupled cells
+# The paper's multi-cell system (Implementations, Multi-cells): the cells of a
+# group are integrated as one ODE system.  The oracle writes that system out as
+# one mechanism over all the group's species, reaction j of cell g acting on
+# species g*S + s with cell g's rate constant, and integrates it with the same
+# integrator (one step size, order and Newton iteration, one WRMS norm over
+# every species of the group; the dense LU factors the block-diagonal matrix).
+
+def replicate(mech, G: int):
+    """The mechanism of G cells as one system (species g*S + s, reactions g*R + j)."""
+    from paper_2501_00011_gb300 import synth
+    S, R = mech.n_species, mech.n_reactions
+    big = synth.empty_mechanism(G * S, G * R, f"{mech.name}_x{G}")
+    for g in range(G):
+        sl = slice(g * R, (g + 1) * R)
+        big.kind[sl] = mech.kind
+        big.n_reac[sl] = mech.n_reac
+        big.n_prod[sl] = mech.n_prod
+        big.reac[sl] = np.where(mech.reac >= 0, mech.reac + g * S, -1)
+        big.prod[sl] = np.where(mech.prod >= 0, mech.prod + g * S, -1)
+        big.yld[sl] = mech.yld
+        big.A[sl], big.Ea[sl], big.B[sl], big.J[sl] = mech.A, mech.Ea, mech.B, mech.J
+    return big
+
+
+def solve_coupled(mech, cells, dt, rtol, atol, G: int, max_order=5, max_steps=5000):
+    """Every group of G consecutive cells (the last may be shorter) integrated as one
+    system over [0, dt].  Returns (y [S, C], stats [C]: each cell has its group's)."""
+    S, C = mech.n_species, cells.n_cells
+    y = np.array(cells.y, np.float64, order="C")
+    st = np.zeros(C, STATS_DTYPE)
+    for c0 in range(0, C, G):
+        idx = np.arange(c0, min(C, c0 + G))
+        big = replicate(mech, idx.size)
+        kt = np.concatenate([rate_constants(mech, cells.T[c], cells.P[c],
+                                            jphot=None if cells.J is None else cells.J[:, c]) for c in idx])
+        y0 = np.concatenate([cells.y[:, c] for c in idx])
+        yg, sg = integrate(big, kt, y0, dt, rtol, atol, max_order=max_order, max_steps=max_steps)
+        y[:, idx] = yg.reshape(idx.size, S).T
+        for c in idx:
+            for k in STATS_DTYPE.names:
+                if k in sg:
+                    st[c][k] = sg[k]
+    return y, st

@@ -46,7 +46,7 @@ class Opts(ct.Structure):
     _fields_ = [("rtol", ct.c_double), ("atol", ct.c_double), ("max_order", ct.c_int32),
                 ("max_steps", ct.c_int32), ("lu_precision", ct.c_int32), ("driver", ct.c_int32),
                 ("cells_per_block", ct.c_int32), ("blocks_per_sm", ct.c_int32),
-                ("record_adjoint", ct.c_int32), ("tape_steps", ct.c_int32)]
+                ("record_adjoint", ct.c_int32), ("tape_steps", ct.c_int32), ("couple_cells", ct.c_int32)]
 
 
 class MechInfo(ct.Structure):
@@ -209,7 +209,7 @@ class Cells:
     def __init__(self, mech: Mechanism, n_cells: int, rtol: float = 1e-4, atol: float = 1e-10,
                  max_order: int = 5, max_steps: int = 5000, lu_precision: int = 64,
                  driver: str = "plain", cells_per_block: int = 0, blocks_per_sm: int = 0,
-                 record_adjoint: bool = False, tape_steps: int = 0):
+                 record_adjoint: bool = False, tape_steps: int = 0, couple_cells: int = 1):
         L = load()
         self.mech = mech
         self.n_cells = int(n_cells)
@@ -219,6 +219,7 @@ class Cells:
         o.lu_precision, o.driver = lu_precision, DRIVERS[driver]
         o.cells_per_block, o.blocks_per_sm = cells_per_block, blocks_per_sm
         o.record_adjoint, o.tape_steps = int(record_adjoint), tape_steps
+        o.couple_cells = int(couple_cells)
         self.opts = o
         h = ct.c_void_p()
         _check(L.chem_cells_create(mech.handle, self.n_cells, ct.byref(o), ct.byref(h)), "chem_cells_create")

@@ -71,6 +71,7 @@ void chem_opts_default(chem_opts *o) {
   o->max_order = 5;
   o->max_steps = 5000;
   o->lu_precision = 64;
+  o->couple_cells = 1;
   o->driver = CHEM_DRIVER_PLAIN;
 }
 
@@ -150,6 +151,16 @@ int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *o
   if (o.lu_precision != 64 && o.lu_precision != 32) return fail(CHEM_EINVAL, "lu_precision must be 64 or 32");
   if (o.driver != CHEM_DRIVER_PLAIN && o.driver != CHEM_DRIVER_PERSISTENT) return fail(CHEM_EINVAL, "bad driver");
   if (o.cells_per_block < 0 || o.cells_per_block > MAX_WARPS_PER_BLOCK || o.blocks_per_sm < 0) return fail(CHEM_EINVAL, "bad launch shape");
+  if (o.couple_cells < 0 || o.couple_cells > MAX_WARPS_PER_BLOCK) return fail(CHEM_EINVAL, "couple_cells out of range");
+  if (o.couple_cells == 0) o.couple_cells = 1;
+  if (o.couple_cells > 1) {
+    if (o.lu_precision != 64) return fail(CHEM_EINVAL, "coupled cells need lu_precision 64");
+    if (o.record_adjoint) return fail(CHEM_EINVAL, "coupled cells have no adjoint");
+    const int wmax = max_warps_per_block(mech->m.dev, o.lu_precision, o.driver);
+    if (o.couple_cells > wmax) return fail(CHEM_EINVAL, "couple_cells exceeds the cells a block can hold");
+    if (o.cells_per_block == 0) o.cells_per_block = (wmax / o.couple_cells) * o.couple_cells;   // whole groups per block
+    if (o.cells_per_block % o.couple_cells) return fail(CHEM_EINVAL, "cells_per_block must be a multiple of couple_cells");
+  }
   const int wmax = max_warps_per_block(mech->m.dev, o.lu_precision, o.driver);
   if (wmax < 1) return fail(CHEM_EINVAL, "mechanism working set does not fit in shared memory");
   if (o.cells_per_block > wmax) return fail(CHEM_EINVAL, "cells_per_block exceeds the shared-memory limit");
@@ -324,9 +335,10 @@ CellsDev solve_dev(chem_cells *c) {
 }
 
 LaunchCfg launch_cfg(const chem_opts &o, double dt) {
-  LaunchCfg cfg;
+  LaunchCfg cfg{};
   cfg.lu_precision = o.lu_precision;
   cfg.driver = o.driver;
+  cfg.couple = o.couple_cells;
   cfg.warps_per_block = o.cells_per_block;
   cfg.blocks_per_sm = o.blocks_per_sm;
   cfg.rtol = o.rtol;
@@ -345,11 +357,14 @@ cudaError_t enqueue_solve(chem_cells *c, double dt, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(c->queue, 0, sizeof(long long), s);
     if (e != cudaSuccess) return e;
     cd.queue = c->queue;
-    // stiffest cells first, so the longest solves do not start last
-    if ((e = launch_order(c->mech->m.dev, cd, c->opts.rtol, c->opts.atol, c->order_bucket, c->order_hist, c->order, s)) !=
-        cudaSuccess)
-      return e;
-    cd.order = c->order;
+    // most expensive cells first, so the longest solves do not start last
+    // (coupled groups are fixed sets of consecutive cells, handed out whole)
+    if (c->opts.couple_cells <= 1) {
+      if ((e = launch_order(c->mech->m.dev, cd, c->opts.rtol, c->opts.atol, c->order_bucket, c->order_hist, c->order,
+                            s)) != cudaSuccess)
+        return e;
+      cd.order = c->order;
+    }
   }
   return launch_solve(c->mech->m.dev, cd, launch_cfg(c->opts, dt), s);
 }
@@ -423,6 +438,7 @@ int chem_autotune(chem_cells *c, double dt, int64_t n_sample, int32_t *cells_per
   g_err.clear();
   if (int rc = check_solve_args(c, dt)) return rc;
   if (n_sample < 0) return fail(CHEM_EINVAL, "n_sample must be >= 0");
+  if (c->opts.couple_cells > 1) return fail(CHEM_EINVAL, "a coupled batch's launch shape is its group size");
   if (c->n == 0) return 0;
   const int64_t ns = (n_sample == 0 || n_sample > c->n) ? (c->n < CHEM_AUTOTUNE_SAMPLE ? c->n : CHEM_AUTOTUNE_SAMPLE) : n_sample;
   const MechDev &M = c->mech->m.dev;

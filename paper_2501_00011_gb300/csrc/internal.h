@@ -178,6 +178,7 @@ struct AdjDev {
 struct LaunchCfg {
   int lu_precision;     // 64 / 32
   int driver;           // CHEM_DRIVER_*
+  int couple;           // > 1: cells integrated in coupled groups of this many (one block each)
   int warps_per_block;
   int blocks_per_sm;
   double rtol, atol, dt;

@@ -51,6 +51,7 @@ struct SolveParams {
   int warps_per_block;
   int prec;            // 0: FP64 LU, 1: FP32 LU
   int tab_bytes;       // staged table bytes at the start of shared memory (0 if not staged)
+  int couple;          // coupled group size (warps_per_block is a multiple of it); 1: independent cells
 };
 
 // Newton-Raphson refinement of the hardware reciprocal approximation:
@@ -344,6 +345,18 @@ struct Cell {
     return sqrt(s * invS);
   }
 
+  // warp sum of (v_i w_i)^2 over this cell's species
+  __device__ __forceinline__ double sumsq(const double (&v)[KS], const double (&w)[KS]) const {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < KS; ++k)
+      if (own[k]) {
+        const double t = v[k] * w[k];
+        s = fma(t, t, s);
+      }
+    return warp_sum(s);
+  }
+
   // squared norm (1/S) sum (v_i w_i)^2: the corrector, constraint and error
   // tests compare squared norms with squared bounds (no square root)
   __device__ __forceinline__ double norm2(const double (&v)[KS], const double (&w)[KS]) const {
@@ -494,6 +507,40 @@ __device__ __forceinline__ bool load_cell(const MechDev &M, const CellsDev &C, d
   return bad;
 }
 
+// Reductions across the warps of a coupled group (the paper's multi-cell
+// system: one integration over a group of cells, one warp per cell; a block
+// holds several groups, each with its own named barrier).  Each warp's partial
+// goes to a shared slot; after the group's barrier every thread combines the
+// slots in warp order, so all warps of the group see the same bits and take
+// the same decisions.  Uncoupled: identity.
+template <bool COUPLED>
+struct Grp {
+  double *slot;     // [g] in shared memory, this group's
+  int w, g, bar;    // warp index in the group, warps in the group, named barrier of the group
+  __device__ __forceinline__ void sync() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(g * WARP) : "memory");
+  }
+  __device__ __forceinline__ double sum(double v) const {
+    if (!COUPLED) return v;
+    sync();                              // earlier readers of the slots are done
+    if ((threadIdx.x & (WARP - 1)) == 0) slot[w] = v;
+    sync();
+    double s = 0.0;
+    for (int i = 0; i < g; ++i) s += slot[i];
+    return s;
+  }
+  __device__ __forceinline__ double min(double v) const {
+    if (!COUPLED) return v;
+    sync();
+    if ((threadIdx.x & (WARP - 1)) == 0) slot[w] = v;
+    sync();
+    double s = slot[0];
+    for (int i = 1; i < g; ++i) s = fmin(s, slot[i]);
+    return s;
+  }
+  __device__ __forceinline__ bool any(bool b) const { return COUPLED ? sum(b ? 1.0 : 0.0) > 0.0 : b; }
+};
+
 // Event tape of one cell for the discrete adjoint (event kinds and rows as
 // CellsDev documents them).  Every lane keeps the counters; lane 0 writes the
 // events, each lane its own species of a row.  With ON false every method is
@@ -581,17 +628,28 @@ struct Recorder {
   }
 };
 
-template <typename T, int KS, bool STAGED, bool REC>
+// One cell (COUPLED: one cell of a coupled group; cell < 0 marks a warp
+// without a cell in a ragged last group, which follows the group's control
+// flow and contributes nothing).  invN scales the norms' sums: 1/S alone,
+// 1/(cells in the group * S) coupled.
+template <typename T, int KS, bool STAGED, bool REC, bool COUPLED>
 __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, const SolveParams &P, const Tabs &tb, double *Wd,
-                           T *WL, const int lane, const int64_t cell) {
+                           T *WL, const int lane, const int64_t cell, const Grp<COUPLED> &grp, const double invN) {
   const int64_t NC = C.n_cells;
   chem_cell_stats st = {};
   int status = CHEM_CELL_OK;
+  const bool phantom = COUPLED && cell < 0;
 
   Cell<T, KS, STAGED> cl(M, P, tb, Wd, WL, lane);
+  if (phantom) {
+#pragma unroll
+    for (int k = 0; k < KS; ++k) cl.own[k] = false;
+  }
   cl.init_constants();
   double y0[KS];
-  const bool bad = load_cell<KS>(M, C, Wd, lane, cell, cl.own, y0);
+#pragma unroll
+  for (int k = 0; k < KS; ++k) y0[k] = 0.0;
+  const bool bad = grp.any(phantom ? false : load_cell<KS>(M, C, Wd, lane, cell, cl.own, y0));
   Recorder<KS, REC> rec(C, cell, M.S);
 
   const double dt = P.dt;
@@ -606,7 +664,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
     // initial step (order 1)
     cl.eval_f(y0, f0);
     st.f_evals++;
-    const double d0 = cl.wrms(y0, w), d1 = cl.wrms(f0, w);
+    const double d0 = sqrt(grp.sum(cl.sumsq(y0, w)) * invN), d1 = sqrt(grp.sum(cl.sumsq(f0, w)) * invN);
     double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 * dt : 0.01 * d0 / d1;
     if (h0 > dt) h0 = dt;
 #pragma unroll
@@ -615,7 +673,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
     st.f_evals++;
 #pragma unroll
     for (int k = 0; k < KS; ++k) tmp[k] = f[k] - f0[k];
-    const double d2 = cl.wrms(tmp, w) / h0;
+    const double d2 = sqrt(grp.sum(cl.sumsq(tmp, w)) * invN) / h0;
     const double dm = d1 > d2 ? d1 : d2;
     const double h1 = (dm <= 1e-15) ? fmax(1e-6 * dt, h0 * 1e-3) : sqrt(0.01 / dm);
     h = fmin(fmin(100.0 * h0, h1), dt);
@@ -709,7 +767,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
 #pragma unroll
           for (int k = 0; k < KS; ++k) x[k] *= scale;
         }
-        del2 = cl.norm2(x, w);
+        del2 = grp.sum(cl.sumsq(x, w)) * invN;
 #pragma unroll
         for (int k = 0; k < KS; ++k) {
           d[k] += x[k];
@@ -744,7 +802,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
         bool neg = false;
 #pragma unroll
         for (int k = 0; k < KS; ++k) neg |= cl.own[k] && y[k] < 0.0;
-        if (__any_sync(FULL, neg)) {
+        if (grp.any(__any_sync(FULL, neg))) {
           double vs = 0.0, eta_c = 1.0;
 #pragma unroll
           for (int k = 0; k < KS; ++k)
@@ -754,9 +812,9 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
               const double r = (D[0][k] > 0.0) ? D[0][k] / (D[0][k] - y[k]) : 0.0;
               eta_c = fmin(eta_c, r);
             }
-          vs = warp_sum(vs);
-          eta_c = warp_min(eta_c);
-          if (vs * cl.invS <= tol2) {
+          vs = grp.sum(warp_sum(vs));
+          eta_c = grp.min(warp_min(eta_c));
+          if (vs * invN <= tol2) {
 #pragma unroll
             for (int k = 0; k < KS; ++k) {
               const bool p = cl.own[k] && y[k] < 0.0;
@@ -782,7 +840,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
       }
 
       // local error test
-      const double err2 = cl.norm2(d, w) * c_isq[q + 1];     // (||d|| / (q+1))^2
+      const double err2 = grp.sum(cl.sumsq(d, w)) * invN * c_isq[q + 1];     // (||d|| / (q+1))^2
       if (!(err2 <= 1.0)) {
         st.rejects++;
         nef++;
@@ -816,14 +874,14 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
         if (q > 1) {
           double row[KS];
           get_row<KS>(D, q, row);
-          const double e2 = cl.norm2(row, w) * c_isq[q];
+          const double e2 = grp.sum(cl.sumsq(row, w)) * invN * c_isq[q];
           const double em = grid_eta(gtab<double>(tb, M.tab.thr2), gtab<double>(tb, M.tab.g), e2, q - 1, lane);
           if (em > eta) { eta = em; qn = q - 1; }
         }
         if (q < qmax) {
           double row[KS];
           get_row<KS>(D, q + 2, row);
-          const double e2 = cl.norm2(row, w) * c_isq[q + 2];
+          const double e2 = grp.sum(cl.sumsq(row, w)) * invN * c_isq[q + 2];
           const double ep = grid_eta(gtab<double>(tb, M.tab.thr3), gtab<double>(tb, M.tab.g), e2, q + 1, lane);
           if (ep > eta) { eta = ep; qn = q + 1; }
         }
@@ -844,7 +902,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
       bool nf = false;
 #pragma unroll
       for (int k = 0; k < KS; ++k) nf |= cl.own[k] && !isfinite(D[0][k]);
-      if (__any_sync(FULL, nf)) status = CHEM_CELL_NONFINITE;
+      if (grp.any(__any_sync(FULL, nf))) status = CHEM_CELL_NONFINITE;
     }
     if (status == CHEM_CELL_OK) {
 #pragma unroll
@@ -853,7 +911,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
     }
   }
   rec.finish(status != CHEM_CELL_OK, lane);
-  if (lane == 0) {
+  if (lane == 0 && !phantom) {
     st.status = status;
     st.final_order = q;
     st.final_h = h;
@@ -884,10 +942,12 @@ __device__ bool stage_tables(const unsigned char *blob, int bytes, unsigned char
   return ok;
 }
 
-template <typename T, int KS, bool STAGED, bool REC>
+template <typename T, int KS, bool STAGED, bool REC, bool COUPLED>
 __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const __grid_constant__ MechDev M, const CellsDev C, const SolveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t tma_bar;
+  __shared__ double grp_slot[COUPLED ? MAX_WARPS_PER_BLOCK : 1];
+  __shared__ long long grp_next[COUPLED ? MAX_WARPS_PER_BLOCK : 1];
   const int lane = threadIdx.x & (WARP - 1);
   const int warp = threadIdx.x / WARP;
   Tabs tb;
@@ -901,18 +961,45 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const
   }
   double *Wd = reinterpret_cast<double *>(smem + P.tab_bytes + (size_t)warp * P.cell_bytes);
   T *WL = reinterpret_cast<T *>(Wd + P.wd_pad);
-  if (C.queue) {
+  Grp<COUPLED> grp;
+  const double invS = 1.0 / (double)M.S;
+  if (COUPLED) {
+    // groups of P.couple consecutive cells, P.warps_per_block / P.couple per
+    // block, each with named barrier 1 + its index; with the queue, groups are
+    // handed out whole
+    const int G = P.couple, gpb = P.warps_per_block / G, gl = warp / G;
+    grp.slot = grp_slot + gl * G;
+    grp.w = warp - gl * G;
+    grp.g = G;
+    grp.bar = 1 + gl;
+    if (gl < gpb) {
+      for (int64_t gi = (int64_t)blockIdx.x * gpb + gl;;) {
+        if (C.queue) {
+          grp.sync();
+          if (grp.w == 0 && lane == 0) grp_next[gl] = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(C.queue), 1ull);
+          grp.sync();
+          gi = grp_next[gl];
+        }
+        const int64_t c0 = gi * G;
+        if (c0 >= C.n_cells) break;
+        const int n_act = (int)((C.n_cells - c0) < G ? (C.n_cells - c0) : G);
+        const int64_t cell = grp.w < n_act ? c0 + grp.w : -1;
+        solve_cell<T, KS, STAGED, REC, COUPLED>(M, C, P, tb, Wd, WL, lane, cell, grp, 1.0 / (double)(n_act * M.S));
+        if (!C.queue) break;
+      }
+    }
+  } else if (C.queue) {
     for (;;) {
       long long cell = 0;
       if (lane == 0) cell = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(C.queue), 1ull);
       cell = __shfl_sync(FULL, cell, 0);
       if (cell >= C.n_cells) break;
       if (C.order) cell = __ldg(C.order + cell);
-      solve_cell<T, KS, STAGED, REC>(M, C, P, tb, Wd, WL, lane, cell);
+      solve_cell<T, KS, STAGED, REC, COUPLED>(M, C, P, tb, Wd, WL, lane, cell, grp, invS);
     }
   } else {
     const int64_t cell = (int64_t)blockIdx.x * P.warps_per_block + warp;
-    if (cell < C.n_cells) solve_cell<T, KS, STAGED, REC>(M, C, P, tb, Wd, WL, lane, cell);
+    if (cell < C.n_cells) solve_cell<T, KS, STAGED, REC, COUPLED>(M, C, P, tb, Wd, WL, lane, cell, grp, invS);
   }
   if (STAGED && !staged_ok) {
     __syncthreads();
@@ -988,7 +1075,7 @@ cudaError_t launch_probe_t(const MechDev &M, const CellsDev &C, const SolveParam
   return cudaGetLastError();
 }
 
-template <typename T, int KS, bool STAGED, bool REC>
+template <typename T, int KS, bool STAGED, bool REC, bool COUPLED>
 cudaError_t configure_t() {
   static bool configured[64] = {false};
   int dev = 0;
@@ -997,9 +1084,9 @@ cudaError_t configure_t() {
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, solve_kernel<T, KS, STAGED, REC>);
+  cudaError_t e = cudaFuncGetAttributes(&fa, solve_kernel<T, KS, STAGED, REC, COUPLED>);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(solve_kernel<T, KS, STAGED, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(solve_kernel<T, KS, STAGED, REC, COUPLED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            optin - (int)fa.sharedSizeBytes);
   if (e == cudaSuccess && dev < 64) configured[dev] = true;
   return e;
@@ -1007,33 +1094,36 @@ cudaError_t configure_t() {
 
 template <typename T, int KS, bool STAGED>
 int occupancy_t(int warps_per_block, size_t smem) {
-  if (configure_t<T, KS, STAGED, false>() != cudaSuccess) return 0;
+  if (configure_t<T, KS, STAGED, false, false>() != cudaSuccess) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, solve_kernel<T, KS, STAGED, false>, warps_per_block * WARP, smem) !=
-      cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, solve_kernel<T, KS, STAGED, false, false>, warps_per_block * WARP,
+                                                    smem) != cudaSuccess)
     return 0;
   return n;
 }
 
-template <typename T, int KS, bool STAGED, bool REC>
+template <typename T, int KS, bool STAGED, bool REC, bool COUPLED>
 cudaError_t launch_rec_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int blocks, cudaStream_t stream) {
   const size_t smem = (size_t)P.tab_bytes + (size_t)P.cell_bytes * P.warps_per_block;
-  cudaError_t e = configure_t<T, KS, STAGED, REC>();
+  cudaError_t e = configure_t<T, KS, STAGED, REC, COUPLED>();
   if (e != cudaSuccess) return e;
-  solve_kernel<T, KS, STAGED, REC><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, P);
+  solve_kernel<T, KS, STAGED, REC, COUPLED><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, P);
   return cudaGetLastError();
 }
 
-// The recording kernel exists for the FP64 iteration only (the adjoint
-// differentiates FP64 LU solves).
+// The recording kernel and the coupled (multi-cell) kernel exist for the
+// FP64 iteration only; they do not combine.
 template <typename T, int KS, bool STAGED>
-cudaError_t launch_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int blocks, cudaStream_t stream) {
+cudaError_t launch_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int blocks, bool coupled,
+                     cudaStream_t stream) {
   if constexpr (std::is_same<T, double>::value) {
-    if (C.tape_n) return launch_rec_t<T, KS, STAGED, true>(M, C, P, blocks, stream);
+    if (C.tape_n && coupled) return cudaErrorInvalidValue;
+    if (C.tape_n) return launch_rec_t<T, KS, STAGED, true, false>(M, C, P, blocks, stream);
+    if (coupled) return launch_rec_t<T, KS, STAGED, false, true>(M, C, P, blocks, stream);
   } else {
-    if (C.tape_n) return cudaErrorInvalidValue;
+    if (C.tape_n || coupled) return cudaErrorInvalidValue;
   }
-  return launch_rec_t<T, KS, STAGED, false>(M, C, P, blocks, stream);
+  return launch_rec_t<T, KS, STAGED, false, false>(M, C, P, blocks, stream);
 }
 
 template <typename T, bool STAGED>
@@ -1048,12 +1138,13 @@ int occupancy_ks(const MechDev &M, int warps_per_block, size_t smem) {
 }
 
 template <typename T, bool STAGED>
-cudaError_t launch_ks(const MechDev &M, const CellsDev &C, const SolveParams &P, int blocks, cudaStream_t stream) {
+cudaError_t launch_ks(const MechDev &M, const CellsDev &C, const SolveParams &P, int blocks, bool coupled,
+                      cudaStream_t stream) {
   switch ((M.S + WARP - 1) / WARP) {
-    case 1: return launch_t<T, 1, STAGED>(M, C, P, blocks, stream);
-    case 2: return launch_t<T, 2, STAGED>(M, C, P, blocks, stream);
-    case 3: return launch_t<T, 3, STAGED>(M, C, P, blocks, stream);
-    case 4: return launch_t<T, 4, STAGED>(M, C, P, blocks, stream);
+    case 1: return launch_t<T, 1, STAGED>(M, C, P, blocks, coupled, stream);
+    case 2: return launch_t<T, 2, STAGED>(M, C, P, blocks, coupled, stream);
+    case 3: return launch_t<T, 3, STAGED>(M, C, P, blocks, coupled, stream);
+    case 4: return launch_t<T, 4, STAGED>(M, C, P, blocks, coupled, stream);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1587,19 +1678,25 @@ cudaError_t launch_solve(const MechDev &M, const CellsDev &C, const LaunchCfg &c
   int dev = 0, n_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  P.couple = cfg.couple > 1 ? cfg.couple : 1;
+  if (P.warps_per_block % P.couple) return cudaErrorInvalidValue;
+  // blocks needed to give every cell (every group) a warp (group of warps)
+  const int64_t units = (C.n_cells + P.couple - 1) / P.couple, per_block = P.warps_per_block / P.couple;
+  const int64_t need = (units + per_block - 1) / per_block;
   int blocks;
   if (cfg.driver == CHEM_DRIVER_PERSISTENT) {
     int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : occupancy(M, cfg.lu_precision, cfg.driver, cfg.warps_per_block);
     if (bps < 1) bps = 1;
     blocks = n_sm * bps;
-    const int64_t need = (C.n_cells + P.warps_per_block - 1) / P.warps_per_block;
     if (blocks > need) blocks = (int)need;
   } else {
-    blocks = (int)((C.n_cells + P.warps_per_block - 1) / P.warps_per_block);
+    blocks = (int)need;
   }
   const bool f32 = cfg.lu_precision == 32;
-  if (staged) return f32 ? launch_ks<float, true>(M, C, P, blocks, stream) : launch_ks<double, true>(M, C, P, blocks, stream);
-  return f32 ? launch_ks<float, false>(M, C, P, blocks, stream) : launch_ks<double, false>(M, C, P, blocks, stream);
+  const bool coupled = cfg.couple > 1;      // warps_per_block is then the group size
+  if (staged)
+    return f32 ? launch_ks<float, true>(M, C, P, blocks, coupled, stream) : launch_ks<double, true>(M, C, P, blocks, coupled, stream);
+  return f32 ? launch_ks<float, false>(M, C, P, blocks, coupled, stream) : launch_ks<double, false>(M, C, P, blocks, coupled, stream);
 }
 
 cudaError_t launch_adjoint(const MechDev &M, const CellsDev &C, const AdjDev &A, cudaStream_t stream) {

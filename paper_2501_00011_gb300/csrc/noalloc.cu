@@ -63,6 +63,7 @@ extern "C" int chem_solve_step_noalloc(const chem_mech *mech, int64_t n_cells, c
   if (o.lu_precision != 64 && o.lu_precision != 32) return fail(CHEM_EINVAL, "lu_precision must be 64 or 32");
   if (o.cells_per_block < 0 || o.cells_per_block > MAX_WARPS_PER_BLOCK || o.blocks_per_sm < 0)
     return fail(CHEM_EINVAL, "bad launch shape");
+  if (o.couple_cells > 1) return fail(CHEM_EINVAL, "coupled cells are not supported here");
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -96,7 +97,7 @@ extern "C" int chem_solve_step_noalloc(const chem_mech *mech, int64_t n_cells, c
   cd.stats = stats;
   cd.queue = reinterpret_cast<int *>(g_scratch_addr[dev]);
   cd.error = reinterpret_cast<int *>(reinterpret_cast<unsigned long long *>(g_scratch_addr[dev]) + 1);
-  LaunchCfg cfg;
+  LaunchCfg cfg{};
   cfg.lu_precision = o.lu_precision;
   cfg.driver = CHEM_DRIVER_PERSISTENT;
   cfg.warps_per_block = o.cells_per_block;
