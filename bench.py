@@ -320,9 +320,13 @@ def run_gpu(args):
         w5 = torch.from_numpy(synth.loss_weights(wl5.mech.n_species, n5)).to(dev)
         gth = torch.zeros(wl5.mech.n_reactions, dtype=torch.float64, device=dev)
         gy0 = torch.zeros_like(y5)
-        fwd, bwd = [], []
+        rng5 = np.random.default_rng(22)
+        dy05 = torch.from_numpy(rng5.standard_normal(wl5.cells.y.shape) * wl5.cells.y).to(dev)
+        dth5 = torch.from_numpy(rng5.standard_normal(wl5.mech.n_reactions)).to(dev)
+        dy5 = torch.zeros_like(y5)
+        fwd, bwd, tan = [], [], []
         for rep in range(3):
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             flush.fill_(float(rep))
             e[0].record(stream)
             c5.set_state(T5, P5, y5, stream=stream)
@@ -333,16 +337,21 @@ def run_gpu(args):
             if ws > 1:                    # the one exchange: dL/dtheta summed over ranks in rank order
                 gth = shard.reduce_theta_grad(gth)
             e[2].record(stream)
+            _, n_bad_t = c5.tangent(dy05, dth5, dy5, stream=stream)
+            e[3].record(stream)
             barrier()
             if rep > 0:
                 fwd.append(e[0].elapsed_time(e[1]))
                 bwd.append(e[1].elapsed_time(e[2]))
+                tan.append(e[2].elapsed_time(e[3]))
         c5.close()
         tf, tb = min(fwd), min(bwd)
         out["adjoint_2k"] = {
             "value": n5 / ((tf + tb) / 1e3), "unit": "cells/s (4-step forward with tape + discrete adjoint)",
             "forward_ms": tf, "backward_ms": tb, "cells": n5, "steps": wl5.n_steps, "cells_bad": n_bad,
-            "form": "persistent forward recording the tape; one warp per cell backward through transposed sparse LU"}
+            "tangent_ms": min(tan), "tangent_cells_bad": n_bad_t,
+            "form": "persistent forward recording the tape; one warp per cell backward through transposed sparse LU; "
+                    "tangent: one warp per cell forward along the tape (one direction in y0 and theta)"}
         return out
 
     def time_form(lu_precision, driver, steps, warmup):

@@ -232,6 +232,23 @@ int chem_get_stats(const chem_cells *cells, chem_cell_stats *out, int32_t mem, v
  * dL_dtheta). */
 int chem_sensitivity(chem_cells *cells, const double *dL_dy, double *dL_dtheta, double *dL_dy0, int32_t mem,
                      void *stream);
+/* Tangent (forward-mode) sensitivity of the same frozen-control map
+ * (needs opts.record_adjoint): the directional derivative
+ *   dy[n_species][n_cells] = (d y / d y0) dy0 + (d y / d theta) dtheta
+ * of the current state along dy0[n_species][n_cells] (a direction in the state
+ * at set_state) and dtheta[n_reactions] (a direction in the log multipliers,
+ * shared by all cells; NULL = 0).  Its dot product with any dL_dy equals
+ * <dL_dy0, dy0> + <dL_dtheta, dtheta> from chem_sensitivity, up to rounding.
+ * One warp per cell walks its tape forward: each corrector iteration applies
+ * the f program to the tangent rates k~_j sum_s (prod_{s' != s} y) v_s +
+ * r_j dtheta_j (that is J v + F_theta dtheta) and one sparse LU solve with the
+ * recorded iteration matrix.  The paper has no tangent; it differentiates the
+ * paper's BDF/Newton integration.  Inputs and output in `mem` space,
+ * asynchronous copies on `stream`, then synchronises stream.  Returns 0, a
+ * negative error, or the number of cells whose tape overflowed or whose
+ * forward solve failed (their dy is 0).  Errors: CHEM_EINVAL, CHEM_ESTATE (no
+ * recording, no state), CHEM_ECUDA. */
+int chem_tangent(chem_cells *cells, const double *dy0, const double *dtheta, double *dy, int32_t mem, void *stream);
 /* The recorded tape of one cell, in host arrays of `capacity` events: kind
  * 0 = INIT (val h0), 1 = RESCALE (q order, val eta), 2 = STEP (q order, val
  * c = h/gamma_q), 3 = PROJECT (q the species the next STEP projects onto 0),

@@ -30,7 +30,7 @@ EXPORTS = ["chem_opts_default", "chem_mechanism_create", "chem_mechanism_destroy
            "chem_cells_set_theta", "chem_solve_step", "chem_solve_steps", "chem_autotune",
            "chem_get_state", "chem_get_stats",
            "chem_eval_deriv", "chem_eval_newton_solve", "chem_eval_deriv_design", "chem_solve_step_noalloc", "chem_sensitivity",
-           "chem_get_tape", "chem_last_error"]
+           "chem_tangent", "chem_get_tape", "chem_last_error"]
 
 
 DERIV_GATHER, DERIV_ATOMIC_AOS, DERIV_ATOMIC_SOA = 0, 1, 2
@@ -100,6 +100,7 @@ def load(path: str | None = None):
         L.chem_eval_deriv_design.argtypes = [V, ct.c_int32, V, V, ct.c_int32, V]
         L.chem_solve_step_noalloc.argtypes = [V, ct.c_int64, V, V, V, V, V, V, ct.c_double, V, V]
         L.chem_sensitivity.argtypes = [V, V, V, V, ct.c_int32, V]
+        L.chem_tangent.argtypes = [V, V, V, V, ct.c_int32, V]
         L.chem_solve_steps.argtypes = [V, ct.c_double, ct.c_int32, V]
         L.chem_autotune.argtypes = [V, ct.c_double, ct.c_int64, V, V]
         L.chem_get_tape.argtypes = [V, ct.c_int64, V, V, V, V, ct.c_int32, V, V]
@@ -320,6 +321,18 @@ class Cells:
             raise ChemError("dL_dy, dL_dtheta and dL_dy0 must all be on the host or all on the device")
         n_bad = _check(load().chem_sensitivity(self._h, pa, pt, p0, ma, _stream_ptr(stream)), "chem_sensitivity")
         return dL_dtheta, dL_dy0, n_bad
+
+    def tangent(self, dy0, dtheta=None, dy=None, stream=None):
+        """(dy [S, C], n_bad): the directional derivative of the current state
+        along dy0 [S, C] (the state at set_state) and dtheta [R] (None: 0)."""
+        if dy is None:
+            dy = np.zeros((self.mech.n_species, self.n_cells))
+        (p0, m0, k1), (po, mo, k2) = _ptr(dy0), _ptr(dy)
+        pt, mt, k3 = _ptr(dtheta) if dtheta is not None else (None, m0, None)
+        if not (m0 == mo == mt):
+            raise ChemError("dy0, dtheta and dy must all be on the host or all on the device")
+        n_bad = _check(load().chem_tangent(self._h, p0, pt, po, m0, _stream_ptr(stream)), "chem_tangent")
+        return dy, n_bad
 
     def get_tape(self, cell: int):
         """(kind, q, val, rows) of one cell's recorded tape; rows [n_rows, S] belong,

@@ -718,6 +718,52 @@ int chem_sensitivity(chem_cells *c, const double *dL_dy, double *dL_dtheta, doub
   return n_bad;
 }
 
+int chem_tangent(chem_cells *c, const double *dy0, const double *dtheta, double *dy, int32_t mem, void *stream) {
+  g_err.clear();
+  if (!c || !dy0 || !dy) return fail(CHEM_EINVAL, "NULL argument");
+  if (int rc = check_mem(mem)) return rc;
+  if (!c->tape_n) return fail(CHEM_ESTATE, "the batch was created without record_adjoint");
+  if (!c->have_state) return fail(CHEM_ESTATE, "tangent before set_state");
+  const size_t n = (size_t)c->n, S = (size_t)c->mech->m.S, R = (size_t)c->mech->m.R;
+  if (n == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  // the adjoint's buffers hold the tangent's input and output
+  if ((e = cudaMemcpyAsync(c->dLdy, dy0, n * S * sizeof(double), kind_in(mem), s)) != cudaSuccess ||
+      (dtheta && R > 0 && (e = cudaMemcpyAsync(c->dLdtheta, dtheta, R * sizeof(double), kind_in(mem), s)) != cudaSuccess))
+    return cuda_fail(e, "tangent copy-in");
+  CellsDev cd{};
+  cd.n_cells = c->n;
+  cd.T = c->T;
+  cd.P = c->P;
+  cd.J = c->use_J ? c->J : nullptr;
+  cd.theta = c->use_theta ? c->theta : nullptr;
+  cd.y = c->y;
+  cd.stats = c->stats;
+  cd.tape_kq = c->tape_kq;
+  cd.ytape = c->ytape;
+  cd.tape_val = c->tape_val;
+  cd.tape_n = c->tape_n;
+  cd.tape_rows = c->tape_rows;
+  cd.tape_bad = c->tape_bad;
+  cd.tape_cap = c->tape_cap;
+  cd.row_cap = c->row_cap;
+  TanDev td;
+  td.dy0 = c->dLdy;
+  td.dtheta = (dtheta && R > 0) ? c->dLdtheta : nullptr;
+  td.dy = c->dLdy0;
+  if ((e = launch_tangent(c->mech->m.dev, cd, td, s)) != cudaSuccess) return cuda_fail(e, "tangent kernel");
+  if ((e = cudaMemcpyAsync(dy, c->dLdy0, n * S * sizeof(double), kind_out(mem), s)) != cudaSuccess)
+    return cuda_fail(e, "tangent copy-out");
+  std::vector<int> bad(n);
+  if ((e = cudaMemcpyAsync(bad.data(), c->tape_bad, n * sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_fail(e, "tangent sync");
+  int n_bad = 0;
+  for (int v : bad) n_bad += v != 0;
+  return n_bad;
+}
+
 int chem_get_tape(const chem_cells *c, int64_t cell, int32_t *kind, int32_t *q, double *val, double *rows,
                   int32_t capacity, int32_t *n_events, int32_t *n_rows) {
   g_err.clear();

@@ -175,6 +175,13 @@ struct AdjDev {
   double *dLdtheta;             // [R]
 };
 
+// Buffers of chem_tangent (device, owned by the batch).
+struct TanDev {
+  const double *dy0;            // [S][C] direction in the initial state
+  const double *dtheta;         // [R] direction in theta (shared by all cells)
+  double *dy;                   // [S][C] out: the directional derivative of the state
+};
+
 struct LaunchCfg {
   int lu_precision;     // 64 / 32
   int driver;           // CHEM_DRIVER_*
@@ -207,6 +214,7 @@ cudaError_t launch_probe(const MechDev &M, const CellsDev &C, int lu_precision, 
 
 // discrete adjoint: replay (exact steps, y rows), backward sweep, theta reduction
 cudaError_t launch_adjoint(const MechDev &m, const CellsDev &c, const AdjDev &a, cudaStream_t stream);
+cudaError_t launch_tangent(const MechDev &m, const CellsDev &c, const TanDev &t, cudaStream_t stream);
 // deriv.cu: derivative-only kernels for comparing designs.  kt[R][C] rate
 // constants of the batch (launch_rates fills it); y, f [S][C] on the device.
 cudaError_t launch_rates(const MechDev &m, const CellsDev &c, double *kt, cudaStream_t stream);

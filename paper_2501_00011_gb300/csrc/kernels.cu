@@ -1433,6 +1433,228 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) adjoint_kernel(con
   backward_cell<KS>(M, C, A, P, tb, Wd, WL, lane, cell);
 }
 
+// ---------------------------------------------------------------- tangent
+// Forward-mode derivative of the same frozen-control map the adjoint
+// differentiates: one warp per cell walks its tape forward carrying the
+// tangent dD of the history in registers.  The iterations need
+// c (J(y_k) v + F_theta(y_k) dtheta) - dpsi - dd, and J v + F_theta dtheta is
+// the f program applied to s_j = k~_j sum_s (prod_{s' != s} y) v_s + r_j dtheta_j
+// in place of the rates r_j; then one solve with the REFACTOR's LU.
+
+// f-program image of J(y) v + F_theta dtheta; y in Wd[Y], v in Wd[a_MU]
+template <int KS>
+__device__ __forceinline__ void tangent_f(const MechDev &M, const Tabs &tb, double *Wd, const double *dtheta,
+                                          const bool (&own)[KS], const double (&v)[KS], double (&out)[KS], int lane) {
+#pragma unroll
+  for (int k = 0; k < KS; ++k)
+    if (own[k]) Wd[M.a_MU + lane + WARP * k] = v[k];
+  __syncwarp();
+  unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
+  const unsigned dv = (unsigned)(M.a_MU - M.d_Y) * 8u;      // from y_l to v_l
+  for (int j = lane; j < M.R; j += WARP) {
+    const uint2 sl = tab<uint2>(tb, M.tab.rx_slots)[j];
+    const unsigned o1 = sl.x & 0xffff, o2 = sl.x >> 16, o3 = sl.y & 0xffff;
+    const int nr = __ldg(M.rx_nreac + j);
+    const double kt = Wd[M.d_KT + j];
+    const double y1 = at<double>(wd, o1), v1 = at<double>(wd, o1 + dv);
+    double sv, r;
+    if (nr == 1) {
+      sv = v1;
+      r = y1;
+    } else {
+      const double y2 = at<double>(wd, o2), v2 = at<double>(wd, o2 + dv);
+      if (nr == 2) {
+        sv = v1 * y2 + y1 * v2;
+        r = y1 * y2;
+      } else {
+        const double y3 = at<double>(wd, o3), v3 = at<double>(wd, o3 + dv);
+        sv = v1 * y2 * y3 + y1 * v2 * y3 + y1 * y2 * v3;
+        r = y1 * y2 * y3;
+      }
+    }
+    double sj = kt * sv;
+    if (dtheta) sj = fma(kt * r, dtheta[j], sj);
+    Wd[M.d_RT + j] = sj;
+  }
+  __syncwarp();
+  run_ops<double, false, false>(tab<ushort4>(tb, M.tab.f_ops), M.f_npass, Wd, lane);
+#pragma unroll
+  for (int k = 0; k < KS; ++k) out[k] = own[k] ? Wd[M.d_F + lane + WARP * k] : 0.0;
+  __syncwarp();
+}
+
+template <int KS>
+__device__ void tangent_cell(const MechDev &M, const CellsDev &C, const TanDev &A, const SolveParams &P, const Tabs &tb,
+                             double *Wd, double *WL, const int lane, const int64_t cell) {
+  const int64_t NC = C.n_cells;
+  Cell<double, KS, false> cl(M, P, tb, Wd, WL, lane);
+  cl.init_constants();
+  double y0[KS];
+  load_cell<KS>(M, C, Wd, lane, cell, cl.own, y0);   // rate constants
+  double dD[NROW][KS];
+#pragma unroll
+  for (int m = 0; m < NROW; ++m)
+#pragma unroll
+    for (int k = 0; k < KS; ++k) dD[m][k] = 0.0;
+#pragma unroll
+  for (int k = 0; k < KS; ++k) dD[0][k] = cl.own[k] ? A.dy0[(int64_t)(lane + WARP * k) * NC + cell] : 0.0;
+  const int n = C.tape_n[cell], nrows = C.tape_rows[cell];
+  const int *kqs = C.tape_kq + cell * (int64_t)C.tape_cap;
+  const double *vals = C.tape_val + cell * (int64_t)C.tape_cap;
+  const double *yt = C.ytape + cell * (int64_t)C.row_cap * M.S;
+  int row = 0;
+  bool in_step = false, have_M = false, bad = false;
+  double cM = 0.0, sc = 0.0, ss = 1.0;
+  int sq = 1;
+  double dyp[KS], dpsi[KS], dd[KS];
+  bool pm[KS];
+#pragma unroll
+  for (int k = 0; k < KS; ++k) {
+    dyp[k] = dpsi[k] = dd[k] = 0.0;
+    pm[k] = false;
+  }
+  for (int e = 0; e < n; ++e) {
+    const int kq = __ldg(kqs + e);
+    const double val = __ldg(vals + e);
+    const int kind = kq & 0xff, q = kq >> 8;
+    if (!in_step && (kind == EV_ITER || kind == EV_PROJECT || kind == EV_STEP)) {
+      // a step's events are its iterations, its projections, then the STEP (q, c):
+      // read ahead to the STEP and form the predictor's tangent
+      int es = e;
+      for (; es < n; ++es) {
+        const int kq2 = __ldg(kqs + es);
+        if ((kq2 & 0xff) == EV_STEP) break;
+        if ((kq2 & 0xff) == EV_PROJECT) {
+#pragma unroll
+          for (int k = 0; k < KS; ++k)
+            if ((kq2 >> 8) == lane + WARP * k) pm[k] = true;
+        }
+      }
+      if (es >= n || !have_M) {
+        bad = true;
+        break;
+      }
+      sq = __ldg(kqs + es) >> 8;
+      sc = __ldg(vals + es);
+      ss = (sc == cM) ? 1.0 : 2.0 / (1.0 + sc * (1.0 / cM));   // as the forward formed it
+      const double iq = c_igam[sq];
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        dyp[k] = dD[0][k];
+        dpsi[k] = 0.0;
+        dd[k] = 0.0;
+      }
+#pragma unroll
+      for (int m = 1; m <= QMAX; ++m) {
+        if (m > sq) continue;
+        const double gm = c_gam[m];
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+          dyp[k] += dD[m][k];
+          dpsi[k] = fma(gm, dD[m][k], dpsi[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < KS; ++k) dpsi[k] *= iq;
+      in_step = true;
+    }
+    if (kind == EV_RESCALE) {
+      rescale<KS>(dD, q, val, M.rescale_coef, lane);
+    } else if (kind == EV_INIT) {
+      // D_0 = y, D_1 = h0 f(y), higher rows reset
+      if (row >= nrows) {
+        bad = true;
+        break;
+      }
+      double y[KS], g[KS], d0[KS];
+      read_row<KS>(yt, row++, M.S, cl.own, lane, y);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        d0[k] = dD[0][k];
+        if (cl.own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
+      }
+      tangent_f<KS>(M, tb, Wd, A.dtheta, cl.own, d0, g, lane);
+#pragma unroll
+      for (int m = 1; m < NROW; ++m)
+#pragma unroll
+        for (int k = 0; k < KS; ++k) dD[m][k] = 0.0;
+#pragma unroll
+      for (int k = 0; k < KS; ++k) dD[1][k] = val * g[k];
+    } else if (kind == EV_REFACTOR) {
+      // the iteration matrix of the recorded run (a constant of the map)
+      if (row >= nrows) {
+        bad = true;
+        break;
+      }
+      double yJ[KS];
+      read_row<KS>(yt, row++, M.S, cl.own, lane, yJ);
+      cl.form_and_factor(val, yJ);
+      cM = val;
+      have_M = true;
+    } else if (kind == EV_ITER) {
+      if (row >= nrows) {
+        bad = true;
+        break;
+      }
+      double y[KS], v[KS], g[KS], b[KS], x[KS];
+      read_row<KS>(yt, row++, M.S, cl.own, lane, y);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        v[k] = dyp[k] + dd[k];
+        if (cl.own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
+      }
+      tangent_f<KS>(M, tb, Wd, A.dtheta, cl.own, v, g, lane);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) b[k] = sc * g[k] - dpsi[k] - dd[k];
+      cl.solve(b, x);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) dd[k] = fma(ss, x[k], dd[k]);
+    } else if (kind == EV_STEP) {
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        if (pm[k]) dd[k] = -dyp[k];          // projected onto y = 0
+        pm[k] = false;
+      }
+      accept_update<KS>(dD, sq, dd);
+      in_step = false;
+    }
+    // PROJECT events were read with their step's predictor
+  }
+#pragma unroll
+  for (int k = 0; k < KS; ++k)
+    if (cl.own[k]) A.dy[(int64_t)(lane + WARP * k) * NC + cell] = bad ? 0.0 : dD[0][k];
+  if (bad && lane == 0) C.tape_bad[cell] = 1;
+}
+
+template <int KS>
+__global__ void __launch_bounds__(ADJ_WARPS_PER_BLOCK * WARP) tangent_kernel(const __grid_constant__ MechDev M, const CellsDev C,
+                                                                    const TanDev A, const SolveParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & (WARP - 1);
+  const int warp = threadIdx.x / WARP;
+  const int64_t cell = (int64_t)blockIdx.x * P.warps_per_block + warp;
+  if (cell >= C.n_cells) return;
+  Tabs tb;
+  tb.base = tb.gbase = M.blob[0];
+  double *Wd = reinterpret_cast<double *>(smem + (size_t)warp * P.cell_bytes);
+  double *WL = Wd + P.wd_pad;
+  if (C.tape_bad[cell]) {
+    for (int i = lane; i < M.S; i += WARP) A.dy[(int64_t)i * C.n_cells + cell] = 0.0;
+    return;
+  }
+  tangent_cell<KS>(M, C, A, P, tb, Wd, WL, lane, cell);
+}
+
+template <int KS>
+cudaError_t launch_tan_t(const MechDev &M, const CellsDev &C, const TanDev &A, const SolveParams &P, cudaStream_t stream) {
+  const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
+  cudaError_t e = allow_max_smem<tangent_kernel<KS>>();
+  if (e != cudaSuccess) return e;
+  const int blocks = (int)((C.n_cells + P.warps_per_block - 1) / P.warps_per_block);
+  tangent_kernel<KS><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, A, P);
+  return cudaGetLastError();
+}
+
 // dL/dtheta_j = sum over cells of the per-cell gradients, in cell order
 __global__ void theta_reduce_kernel(const double *gcell, int64_t n_cells, int R, double *out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1725,6 +1947,28 @@ cudaError_t launch_adjoint(const MechDev &M, const CellsDev &C, const AdjDev &A,
   if (e != cudaSuccess) return e;
   theta_reduce_kernel<<<(M.R + 127) / 128, 128, 0, stream>>>(A.gcell, C.n_cells, M.R, A.dLdtheta);
   return cudaGetLastError();
+}
+
+cudaError_t launch_tangent(const MechDev &M, const CellsDev &C, const TanDev &A, cudaStream_t stream) {
+  if (C.n_cells <= 0) return cudaSuccess;
+  SolveParams P{};
+  P.wd_pad = (M.Wda_len + 1) & ~1;
+  P.cell_bytes = (int)(((size_t)P.wd_pad * sizeof(double) + (size_t)M.WL_len * sizeof(double) + 15) & ~(size_t)15);
+  P.prec = 0;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int w = optin / P.cell_bytes;
+  if (w > ADJ_WARPS_PER_BLOCK) w = ADJ_WARPS_PER_BLOCK;
+  if (w < 1) return cudaErrorInvalidValue;
+  P.warps_per_block = w;
+  switch ((M.S + WARP - 1) / WARP) {
+    case 1: return launch_tan_t<1>(M, C, A, P, stream);
+    case 2: return launch_tan_t<2>(M, C, A, P, stream);
+    case 3: return launch_tan_t<3>(M, C, A, P, stream);
+    case 4: return launch_tan_t<4>(M, C, A, P, stream);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_deriv_gather(const MechDev &M, const CellsDev &C, const double *kt, const double *y, double *f,
