@@ -58,9 +58,21 @@ extern "C" {
 #define CHEM_MEM_HOST 0
 #define CHEM_MEM_DEVICE 1
 
-/* reaction kinds */
-#define CHEM_THERMAL 0     /* k = A exp(-Ea/T) (T/300)^B, times n_air^(n_reac-1) */
+/* reaction kinds.  The rate r_j is a function of the state, T and P
+ * (Background section); every kind keeps mass action r = k~(T, P) prod y, with
+ * k~ the rate constant below times n_air^(n_reac-1) so that rates act on
+ * mixing ratios.  Arrhenius terms: k_a = A exp(-Ea/T) (T/300)^B (parameters
+ * A, Ea_over_R, B), k_b likewise from A2, Ea2_over_R, B2 and k_c from A3,
+ * Ea3_over_R, B3; [M] = n_air, the number density of air (molecules cm^-3). */
+#define CHEM_THERMAL 0     /* k = k_a */
 #define CHEM_PHOTOLYSIS 1  /* first-order rate J (s^-1), optionally per cell */
+#define CHEM_TROE 2        /* pressure fall-off between k0 = k_a (low-pressure limit, per [M]) and
+                              kinf = k_b (high-pressure limit): with x = k0 [M] / kinf,
+                              k = k0 [M] / (1 + x) * Fc^(1 / (1 + (log10(x) / N)^2)); Fc in (0, 1],
+                              N > 0 (Fc = 1: Lindemann-Hinshelwood) */
+#define CHEM_PRESSURE_SUM 3   /* k = k_a + k_b [M] (a pressure-dependent term added to a
+                                 bimolecular one, as for HO2 + HO2) */
+#define CHEM_FALLOFF_SUM 4    /* k = k_a + k_c [M] / (1 + k_c [M] / k_b) (as for OH + HNO3) */
 
 /* per-cell status */
 #define CHEM_CELL_OK 0
@@ -85,14 +97,17 @@ extern "C" {
  * product gains yield * r (Background section, per-reaction rate of change).
  */
 typedef struct {
-  int32_t kind;                   /* CHEM_THERMAL or CHEM_PHOTOLYSIS */
+  int32_t kind;                   /* CHEM_THERMAL .. CHEM_FALLOFF_SUM */
   int32_t n_reac;                 /* 1..CHEM_MAX_REAC */
   int32_t reac[CHEM_MAX_REAC];
   int32_t n_prod;                 /* 0..CHEM_MAX_PROD */
   int32_t prod[CHEM_MAX_PROD];
   double yield[CHEM_MAX_PROD];
-  double A, Ea_over_R, B;         /* thermal parameters */
+  double A, Ea_over_R, B;         /* Arrhenius term k_a */
   double J;                       /* photolysis rate (s^-1) */
+  double A2, Ea2_over_R, B2;      /* Arrhenius term k_b (TROE, PRESSURE_SUM, FALLOFF_SUM) */
+  double A3, Ea3_over_R, B3;      /* Arrhenius term k_c (FALLOFF_SUM) */
+  double Fc, N;                   /* TROE broadening */
 } chem_reaction;
 
 typedef struct chem_mech chem_mech;

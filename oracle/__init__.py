@@ -46,7 +46,7 @@ class _Mech(ct.Structure):
                 ("kind", ct.c_void_p), ("n_reac", ct.c_void_p), ("reac", ct.c_void_p),
                 ("n_prod", ct.c_void_p), ("prod", ct.c_void_p),
                 ("yld", ct.c_void_p), ("A", ct.c_void_p), ("Ea", ct.c_void_p),
-                ("B", ct.c_void_p), ("J", ct.c_void_p)]
+                ("B", ct.c_void_p), ("J", ct.c_void_p), ("ext", ct.c_void_p)]
 
 
 class _Opts(ct.Structure):
@@ -124,11 +124,14 @@ class OracleMechanism:
             prod=np.ascontiguousarray(mech.prod, np.int32),
             yld=np.ascontiguousarray(mech.yld, np.float64),
             A=np.ascontiguousarray(mech.A, np.float64), Ea=np.ascontiguousarray(mech.Ea, np.float64),
-            B=np.ascontiguousarray(mech.B, np.float64), J=np.ascontiguousarray(mech.J, np.float64))
+            B=np.ascontiguousarray(mech.B, np.float64), J=np.ascontiguousarray(mech.J, np.float64),
+            ext=np.ascontiguousarray(np.zeros((self.R, 8)) if getattr(mech, "ext", None) is None else mech.ext,
+                                     np.float64))
         assert self._arrs["reac"].shape[1] == 3 and self._arrs["prod"].shape[1] == 8
         a = self._arrs
         self.c = _Mech(self.S, self.R, *(a[k].ctypes.data for k in
-                                         ("kind", "n_reac", "reac", "n_prod", "prod", "yld", "A", "Ea", "B", "J")))
+                                         ("kind", "n_reac", "reac", "n_prod", "prod", "yld", "A", "Ea", "B", "J",
+                                          "ext")))
         self.n_phot = int(np.count_nonzero(a["kind"] == 1))
 
     @property
@@ -345,6 +348,7 @@ def replicate(mech, G: int):
         big.prod[sl] = np.where(mech.prod >= 0, mech.prod + g * S, -1)
         big.yld[sl] = mech.yld
         big.A[sl], big.Ea[sl], big.B[sl], big.J[sl] = mech.A, mech.Ea, mech.B, mech.J
+        big.ext[sl] = synth.rate_ext(mech)
     return big
 
 

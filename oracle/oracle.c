@@ -50,6 +50,43 @@ static double gamma_of(int m) {
 
 /* ------------------------------------------------------------ a1: k~_j(T,P) */
 
+static double arrhenius(double A, double Ea_over_R, double B, double T) {
+  return A * exp(-Ea_over_R / T) * pow(T / 300.0, B);
+}
+
+/*
+ * The rate constant of a pressure-dependent reaction (the rate is a function of
+ * the state, T and P: Background section), from the first Arrhenius term ka
+ * and the air number density nm = [M]:
+ *   Troe fall-off: the Lindemann-Hinshelwood interpolation between the
+ *     low-pressure rate k0 [M] (k0 = ka) and the high-pressure limit kinf
+ *     (second term), times the broadening factor F with
+ *     log10 F = log10 Fc / (1 + (log10(k0 [M] / kinf) / N)^2);
+ *   pressure sum: ka + kb [M];
+ *   fall-off sum: ka plus a Lindemann term between kc [M] and kb.
+ */
+static double pressure_dependent(const orc_mech *m, int j, double ka, double T, double nm) {
+  const double *e = m->ext + (size_t)j * 8;
+  const double kb = arrhenius(e[0], e[1], e[2], T);
+  switch (m->kind[j]) {
+    case ORC_TROE: {
+      const double low = ka * nm;                 /* k0 [M] */
+      const double lindemann = low * kb / (low + kb);
+      const double c = log10(low / kb) / e[7];
+      const double logF = log10(e[6]) / (1.0 + c * c);
+      return lindemann * pow(10.0, logF);
+    }
+    case ORC_PRESSURE_SUM:
+      return ka + kb * nm;
+    case ORC_FALLOFF_SUM: {
+      const double low = arrhenius(e[3], e[4], e[5], T) * nm;   /* kc [M] */
+      return ka + low * kb / (low + kb);
+    }
+    default:
+      return ka;
+  }
+}
+
 void orc_rate_constants(const orc_mech *m, double T, double P, const double *jphot,
                         const double *theta, double *kt) {
   const double n_air = P / (K_BOLTZMANN * T) * 1e-6;
@@ -62,7 +99,8 @@ void orc_rate_constants(const orc_mech *m, double T, double P, const double *jph
     } else {
       /* Arrhenius k = A exp(-Ea/T) (T/300)^B; n-th order rates act on mixing
        * ratios, so multiply by n_air once per reactant beyond the first. */
-      k = m->A[j] * exp(-m->Ea[j] / T) * pow(T / 300.0, m->B[j]);
+      k = arrhenius(m->A[j], m->Ea[j], m->B[j], T);
+      if (m->kind[j] != ORC_THERMAL) k = pressure_dependent(m, j, k, T, n_air);
       for (int r = 1; r < m->n_reac[j]; ++r) k *= n_air;
     }
     if (theta) k *= exp(theta[j]);

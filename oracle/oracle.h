@@ -42,7 +42,7 @@ extern "C" {
 #define ORC_MAX_PROD 8
 #define ORC_QMAX 5
 
-enum { ORC_THERMAL = 0, ORC_PHOTOLYSIS = 1 };
+enum { ORC_THERMAL = 0, ORC_PHOTOLYSIS = 1, ORC_TROE = 2, ORC_PRESSURE_SUM = 3, ORC_FALLOFF_SUM = 4 };
 
 enum {
   ORC_OK = 0,
@@ -54,11 +54,15 @@ enum {
   ORC_BAD_INPUT = 6
 };
 
-/* Reaction tables; arrays owned by the caller. reac is [R][3], prod/yld [R][8]. */
+/* Reaction tables; arrays owned by the caller. reac is [R][3], prod/yld [R][8].
+ * ext [R][8] (may be NULL when every reaction is thermal or photolysis): the
+ * second Arrhenius term (A2, Ea2/R, B2), the third (A3, Ea3/R, B3), and the
+ * Troe broadening Fc, N. */
 typedef struct {
   int32_t n_species, n_reactions;
   const int32_t *kind, *n_reac, *reac, *n_prod, *prod;
   const double *yld, *A, *Ea, *B, *J;
+  const double *ext;
 } orc_mech;
 
 typedef struct {

@@ -39,7 +39,10 @@ DERIV_GATHER, DERIV_ATOMIC_AOS, DERIV_ATOMIC_SOA = 0, 1, 2
 class Reaction(ct.Structure):
     _fields_ = [("kind", ct.c_int32), ("n_reac", ct.c_int32), ("reac", ct.c_int32 * 3),
                 ("n_prod", ct.c_int32), ("prod", ct.c_int32 * 8), ("yld", ct.c_double * 8),
-                ("A", ct.c_double), ("Ea_over_R", ct.c_double), ("B", ct.c_double), ("J", ct.c_double)]
+                ("A", ct.c_double), ("Ea_over_R", ct.c_double), ("B", ct.c_double), ("J", ct.c_double),
+                ("A2", ct.c_double), ("Ea2_over_R", ct.c_double), ("B2", ct.c_double),
+                ("A3", ct.c_double), ("Ea3_over_R", ct.c_double), ("B3", ct.c_double),
+                ("Fc", ct.c_double), ("N", ct.c_double)]
 
 
 class Opts(ct.Structure):
@@ -148,6 +151,7 @@ def _ptr(a, dtype=np.float64):
 def reactions_from_synth(m: synth.Mechanism):
     R = m.n_reactions
     arr = (Reaction * max(R, 1))()
+    ext = synth.rate_ext(m)
     for j in range(R):
         r = arr[j]
         r.kind = int(m.kind[j])
@@ -159,6 +163,7 @@ def reactions_from_synth(m: synth.Mechanism):
             r.prod[p] = int(m.prod[j, p]) if p < m.n_prod[j] else 0
             r.yld[p] = float(m.yld[j, p]) if p < m.n_prod[j] else 0.0
         r.A, r.Ea_over_R, r.B, r.J = float(m.A[j]), float(m.Ea[j]), float(m.B[j]), float(m.J[j])
+        (r.A2, r.Ea2_over_R, r.B2, r.A3, r.Ea3_over_R, r.B3, r.Fc, r.N) = (float(v) for v in ext[j])
     return arr
 
 

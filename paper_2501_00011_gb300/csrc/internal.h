@@ -59,6 +59,8 @@ struct TableOffsets {
   int bytes;                       // total, a multiple of 16
 };
 
+constexpr int RX_EXT = 8;   // extra rate parameters per reaction
+
 // Everything a solve kernel needs about a mechanism; passed by value.
 struct MechDev {
   int S, R, max_reac, n_phot, n_pairs;
@@ -67,6 +69,7 @@ struct MechDev {
   const int *rx_nreac;     // [R]
   const int *rx_phot;      // [R] index among photolysis reactions, or -1
   const double *rx_A, *rx_Ea, *rx_B, *rx_J;
+  const double *rx_ext;    // [R][RX_EXT]: A2, Ea2, B2, A3, Ea3, B3, Fc, N (pressure-dependent kinds)
   // reaction data for the derivative-design comparison (chem_eval_deriv_design):
   // the caller's records as uploaded (array of structures), and the same as
   // structure of arrays: reactants [R][3], product counts [R], products and yields [R][8]

@@ -201,7 +201,7 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
   if (R > 0 && !rx) { msg = "reaction table is NULL"; return CHEM_EINVAL; }
   for (int j = 0; j < R; ++j) {
     const chem_reaction &r = rx[j];
-    if (r.kind != CHEM_THERMAL && r.kind != CHEM_PHOTOLYSIS) { msg = "reaction " + std::to_string(j) + ": bad kind"; return CHEM_EINVAL; }
+    if (r.kind < CHEM_THERMAL || r.kind > CHEM_FALLOFF_SUM) { msg = "reaction " + std::to_string(j) + ": bad kind"; return CHEM_EINVAL; }
     if (r.n_reac < 1 || r.n_reac > CHEM_MAX_REAC) { msg = "reaction " + std::to_string(j) + ": n_reac must be 1..3"; return CHEM_EINVAL; }
     if (r.n_prod < 0 || r.n_prod > CHEM_MAX_PROD) { msg = "reaction " + std::to_string(j) + ": n_prod must be 0..8"; return CHEM_EINVAL; }
     for (int s = 0; s < r.n_reac; ++s)
@@ -210,8 +210,21 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
       if (r.prod[p] < 0 || r.prod[p] >= S) { msg = "reaction " + std::to_string(j) + ": product index out of range"; return CHEM_EINVAL; }
       if (!std::isfinite(r.yield[p])) { msg = "reaction " + std::to_string(j) + ": non-finite yield"; return CHEM_EINVAL; }
     }
-    if (r.kind == CHEM_THERMAL && !(std::isfinite(r.A) && std::isfinite(r.Ea_over_R) && std::isfinite(r.B))) {
+    if (r.kind != CHEM_PHOTOLYSIS && !(std::isfinite(r.A) && std::isfinite(r.Ea_over_R) && std::isfinite(r.B))) {
       msg = "reaction " + std::to_string(j) + ": non-finite Arrhenius parameters"; return CHEM_EINVAL;
+    }
+    if ((r.kind == CHEM_TROE || r.kind == CHEM_PRESSURE_SUM || r.kind == CHEM_FALLOFF_SUM) &&
+        !(std::isfinite(r.A2) && std::isfinite(r.Ea2_over_R) && std::isfinite(r.B2))) {
+      msg = "reaction " + std::to_string(j) + ": non-finite second Arrhenius term"; return CHEM_EINVAL;
+    }
+    if (r.kind == CHEM_FALLOFF_SUM && !(std::isfinite(r.A3) && std::isfinite(r.Ea3_over_R) && std::isfinite(r.B3))) {
+      msg = "reaction " + std::to_string(j) + ": non-finite third Arrhenius term"; return CHEM_EINVAL;
+    }
+    if ((r.kind == CHEM_TROE || r.kind == CHEM_FALLOFF_SUM) && !(r.A2 > 0.0)) {
+      msg = "reaction " + std::to_string(j) + ": the high-pressure limit needs A2 > 0"; return CHEM_EINVAL;
+    }
+    if (r.kind == CHEM_TROE && !(r.Fc > 0.0 && r.Fc <= 1.0 && r.N > 0.0 && std::isfinite(r.N))) {
+      msg = "reaction " + std::to_string(j) + ": Troe needs Fc in (0, 1] and N > 0"; return CHEM_EINVAL;
     }
     if (r.kind == CHEM_PHOTOLYSIS && !std::isfinite(r.J)) { msg = "reaction " + std::to_string(j) + ": non-finite J"; return CHEM_EINVAL; }
   }
@@ -601,7 +614,7 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
   const int R = m.R, S = m.S;
   cudaGetDevice(&m.device);
   std::vector<int> kind(R), nreac(R), phot(R);
-  std::vector<double> A(R), Ea(R), B(R), J(R);
+  std::vector<double> A(R), Ea(R), B(R), J(R), ext((size_t)R * RX_EXT, 0.0);
   int ip = 0;
   for (int j = 0; j < R; ++j) {
     const chem_reaction &r = m.rx[j];
@@ -612,6 +625,8 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
     Ea[j] = r.Ea_over_R;
     B[j] = r.B;
     J[j] = r.J;
+    const double e[RX_EXT] = {r.A2, r.Ea2_over_R, r.B2, r.A3, r.Ea3_over_R, r.B3, r.Fc, r.N};
+    for (int k = 0; k < RX_EXT; ++k) ext[(size_t)j * RX_EXT + k] = e[k];
   }
   std::vector<double> thr2(7 * GRID_N), thr3(7 * GRID_N), g(GRID_N);
   for (int p = 0; p < 7; ++p)
@@ -708,6 +723,7 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
   if ((rc = put(m, kind, &d.rx_kind, msg)) || (rc = put(m, nreac, &d.rx_nreac, msg)) ||
       (rc = put(m, phot, &d.rx_phot, msg)) || (rc = put(m, A, &d.rx_A, msg)) ||
       (rc = put(m, Ea, &d.rx_Ea, msg)) || (rc = put(m, B, &d.rx_B, msg)) || (rc = put(m, J, &d.rx_J, msg)) ||
+      (rc = put(m, ext, &d.rx_ext, msg)) ||
       (rc = put(m, m.pos, &d.sp_pos, msg)) || (rc = put(m, coef, &d.rescale_coef, msg))) {
     free_mechanism(m);
     return rc;

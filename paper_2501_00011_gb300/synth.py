@@ -32,6 +32,11 @@ import numpy as np
 # reaction kinds
 THERMAL = 0      # Arrhenius rate, any number of reactants
 PHOTOLYSIS = 1   # first-order, rate J (s^-1), optionally scaled per cell
+TROE = 2         # pressure fall-off between a low- and a high-pressure Arrhenius limit
+PRESSURE_SUM = 3   # an Arrhenius term plus a second one times the air number density
+FALLOFF_SUM = 4    # an Arrhenius term plus a Lindemann fall-off term
+# columns of Mechanism.ext: the second and third Arrhenius terms and the Troe broadening
+EXT_A2, EXT_EA2, EXT_B2, EXT_A3, EXT_EA3, EXT_B3, EXT_FC, EXT_N = range(8)
 
 MAX_REAC = 3
 MAX_PROD = 8
@@ -58,6 +63,7 @@ class Mechanism:
     J: np.ndarray             # float64 [R]  photolysis rate (0 for thermal)
     weights: np.ndarray | None = None   # int64 [S] conserved atom weights
     name: str = "mechanism"
+    ext: np.ndarray | None = None       # float64 [R, 8] parameters of the pressure-dependent kinds (EXT_*)
 
     @property
     def n_reactions(self) -> int:
@@ -95,8 +101,13 @@ def empty_mechanism(n_species: int, n_reactions: int, name: str = "mechanism") -
         prod=np.full((R, MAX_PROD), -1, np.int32),
         yld=np.zeros((R, MAX_PROD), np.float64),
         A=np.zeros(R), Ea=np.zeros(R), B=np.zeros(R), J=np.zeros(R),
-        name=name,
+        name=name, ext=np.zeros((R, 8)),
     )
+
+
+def rate_ext(m: Mechanism) -> np.ndarray:
+    """m.ext, or zeros for a mechanism without pressure-dependent kinds."""
+    return np.zeros((m.n_reactions, 8)) if m.ext is None else np.asarray(m.ext, np.float64)
 
 
 def mechanism_from_list(n_species: int, reactions: list[dict], name: str = "mechanism") -> Mechanism:
@@ -104,7 +115,10 @@ def mechanism_from_list(n_species: int, reactions: list[dict], name: str = "mech
 
     Each dict: ``reac`` (list of species, repeats allowed), ``prod`` (list of
     species), optional ``yld`` (list of yields, default 1.0 each) and either
-    ``J`` (photolysis) or ``A`` [, ``Ea``, ``B``] (thermal).
+    ``J`` (photolysis) or ``A`` [, ``Ea``, ``B``] (thermal), the latter with an
+    optional ``kind`` (TROE, PRESSURE_SUM, FALLOFF_SUM) and its parameters
+    ``A2``, ``Ea2``, ``B2``, ``A3``, ``Ea3``, ``B3``, ``Fc``, ``N`` (default 0;
+    Fc 0.6 and N 1 for TROE).
     """
     m = empty_mechanism(n_species, len(reactions), name)
     for j, rx in enumerate(reactions):
@@ -121,10 +135,14 @@ def mechanism_from_list(n_species: int, reactions: list[dict], name: str = "mech
             m.kind[j] = PHOTOLYSIS
             m.J[j] = rx["J"]
         else:
-            m.kind[j] = THERMAL
+            m.kind[j] = rx.get("kind", THERMAL)
             m.A[j] = rx["A"]
             m.Ea[j] = rx.get("Ea", 0.0)
             m.B[j] = rx.get("B", 0.0)
+            troe = m.kind[j] == TROE
+            m.ext[j] = [rx.get("A2", 0.0), rx.get("Ea2", 0.0), rx.get("B2", 0.0), rx.get("A3", 0.0),
+                        rx.get("Ea3", 0.0), rx.get("B3", 0.0), rx.get("Fc", 0.6 if troe else 0.0),
+                        rx.get("N", 1.0 if troe else 0.0)]
     return m
 
 
@@ -329,6 +347,52 @@ def mechanism_small() -> Mechanism:
 def mechanism_tropo() -> Mechanism:
     """72 species / 186 reactions: 56 unimolecular (30%) of which 19 photolysis, 130 bimolecular."""
     return random_mechanism(72, 186, 56, 19, name="synthetic_72sp_186rx")
+
+
+def mechanism_tropo_pressure() -> Mechanism:
+    """The 72/186 mechanism with 18 of its bimolecular thermal reactions made
+    pressure-dependent, about as many as a condensed tropospheric mechanism
+    has: 12 Troe fall-off reactions (log10 k0 ~ U[-32,-29] cm^6 s^-1,
+    k0 temperature exponent B ~ U[-4,-1], log10 kinf ~ U[-12,-10], kinf exponent
+    ~ U[-1,0], no activation energies, Fc = 0.6, N = 1), three k_a + k_b [M]
+    (log10 A ~ U[-13.5,-12.5], Ea/R ~ U[-600,0] K; log10 A2 ~ U[-33.5,-32.5],
+    Ea2/R ~ U[-1000,0] K) and three k_a + k_c [M] / (1 + k_c [M] / k_b)
+    (log10 A ~ U[-14.5,-13.5], Ea/R ~ U[-600,0]; log10 A2 ~ U[-17.5,-16.5],
+    Ea2/R ~ U[-2400,-2000]; log10 A3 ~ U[-34,-33], Ea3/R ~ U[-1500,-1200]).
+    Species, stoichiometry and sparsity are those of mechanism_tropo()."""
+    m = mechanism_tropo()
+    m.name = "synthetic_72sp_186rx_pressure"
+    rng = np.random.Generator(np.random.PCG64([SEED_MECHANISM, 72, 186, 2]))
+    cand = np.nonzero((m.kind == THERMAL) & (m.n_reac == 2))[0]
+    pick = rng.choice(cand, 18, replace=False)
+    ext = np.zeros((m.n_reactions, 8))
+    for i, j in enumerate(pick):
+        if i < 12:
+            m.kind[j] = TROE
+            m.A[j], m.Ea[j], m.B[j] = 10.0 ** rng.uniform(-32.0, -29.0), 0.0, rng.uniform(-4.0, -1.0)
+            ext[j, EXT_A2], ext[j, EXT_EA2], ext[j, EXT_B2] = 10.0 ** rng.uniform(-12.0, -10.0), 0.0, rng.uniform(-1.0, 0.0)
+            ext[j, EXT_FC], ext[j, EXT_N] = 0.6, 1.0
+        elif i < 15:
+            m.kind[j] = PRESSURE_SUM
+            m.A[j], m.Ea[j], m.B[j] = 10.0 ** rng.uniform(-13.5, -12.5), rng.uniform(-600.0, 0.0), 0.0
+            ext[j, EXT_A2], ext[j, EXT_EA2] = 10.0 ** rng.uniform(-33.5, -32.5), rng.uniform(-1000.0, 0.0)
+        else:
+            m.kind[j] = FALLOFF_SUM
+            m.A[j], m.Ea[j], m.B[j] = 10.0 ** rng.uniform(-14.5, -13.5), rng.uniform(-600.0, 0.0), 0.0
+            ext[j, EXT_A2], ext[j, EXT_EA2] = 10.0 ** rng.uniform(-17.5, -16.5), rng.uniform(-2400.0, -2000.0)
+            ext[j, EXT_A3], ext[j, EXT_EA3] = 10.0 ** rng.uniform(-34.0, -33.0), rng.uniform(-1500.0, -1200.0)
+    m.ext = ext
+    return m
+
+
+def workload_pressure(n_cells: int = 10_000) -> Workload:
+    """One 600 s step of the pressure-dependent 72/186 mechanism over cells
+    spanning the troposphere and lower stratosphere: T in [200, 310] K, P in
+    [1e3, 1.05e5] Pa (log-uniform), so the fall-off reactions run from near
+    their low-pressure to near their high-pressure limits."""
+    m = mechanism_tropo_pressure()
+    c = random_cells(m.n_species, n_cells, T_range=(200.0, 310.0), P_range=(1e3, 1.05e5))
+    return Workload("tropo_pressure_72sp_186rx", m, c, 600.0, 1, 1e-4, 1e-10)
 
 
 def workload_small(n_cells: int = 10) -> Workload:

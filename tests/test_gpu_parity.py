@@ -28,15 +28,17 @@ def cg():
 
 @pytest.fixture(scope="module")
 def mechs(cg):
-    return {"small": cg.Mechanism(synth.mechanism_small()), "tropo": cg.Mechanism(synth.mechanism_tropo())}
+    return {"small": cg.Mechanism(synth.mechanism_small()), "tropo": cg.Mechanism(synth.mechanism_tropo()),
+            "pressure": cg.Mechanism(synth.mechanism_tropo_pressure())}
 
 
 # ---------------------------------------------------------------- kernel level
 
-@pytest.mark.parametrize("name", ["small", "tropo"])
+@pytest.mark.parametrize("name", ["small", "tropo", "pressure"])
 def test_deriv_matches_oracle(oracle_lib, cg, mechs, name):
+    # pressures from 1e3 to 1.05e5 Pa: the fall-off reactions from near one limit to near the other
     m = mechs[name]
-    cells = synth.random_cells(m.n_species, 70, T_range=(220, 310), P_range=(2e4, 1e5), seed=5)
+    cells = synth.random_cells(m.n_species, 70, T_range=(200, 310), P_range=(1e3, 1.05e5), seed=5)
     c = cg.Cells(m, cells.n_cells)
     c.set_state(cells.T, cells.P, cells.y)
     ytest = synth.random_cells(m.n_species, 70, seed=6).y
@@ -50,7 +52,7 @@ def test_deriv_matches_oracle(oracle_lib, cg, mechs, name):
         assert np.all(np.abs(f[:, k] - fo) <= 1e-13 * scale)
 
 
-@pytest.mark.parametrize("name", ["small", "tropo"])
+@pytest.mark.parametrize("name", ["small", "tropo", "pressure"])
 @pytest.mark.parametrize("design", [0, 1, 2])
 def test_deriv_designs_match_oracle(oracle_lib, cg, mechs, name, design):
     # the gather design and the paper's reaction-parallel atomic design (both
@@ -120,6 +122,17 @@ def test_solve_tropo_subset(oracle_lib, cg, mechs, driver):
     err, flips, odd = _compare(y, st, yo, so, oracle_lib, wl, wl.cells)
     print(f"tropo 301 cells ({driver}): max rel err {err:.2e} on well-determined cells, "
           f"decision flips {flips}, rounding-limited cells {odd}")
+
+
+@pytest.mark.parametrize("driver", ["plain", "persistent"])
+def test_solve_pressure_dependent(oracle_lib, cg, mechs, driver):
+    # Troe fall-off, k_a + k_b [M] and k_a + k_c [M] / (1 + k_c [M] / k_b) reactions,
+    # 1e3..1.05e5 Pa; 301 cells
+    wl = synth.workload_pressure(301)
+    y, st = cg.solve(mechs["pressure"], wl.cells, wl.dt, wl.rtol, wl.atol, driver=driver)
+    yo, so = oracle_lib.solve_cells(wl.mech, wl.cells, wl.dt, wl.rtol, wl.atol)
+    err, flips, odd = _compare(y, st, yo, so, oracle_lib, wl, wl.cells)
+    print(f"pressure-dependent 301 cells ({driver}): max rel err {err:.2e}, flips {flips}, rounding-limited {odd}")
 
 
 def test_drivers_agree_bitwise(cg, mechs):
@@ -193,3 +206,12 @@ def test_api_errors(cg, mechs):
     bad = synth.mechanism_from_list(2, [dict(reac=[0], prod=[5], A=1.0)])
     with pytest.raises(cg.ChemError):
         cg.Mechanism(bad)
+    # pressure-dependent kinds: a high-pressure limit must be positive, Troe needs Fc in (0, 1] and N > 0
+    for rx in (dict(reac=[0, 1], prod=[0, 1], A=1e-30, kind=synth.TROE, A2=0.0),
+               dict(reac=[0, 1], prod=[0, 1], A=1e-30, kind=synth.TROE, A2=1e-11, Fc=1.5),
+               dict(reac=[0, 1], prod=[0, 1], A=1e-30, kind=synth.TROE, A2=1e-11, N=0.0),
+               dict(reac=[0, 1], prod=[0, 1], A=1e-13, kind=synth.FALLOFF_SUM, A2=-1.0, A3=1e-33),
+               dict(reac=[0, 1], prod=[0, 1], A=1e-13, kind=synth.PRESSURE_SUM, A2=float("nan")),
+               dict(reac=[0, 1], prod=[0, 1], A=1e-13, kind=7)):
+        with pytest.raises(cg.ChemError):
+            cg.Mechanism(synth.mechanism_from_list(2, [rx]))
