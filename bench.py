@@ -36,7 +36,7 @@ L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 FP64_PEAK_NOMINAL = 152 * 2070e6 * 2 * 2   # SMs x clock x 2 FP64 FMA lanes/SM/clk x 2 flops
 PROFILE = os.path.join(ROOT, "profiles", "solve_kernel_fp64_persistent_tropo10k.md")
 KERNEL_SOURCES = ("paper_2501_00011_gb300/csrc/kernels.cu", "paper_2501_00011_gb300/csrc/internal.h",
-                  "paper_2501_00011_gb300/csrc/mechanism.cpp")
+                  "paper_2501_00011_gb300/csrc/mechanism.cpp", "paper_2501_00011_gb300/csrc/device_common.cuh")
 
 
 def _kernel_sha():
@@ -214,6 +214,66 @@ def run_gpu(args):
             import torch.distributed as dist
             dist.barrier()
 
+    def column_mixing(y, c0, c1, levels=50, a=0.2):
+        """Host stand-in for the model's work between chemistry steps: one implicit
+        vertical-diffusion step (I - a D2) y_new = y in columns of `levels` consecutive
+        cells (zero-flux ends), every species, by the Thomas algorithm in numpy."""
+        blk = y[:, c0:c1].reshape(y.shape[0], -1, levels)
+        d = np.full(levels, 1.0 + 2.0 * a)
+        d[0] = d[-1] = 1.0 + a
+        cp = np.empty(levels)
+        cp[0] = -a / d[0]
+        for i in range(1, levels):
+            cp[i] = -a / (d[i] + a * cp[i - 1])
+        x = np.empty_like(blk)
+        x[:, :, 0] = blk[:, :, 0] / d[0]
+        for i in range(1, levels):
+            x[:, :, i] = (blk[:, :, i] + a * x[:, :, i - 1]) / (d[i] + a * cp[i - 1])
+        for i in range(levels - 2, -1, -1):
+            x[:, :, i] -= cp[i] * x[:, :, i + 1]
+        y[:, c0:c1] = x.reshape(y.shape[0], -1)
+
+    def time_host_overlap(chemgpu, mech, barrier):
+        """The 10,000 cells with their state in (pinned) host memory and host work between
+        chemistry steps, through chem_pipeline_run with 1, 2, 4 and 8 chunks; wall clock."""
+        n_steps = 2
+        host_y = chemgpu.pinned_empty(wl.cells.y.shape)
+        ms_host = []
+        for _ in range(3):
+            host_y[:] = wl.cells.y
+            t = time.perf_counter()
+            column_mixing(host_y, 0, C)
+            ms_host.append((time.perf_counter() - t) * 1e3)
+        forms = {}
+        for K in (1, 2, 4, 8):
+            p = chemgpu.Pipeline(mech, C, K, rtol=wl.rtol, atol=wl.atol, driver="persistent")
+            T, P = wl.cells.T.copy(), wl.cells.P.copy()
+            res = {}
+            for with_host in (False, True):
+                # chemistry only: the headline's single step from the initial state, end to end;
+                # with host work: two model steps, each chunk's host work right after its solve
+                fn = (lambda c0, c1, s: column_mixing(host_y, c0, c1)) if with_host else None
+                ns = n_steps if with_host else 1
+                ts = []
+                for rep in range(3):
+                    host_y[:] = wl.cells.y
+                    barrier()
+                    t = time.perf_counter()
+                    p.run(T, P, host_y, wl.dt, ns, fn=fn)
+                    ts.append((time.perf_counter() - t) * 1e3 / ns)
+                res["with_host_work" if with_host else "chemistry_only"] = {
+                    "ms_per_step": min(ts), "cells_per_s": C / (min(ts) / 1e3)}
+            p.close()
+            forms[f"chunks_{K}"] = res
+        return {
+            "cells": C, "steps": n_steps, "host_work_ms_per_step": min(ms_host), "forms": forms,
+            "note": "state in pinned host memory; per step and chunk: T, P, y host->device, the persistent FP64 "
+                    "solve, y back, then the host work on that chunk (one implicit vertical-diffusion step in "
+                    "columns of 50 cells, numpy) while the GPU solves the other chunks; wall clock per model "
+                    "step, best of 3; chunks_1 = no overlap (copies, solve, copies, host work in sequence). "
+                    "chemistry_only is one step from the initial state (the headline's work, end to end); "
+                    "with_host_work is two steps, the second from the mixed state"}
+
     def time_extras(chemgpu, mech, dev, stream, flush, barrier):
         """The batching form (50,000 cells, six 600 s steps as one captured graph,
         autotuned launch shape) and the adjoint form (2,048 cells, four steps
@@ -337,6 +397,7 @@ def run_gpu(args):
             "cells_ok": int(np.sum(stp["status"] == 0)),
             "note": "72/186 mechanism with 12 Troe fall-off, 3 k_a + k_b[M] and 3 k_a + k_c[M]/(1 + k_c[M]/k_b) "
                     "reactions, P log-uniform 1e3..1.05e5 Pa, T 200..310 K; persistent FP64 form, best of 3"}
+        out["host_overlap"] = time_host_overlap(chemgpu, mech, barrier)
         wl5 = synth.workload_adjoint(args.adjoint_cells)
         n5 = wl5.cells.n_cells
         c5 = chemgpu.Cells(mech, n5, rtol=wl5.rtol, atol=wl5.atol, driver="persistent", record_adjoint=True)

@@ -53,6 +53,7 @@ extern "C" {
 #define CHEM_ENOMEM (-2)   /* device or host allocation failed */
 #define CHEM_ECUDA (-3)    /* a CUDA runtime call failed */
 #define CHEM_ESTATE (-4)   /* call out of order (e.g. solve before set_state) */
+#define CHEM_EABORTED (-5) /* a chem_pipeline_run callback asked to stop */
 
 /* where a pointer lives */
 #define CHEM_MEM_HOST 0
@@ -334,6 +335,46 @@ int chem_eval_newton_solve(chem_cells *cells, double c, const double *y, const d
 int chem_solve_step_noalloc(const chem_mech *mech, int64_t n_cells, const double *T, const double *P,
                             const double *J, const double *theta, double *y, chem_cell_stats *stats,
                             double dt, const chem_opts *opts, void *stream);
+
+/*
+ * Host-resident state with the chemistry on the GPU, overlapped chunk by
+ * chunk.  The paper found that moving the state between host and device
+ * every call took about 90% of its GPU time and named overlapping CPU and GPU
+ * work with asynchronous transfers as future work (Results and Conclusions
+ * sections); this is that overlap for a host model that owns y.  The
+ * n_cells cells are split into n_chunks contiguous chunks (sizes differ by at
+ * most one, larger first), each with its own device batch (created with
+ * opts, which must not ask for record_adjoint or couple_cells) and its own
+ * non-blocking stream.  Allocates the batches, streams and events.
+ * Errors: CHEM_EINVAL, CHEM_ENOMEM, CHEM_ECUDA.
+ */
+typedef struct chem_pipeline chem_pipeline;
+int chem_pipeline_create(const chem_mech *mech, int64_t n_cells, int32_t n_chunks, const chem_opts *opts,
+                         chem_pipeline **out);
+void chem_pipeline_destroy(chem_pipeline *p);   /* NULL is a no-op */
+/* Called on the thread of chem_pipeline_run once the solved state of cells
+ * [c0, c1) for model step `step` is back in the host y.  It may update those
+ * columns of y, T, P (and J) -- a transport, emission or deposition stand-in
+ * of the host model -- and nothing else of them, while the GPU keeps solving
+ * the other chunks.  Return 0 to go on, anything else to stop the run. */
+typedef int (*chem_chunk_fn)(int64_t c0, int64_t c1, int32_t step, void *user);
+/* n_steps model steps of length dt over host arrays T[n_cells], P[n_cells],
+ * y[n_species][n_cells] (cell index unit stride; integrated in place) and
+ * optionally J[n_photolysis][n_cells] (NULL: the mechanism's J).  Per chunk
+ * and step, on the chunk's stream: T, P, (J,) y columns host -> device (2-D
+ * strided copies), the solve, y back device -> host; then, on this thread,
+ * fn(c0, c1, step, user) (fn may be NULL), after which that chunk's next step
+ * is queued at once, so host work on one chunk overlaps the GPU's work on the
+ * others and the copies overlap the solves.  Results equal those of n_steps
+ * chem_solve_step calls on one batch with fn applied between them, bit for
+ * bit.  The host arrays should be page-locked (cudaHostRegister or a pinned
+ * allocation) for the copies to run asynchronously.  stats (may be NULL)
+ * receives the statistics of the last step, [n_cells].  Synchronous: returns
+ * when every chunk's last step is back and its callback has returned.
+ * Returns 0 or a negative error: CHEM_EINVAL, CHEM_ECUDA, CHEM_EABORTED (fn
+ * returned nonzero; work already queued is drained first). */
+int chem_pipeline_run(chem_pipeline *p, const double *T, const double *P, const double *J, double *y, double dt,
+                      int32_t n_steps, chem_chunk_fn fn, void *user, chem_cell_stats *stats);
 
 /* Thread-local description of the last error ("" if none). */
 const char *chem_last_error(void);

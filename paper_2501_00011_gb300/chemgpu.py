@@ -30,7 +30,7 @@ EXPORTS = ["chem_opts_default", "chem_mechanism_create", "chem_mechanism_destroy
            "chem_cells_set_theta", "chem_solve_step", "chem_solve_steps", "chem_autotune",
            "chem_get_state", "chem_get_stats",
            "chem_eval_deriv", "chem_eval_newton_solve", "chem_eval_deriv_design", "chem_solve_step_noalloc", "chem_sensitivity",
-           "chem_tangent", "chem_get_tape", "chem_last_error"]
+           "chem_tangent", "chem_get_tape", "chem_pipeline_create", "chem_pipeline_destroy", "chem_pipeline_run", "chem_last_error"]
 
 
 DERIV_GATHER, DERIV_ATOMIC_AOS, DERIV_ATOMIC_SOA = 0, 1, 2
@@ -107,10 +107,13 @@ def load(path: str | None = None):
         L.chem_solve_steps.argtypes = [V, ct.c_double, ct.c_int32, V]
         L.chem_autotune.argtypes = [V, ct.c_double, ct.c_int64, V, V]
         L.chem_get_tape.argtypes = [V, ct.c_int64, V, V, V, V, ct.c_int32, V, V]
+        L.chem_pipeline_create.argtypes = [V, ct.c_int64, ct.c_int32, V, ct.POINTER(V)]
+        L.chem_pipeline_destroy.argtypes = [V]
+        L.chem_pipeline_run.argtypes = [V, V, V, V, V, ct.c_double, ct.c_int32, CHUNK_FN, V, V]
         L.chem_last_error.restype = ct.c_char_p
         for name in EXPORTS:
             if name not in ("chem_opts_default", "chem_mechanism_destroy", "chem_cells_destroy",
-                            "chem_last_error"):
+                            "chem_pipeline_destroy", "chem_last_error"):
                 getattr(L, name).restype = ct.c_int
         _lib = L
         return L
@@ -357,6 +360,89 @@ class Cells:
     def close(self):
         if getattr(self, "_h", None):
             load().chem_cells_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+CHUNK_FN = ct.CFUNCTYPE(ct.c_int, ct.c_int64, ct.c_int64, ct.c_int32, ct.c_void_p)
+
+
+def _host_ptr(a, what):
+    """Pointer to a host array the library reads and writes in place: a C-contiguous
+    float64 numpy array or CPU torch tensor (no copies are made)."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous():
+                raise ChemError(f"{what} must be a contiguous float64 host tensor")
+            return ct.c_void_p(a.data_ptr())
+    except ImportError:
+        pass
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.flags.writeable):
+        raise ChemError(f"{what} must be a writeable C-contiguous float64 numpy array")
+    return ct.c_void_p(a.ctypes.data)
+
+
+def pinned_empty(shape):
+    """A page-locked float64 host array (numpy view of a pinned torch tensor), so the
+    pipeline's copies run asynchronously."""
+    import torch
+    return torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+
+
+class Pipeline:
+    """Host-resident state with the chemistry on the GPU, overlapped chunk by chunk
+    (chem_pipeline_*): per chunk its own device batch and stream; the host's work on
+    a chunk whose result is back runs while the GPU solves the others."""
+
+    def __init__(self, mech: Mechanism, n_cells: int, n_chunks: int, rtol: float = 1e-4, atol: float = 1e-10,
+                 max_order: int = 5, max_steps: int = 5000, lu_precision: int = 64, driver: str = "persistent",
+                 cells_per_block: int = 0, blocks_per_sm: int = 0):
+        L = load()
+        self.mech = mech
+        self.n_cells, self.n_chunks = int(n_cells), int(n_chunks)
+        o = Opts()
+        L.chem_opts_default(ct.byref(o))
+        o.rtol, o.atol, o.max_order, o.max_steps = rtol, atol, max_order, max_steps
+        o.lu_precision, o.driver = lu_precision, DRIVERS[driver]
+        o.cells_per_block, o.blocks_per_sm = cells_per_block, blocks_per_sm
+        h = ct.c_void_p()
+        _check(L.chem_pipeline_create(mech.handle, self.n_cells, self.n_chunks, ct.byref(o), ct.byref(h)),
+               "chem_pipeline_create")
+        self._h = h
+
+    def run(self, T, P, y, dt: float, n_steps: int = 1, fn=None, J=None, stats: bool = False):
+        """Integrate host y [S, C] in place over n_steps steps of dt; fn(c0, c1, step) runs on
+        this thread once cells [c0, c1) of a step are back (it may update those columns of
+        y, T, P, J; a true return value stops the run).  Returns the last step's stats
+        (stats=True) or None."""
+        err = []
+
+        def cb(c0, c1, step, user):
+            try:
+                return 1 if fn(int(c0), int(c1), int(step)) else 0
+            except BaseException as e:          # re-raised after the library has drained its streams
+                err.append(e)
+                return 1
+
+        cfn = CHUNK_FN(cb) if fn is not None else CHUNK_FN()
+        st = np.zeros(self.n_cells, STATS_DTYPE) if stats else None
+        rc = load().chem_pipeline_run(self._h, _host_ptr(T, "T"), _host_ptr(P, "P"),
+                                      None if J is None else _host_ptr(J, "J"), _host_ptr(y, "y"), float(dt),
+                                      int(n_steps), cfn, None, None if st is None else ct.c_void_p(st.ctypes.data))
+        if err:
+            raise err[0]
+        _check(rc, "chem_pipeline_run")
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().chem_pipeline_destroy(self._h)
             self._h = None
 
     def __del__(self):

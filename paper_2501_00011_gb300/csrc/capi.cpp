@@ -794,4 +794,132 @@ int chem_get_tape(const chem_cells *c, int64_t cell, int32_t *kind, int32_t *q, 
   return 0;
 }
 
+// ---------------------------------------------------------------- pipeline
+// Host-resident state, chunked: per chunk its own batch and stream, so the
+// copies of one chunk overlap the solves of the others and the host's work on
+// a chunk that is back overlaps the GPU's work on the rest.
+
+struct chem_pipeline {
+  const chem_mech *mech = nullptr;
+  int64_t n = 0;
+  std::vector<int64_t> c0;                 // chunk k is cells [c0[k], c0[k + 1])
+  std::vector<chem_cells *> sub;
+  std::vector<cudaStream_t> stream;
+  std::vector<cudaEvent_t> done;
+};
+
+void chem_pipeline_destroy(chem_pipeline *p) {
+  if (!p) return;
+  for (cudaStream_t s : p->stream)
+    if (s) cudaStreamSynchronize(s);
+  for (cudaEvent_t e : p->done)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t s : p->stream)
+    if (s) cudaStreamDestroy(s);
+  for (chem_cells *c : p->sub) chem_cells_destroy(c);
+  delete p;
+}
+
+int chem_pipeline_create(const chem_mech *mech, int64_t n_cells, int32_t n_chunks, const chem_opts *opts,
+                         chem_pipeline **out) {
+  g_err.clear();
+  if (!out) return fail(CHEM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!mech) return fail(CHEM_EINVAL, "mechanism is NULL");
+  if (n_cells < 0 || n_cells > ((int64_t)1 << 31)) return fail(CHEM_EINVAL, "n_cells must be in 0..2^31");
+  if (n_chunks < 1 || n_chunks > 64) return fail(CHEM_EINVAL, "n_chunks must be in 1..64");
+  if (n_cells > 0 && n_chunks > n_cells) return fail(CHEM_EINVAL, "more chunks than cells");
+  if (opts && (opts->record_adjoint || opts->couple_cells > 1))
+    return fail(CHEM_EINVAL, "a pipeline takes neither record_adjoint nor couple_cells");
+  chem_pipeline *p = new (std::nothrow) chem_pipeline();
+  if (!p) return fail(CHEM_ENOMEM, "host allocation failed");
+  p->mech = mech;
+  p->n = n_cells;
+  const int K = n_cells > 0 ? n_chunks : 1;
+  const int64_t base = n_cells / K, extra = n_cells % K;
+  p->c0.push_back(0);
+  for (int k = 0; k < K; ++k) p->c0.push_back(p->c0.back() + base + (k < extra ? 1 : 0));
+  p->sub.assign(K, nullptr);
+  p->stream.assign(K, nullptr);
+  p->done.assign(K, nullptr);
+  for (int k = 0; k < K; ++k) {
+    if (int rc = chem_cells_create(mech, p->c0[k + 1] - p->c0[k], opts, &p->sub[k])) {
+      const std::string msg = g_err;
+      chem_pipeline_destroy(p);
+      return fail(rc, msg);
+    }
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&p->stream[k], cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&p->done[k], cudaEventDisableTiming)) != cudaSuccess) {
+      chem_pipeline_destroy(p);
+      return cuda_fail(e, "pipeline streams");
+    }
+  }
+  *out = p;
+  return 0;
+}
+
+namespace {
+
+// chunk k, one model step: inputs in, the solve, y out, then the chunk's event
+cudaError_t pipeline_enqueue(chem_pipeline *p, int k, const double *T, const double *P, const double *J, double *y,
+                             double dt) {
+  chem_cells *c = p->sub[k];
+  const cudaStream_t s = p->stream[k];
+  const int64_t c0 = p->c0[k], nk = c->n;
+  const size_t S = (size_t)p->mech->m.S, np = (size_t)p->mech->m.n_phot;
+  const size_t ld = (size_t)p->n * sizeof(double), w = (size_t)nk * sizeof(double);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(c->T, T + c0, w, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(c->P, P + c0, w, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpy2DAsync(c->y, w, y + c0, ld, w, S, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  c->use_J = J && np > 0;
+  if (c->use_J && (e = cudaMemcpy2DAsync(c->J, w, J + c0, ld, w, np, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  c->have_state = true;
+  c->kt_valid = false;
+  if ((e = enqueue_solve(c, dt, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpy2DAsync(y + c0, ld, c->y, w, w, S, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+  return cudaEventRecord(p->done[k], s);
+}
+
+}  // namespace
+
+int chem_pipeline_run(chem_pipeline *p, const double *T, const double *P, const double *J, double *y, double dt,
+                      int32_t n_steps, chem_chunk_fn fn, void *user, chem_cell_stats *stats) {
+  g_err.clear();
+  if (!p || !T || !P || !y) return fail(CHEM_EINVAL, "NULL argument");
+  if (!(dt > 0.0) || !(dt < 1e300)) return fail(CHEM_EINVAL, "dt must be positive and finite");
+  if (n_steps < 0) return fail(CHEM_EINVAL, "n_steps must be >= 0");
+  if (p->n == 0 || n_steps == 0) return 0;
+  const int K = (int)p->sub.size();
+  cudaError_t e = cudaSuccess;
+  int rc = 0;
+  for (int k = 0; k < K && e == cudaSuccess; ++k) e = pipeline_enqueue(p, k, T, P, J, y, dt);
+  // visit the chunks in queue order; a chunk's next step goes in as soon as its callback returns
+  for (int step = 0; step < n_steps && e == cudaSuccess && rc == 0; ++step)
+    for (int k = 0; k < K && e == cudaSuccess && rc == 0; ++k) {
+      if ((e = cudaEventSynchronize(p->done[k])) != cudaSuccess) break;
+      if (fn && fn(p->c0[k], p->c0[k + 1], step, user) != 0) {
+        rc = fail(CHEM_EABORTED, "a chunk callback stopped the pipeline");
+        break;
+      }
+      if (step + 1 < n_steps) e = pipeline_enqueue(p, k, T, P, J, y, dt);
+    }
+  // drain whatever is still queued, also on the error paths
+  for (int k = 0; k < K; ++k) {
+    const cudaError_t es = cudaStreamSynchronize(p->stream[k]);
+    if (e == cudaSuccess) e = es;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "pipeline");
+  if (rc) return rc;
+  if (stats)
+    for (int k = 0; k < K; ++k)
+      if ((e = cudaMemcpy(stats + p->c0[k], p->sub[k]->stats, (size_t)p->sub[k]->n * sizeof(chem_cell_stats),
+                          cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "pipeline stats");
+  return 0;
+}
+
 }  // extern "C"
