@@ -553,7 +553,7 @@ def run_gpu(args):
                                       "(a model's consecutive steps give an approximate one)",
                        "first_solve_ms": time_form.first.get((64, "persistent")),
                        "first_solve_note": "a fresh batch's first solve (untimed warm-up 0): no cost history, "
-                                           "cells handed out in cell order",
+                                           "cells ordered by a one-f-evaluation stiffness estimate",
                        "l2": "flushed between timed steps (512 MB write)", "cells_ok": ok},
             "plain_fp64": {"value": plain, "unit": UNIT, "ms_per_step": tot_plain / args.steps,
                            "form": "one warp per cell, one cell per block, tables read from L2, FP64 throughout",

@@ -87,9 +87,9 @@ extern "C" {
 /* drivers */
 #define CHEM_DRIVER_PLAIN 0       /* one warp per cell, cells assigned by block */
 #define CHEM_DRIVER_PERSISTENT 1  /* resident warps pop cells from a device queue, most expensive
-                                     first by each cell's cost in the previous solve of the batch
-                                     (a batch's first solve: cell order); results do not depend
-                                     on the order */
+                                     first: by each cell's cost in the previous solve of the
+                                     batch, or for the first solve by a one-f-evaluation
+                                     stiffness estimate (results do not depend on the order) */
 
 /*
  * One reaction: reactant slots reac[0..n_reac-1] (a species listed twice is a

@@ -199,12 +199,13 @@ size_t smem_per_cell(const MechDev &m, int lu_precision);
 size_t staged_bytes(const MechDev &m, int driver);   // tables staged per block by the driver
 cudaError_t set_constants();   // gamma_m, 1/gamma_m into constant memory of the current device
 cudaError_t launch_solve(const MechDev &m, const CellsDev &c, const LaunchCfg &cfg, cudaStream_t stream);
-// Most expensive cells first for the persistent queue: per cell its cost in
-// the previous solve (cells without one first) bucketed on a log scale, then a
-// counting sort into order[n_cells].  bucket[n_cells] and
+// Cells stiffest first for the persistent queue: per cell the ratio
+// ||f(y0)|| / ||y0|| (the initial-step estimate of 1/h0) bucketed on a log
+// scale, then a counting sort into order[n_cells].  bucket[n_cells] and
 // hist[2 * ORDER_BUCKETS] are scratch.  Stream-ordered (capturable).
 constexpr int ORDER_BUCKETS = 256;
-cudaError_t launch_order(const CellsDev &c, int *bucket, int *hist, int *order, cudaStream_t stream);
+cudaError_t launch_order(const MechDev &m, const CellsDev &c, double rtol, double atol, int *bucket, int *hist,
+                         int *order, cudaStream_t stream);
 int max_warps_per_block(const MechDev &m, int lu_precision, int driver);
 // resident blocks per SM of the solve kernel for a block of warps_per_block cells
 int occupancy(const MechDev &m, int lu_precision, int driver, int warps_per_block);

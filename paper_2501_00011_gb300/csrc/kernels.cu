@@ -41,6 +41,7 @@ constexpr double CRDOWN = 0.3, RDIV = 2.0, NLSCOEF = 0.1, DGMAX = 0.3, THRESH = 
 constexpr int MSBP = 20, MXNEF = 7, MXNCF = 10;
 constexpr double ETA_CF = 0.25, ETA_MXF = 0.2, ETA_CST_SAFETY = 0.9, ETA_CST_MIN = 0.1, STRETCH = 1e-3;
 constexpr long TMA_WAIT_LIMIT = 1L << 22;
+constexpr int ORDER_WARPS = 8;          // cells per block of the queue-order kernel
 
 struct SolveParams {
   double rtol, atol, dt;
@@ -1674,28 +1675,51 @@ cudaError_t launch_adj_t(const MechDev &M, const CellsDev &C, const AdjDev &A, c
 }
 
 // ----------------------------------------------------------- queue order
-// The queue hands out the most expensive cells first, so that the slowest
-// solves do not start last (with a few cells per warp, one late expensive
-// cell otherwise holds a whole SM).  The key is the cell's cost in the
-// previous solve of the batch: its f evaluations, solves, factorisations and
-// steps, weighted by their FP64 work.  Cells without a previous solve come
-// first, in cell order: no cheap estimate tried (the stiffness ratio
-// ||f(y0)|| / ||y0||, the initial step size, Jacobian diagonals and row sums,
-// a regression on them) ordered the 72/186 cells better than no order at all,
-// because a noisy key sends some expensive cells to the end of the queue.
-__global__ void order_keys_kernel(const CellsDev C, int *bucket, int *hist) {
-  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per cell computes a cost key; the queue then hands out the most
+// expensive cells first, so that the slowest solves do not start last (with a
+// few cells per warp, one late expensive cell otherwise holds a whole SM).
+// The key is the cell's cost in the previous solve of the batch (the f
+// evaluations, solves, factorisations and steps of its statistics, weighted
+// by their FP64 work), and for a batch's first solve the stiffness ratio
+// ||f(y0)|| / ||y0|| in the weighted norm (the integrator's initial step is
+// h0 ~ ||y0|| / ||f(y0)||), which takes the rate constants and one f.
+template <int KS>
+__global__ void __launch_bounds__(ORDER_WARPS * WARP) order_keys_kernel(const __grid_constant__ MechDev M, const CellsDev C,
+                                                                          const SolveParams P, int *bucket, int *hist) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & (WARP - 1);
+  const int warp = threadIdx.x / WARP;
+  const int64_t cell = (int64_t)blockIdx.x * ORDER_WARPS + warp;
   if (cell >= C.n_cells) return;
+  Tabs tb;
+  tb.base = tb.gbase = M.blob[0];
+  double *Wd = reinterpret_cast<double *>(smem + (size_t)warp * P.cell_bytes);
+  double l;                                  // log2 of the key, larger first
   const chem_cell_stats prev = C.stats[cell];
-  int b = 0;
   if (prev.steps > 0) {
-    // 4 buckets per octave of the cost, largest first: 2 .. 254
-    const double l = log2(65.0 * prev.f_evals + 100.0 * prev.solves + 560.0 * prev.jac_evals + 150.0 * prev.steps);
-    const int k = (int)fmin(fmax(floor(4.0 * l), -126.0), 126.0);
-    b = 128 - k;
+    l = log2(65.0 * prev.f_evals + 100.0 * prev.solves + 560.0 * prev.jac_evals + 150.0 * prev.steps);
+  } else {
+    Cell<double, KS, false> cl(M, P, tb, Wd, nullptr, lane);
+    unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
+    for (int k = lane; k < M.d_nconst; k += WARP) at<double>(wd, gtab<int>(tb, M.tab.dconst_off)[k]) = gtab<double>(tb, M.tab.dconst_val)[k];
+    double y0[KS], w[KS], f0[KS];
+    const bool bad = load_cell<KS>(M, C, Wd, lane, cell, cl.own, y0);
+    l = -1e9;                                // bad inputs last
+    if (!bad) {
+      cl.weights(y0, w);
+      cl.eval_f(y0, f0);
+      const double d0 = cl.wrms(y0, w), d1 = cl.wrms(f0, w);
+      const double r = d1 / fmax(d0, 1e-5);
+      if (r > 0.0 && isfinite(r)) l = log2(r);
+    }
   }
-  bucket[cell] = b;
-  atomicAdd(hist + b, 1);
+  // 4 buckets per octave of the key, largest first
+  const int k = (int)fmin(fmax(floor(4.0 * l), -127.0), 127.0);
+  const int b = 127 - k;                     // 0 .. 254
+  if (lane == 0) {
+    bucket[cell] = b;
+    atomicAdd(hist + b, 1);
+  }
 }
 
 // exclusive prefix sum of the bucket counts into the scatter cursors
@@ -1714,6 +1738,16 @@ __global__ void order_scatter_kernel(const int *bucket, int *hist, int *order, i
   if (c >= n) return;
   const int pos = atomicAdd(hist + ORDER_BUCKETS + bucket[c], 1);
   order[pos] = (int)c;
+}
+
+template <int KS>
+cudaError_t launch_order_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int *bucket, int *hist, cudaStream_t s) {
+  const size_t smem = (size_t)P.cell_bytes * ORDER_WARPS;
+  cudaError_t e = allow_max_smem<order_keys_kernel<KS>>();
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (C.n_cells + ORDER_WARPS - 1) / ORDER_WARPS;
+  order_keys_kernel<KS><<<(unsigned)blocks, ORDER_WARPS * WARP, smem, s>>>(M, C, P, bucket, hist);
+  return cudaGetLastError();
 }
 
 // ----------------------------------------------------- derivative only
@@ -1958,16 +1992,28 @@ cudaError_t launch_deriv_gather(const MechDev &M, const CellsDev &C, const doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_order(const CellsDev &C, int *bucket, int *hist, int *order, cudaStream_t stream) {
+cudaError_t launch_order(const MechDev &M, const CellsDev &C, double rtol, double atol, int *bucket, int *hist,
+                         int *order, cudaStream_t stream) {
   if (C.n_cells <= 0) return cudaSuccess;
+  SolveParams P{};
+  P.rtol = rtol;
+  P.atol = atol;
+  P.wd_pad = (M.Wd_len + 1) & ~1;
+  P.cell_bytes = (int)(((size_t)P.wd_pad * sizeof(double) + 15) & ~(size_t)15);
+  P.warps_per_block = ORDER_WARPS;
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * ORDER_BUCKETS, stream);
   if (e != cudaSuccess) return e;
-  const unsigned blocks = (unsigned)((C.n_cells + 255) / 256);
-  order_keys_kernel<<<blocks, 256, 0, stream>>>(C, bucket, hist);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  switch ((M.S + WARP - 1) / WARP) {
+    case 1: e = launch_order_t<1>(M, C, P, bucket, hist, stream); break;
+    case 2: e = launch_order_t<2>(M, C, P, bucket, hist, stream); break;
+    case 3: e = launch_order_t<3>(M, C, P, bucket, hist, stream); break;
+    case 4: e = launch_order_t<4>(M, C, P, bucket, hist, stream); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
   order_scan_kernel<<<1, 32, 0, stream>>>(hist);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  order_scatter_kernel<<<blocks, 256, 0, stream>>>(bucket, hist, order, C.n_cells);
+  order_scatter_kernel<<<(unsigned)((C.n_cells + 255) / 256), 256, 0, stream>>>(bucket, hist, order, C.n_cells);
   return cudaGetLastError();
 }
 
