@@ -523,10 +523,16 @@ def run_gpu(args):
     chosen = ws * C * args.steps / (tot_chosen / 1e3)
     e2e = ws * C * args.steps / (e2e_ms / 1e3)
 
-    # roofline: FP64 arithmetic of the solve kernel (algorithmic flops from the counters)
+    # roofline: FP64 arithmetic of the solve kernel (algorithmic flops from the counters):
+    # F = n_f F_f + n_J (F_J + F_LU) + n_sol F_sol + F_vec, with F_vec a lower bound of the
+    # integrator's vector work on S species: per accepted step 11 S (order-1 predictor and psi
+    # 2 S, weights 3 S, error norm 3 S, history update 3 S), per Newton iteration 8 S
+    # (residual 3 S, norm 3 S, correction and iterate 2 S)
     def flops(st):
+        Sv = float(info["n_species"])
         return float(np.sum(st["f_evals"]) * info["flops_f"] + np.sum(st["jac_evals"]) * (info["flops_jac"] + info["flops_lu"])
-                     + np.sum(st["solves"]) * info["flops_solve"])
+                     + np.sum(st["solves"]) * info["flops_solve"]
+                     + 11.0 * Sv * np.sum(st["steps"]) + 8.0 * Sv * np.sum(st["newton_iters"]))
     kernel_ms = statistics.mean(ms_head)
     achieved = flops(st_head) / (kernel_ms / 1e3)
     hbm_peak = None
@@ -568,7 +574,8 @@ def run_gpu(args):
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_NOMINAL, "traffic": _profiled_traffic(),
                          "kernel": "solve_kernel<double,3,staged> (FP64 pipe)",
                          "note": "peak = 152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM x 2 flops (derived); "
-                                 "algorithmic FP64 flops from per-cell counters; traffic = ncu DRAM bytes per launch "
+                                 "algorithmic FP64 flops from per-cell counters (f, J, LU, solves, and a lower bound "
+                                 "of the per-step and per-iteration vector work); traffic = ncu DRAM bytes per launch "
                                  "(null when the kernel changed since the capture)"},
             "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
                     "bytes_per_cell": hbm_bytes // C, "note": "algorithmic HBM bytes of the same kernel; "

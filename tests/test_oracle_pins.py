@@ -400,3 +400,20 @@ def test_failure_status_keeps_input(oracle_lib):
     assert st["status"][1] == 6 and st["status"][2] == 6
     assert st["status"][0] == 1 and st["status"][3] == 1          # MAX_STEPS
     np.testing.assert_array_equal(y[:, [0, 3]], cells.y[:, [0, 3]])
+
+
+def test_tropo_workload_stiffness_ratio(oracle_lib):
+    """The 72/186 workload has the stiffness the benchmark is quoted for: the ratio of the
+    largest to the smallest nonzero |eigenvalue| of J at t = 0 is about 1e10 (median over
+    cells; the conserved weighted sum makes one eigenvalue zero)."""
+    wl = synth.workload_tropo(10_000)
+    m = oracle_lib.OracleMechanism(wl.mech)
+    ratios = []
+    for c in np.linspace(0, wl.cells.n_cells - 1, 50).astype(int):
+        kt = oracle_lib.rate_constants(m, wl.cells.T[c], wl.cells.P[c])
+        ev = np.abs(np.linalg.eigvals(oracle_lib.jacobian(m, kt, wl.cells.y[:, c])))
+        nz = ev[ev > 1e-12 * ev.max()]
+        ratios.append(ev.max() / nz.min())
+    med = float(np.median(ratios))
+    print(f"median stiffness ratio {med:.2e}")
+    assert 1e9 <= med <= 1e11
