@@ -260,10 +260,12 @@ int chem_sensitivity(chem_cells *cells, const double *dL_dy, double *dL_dtheta, 
  * r_j dtheta_j (that is J v + F_theta dtheta) and one sparse LU solve with the
  * recorded iteration matrix.  The paper has no tangent; it differentiates the
  * paper's BDF/Newton integration.  Inputs and output in `mem` space,
- * asynchronous copies on `stream`, then synchronises stream.  Returns 0, a
- * negative error, or the number of cells whose tape overflowed or whose
- * forward solve failed (their dy is 0).  Errors: CHEM_EINVAL, CHEM_ESTATE (no
- * recording, no state), CHEM_ECUDA. */
+ * asynchronous copies on `stream`, then synchronises stream.  It stages its
+ * input and output in the batch's adjoint buffers, so it must not overlap a
+ * chem_sensitivity call on the same batch.  Returns 0, a negative error, or
+ * the number of cells whose tape overflowed or whose forward solve failed
+ * (their dy is 0).  Errors: CHEM_EINVAL, CHEM_ESTATE (no recording, no
+ * state), CHEM_ECUDA. */
 int chem_tangent(chem_cells *cells, const double *dy0, const double *dtheta, double *dy, int32_t mem, void *stream);
 /* The recorded tape of one cell, in host arrays of `capacity` events: kind
  * 0 = INIT (val h0), 1 = RESCALE (q order, val eta), 2 = STEP (q order, val
