@@ -311,6 +311,37 @@ def run_gpu(args):
             "integrator_steps_last_600s": {"min": int(st3["steps"].min()), "median": float(np.median(st3["steps"])),
                                            "max": int(st3["steps"].max())},
             "cells_ok": int(np.sum(st3["status"] == 0))}
+        # the FP32-LU form on its own workload: the batching cells, one step, against the FP64 form
+        wl4 = synth.workload_precision(args.batch_cells)
+        prec = {}
+        for lp in (64, 32):
+            c4 = chemgpu.Cells(mech, n3, rtol=wl4.rtol, atol=wl4.atol, driver="persistent", lu_precision=lp)
+            ts = []
+            for k in range(4):
+                c4.set_state(T3, P3, y3, stream=stream)
+                c4.set_photolysis(J3, stream=stream)
+                flush.fill_(float(k))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                c4.solve_step(wl4.dt, stream=stream)
+                e1.record(stream)
+                barrier()
+                if k > 0:
+                    ts.append(e0.elapsed_time(e1))
+            prec[lp] = (min(ts), c4.get_state(stream=stream), c4.get_stats(stream=stream))
+            c4.close()
+        y64, y32 = prec[64][1], prec[32][1]
+        tu = (np.abs(y32 - y64) / (wl4.rtol * np.abs(y64) + wl4.atol)).max(axis=1)   # per species, tolerance units
+        out["precision_50k"] = {
+            "value": n3 / (prec[32][0] / 1e3), "unit": "cells/s", "ms": prec[32][0], "fp64_ms": prec[64][0],
+            "cells": n3, "speedup_vs_fp64": prec[64][0] / prec[32][0],
+            "newton_iters_vs_fp64": float(np.sum(prec[32][2]["newton_iters"]) / np.sum(prec[64][2]["newton_iters"])),
+            "per_species_max_diff_vs_fp64_gpu_tol_units": {"median": float(np.median(tu)), "max": float(tu.max())},
+            "cells_ok": int(np.sum(prec[32][2]["status"] == 0)),
+            "form": "the batching cells (per-cell photolysis) for one 600 s step, persistent driver, LU factor/solve "
+                    "in FP32, everything else FP64; best of 3 after one warm-up; differences from the FP64 GPU "
+                    "solve of the same cells in tolerance units rtol*|y| + atol (max over cells, then median and "
+                    "max over species): the FP32 factor changes the corrector iterates, so step sequences differ"}
         # f(y) alone by three kernel designs on the 10,000-cell state, rate constants precomputed:
         # this library's gather and the paper's reaction-parallel atomic design (AoS / SoA reaction data)
         cd = chemgpu.Cells(mech, C, rtol=wl.rtol, atol=wl.atol)
