@@ -1,5 +1,6 @@
 // capi.cpp -- the extern "C" entry points declared in include/chemgpu.h.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstring>
 #include <new>
@@ -38,6 +39,15 @@ struct chem_cells {
 namespace {
 
 thread_local std::string g_err;
+
+// An NVTX range around an entry point, so profilers show the API calls on the
+// host timeline (a no-op unless a tool is attached).
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
 
 int fail(int code, const std::string &msg) {
   g_err = msg;
@@ -259,6 +269,7 @@ void chem_cells_destroy(chem_cells *c) {
 }
 
 int chem_cells_set_state(chem_cells *c, const double *T, const double *P, const double *y, int32_t mem, void *stream) {
+  Range range("chem_cells_set_state");
   g_err.clear();
   if (!c || !T || !P || !y) return fail(CHEM_EINVAL, "NULL argument");
   c->kt_valid = false;
@@ -381,6 +392,7 @@ int check_solve_args(chem_cells *c, double dt) {
 extern "C" {
 
 int chem_solve_step(chem_cells *c, double dt, void *stream) {
+  Range range("chem_solve_step");
   g_err.clear();
   if (int rc = check_solve_args(c, dt)) return rc;
   if (c->n == 0) return 0;
@@ -390,6 +402,7 @@ int chem_solve_step(chem_cells *c, double dt, void *stream) {
 }
 
 int chem_solve_steps(chem_cells *c, double dt, int32_t n_steps, void *stream) {
+  Range range("chem_solve_steps");
   g_err.clear();
   if (int rc = check_solve_args(c, dt)) return rc;
   if (n_steps < 1 || n_steps > CHEM_MAX_GRAPH_STEPS) return fail(CHEM_EINVAL, "n_steps out of range");
@@ -435,6 +448,7 @@ int chem_solve_steps(chem_cells *c, double dt, int32_t n_steps, void *stream) {
 }
 
 int chem_autotune(chem_cells *c, double dt, int64_t n_sample, int32_t *cells_per_block, int32_t *blocks_per_sm) {
+  Range range("chem_autotune");
   g_err.clear();
   if (int rc = check_solve_args(c, dt)) return rc;
   if (n_sample < 0) return fail(CHEM_EINVAL, "n_sample must be >= 0");
@@ -535,6 +549,7 @@ int chem_autotune(chem_cells *c, double dt, int64_t n_sample, int32_t *cells_per
 }
 
 int chem_get_state(const chem_cells *c, double *y, int32_t mem, void *stream) {
+  Range range("chem_get_state");
   g_err.clear();
   if (!c || !y) return fail(CHEM_EINVAL, "NULL argument");
   if (int rc = check_mem(mem)) return rc;
@@ -626,6 +641,7 @@ int chem_eval_newton_solve(chem_cells *c, double cc, const double *y, const doub
 }
 
 int chem_eval_deriv_design(chem_cells *c, int32_t design, const double *y, double *f, int32_t mem, void *stream) {
+  Range range("chem_eval_deriv_design");
   g_err.clear();
   if (!c || !y || !f) return fail(CHEM_EINVAL, "NULL argument");
   if (design != CHEM_DERIV_GATHER && design != CHEM_DERIV_ATOMIC_AOS && design != CHEM_DERIV_ATOMIC_SOA)
@@ -667,6 +683,7 @@ int chem_eval_deriv_design(chem_cells *c, int32_t design, const double *y, doubl
 }
 
 int chem_sensitivity(chem_cells *c, const double *dL_dy, double *dL_dtheta, double *dL_dy0, int32_t mem, void *stream) {
+  Range range("chem_sensitivity");
   g_err.clear();
   if (!c || !dL_dy || !dL_dtheta || !dL_dy0) return fail(CHEM_EINVAL, "NULL argument");
   if (int rc = check_mem(mem)) return rc;
@@ -719,6 +736,7 @@ int chem_sensitivity(chem_cells *c, const double *dL_dy, double *dL_dtheta, doub
 }
 
 int chem_tangent(chem_cells *c, const double *dy0, const double *dtheta, double *dy, int32_t mem, void *stream) {
+  Range range("chem_tangent");
   g_err.clear();
   if (!c || !dy0 || !dy) return fail(CHEM_EINVAL, "NULL argument");
   if (int rc = check_mem(mem)) return rc;
@@ -888,6 +906,7 @@ cudaError_t pipeline_enqueue(chem_pipeline *p, int k, const double *T, const dou
 
 int chem_pipeline_run(chem_pipeline *p, const double *T, const double *P, const double *J, double *y, double dt,
                       int32_t n_steps, chem_chunk_fn fn, void *user, chem_cell_stats *stats) {
+  Range range("chem_pipeline_run");
   g_err.clear();
   if (!p || !T || !P || !y) return fail(CHEM_EINVAL, "NULL argument");
   if (!(dt > 0.0) || !(dt < 1e300)) return fail(CHEM_EINVAL, "dt must be positive and finite");
@@ -901,7 +920,12 @@ int chem_pipeline_run(chem_pipeline *p, const double *T, const double *P, const 
   for (int step = 0; step < n_steps && e == cudaSuccess && rc == 0; ++step)
     for (int k = 0; k < K && e == cudaSuccess && rc == 0; ++k) {
       if ((e = cudaEventSynchronize(p->done[k])) != cudaSuccess) break;
-      if (fn && fn(p->c0[k], p->c0[k + 1], step, user) != 0) {
+      int stop = 0;
+      if (fn) {
+        Range cb("chem_pipeline host work");
+        stop = fn(p->c0[k], p->c0[k + 1], step, user);
+      }
+      if (stop != 0) {
         rc = fail(CHEM_EABORTED, "a chunk callback stopped the pipeline");
         break;
       }
