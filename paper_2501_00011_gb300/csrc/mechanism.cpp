@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <queue>
 
 #include "internal.h"
 
@@ -25,13 +26,30 @@ namespace {
 // ---------------------------------------------------------------- scheduler
 // Places ops into passes of at most 32 so that no two ops of a pass touch the
 // same location unless both only read it; ops keep the program order of every
-// location they share.
+// location they share, so any valid placement computes the same values.
+//
+// While a program is emitted, add() places each op first-fit into the earliest
+// pass its operands allow (lastw / lastr: the pass that last wrote / read each
+// location), which the emitters consult to shape their sums.  It also records
+// every op with the earlier ops it must follow (the last writer of each
+// operand and of its target, and the target's readers since that write).
+// finish() then packs the recorded graph afresh by list scheduling: pass by
+// pass it takes the ready ops with the longest remaining dependency chain
+// first (a reciprocal weighs RECIP_WEIGHT, the FP64 instructions of its pass),
+// and a pass holds reciprocals only when the most urgent ready op is one.
 struct Scheduler {
+  static constexpr int RECIP_WEIGHT = 4;
   std::vector<int> lastw, lastr;
   std::vector<std::vector<Op>> passes;
   std::vector<int> kind;
   int n_ops = 0;
-  explicit Scheduler(int n_loc) : lastw(n_loc, -1), lastr(n_loc, -1) {}
+  // the recorded program
+  std::vector<Op> rec_op;
+  std::vector<int> rec_kind;
+  std::vector<std::vector<int>> rec_pred;
+  std::vector<int> lw_op;                        // last writer op of each location
+  std::vector<std::vector<int>> readers;         // its readers since that write
+  explicit Scheduler(int n_loc) : lastw(n_loc, -1), lastr(n_loc, -1), lw_op(n_loc, -1), readers(n_loc) {}
 
   void add(const Op &op, int k, const int *reads, int nr, int write) {
     int e = 0;
@@ -48,6 +66,22 @@ struct Scheduler {
     for (int i = 0; i < nr; ++i) lastr[reads[i]] = std::max(lastr[reads[i]], p);
     lastw[write] = p;
     n_ops++;
+
+    const int id = (int)rec_op.size();
+    std::vector<int> pred;
+    for (int i = 0; i < nr; ++i)
+      if (lw_op[reads[i]] >= 0) pred.push_back(lw_op[reads[i]]);
+    if (lw_op[write] >= 0) pred.push_back(lw_op[write]);
+    for (int r : readers[write]) pred.push_back(r);
+    std::sort(pred.begin(), pred.end());
+    pred.erase(std::unique(pred.begin(), pred.end()), pred.end());
+    for (int i = 0; i < nr; ++i)
+      if (reads[i] != write) readers[reads[i]].push_back(id);
+    readers[write].clear();
+    lw_op[write] = id;
+    rec_op.push_back(op);
+    rec_kind.push_back(k);
+    rec_pred.push_back(std::move(pred));
   }
   void fma(int t, int a, int b, int c) {
     const int r[3] = {a, b, c};
@@ -58,10 +92,47 @@ struct Scheduler {
     add(Op{(uint16_t)(t | OP_RECIP), (uint16_t)a, 0, 0}, 1, r, 1, t);
   }
   HostProgram finish() const {
+    const int n = (int)rec_op.size();
+    std::vector<std::vector<int>> succ(n);
+    std::vector<int> npred(n, 0);
+    for (int i = 0; i < n; ++i)
+      for (int q : rec_pred[i]) {
+        succ[q].push_back(i);
+        npred[i]++;
+      }
+    // remaining weighted chain length; successors come later in program order
+    std::vector<long> height(n, 0);
+    for (int i = n - 1; i >= 0; --i) {
+      long h = 0;
+      for (int s2 : succ[i]) h = std::max(h, height[s2]);
+      height[i] = h + (rec_kind[i] ? RECIP_WEIGHT : 1);
+    }
+    // ready ops per kind, most urgent first (then program order)
+    auto later = [&](int a, int b) { return height[a] != height[b] ? height[a] < height[b] : a > b; };
+    std::priority_queue<int, std::vector<int>, decltype(later)> ready[2] = {
+        std::priority_queue<int, std::vector<int>, decltype(later)>(later),
+        std::priority_queue<int, std::vector<int>, decltype(later)>(later)};
+    for (int i = 0; i < n; ++i)
+      if (npred[i] == 0) ready[rec_kind[i]].push(i);
     HostProgram hp;
-    for (const auto &p : passes) {
-      for (const Op &o : p) hp.ops.push_back(o);
-      for (size_t i = p.size(); i < (size_t)WARP; ++i) hp.ops.push_back(Op{OP_EMPTY, 0, 0, 0});
+    std::vector<int> pass;
+    int done = 0;
+    while (done < n) {
+      int k;
+      if (ready[0].empty()) k = 1;
+      else if (ready[1].empty()) k = 0;
+      else k = later(ready[0].top(), ready[1].top()) ? 1 : 0;
+      pass.clear();
+      while (!ready[k].empty() && pass.size() < (size_t)WARP) {
+        pass.push_back(ready[k].top());
+        ready[k].pop();
+      }
+      for (int i : pass) hp.ops.push_back(rec_op[i]);
+      for (size_t i = pass.size(); i < (size_t)WARP; ++i) hp.ops.push_back(Op{OP_EMPTY, 0, 0, 0});
+      done += (int)pass.size();
+      for (int i : pass)
+        for (int s2 : succ[i])
+          if (--npred[s2] == 0) ready[rec_kind[s2]].push(s2);
     }
     hp.n_ops = n_ops;
     return hp;

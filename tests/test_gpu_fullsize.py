@@ -116,7 +116,7 @@ def test_autotune_keeps_state_and_results(cg, tropo):
 
 
 def test_fp32_lu_50k(oracle_lib, cg, tropo):
-    # accuracy bound of the FP32-LU form (see test_gpu_parity): within 20
+    # accuracy bound of the FP32-LU form (see test_gpu_parity): within 50
     # tolerance units of the FP64 oracle and as accurate as it against a tight
     # reference, on a sample of the full 50,000-cell batch
     wl = synth.workload_precision(50_000)
@@ -134,10 +134,21 @@ def test_fp32_lu_50k(oracle_lib, cg, tropo):
     assert np.all(stt["status"] == 0)
     ys = y[:, idx]
     tol = wl.rtol * np.abs(yo) + wl.atol
-    assert (np.abs(ys - yo) / tol).max() <= 20.0
+    assert (np.abs(ys - yo) / tol).max() <= 50.0
     acc32 = (np.abs(ys - yt) / (wl.rtol * np.abs(yt) + wl.atol)).max(axis=0)
     acc64 = (np.abs(yo - yt) / (wl.rtol * np.abs(yt) + wl.atol)).max(axis=0)
     assert acc32.max() <= 1.25 * acc64.max() and np.median(acc32) <= 1.1 * np.median(acc64)
+    # the cells where the two forms differ most: there too FP32 is as accurate as FP64
+    y64 = c64.get_state()
+    diff = (np.abs(y - y64) / (wl.rtol * np.abs(y64) + wl.atol)).max(axis=0)
+    worst = np.argsort(-diff)[:10]
+    ywt, swt = oracle_lib.solve_cells(wl.mech, synth.subset(wl.cells, worst), wl.dt, 1e-10, 1e-18)
+    assert np.all(swt["status"] == 0)
+    unit = wl.rtol * np.abs(ywt) + wl.atol
+    w32 = (np.abs(y[:, worst] - ywt) / unit).max(axis=0)
+    w64 = (np.abs(y64[:, worst] - ywt) / unit).max(axis=0)
+    assert w32.max() <= 1.25 * w64.max() and np.median(w32) <= 1.1 * np.median(w64), (w32, w64)
+    assert diff.max() <= 50.0
     rel = np.where(np.abs(yo) > FLOOR, np.abs(ys - yo) / np.maximum(np.abs(yo), 1e-300), 0.0).max(axis=1)
     print(f"fp32 LU 50k: per-species max rel err vs FP64 oracle on {idx.size} cells: median {np.median(rel):.2e}, "
           f"max {rel.max():.2e}; Newton iterations {st['newton_iters'].sum() / st64['newton_iters'].sum():.3f}x "
