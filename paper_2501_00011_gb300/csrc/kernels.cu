@@ -296,11 +296,34 @@ __device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *
 }
 
 // a5: forward and backward substitution with the LDU factors on the vector in
-// WL[X]; it leaves -x there (the programs run without negation).
+// WL[X]; it leaves -x there (the programs run without negation).  Staged (the
+// persistent driver) the programs are read from shared memory; otherwise they
+// are streamed from L2 through a ring in the pair products, which are dead
+// from the end of the factorisation to the next one.  (Streaming them in the
+// staged form too would free room for an eleventh cell per SM, but measured
+// slower: 28.2 against 27.4 ms on the 10,000-cell step.)
 template <typename T, bool STAGED>
 __device__ __forceinline__ void solve_core(const MechDev &M, const unsigned char *tbase, T *WL, const int lane) {
-  run_ops<T, false, STAGED>(reinterpret_cast<const ushort4 *>(tbase + M.tab.fwd_ops), M.fwd_npass, WL, lane);
-  run_ops<T, false, STAGED>(reinterpret_cast<const ushort4 *>(tbase + M.tab.bwd_ops), M.bwd_npass, WL, lane);
+  const ushort4 *fwd = reinterpret_cast<const ushort4 *>(tbase + M.tab.fwd_ops);
+  const ushort4 *bwd = reinterpret_cast<const ushort4 *>(tbase + M.tab.bwd_ops);
+  if (STAGED) {
+    run_ops<T, false, true>(fwd, M.fwd_npass, WL, lane);
+    run_ops<T, false, true>(bwd, M.bwd_npass, WL, lane);
+    return;
+  }
+  const uint32_t pb = smem_addr(WL + M.L_P);
+  const uint32_t rb = (pb + 7u) & ~7u;
+  const int cap = M.n_pairs * (int)sizeof(T) - (int)(rb - pb);
+  if (cap >= 8 * 256) {
+    run_ops_ring<T, false, 8>(fwd, M.fwd_npass, WL, lane, rb);
+    run_ops_ring<T, false, 8>(bwd, M.bwd_npass, WL, lane, rb);
+  } else if (cap >= 4 * 256) {
+    run_ops_ring<T, false, 4>(fwd, M.fwd_npass, WL, lane, rb);
+    run_ops_ring<T, false, 4>(bwd, M.bwd_npass, WL, lane, rb);
+  } else {
+    run_ops<T, false, false>(fwd, M.fwd_npass, WL, lane);
+    run_ops<T, false, false>(bwd, M.bwd_npass, WL, lane);
+  }
 }
 
 template <typename T, int KS, bool STAGED>
