@@ -200,7 +200,7 @@ int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *o
     chem_cells_destroy(c);
     return fail(CHEM_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
   }
-  if (o.driver == CHEM_DRIVER_PERSISTENT &&
+  if ((o.driver == CHEM_DRIVER_PERSISTENT || o.record_adjoint) &&
       ((e = cudaMalloc(&c->order, n * sizeof(int))) != cudaSuccess ||
        (e = cudaMalloc(&c->order_bucket, n * sizeof(int))) != cudaSuccess ||
        (e = cudaMalloc(&c->order_hist, 2 * ORDER_BUCKETS * sizeof(int))) != cudaSuccess)) {
@@ -722,6 +722,10 @@ int chem_sensitivity(chem_cells *c, const double *dL_dy, double *dL_dtheta, doub
   ad.dLdy0 = c->dLdy0;
   ad.gcell = c->gcell;
   ad.dLdtheta = c->dLdtheta;
+  // the longest tapes first
+  if ((e = launch_order_tape(cd, c->order_bucket, c->order_hist, c->order, s)) != cudaSuccess)
+    return cuda_fail(e, "adjoint order");
+  cd.order = c->order;
   if ((e = launch_adjoint(c->mech->m.dev, cd, ad, s)) != cudaSuccess) return cuda_fail(e, "adjoint kernels");
   if ((e = cudaMemcpyAsync(dL_dy0, c->dLdy0, n * S * sizeof(double), kind_out(mem), s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(dL_dtheta, c->dLdtheta, R * sizeof(double), kind_out(mem), s)) != cudaSuccess)
@@ -770,6 +774,9 @@ int chem_tangent(chem_cells *c, const double *dy0, const double *dtheta, double 
   td.dy0 = c->dLdy;
   td.dtheta = (dtheta && R > 0) ? c->dLdtheta : nullptr;
   td.dy = c->dLdy0;
+  if ((e = launch_order_tape(cd, c->order_bucket, c->order_hist, c->order, s)) != cudaSuccess)
+    return cuda_fail(e, "tangent order");
+  cd.order = c->order;
   if ((e = launch_tangent(c->mech->m.dev, cd, td, s)) != cudaSuccess) return cuda_fail(e, "tangent kernel");
   if ((e = cudaMemcpyAsync(dy, c->dLdy0, n * S * sizeof(double), kind_out(mem), s)) != cudaSuccess)
     return cuda_fail(e, "tangent copy-out");

@@ -146,7 +146,8 @@ struct CellsDev {
   double *y;                    // [S][C] in/out
   chem_cell_stats *stats;       // [C]
   int *queue;                   // persistent driver work counter (may be null)
-  const int *order;             // persistent driver: the queue hands out order[0], order[1], ...
+  const int *order;             // persistent driver: the queue hands out order[0], order[1], ...;
+                                // adjoint / tangent: warp slot i takes cell order[i] (NULL: cell i)
                                 // (null: cell index order)
   int *error;                   // counts blocks whose table staging fell back to plain loads (may be null)
   // adjoint tape (tape_n null: not recording).  Per cell e < tape_cap events,
@@ -204,6 +205,9 @@ cudaError_t launch_solve(const MechDev &m, const CellsDev &c, const LaunchCfg &c
 // scale, then a counting sort into order[n_cells].  bucket[n_cells] and
 // hist[2 * ORDER_BUCKETS] are scratch.  Stream-ordered (capturable).
 constexpr int ORDER_BUCKETS = 256;
+// The same counting sort keyed by tape length (events), longest first: the
+// order in which the adjoint and tangent kernels take the cells.
+cudaError_t launch_order_tape(const CellsDev &c, int *bucket, int *hist, int *order, cudaStream_t stream);
 cudaError_t launch_order(const MechDev &m, const CellsDev &c, double rtol, double atol, int *bucket, int *hist,
                          int *order, cudaStream_t stream);
 int max_warps_per_block(const MechDev &m, int lu_precision, int driver);

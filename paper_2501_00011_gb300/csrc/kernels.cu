@@ -1442,8 +1442,9 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) adjoint_kernel(con
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & (WARP - 1);
   const int warp = threadIdx.x / WARP;
-  const int64_t cell = (int64_t)blockIdx.x * P.warps_per_block + warp;
-  if (cell >= C.n_cells) return;
+  const int64_t slot = (int64_t)blockIdx.x * P.warps_per_block + warp;
+  if (slot >= C.n_cells) return;
+  const int64_t cell = C.order ? (int64_t)C.order[slot] : slot;
   Tabs tb;
   tb.base = tb.gbase = M.blob[0];
   double *Wd = reinterpret_cast<double *>(smem + (size_t)warp * P.cell_bytes);
@@ -1655,8 +1656,9 @@ __global__ void __launch_bounds__(ADJ_WARPS_PER_BLOCK * WARP) tangent_kernel(con
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & (WARP - 1);
   const int warp = threadIdx.x / WARP;
-  const int64_t cell = (int64_t)blockIdx.x * P.warps_per_block + warp;
-  if (cell >= C.n_cells) return;
+  const int64_t slot = (int64_t)blockIdx.x * P.warps_per_block + warp;
+  if (slot >= C.n_cells) return;
+  const int64_t cell = C.order ? (int64_t)C.order[slot] : slot;
   Tabs tb;
   tb.base = tb.gbase = M.blob[0];
   double *Wd = reinterpret_cast<double *>(smem + (size_t)warp * P.cell_bytes);
@@ -1743,6 +1745,22 @@ __global__ void __launch_bounds__(ORDER_WARPS * WARP) order_keys_kernel(const __
     bucket[cell] = b;
     atomicAdd(hist + b, 1);
   }
+}
+
+// For the adjoint and tangent walks: the cells by the length of their tapes,
+// longest first (the walk's work is proportional to it), so that the blocks the
+// hardware dispatches last hold the shortest walks.
+__global__ void order_tape_keys_kernel(const CellsDev C, int *bucket, int *hist) {
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= C.n_cells) return;
+  const int n = C.tape_n[cell];
+  int b = ORDER_BUCKETS - 1;
+  if (n > 0) {
+    const int k = (int)fmin(floor(8.0 * log2((double)n)), 254.0);   // 8 buckets per octave
+    b = 254 - k;
+  }
+  bucket[cell] = b;
+  atomicAdd(hist + b, 1);
 }
 
 // exclusive prefix sum of the bucket counts into the scatter cursors
@@ -2012,6 +2030,19 @@ cudaError_t launch_deriv_gather(const MechDev &M, const CellsDev &C, const doubl
     default:
       return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order_tape(const CellsDev &C, int *bucket, int *hist, int *order, cudaStream_t stream) {
+  if (C.n_cells <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * ORDER_BUCKETS, stream);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((C.n_cells + 255) / 256);
+  order_tape_keys_kernel<<<blocks, 256, 0, stream>>>(C, bucket, hist);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  order_scan_kernel<<<1, 32, 0, stream>>>(hist);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  order_scatter_kernel<<<blocks, 256, 0, stream>>>(bucket, hist, order, C.n_cells);
   return cudaGetLastError();
 }
 
