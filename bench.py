@@ -400,7 +400,7 @@ def run_gpu(args):
             "cells": C, "groups": coupled,
             "note": "couple_cells = G: each group of G consecutive cells is one ODE system (shared step size, "
                     "order, Newton iterations, one norm), whole groups per block (10 cells, 8 for G = 4), "
-                    "groups handed out in index order; G1 = independent cells, the headline form. "
+                    "groups handed out most expensive first by their cost in the previous solve; G1 = independent cells, the headline form. "
                     "solver_iterations_total counts Newton iterations once per system, the paper's measure of "
                     "its Multi-cells saving"}
         # pressure-dependent rate laws (Troe fall-off and the two pressure sums) on the same

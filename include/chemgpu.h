@@ -148,7 +148,9 @@ typedef struct {
                                       one WRMS norm over all its species (the linear systems stay
                                       block-diagonal, one block per cell).  FP64 only, no adjoint;
                                       cells_per_block must be a multiple of G (0: the largest that
-                                      fits); a CUDA block holds whole groups. */
+                                      fits); a CUDA block holds whole groups; the persistent
+                                      driver hands out whole groups, most expensive first by
+                                      their cost in the previous solve. */
 } chem_opts;
 
 typedef struct {

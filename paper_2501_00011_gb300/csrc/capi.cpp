@@ -370,7 +370,11 @@ cudaError_t enqueue_solve(chem_cells *c, double dt, cudaStream_t s) {
     cd.queue = c->queue;
     // most expensive cells first, so the longest solves do not start last
     // (coupled groups are fixed sets of consecutive cells, handed out whole)
-    if (c->opts.couple_cells <= 1) {
+    if (c->opts.couple_cells > 1) {
+      if ((e = launch_order_groups(cd, c->opts.couple_cells, c->order_bucket, c->order_hist, c->order, s)) != cudaSuccess)
+        return e;
+      cd.order = c->order;
+    } else {
       if ((e = launch_order(c->mech->m.dev, cd, c->opts.rtol, c->opts.atol, c->order_bucket, c->order_hist, c->order,
                             s)) != cudaSuccess)
         return e;

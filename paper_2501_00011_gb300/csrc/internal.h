@@ -208,6 +208,8 @@ constexpr int ORDER_BUCKETS = 256;
 // The same counting sort keyed by tape length (events), longest first: the
 // order in which the adjoint and tangent kernels take the cells.
 cudaError_t launch_order_tape(const CellsDev &c, int *bucket, int *hist, int *order, cudaStream_t stream);
+// ... and keyed by the cost of coupled groups of G cells: order[i] is a group index.
+cudaError_t launch_order_groups(const CellsDev &c, int G, int *bucket, int *hist, int *order, cudaStream_t stream);
 cudaError_t launch_order(const MechDev &m, const CellsDev &c, double rtol, double atol, int *bucket, int *hist,
                          int *order, cudaStream_t stream);
 int max_warps_per_block(const MechDev &m, int lu_precision, int driver);

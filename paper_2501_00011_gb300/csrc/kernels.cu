@@ -1002,6 +1002,7 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const
           if (grp.w == 0 && lane == 0) grp_next[gl] = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(C.queue), 1ull);
           grp.sync();
           gi = grp_next[gl];
+          if (C.order && gi * G < C.n_cells) gi = __ldg(C.order + gi);   // groups most expensive first
         }
         const int64_t c0 = gi * G;
         if (c0 >= C.n_cells) break;
@@ -1763,6 +1764,23 @@ __global__ void order_tape_keys_kernel(const CellsDev C, int *bucket, int *hist)
   atomicAdd(hist + b, 1);
 }
 
+// Coupled groups of G consecutive cells (which share their statistics): the
+// groups by their cost in the previous solve, largest first; groups without
+// one first, in group order.
+__global__ void order_group_keys_kernel(const CellsDev C, int G, int64_t n_groups, int *bucket, int *hist) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_groups) return;
+  const chem_cell_stats prev = C.stats[g * G];
+  int b = 0;
+  if (prev.steps > 0) {
+    const double l = log2(65.0 * prev.f_evals + 100.0 * prev.solves + 560.0 * prev.jac_evals + 150.0 * prev.steps);
+    const int k = (int)fmin(fmax(floor(4.0 * l), -126.0), 126.0);
+    b = 128 - k;
+  }
+  bucket[g] = b;
+  atomicAdd(hist + b, 1);
+}
+
 // exclusive prefix sum of the bucket counts into the scatter cursors
 __global__ void order_scan_kernel(int *hist) {
   if (threadIdx.x != 0) return;
@@ -2030,6 +2048,20 @@ cudaError_t launch_deriv_gather(const MechDev &M, const CellsDev &C, const doubl
     default:
       return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order_groups(const CellsDev &C, int G, int *bucket, int *hist, int *order, cudaStream_t stream) {
+  if (C.n_cells <= 0 || G < 1) return cudaSuccess;
+  const int64_t ng = (C.n_cells + G - 1) / G;
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * ORDER_BUCKETS, stream);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((ng + 255) / 256);
+  order_group_keys_kernel<<<blocks, 256, 0, stream>>>(C, G, ng, bucket, hist);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  order_scan_kernel<<<1, 32, 0, stream>>>(hist);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  order_scatter_kernel<<<blocks, 256, 0, stream>>>(bucket, hist, order, ng);
   return cudaGetLastError();
 }
 
