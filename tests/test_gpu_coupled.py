@@ -120,3 +120,16 @@ def test_coupled_options_rejected(cg, tropo):
     c.set_state(wl.cells.T, wl.cells.P, wl.cells.y)
     with pytest.raises(cg.ChemError):
         c.autotune(600.0)
+
+
+def test_coupled_group_order_does_not_change_results(cg, tropo):
+    # the persistent queue hands out groups by their previous cost (a second solve of the
+    # same batch runs in another order than the first); results equal the plain driver's
+    wl = synth.workload_batching(97)
+    ref, sref = _solve(cg, tropo, wl, wl.cells, 4, "plain")
+    c = cg.Cells(tropo, wl.cells.n_cells, rtol=wl.rtol, atol=wl.atol, driver="persistent", couple_cells=4)
+    for _ in range(2):
+        c.set_state(wl.cells.T, wl.cells.P, wl.cells.y)
+        c.set_photolysis(wl.cells.J)
+        c.solve_step(wl.dt)
+        assert np.array_equal(c.get_state(), ref) and np.array_equal(c.get_stats(), sref)
