@@ -43,10 +43,25 @@ def spread(oracle_lib, wl, cells, c, n_steps=1, n=4):
     return float((np.abs(yp - yo)[mask] / np.abs(yo[mask])).max())
 
 
-def compare(y, st, yo, so, oracle_lib=None, wl=None, cells=None, n_steps=1, max_odd_frac=0.03):
+def tight_errors(oracle_lib, wl, cells, idx, y, yo, n_steps=1):
+    """Errors of y and yo (columns idx) against the oracle at rtol 1e-10, atol 1e-18,
+    in tolerance units of the workload, max over species."""
+    sub = synth.subset(cells, idx)
+    for _ in range(n_steps):
+        sub.y, stt = oracle_lib.solve_cells(wl.mech, sub, wl.dt, 1e-10, 1e-18, max_steps=200_000)
+        assert np.all(stt["status"] == 0)
+    unit = wl.rtol * np.abs(sub.y) + wl.atol
+    return (np.abs(y[:, idx] - sub.y) / unit).max(axis=0), (np.abs(yo[:, idx] - sub.y) / unit).max(axis=0)
+
+
+def compare(y, st, yo, so, oracle_lib=None, wl=None, cells=None, n_steps=1, max_odd_frac=0.03, tight_flips=False):
     """Parity of a batch; returns (max rel err on well-determined cells, flips, ill-conditioned cells).
 
-    cells is the input batch whose columns y / yo hold the results."""
+    cells is the input batch whose columns y / yo hold the results.  With
+    tight_flips, a cell whose step sequence differs may lie farther than 10
+    tolerance units from the oracle's result if it is no less accurate than the
+    oracle's against a tight reference (both are correct results: the tolerance
+    bounds each step's local error, not the global one)."""
     assert np.array_equal(st["status"], so["status"]), (st["status"], so["status"])
     ok = so["status"] == 0
     same = (st["steps"] == so["steps"]) & (st["newton_iters"] == so["newton_iters"])
@@ -54,7 +69,12 @@ def compare(y, st, yo, so, oracle_lib=None, wl=None, cells=None, n_steps=1, max_
     n_ok = max(1, int(ok.sum()))
     flips = np.nonzero(ok & ~same)[0]
     for c in flips:
-        assert np.max(np.abs(y[:, c] - yo[:, c]) / tol[:, c]) <= 10.0, c
+        units = np.max(np.abs(y[:, c] - yo[:, c]) / tol[:, c])
+        if units <= 10.0:
+            continue
+        assert tight_flips, (c, units)
+        eg, eo = tight_errors(oracle_lib, wl, cells, [c], y, yo, n_steps)
+        assert eg[0] <= 1.25 * eo[0] + 1.0, (c, units, eg[0], eo[0])
     worst, odd = 0.0, 0
     for c in np.nonzero(ok & same)[0]:
         mask = np.abs(yo[:, c]) > FLOOR

@@ -135,6 +135,23 @@ def test_solve_pressure_dependent(oracle_lib, cg, mechs, driver):
     print(f"pressure-dependent 301 cells ({driver}): max rel err {err:.2e}, flips {flips}, rounding-limited {odd}")
 
 
+@pytest.mark.parametrize("S,R,U,Ph", [(50, 130, 40, 13), (128, 330, 100, 34)])
+def test_solve_other_species_counts(oracle_lib, cg, S, R, U, Ph):
+    # 33-64 and 97-128 species (128 is the maximum) take the kernels' 2- and 4-slot
+    # register paths, which the named workloads do not reach; both drivers, 61 cells.
+    # The 128-species cells take 200-560 steps, and 3 of 61 flip a borderline decision
+    # (up to 18 tolerance units from the oracle, each closer to a tight reference than
+    # the oracle's own result): flips are checked against the tight reference.
+    m = synth.random_mechanism(S, R, U, Ph, name=f"synthetic_{S}sp_{R}rx")
+    cells = synth.random_cells(S, 61, T_range=(220.0, 310.0), P_range=(2e4, 1e5))
+    wl = synth.Workload(m.name, m, cells, 600.0, 1, 1e-4, 1e-10)
+    mech = cg.Mechanism(m)
+    yo, so = oracle_lib.solve_cells(m, cells, wl.dt, wl.rtol, wl.atol)
+    for driver in ("plain", "persistent"):
+        y, st = cg.solve(mech, cells, wl.dt, wl.rtol, wl.atol, driver=driver)
+        _compare(y, st, yo, so, oracle_lib, wl, cells, max_odd_frac=0.1, tight_flips=True)
+
+
 def test_drivers_agree_bitwise(cg, mechs):
     wl = synth.workload_tropo(97)
     ya, sa = cg.solve(mechs["tropo"], wl.cells, wl.dt, wl.rtol, wl.atol, driver="plain")

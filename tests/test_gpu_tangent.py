@@ -124,3 +124,28 @@ def test_tangent_options_and_devices(cg):
     plain = cg.Cells(m, 4, rtol=wl.rtol, atol=wl.atol)
     with pytest.raises(cg.ChemError):
         plain.tangent(np.zeros((wl.mech.n_species, 4)))
+
+
+def test_tangent_and_adjoint_at_128_species(oracle_lib, cg):
+    # the maximum species count (four register slots per lane): the GPU tangent and
+    # adjoint of the GPU tape against the oracle's
+    m = synth.random_mechanism(128, 330, 100, 34, name="synthetic_128sp_330rx")
+    cells = synth.random_cells(128, 5, T_range=(220.0, 310.0), P_range=(2e4, 1e5))
+    wl = synth.Workload(m.name, m, cells, 600.0, 1, 1e-4, 1e-10)
+    mech, c = _solved(cg, wl, cells, 1)
+    dy0, dth = _directions(m, cells, 24)
+    dy, n_bad = c.tangent(dy0, dth)
+    assert n_bad == 0
+    w = synth.loss_weights(128, cells.n_cells)
+    gth, gy0, n_bad = c.sensitivity(w)
+    assert n_bad == 0
+    g_sum = np.zeros(m.n_reactions)
+    for k in range(cells.n_cells):
+        tape = _tape_for(oracle_lib, *c.get_tape(k))
+        kt = oracle_lib.rate_constants(m, cells.T[k], cells.P[k])
+        ref = oracle_lib.tangent(m, kt, cells.y[:, k], tape, dy0[:, k], dth)
+        assert np.all(np.abs(dy[:, k] - ref) <= 1e-8 * np.abs(ref) + 1e-12 * np.abs(ref).max()), k
+        ly0, g = oracle_lib.adjoint(m, kt, cells.y[:, k], tape, w[:, k])
+        g_sum += g
+        assert np.all(np.abs(gy0[:, k] - ly0) <= 1e-8 * np.abs(ly0) + 1e-12 * np.abs(ly0).max()), k
+    assert np.all(np.abs(gth - g_sum) <= 1e-8 * np.abs(g_sum) + 1e-12 * np.abs(g_sum).max())

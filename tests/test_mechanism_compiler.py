@@ -15,7 +15,10 @@ import pytest
 import program_emulator as pe
 from paper_2501_00011_gb300 import synth
 
-MECHS = {"small": synth.mechanism_small, "tropo": synth.mechanism_tropo, "pressure": synth.mechanism_tropo_pressure}
+MECHS = {"small": synth.mechanism_small, "tropo": synth.mechanism_tropo, "pressure": synth.mechanism_tropo_pressure,
+         # two register-slot sizes the named workloads do not reach: 33-64 and 97-128 (the maximum) species
+         "s50": lambda: synth.random_mechanism(50, 130, 40, 13, name="synthetic_50sp_130rx"),
+         "s128": lambda: synth.random_mechanism(128, 330, 100, 34, name="synthetic_128sp_330rx")}
 
 
 @pytest.fixture(scope="module")
