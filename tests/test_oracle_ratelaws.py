@@ -157,3 +157,20 @@ def test_pressure_workload_spans_the_falloff(oracle_lib):
                  / (m.ext[troe, synth.EXT_A2] * (T / 300.0) ** m.ext[troe, synth.EXT_B2]))
     x = np.array(x)
     assert x.min() < 0.1 and x.max() > 10.0
+
+
+def test_hand_worked_rate_constants(oracle_lib):
+    import os
+    vals = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "pressure_rate_laws.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                k, *v = line.split()
+                vals[k] = np.array([float(x) for x in v])
+    rxs = [dict(reac=[0, 1], prod=[2], kind=synth.TROE, A=1e-30, A2=1e-11, Fc=0.64, N=1.0),
+           dict(reac=[0, 1], prod=[2], kind=synth.PRESSURE_SUM, A=1e-12, A2=1e-32),
+           dict(reac=[0, 1], prod=[2], kind=synth.FALLOFF_SUM, A=1e-13, A2=1e-12, A3=1e-32)]
+    kt = _kt(oracle_lib, rxs, float(vals["T"][0]), float(vals["P"][0]))
+    # P is given to 7 digits, so n_air (and each k~) carries a relative error of about 1e-8
+    np.testing.assert_allclose(kt, vals["kt"], rtol=1e-7)
