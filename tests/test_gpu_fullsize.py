@@ -57,6 +57,21 @@ def test_tropo_10k_persistent(oracle_lib, cg, tropo):
     print(f"10k persistent FP64, {idx.size} sampled cells: max rel err {err:.2e}, flips {flips}, rounding-limited {odd}")
 
 
+def test_one_million_cells(oracle_lib, cg, tropo):
+    # a batch 100x the benchmark's (y alone 576 MB): one persistent launch, a million
+    # queue pops; sampled cells against the oracle, every cell converged and finite
+    wl = synth.workload_tropo(1_000_000)
+    c = _batch(cg, tropo, wl, driver="persistent")
+    c.solve_step(wl.dt)
+    y, st = c.get_state(), c.get_stats()
+    assert np.all(st["status"] == 0) and np.all(np.isfinite(y))
+    idx = sample_cells(wl.cells.n_cells, 12, seed=7)
+    sub = synth.subset(wl.cells, idx)
+    yo, so = oracle_steps(oracle_lib, wl, sub, 1)
+    compare(y[:, idx], st[idx], yo, so, oracle_lib, wl, sub)
+    c.close()
+
+
 def test_batching_50k_graph_autotuned(oracle_lib, cg, tropo):
     wl = synth.workload_batching(50_000)
     c = _batch(cg, tropo, wl, driver="persistent")
