@@ -613,6 +613,14 @@ def run_gpu(args):
                     "peak = measured copy bandwidth; does not bind"},
             "gpu_launches": 4 * args.steps,   # per step: queue-order keys, scan, scatter, solve
             "clocks": clocks,
+            "paper_context": {
+                "note": "the paper's own speedups (Results and Conclusions sections), quoted as context only: "
+                        "other hardware, other work (its GPU code is the derivative alone), not targets",
+                "multi_cell_vs_one_cell_cpu": "about 8x, up to 9x (IBM Power9, one thread)",
+                "gpu_derivative_vs_cpu_derivative": "1.2x at 10,000 cells (V100 vs one Power9 thread)",
+                "reaction_data_layout": "1.3x over the base GPU derivative (V100)",
+                "final_gpu_derivative": "up to 1.7x (V100)",
+                "data_movement_share_of_gpu_time": "about 90% (10,800 cells)"},
         }
         line.update(extras)
         if cpu_rate is not None:
