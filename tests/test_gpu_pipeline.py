@@ -38,8 +38,8 @@ def _host_step(y, T, c0, c1, step):
     T[c0:c1] += 1.5
 
 
-def _reference(cg, mech, wl, cells, n_steps, driver, J=None):
-    c = cg.Cells(mech, cells.n_cells, rtol=wl.rtol, atol=wl.atol, driver=driver)
+def _reference(cg, mech, wl, cells, n_steps, driver, J=None, prec=64):
+    c = cg.Cells(mech, cells.n_cells, rtol=wl.rtol, atol=wl.atol, driver=driver, lu_precision=prec)
     y, T, P = cells.y.copy(), cells.T.copy(), cells.P.copy()
     st = None
     for step in range(n_steps):
@@ -54,12 +54,12 @@ def _reference(cg, mech, wl, cells, n_steps, driver, J=None):
     return y, T, st
 
 
-@pytest.mark.parametrize("n,K,driver", [(301, 4, "persistent"), (301, 3, "plain"), (7, 7, "persistent"),
-                                        (50, 1, "persistent")])
-def test_pipeline_equals_one_batch(cg, tropo, n, K, driver):
+@pytest.mark.parametrize("n,K,driver,prec", [(301, 4, "persistent", 64), (301, 3, "plain", 64), (7, 7, "persistent", 64),
+                                             (50, 1, "persistent", 64), (120, 3, "persistent", 32)])
+def test_pipeline_equals_one_batch(cg, tropo, n, K, driver, prec):
     wl = synth.workload_tropo(n)
     n_steps = 3
-    yr, Tr, sr = _reference(cg, tropo, wl, wl.cells, n_steps, driver)
+    yr, Tr, sr = _reference(cg, tropo, wl, wl.cells, n_steps, driver, prec=prec)
     y = cg.pinned_empty(wl.cells.y.shape)
     y[:] = wl.cells.y
     T, P = wl.cells.T.copy(), wl.cells.P.copy()
@@ -69,7 +69,7 @@ def test_pipeline_equals_one_batch(cg, tropo, n, K, driver):
         seen.append((step, c0, c1))
         _host_step(y, T, c0, c1, step)
 
-    p = cg.Pipeline(tropo, n, K, rtol=wl.rtol, atol=wl.atol, driver=driver)
+    p = cg.Pipeline(tropo, n, K, rtol=wl.rtol, atol=wl.atol, driver=driver, lu_precision=prec)
     st = p.run(T, P, y, wl.dt, n_steps, fn=fn, stats=True)
     p.close()
     assert np.array_equal(y, yr) and np.array_equal(T, Tr) and np.array_equal(st, sr)

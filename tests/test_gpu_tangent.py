@@ -56,9 +56,12 @@ def _solved(cg, wl, cells, n_steps, theta=None):
     return m, c
 
 
-@pytest.mark.parametrize("name,n_steps,with_theta", [("small", 2, False), ("tropo", 4, False), ("tropo", 2, True)])
+@pytest.mark.parametrize("name,n_steps,with_theta", [("small", 2, False), ("tropo", 4, False), ("tropo", 2, True),
+                                                    ("pressure", 2, True)])
 def test_gpu_tangent_matches_oracle_tangent(oracle_lib, cg, name, n_steps, with_theta):
-    wl = synth.workload_small() if name == "small" else synth.workload_adjoint(12)
+    # "pressure": the Troe / pressure-sum kinds, 1e3..1.05e5 Pa (theta scales every kind alike)
+    wl = {"small": synth.workload_small, "tropo": lambda: synth.workload_adjoint(12),
+          "pressure": lambda: synth.workload_pressure(12)}[name]()
     n_cells = 6
     cells = synth.subset(wl.cells, np.arange(n_cells))
     theta = np.random.default_rng(5).uniform(-0.3, 0.3, wl.mech.n_reactions) if with_theta else None
