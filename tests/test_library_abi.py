@@ -59,3 +59,24 @@ def test_binding_refuses_without_library(tmp_path):
             chemgpu.load(str(tmp_path / "missing.so"))
     finally:
         chemgpu._lib = saved
+
+
+def test_pipeline_host_arrays_are_checked_without_copies():
+    # the pipeline reads and writes the caller's host arrays in place, so the binding
+    # must refuse anything it would have to copy
+    import numpy as np
+    from paper_2501_00011_gb300 import chemgpu
+    a = np.zeros((4, 6))
+    assert chemgpu._host_ptr(a, "y").value == a.ctypes.data
+    for bad in (np.zeros((4, 6), np.float32), np.asfortranarray(np.zeros((4, 6))), np.zeros((4, 12))[:, ::2]):
+        with pytest.raises(chemgpu.ChemError):
+            chemgpu._host_ptr(bad, "y")
+    ro = np.zeros(3)
+    ro.flags.writeable = False
+    with pytest.raises(chemgpu.ChemError):
+        chemgpu._host_ptr(ro, "T")
+    torch = pytest.importorskip("torch")
+    t = torch.zeros(5, dtype=torch.float64)
+    assert chemgpu._host_ptr(t, "T").value == t.data_ptr()
+    with pytest.raises(chemgpu.ChemError):
+        chemgpu._host_ptr(torch.zeros(5, dtype=torch.float32), "T")
