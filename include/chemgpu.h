@@ -151,6 +151,11 @@ typedef struct {
                                       fits); a CUDA block holds whole groups; the persistent
                                       driver hands out whole groups, most expensive first by
                                       their cost in the previous solve. */
+  int32_t stage_wait;              /* persistent driver, test hook: polls of the bounded wait for a
+                                      block's bulk copy of the tables into shared memory.  0 (default):
+                                      2^22; -1: none, so every block reads the tables from global
+                                      memory instead (the same bytes; results are identical) and
+                                      counts a fallback, see chem_staging_fallbacks */
 } chem_opts;
 
 typedef struct {
@@ -163,8 +168,13 @@ typedef struct {
  * plain driver, automatic launch shape, no adjoint). */
 void chem_opts_default(chem_opts *opts);
 
-/* Compile a mechanism: validate the tables (species indices in range, yields
- * finite, rate parameters finite, n_species <= CHEM_MAX_SPECIES), build the
+/* Compile a mechanism.  Paper, Background section: reactions of the general
+ * form c1 y1 + ... -> c_{m+1} y_{m+1} + ..., each with a rate r_j that is a
+ * function of the state, T and P, contributing -c_i r_j to each reactant and
+ * +c_i r_j to each product; the derivative is the sum of the contributions.
+ * The rate constants are the CHEM_* kinds above.  Validate the tables
+ * (species indices in range, yields finite, rate parameters finite,
+ * n_species <= CHEM_MAX_SPECIES), build the
  * Jacobian pattern, a static Markowitz pivot order, the LU fill and the warp
  * programs, and copy them to the current device.  rx: n_reactions entries,
  * borrowed.  *out is owned by the caller and released with
@@ -179,27 +189,47 @@ int chem_mechanism_info(const chem_mech *mech, chem_mech_info *out);
 int chem_mechanism_structure(const chem_mech *mech, int32_t *pos, uint8_t *fill);
 
 /* Allocate the device state of n_cells cells for a mechanism (which must
- * outlive the batch).  opts NULL = defaults.  *out released with
- * chem_cells_destroy.  Errors: CHEM_EINVAL, CHEM_ENOMEM, CHEM_ECUDA. */
+ * outlive the batch).  Paper, Background section: every grid cell carries its
+ * own temperature, pressure and concentrations and its chemistry is
+ * independent of the other cells'; Implementations section (Multi-cells): all
+ * cells' data in one structure, with the cell loop inside the solver.  The
+ * batch lives on the current device, which is the mechanism's and must be
+ * current in every later call on the batch (else CHEM_EINVAL).  opts NULL =
+ * defaults.  *out released with chem_cells_destroy.  Errors: CHEM_EINVAL,
+ * CHEM_ENOMEM, CHEM_ECUDA. */
 int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *opts,
                       chem_cells **out);
 void chem_cells_destroy(chem_cells *cells);      /* NULL is a no-op */
 
-/* Copy T[n_cells], P[n_cells] and y[n_species][n_cells] into the batch (D2D for
- * CHEM_MEM_DEVICE, H2D otherwise), asynchronously on stream.  Resets the
- * adjoint tape.  Errors: CHEM_EINVAL, CHEM_ECUDA. */
+/* Copy T[n_cells] (K), P[n_cells] (Pa) and y[n_species][n_cells] (mol/mol,
+ * cell index unit stride) into the batch (D2D for CHEM_MEM_DEVICE, H2D
+ * otherwise), asynchronously on stream; the caller's arrays may be reused once
+ * the stream has passed the copies.  Paper, Background section: the state,
+ * temperature and pressure of each cell that the rates depend on;
+ * Implementations section: the multi-cell state is one array over all cells.
+ * Resets the adjoint tape.  Errors: CHEM_EINVAL, CHEM_ECUDA. */
 int chem_cells_set_state(chem_cells *cells, const double *T, const double *P, const double *y,
                          int32_t mem, void *stream);
-/* Per-cell photolysis rates J[n_photolysis][n_cells] (photolysis reactions in
- * reaction order); NULL reverts to the mechanism's J.  Errors as above. */
+/* Per-cell photolysis rates J[n_photolysis][n_cells] in s^-1 (photolysis
+ * reactions in reaction order); NULL reverts to the mechanism's J.  Paper,
+ * Background section: a rate is a function of the cell's state (here, its
+ * light).  Errors as above. */
 int chem_cells_set_photolysis(chem_cells *cells, const double *J, int32_t mem, void *stream);
 /* Per-reaction log multipliers theta[n_reactions], shared by all cells:
  * k~_j -> k~_j exp(theta_j).  NULL reverts to theta = 0. */
 int chem_cells_set_theta(chem_cells *cells, const double *theta, int32_t mem, void *stream);
 
-/* Integrate every cell over [0, dt] (dt > 0) on stream; the integrator starts
- * afresh and the new state replaces the old.  Asynchronous; per-cell outcomes
- * are read with chem_get_stats.  Errors: CHEM_EINVAL, CHEM_ESTATE, CHEM_ECUDA. */
+/* Integrate every cell over [0, dt] (dt > 0, seconds) on stream; the
+ * integrator starts afresh and the new state replaces the old.  Paper,
+ * Background section: the chemistry module hands CVODE the derivative and a
+ * sparse Jacobian, and CVODE integrates with BDF and Newton iteration; here
+ * the whole integration runs on the GPU (variable-order BDF 1-5, modified
+ * Newton on I - c J with a static-order sparse LU, error test and step/order
+ * control, per cell).  Results do not depend on the driver, the launch shape
+ * or the order the persistent queue takes the cells in.  Asynchronous;
+ * per-cell outcomes are read with chem_get_stats (a failed cell keeps its
+ * input state).  Errors: CHEM_EINVAL, CHEM_ESTATE (before set_state),
+ * CHEM_ECUDA; nothing is launched on error. */
 int chem_solve_step(chem_cells *cells, double dt, void *stream);
 /* n_steps consecutive chem_solve_step calls of dt (1..CHEM_MAX_GRAPH_STEPS) as
  * one CUDA graph launch on stream: the per-step queue resets and solve
@@ -222,12 +252,27 @@ int chem_solve_steps(chem_cells *cells, double dt, int32_t n_steps, void *stream
 int chem_autotune(chem_cells *cells, double dt, int64_t n_sample, int32_t *cells_per_block,
                   int32_t *blocks_per_sm);
 
-/* Copy the state y[n_species][n_cells] out (synchronises stream when mem is
- * CHEM_MEM_HOST). */
+/* Copy the state y[n_species][n_cells] (mol/mol, cell index unit stride) into
+ * the caller's y (synchronises stream when mem is CHEM_MEM_HOST).  Paper,
+ * Background section: the updated concentrations the chemistry step returns to
+ * the model.  Errors: CHEM_EINVAL, CHEM_ECUDA. */
 int chem_get_state(const chem_cells *cells, double *y, int32_t mem, void *stream);
 /* Copy the per-cell statistics of the last solve (out[n_cells]); synchronises
- * stream when mem is CHEM_MEM_HOST. */
+ * stream when mem is CHEM_MEM_HOST.  The counters are those the paper's
+ * Results section compares between its One-cell and Multi-cells forms
+ * (solver iterations).  Errors: CHEM_EINVAL, CHEM_ECUDA. */
 int chem_get_stats(const chem_cells *cells, chem_cell_stats *out, int32_t mem, void *stream);
+/* Staging counters of the last chem_solve_step / chem_solve_steps call on the
+ * batch (persistent driver; every step of a graph launch): *fallbacks = blocks
+ * whose bulk copy of the tables into shared memory was not seen to land within
+ * the bounded wait (they read the tables from global memory: same results,
+ * slower); *unfinished = blocks that exited before such a late copy was seen
+ * to land within a second bounded wait.  Both are 0 in normal operation.  With
+ * cells NULL: the counters of chem_solve_step_noalloc's last call on the
+ * current device.  Reads on stream and synchronises it.  The paper has no
+ * counterpart (it is a diagnostic of this library's table staging).  Errors:
+ * CHEM_EINVAL, CHEM_ECUDA. */
+int chem_staging_fallbacks(const chem_cells *cells, int64_t *fallbacks, int64_t *unfinished, void *stream);
 
 /* Discrete adjoint (needs opts.record_adjoint).  Every solve_step since the
  * last set_state recorded, per cell, everything that determined its result:
@@ -250,6 +295,27 @@ int chem_get_stats(const chem_cells *cells, chem_cell_stats *out, int32_t mem, v
  * dL_dtheta). */
 int chem_sensitivity(chem_cells *cells, const double *dL_dy, double *dL_dtheta, double *dL_dy0, int32_t mem,
                      void *stream);
+/* The same discrete adjoint over n_steps consecutive solve_step calls of dt,
+ * by step checkpointing, for tapes that cannot hold all the steps at once:
+ * states[n_steps][n_species][n_cells] holds the state at the start of each
+ * step (states[0] the state at set_state, states[k] the result of step k-1),
+ * kept by the caller during the forward.  Last step first, the library
+ * re-solves step k from states[k] with a fresh tape (or, when last_recorded
+ * is nonzero, uses the current tape for the last step: the caller's forward
+ * recorded that step alone), runs the adjoint through it with
+ * lambda = dL/d(result of step k), and carries the adjoint of its input to the
+ * step before; dL_dtheta[n_reactions] receives the sum over steps and cells,
+ * dL_dy0[n_species][n_cells] the adjoint of states[0].  The batch's T, P,
+ * photolysis rates and theta must be those of the forward.  Afterwards the
+ * batch holds the result of re-solving step 0 and its tape that step's.  The
+ * paper has no counterpart (it differentiates the Background section's
+ * BDF/Newton integration, step by step).  Inputs and outputs in `mem` space;
+ * synchronises stream.  Returns 0, a negative error (CHEM_EINVAL, CHEM_ESTATE,
+ * CHEM_ECUDA), or the number of (cell, step) pairs whose tape overflowed or
+ * whose re-solve failed: those cells' gradients are then incomplete. */
+int chem_sensitivity_checkpointed(chem_cells *cells, const double *states, int32_t n_steps, double dt,
+                                  int32_t last_recorded, const double *dL_dy, double *dL_dtheta, double *dL_dy0,
+                                  int32_t mem, void *stream);
 /* Tangent (forward-mode) sensitivity of the same frozen-control map
  * (needs opts.record_adjoint): the directional derivative
  *   dy[n_species][n_cells] = (d y / d y0) dy0 + (d y / d theta) dtheta
@@ -323,18 +389,25 @@ int chem_eval_newton_solve(chem_cells *cells, double c, const double *y, const d
  * y[n_species][n_cells] (integrated in place over [0, dt], as
  * chem_solve_step does), stats[n_cells] (written), and optionally
  * J[n_photolysis][n_cells] and theta[n_reactions] (NULL: mechanism J,
- * theta = 0).  opts NULL = defaults; the driver is always the persistent work
- * queue.  The paper has no counterpart of this entry point.
+ * theta = 0).  Every buffer must be memory of the current device (or
+ * managed memory), which must be the mechanism's device; anything else
+ * (host memory included) is refused with CHEM_EINVAL before any launch.
+ * opts NULL = defaults; the driver is always the persistent work queue, in
+ * cell index order; couple_cells > 1 and record_adjoint are refused (both need
+ * buffers a batch allocates).  Results equal those of chem_solve_step on a
+ * persistent batch with the same inputs and options, bit for bit.  The paper
+ * has no counterpart of this entry point.
  *
- * The work-queue counter lives in a 256-byte static device array inside the
- * library (held by every GPU that loads the library until the process
- * exits); the call clears it on stream before the launch and calls no
+ * The work-queue counter and the two staging counters (chem_staging_fallbacks
+ * with cells NULL reads them) live in a 256-byte static device array inside
+ * the library (held by every GPU that loads the library until the process
+ * exits); the call clears them on stream before the launch and calls no
  * cudaMalloc/cudaFree.  The first call on a device looks up that array's
  * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls on a device share its one counter: calls whose
+ * stream capture.  All calls on a device share its one array: calls whose
  * work overlaps on that GPU (e.g. launched on two streams) race and must be
- * serialised by the caller.  n_cells beyond
- * CHEM_NOALLOC_MAX_CELLS is rejected with CHEM_EINVAL. */
+ * serialised by the caller.  n_cells beyond CHEM_NOALLOC_MAX_CELLS is
+ * rejected with CHEM_EINVAL. */
 #define CHEM_NOALLOC_MAX_CELLS 2147483647LL
 int chem_solve_step_noalloc(const chem_mech *mech, int64_t n_cells, const double *T, const double *P,
                             const double *J, const double *theta, double *y, chem_cell_stats *stats,

@@ -28,8 +28,9 @@ EXPORTS = ["chem_opts_default", "chem_mechanism_create", "chem_mechanism_destroy
            "chem_mechanism_info", "chem_mechanism_structure", "chem_cells_create",
            "chem_cells_destroy", "chem_cells_set_state", "chem_cells_set_photolysis",
            "chem_cells_set_theta", "chem_solve_step", "chem_solve_steps", "chem_autotune",
-           "chem_get_state", "chem_get_stats",
+           "chem_get_state", "chem_get_stats", "chem_staging_fallbacks",
            "chem_eval_deriv", "chem_eval_newton_solve", "chem_eval_deriv_design", "chem_solve_step_noalloc", "chem_sensitivity",
+           "chem_sensitivity_checkpointed",
            "chem_tangent", "chem_get_tape", "chem_pipeline_create", "chem_pipeline_destroy", "chem_pipeline_run", "chem_last_error"]
 
 
@@ -49,7 +50,8 @@ class Opts(ct.Structure):
     _fields_ = [("rtol", ct.c_double), ("atol", ct.c_double), ("max_order", ct.c_int32),
                 ("max_steps", ct.c_int32), ("lu_precision", ct.c_int32), ("driver", ct.c_int32),
                 ("cells_per_block", ct.c_int32), ("blocks_per_sm", ct.c_int32),
-                ("record_adjoint", ct.c_int32), ("tape_steps", ct.c_int32), ("couple_cells", ct.c_int32)]
+                ("record_adjoint", ct.c_int32), ("tape_steps", ct.c_int32), ("couple_cells", ct.c_int32),
+                ("stage_wait", ct.c_int32)]
 
 
 class MechInfo(ct.Structure):
@@ -98,11 +100,13 @@ def load(path: str | None = None):
         L.chem_solve_step.argtypes = [V, ct.c_double, V]
         L.chem_get_state.argtypes = [V, V, ct.c_int32, V]
         L.chem_get_stats.argtypes = [V, V, ct.c_int32, V]
+        L.chem_staging_fallbacks.argtypes = [V, V, V, V]
         L.chem_eval_deriv.argtypes = [V, V, V, ct.c_int32, V]
         L.chem_eval_newton_solve.argtypes = [V, ct.c_double, V, V, V, ct.c_int32, V]
         L.chem_eval_deriv_design.argtypes = [V, ct.c_int32, V, V, ct.c_int32, V]
         L.chem_solve_step_noalloc.argtypes = [V, ct.c_int64, V, V, V, V, V, V, ct.c_double, V, V]
         L.chem_sensitivity.argtypes = [V, V, V, V, ct.c_int32, V]
+        L.chem_sensitivity_checkpointed.argtypes = [V, V, ct.c_int32, ct.c_double, ct.c_int32, V, V, V, ct.c_int32, V]
         L.chem_tangent.argtypes = [V, V, V, V, ct.c_int32, V]
         L.chem_solve_steps.argtypes = [V, ct.c_double, ct.c_int32, V]
         L.chem_autotune.argtypes = [V, ct.c_double, ct.c_int64, V, V]
@@ -218,7 +222,7 @@ class Cells:
     def __init__(self, mech: Mechanism, n_cells: int, rtol: float = 1e-4, atol: float = 1e-10,
                  max_order: int = 5, max_steps: int = 5000, lu_precision: int = 64,
                  driver: str = "plain", cells_per_block: int = 0, blocks_per_sm: int = 0,
-                 record_adjoint: bool = False, tape_steps: int = 0, couple_cells: int = 1):
+                 record_adjoint: bool = False, tape_steps: int = 0, couple_cells: int = 1, stage_wait: int = 0):
         L = load()
         self.mech = mech
         self.n_cells = int(n_cells)
@@ -229,6 +233,7 @@ class Cells:
         o.cells_per_block, o.blocks_per_sm = cells_per_block, blocks_per_sm
         o.record_adjoint, o.tape_steps = int(record_adjoint), tape_steps
         o.couple_cells = int(couple_cells)
+        o.stage_wait = int(stage_wait)
         self.opts = o
         h = ct.c_void_p()
         _check(L.chem_cells_create(mech.handle, self.n_cells, ct.byref(o), ct.byref(h)), "chem_cells_create")
@@ -287,6 +292,11 @@ class Cells:
                "chem_get_stats")
         return st
 
+    def staging_fallbacks(self, stream=None):
+        """(fallbacks, unfinished) of the last solve call: blocks whose table staging
+        fell back to global memory, and blocks that exited before a late copy landed."""
+        return staging_fallbacks(self, stream)
+
     def eval_deriv(self, y, stream=None):
         """f(y) for every cell ([S, C] numpy in, numpy out), on the GPU."""
         yy = np.ascontiguousarray(y, np.float64)
@@ -330,6 +340,26 @@ class Cells:
         n_bad = _check(load().chem_sensitivity(self._h, pa, pt, p0, ma, _stream_ptr(stream)), "chem_sensitivity")
         return dL_dtheta, dL_dy0, n_bad
 
+    def sensitivity_checkpointed(self, states, dt: float, dL_dy, last_recorded: bool = False, dL_dtheta=None,
+                                 dL_dy0=None, stream=None):
+        """(dL/dtheta [R], dL/dy0 [S, C], n_bad) through len(states) solve steps of dt by step
+        checkpointing: states [n_steps, S, C] holds the state at the start of each step; the
+        library re-solves each step from it (the last one too unless last_recorded) and chains
+        the adjoint through them, last step first (chem_sensitivity_checkpointed)."""
+        R = self.mech.n_reactions
+        if dL_dtheta is None:
+            dL_dtheta = np.zeros(R)
+        if dL_dy0 is None:
+            dL_dy0 = np.zeros((self.mech.n_species, self.n_cells))
+        n_steps = int(states.shape[0])
+        (ps, ms, k0), (pa, ma, k1), (pt, mt, k2), (p0, m0, k3) = _ptr(states), _ptr(dL_dy), _ptr(dL_dtheta), _ptr(dL_dy0)
+        if not (ms == ma == mt == m0):
+            raise ChemError("states, dL_dy, dL_dtheta and dL_dy0 must all be on the host or all on the device")
+        n_bad = _check(load().chem_sensitivity_checkpointed(self._h, ps, n_steps, float(dt), int(bool(last_recorded)),
+                                                            pa, pt, p0, ma, _stream_ptr(stream)),
+                       "chem_sensitivity_checkpointed")
+        return dL_dtheta, dL_dy0, n_bad
+
     def tangent(self, dy0, dtheta=None, dy=None, stream=None):
         """(dy [S, C], n_bad): the directional derivative of the current state
         along dy0 [S, C] (the state at set_state) and dtheta [R] (None: 0)."""
@@ -367,6 +397,15 @@ class Cells:
             self.close()
         except Exception:
             pass
+
+
+def staging_fallbacks(cells=None, stream=None):
+    """Staging counters (fallbacks, unfinished) of a batch's last solve call, or with
+    cells None of chem_solve_step_noalloc's last call on the current device."""
+    fb, un = ct.c_int64(0), ct.c_int64(0)
+    _check(load().chem_staging_fallbacks(None if cells is None else cells.handle, ct.byref(fb), ct.byref(un),
+                                         _stream_ptr(stream)), "chem_staging_fallbacks")
+    return fb.value, un.value
 
 
 CHUNK_FN = ct.CFUNCTYPE(ct.c_int, ct.c_int64, ct.c_int64, ct.c_int32, ct.c_void_p)
@@ -476,11 +515,12 @@ def _autograd_function():
         discrete adjoint (chem_sensitivity).  theta [R] and y0 [S, C] are float64
         tensors on the batch's device; T, P [C] likewise.
 
-        Step checkpointing: the forward keeps the state after every step
-        (S x C doubles each).  The backward differentiates the whole recorded
-        tape when it fits; when it does not (a cell's tape overflowed) or when
-        checkpoint=True, it re-runs the steps one at a time from the kept
-        states, last first, each with a fresh tape, and chains the adjoint
+        Step checkpointing: the forward keeps the state at the start of every
+        step and the final one (S x C doubles each).  The backward differentiates
+        the whole recorded tape when it fits; when it does not (a cell's tape
+        overflowed) or when checkpoint=True, it hands the kept states to
+        chem_sensitivity_checkpointed, which re-runs the steps one at a time
+        from them, last first, each with a fresh tape, and chains the adjoint
         through them: the tape then only has to hold one step.  The batch must
         not be used otherwise between the forward and the backward."""
 
@@ -489,18 +529,19 @@ def _autograd_function():
             n_steps = int(n_steps)
             th = theta.detach().contiguous()
             cells.set_theta(th)
-            states = [y0.detach().contiguous()]
+            states = torch.empty((n_steps + 1,) + tuple(y0.shape), dtype=y0.dtype, device=y0.device)
+            states[0].copy_(y0.detach())
             if checkpoint:
                 # one tape per step: start every step afresh from the kept state
                 for k in range(n_steps):
-                    cells.set_state(T, P, states[-1])
+                    cells.set_state(T, P, states[k])
                     cells.solve_step(dt)
-                    states.append(cells.get_state(out=torch.empty_like(y0)))
+                    cells.get_state(out=states[k + 1])
             else:
                 cells.set_state(T, P, states[0])
                 for k in range(n_steps):
                     cells.solve_step(dt)
-                    states.append(cells.get_state(out=torch.empty_like(y0)))
+                    cells.get_state(out=states[k + 1])
             ctx.cells, ctx.T, ctx.P, ctx.dt, ctx.theta = cells, T, P, dt, th
             ctx.states, ctx.per_step = states, bool(checkpoint)
             ctx.R = theta.numel()
@@ -512,29 +553,18 @@ def _autograd_function():
             c = ctx.cells
             c.set_theta(ctx.theta)          # the backward evaluates rates with the forward's theta
             gth = _t.zeros(ctx.R, dtype=_t.float64, device=gy.device)
+            gy0 = _t.zeros_like(gy)
             lam = gy.contiguous()
-            n_steps = len(ctx.states) - 1
             if not ctx.per_step:
-                gy0 = _t.zeros_like(gy)
                 _, _, n_bad = c.sensitivity(lam, gth, gy0)
                 if n_bad == 0:
                     return gth, gy0, None, None, None, None, None, None
-            # re-run step k from its kept state (the last step's tape is current
-            # in per-step mode), then carry lambda back through it; a failed
-            # whole-tape attempt above has written partial sums into gth
-            gth.zero_()
-            g_k = _t.empty_like(gth)
-            for k in range(n_steps - 1, -1, -1):
-                if not (ctx.per_step and k == n_steps - 1):
-                    c.set_state(ctx.T, ctx.P, ctx.states[k])
-                    c.solve_step(ctx.dt)
-                lam_prev = _t.empty_like(lam)
-                _, _, n_bad = c.sensitivity(lam, g_k, lam_prev)
-                if n_bad:
-                    raise ChemError(f"{n_bad} cells have no sensitivity for step {k} (tape overflow or failed solve)")
-                gth += g_k
-                lam = lam_prev
-            return gth, lam, None, None, None, None, None, None
+            # the tape is current for the last step in per-step mode
+            _, _, n_bad = c.sensitivity_checkpointed(ctx.states[:-1], ctx.dt, lam, last_recorded=ctx.per_step,
+                                                     dL_dtheta=gth, dL_dy0=gy0)
+            if n_bad:
+                raise ChemError(f"{n_bad} (cell, step) pairs have no sensitivity (tape overflow or failed solve)")
+            return gth, gy0, None, None, None, None, None, None
 
     return ChemSolveFn
 

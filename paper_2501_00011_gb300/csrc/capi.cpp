@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "internal.h"
@@ -17,7 +18,9 @@ struct chem_cells {
   chem_opts opts{};
   double *T = nullptr, *P = nullptr, *y = nullptr, *J = nullptr, *theta = nullptr;
   chem_cell_stats *stats = nullptr;
-  int *queue = nullptr;   // [0..1] work counter, [2] staging fallbacks
+  // device counters: [0] persistent work queue, [1] staging fallbacks and
+  // [2] unfinished staging copies of the last solve call (CellsDev::stage), [3] spare
+  unsigned long long *counters = nullptr;
   int *order = nullptr, *order_bucket = nullptr, *order_hist = nullptr;   // persistent driver: queue order
   double *kt = nullptr;       // chem_eval_deriv_design: rate constants [R][C], allocated on first use
   bool kt_valid = false;      // ... and current for the batch's T, P, photolysis and theta
@@ -64,6 +67,19 @@ cudaMemcpyKind kind_out(int32_t mem) { return mem == CHEM_MEM_DEVICE ? cudaMemcp
 
 int check_mem(int32_t mem) {
   if (mem != CHEM_MEM_HOST && mem != CHEM_MEM_DEVICE) return fail(CHEM_EINVAL, "mem must be CHEM_MEM_HOST or CHEM_MEM_DEVICE");
+  return 0;
+}
+
+// A batch lives on the device that was current when it was created (its
+// buffers, and its mechanism's tables and the solver constants, are there):
+// every call that touches it must be made with that device current.
+int check_device(const chem_cells *c) {
+  int dev = -1;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(CHEM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev != c->device)
+    return fail(CHEM_EINVAL, "the batch belongs to device " + std::to_string(c->device) + " but device " +
+                                 std::to_string(dev) + " is current");
   return 0;
 }
 
@@ -153,6 +169,12 @@ int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *o
   *out = nullptr;
   if (!mech) return fail(CHEM_EINVAL, "mechanism is NULL");
   if (n_cells < 0 || n_cells > ((int64_t)1 << 31)) return fail(CHEM_EINVAL, "n_cells must be in 0..2^31");
+  {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != mech->m.device)
+      return fail(CHEM_EINVAL, "the mechanism belongs to device " + std::to_string(mech->m.device) +
+                                   ", which must be current when a batch is created");
+  }
   chem_opts o;
   if (opts) o = *opts; else chem_opts_default(&o);
   if (!(o.rtol > 0.0) || !(o.atol > 0.0)) return fail(CHEM_EINVAL, "rtol and atol must be > 0");
@@ -180,6 +202,7 @@ int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *o
     return fail(CHEM_EINVAL, "record_adjoint needs lu_precision 64 (the adjoint differentiates the FP64 iteration)");
   if (o.record_adjoint && (o.tape_steps < 0 || o.tape_steps > CHEM_MAX_TAPE_ROWS))
     return fail(CHEM_EINVAL, "tape_steps out of range");
+  if (o.stage_wait < -1) return fail(CHEM_EINVAL, "stage_wait must be -1, 0 or positive");
 
   chem_cells *c = new (std::nothrow) chem_cells();
   if (!c) return fail(CHEM_ENOMEM, "host allocation failed");
@@ -194,7 +217,7 @@ int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *o
       (e = cudaMalloc(&c->P, n * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&c->y, n * S * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&c->stats, n * sizeof(chem_cell_stats))) != cudaSuccess ||
-      (e = cudaMalloc(&c->queue, 4 * sizeof(long long))) != cudaSuccess ||
+      (e = cudaMalloc(&c->counters, 4 * sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaMalloc(&c->theta, (R > 0 ? R : 1) * sizeof(double))) != cudaSuccess ||
       (mech->m.n_phot > 0 && (e = cudaMalloc(&c->J, n * mech->m.n_phot * sizeof(double))) != cudaSuccess)) {
     chem_cells_destroy(c);
@@ -232,7 +255,7 @@ int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *o
     }
   }
   if ((e = cudaMemset(c->stats, 0, n * sizeof(chem_cell_stats))) != cudaSuccess ||
-      (e = cudaMemset(c->queue, 0, 4 * sizeof(long long))) != cudaSuccess) {
+      (e = cudaMemset(c->counters, 0, 4 * sizeof(unsigned long long))) != cudaSuccess) {
     chem_cells_destroy(c);
     return cuda_fail(e, "cudaMemset");
   }
@@ -250,7 +273,7 @@ void chem_cells_destroy(chem_cells *c) {
   cudaFree(c->J);
   cudaFree(c->theta);
   cudaFree(c->stats);
-  cudaFree(c->queue);
+  cudaFree(c->counters);
   cudaFree(c->order);
   cudaFree(c->order_bucket);
   cudaFree(c->order_hist);
@@ -272,6 +295,7 @@ int chem_cells_set_state(chem_cells *c, const double *T, const double *P, const 
   Range range("chem_cells_set_state");
   g_err.clear();
   if (!c || !T || !P || !y) return fail(CHEM_EINVAL, "NULL argument");
+  if (int rc = check_device(c)) return rc;
   c->kt_valid = false;
   if (int rc = check_mem(mem)) return rc;
   if (c->n == 0) { c->have_state = true; return 0; }
@@ -294,6 +318,7 @@ int chem_cells_set_state(chem_cells *c, const double *T, const double *P, const 
 int chem_cells_set_photolysis(chem_cells *c, const double *J, int32_t mem, void *stream) {
   g_err.clear();
   if (!c) return fail(CHEM_EINVAL, "NULL argument");
+  if (int rc = check_device(c)) return rc;
   c->kt_valid = false;
   if (!J) { c->use_J = false; return 0; }
   if (int rc = check_mem(mem)) return rc;
@@ -308,6 +333,7 @@ int chem_cells_set_photolysis(chem_cells *c, const double *J, int32_t mem, void 
 int chem_cells_set_theta(chem_cells *c, const double *theta, int32_t mem, void *stream) {
   g_err.clear();
   if (!c) return fail(CHEM_EINVAL, "NULL argument");
+  if (int rc = check_device(c)) return rc;
   c->kt_valid = false;
   if (!theta) { c->use_theta = false; return 0; }
   if (int rc = check_mem(mem)) return rc;
@@ -333,7 +359,7 @@ CellsDev solve_dev(chem_cells *c) {
   cd.y = c->y;
   cd.stats = c->stats;
   cd.queue = nullptr;
-  cd.error = c->queue + 4;
+  cd.stage = c->counters + 1;
   cd.tape_kq = c->tape_kq;
   cd.ytape = c->ytape;
   cd.tape_val = c->tape_val;
@@ -357,6 +383,7 @@ LaunchCfg launch_cfg(const chem_opts &o, double dt) {
   cfg.dt = dt;
   cfg.max_order = o.max_order;
   cfg.max_steps = o.max_steps;
+  cfg.stage_wait = o.stage_wait;
   return cfg;
 }
 
@@ -365,9 +392,9 @@ LaunchCfg launch_cfg(const chem_opts &o, double dt) {
 cudaError_t enqueue_solve(chem_cells *c, double dt, cudaStream_t s) {
   CellsDev cd = solve_dev(c);
   if (c->opts.driver == CHEM_DRIVER_PERSISTENT) {
-    cudaError_t e = cudaMemsetAsync(c->queue, 0, sizeof(long long), s);
+    cudaError_t e = cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    cd.queue = c->queue;
+    cd.queue = c->counters;
     // most expensive cells first, so the longest solves do not start last
     // (coupled groups are fixed sets of consecutive cells, handed out whole)
     if (c->opts.couple_cells > 1) {
@@ -388,7 +415,12 @@ int check_solve_args(chem_cells *c, double dt) {
   if (!c) return fail(CHEM_EINVAL, "NULL argument");
   if (!(dt > 0.0) || !(dt < 1e300)) return fail(CHEM_EINVAL, "dt must be positive and finite");
   if (!c->have_state) return fail(CHEM_ESTATE, "solve before set_state");
-  return 0;
+  return check_device(c);
+}
+
+// the staging counters report on one solve call (all its steps)
+cudaError_t clear_stage_counters(chem_cells *c, cudaStream_t s) {
+  return cudaMemsetAsync(c->counters + 1, 0, 2 * sizeof(unsigned long long), s);
 }
 
 }  // namespace
@@ -400,7 +432,8 @@ int chem_solve_step(chem_cells *c, double dt, void *stream) {
   g_err.clear();
   if (int rc = check_solve_args(c, dt)) return rc;
   if (c->n == 0) return 0;
-  cudaError_t e = enqueue_solve(c, dt, (cudaStream_t)stream);
+  cudaError_t e = clear_stage_counters(c, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = enqueue_solve(c, dt, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
   return 0;
 }
@@ -425,7 +458,7 @@ int chem_solve_steps(chem_cells *c, double dt, int32_t n_steps, void *stream) {
     // relaxed mode: the launch path may query and set kernel attributes while capturing
     if ((e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
       return cuda_fail(e, "begin capture");
-    cudaError_t le = cudaSuccess;
+    cudaError_t le = clear_stage_counters(c, c->capture_stream);
     for (int k = 0; k < n_steps && le == cudaSuccess; ++k) le = enqueue_solve(c, dt, c->capture_stream);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(c->capture_stream, &g);
@@ -504,7 +537,7 @@ int chem_autotune(chem_cells *c, double dt, int64_t n_sample, int32_t *cells_per
   cd.theta = c->use_theta ? c->theta : nullptr;
   cd.y = y;
   cd.stats = st;
-  cd.error = reinterpret_cast<int *>(q + 2);
+  cd.stage = reinterpret_cast<unsigned long long *>(q + 1);
   const int wmax = max_warps_per_block(M, prec, drv);
   float best = 0.0f;
   int best_w = 0, best_b = 0;
@@ -522,7 +555,7 @@ int chem_autotune(chem_cells *c, double dt, int64_t n_sample, int32_t *cells_per
         cd.queue = nullptr;
         if (drv == CHEM_DRIVER_PERSISTENT) {
           if ((e = cudaMemsetAsync(q, 0, sizeof(long long), s)) != cudaSuccess) break;
-          cd.queue = reinterpret_cast<int *>(q);
+          cd.queue = reinterpret_cast<unsigned long long *>(q);
         }
         float ms = 0.0f;
         if ((e = cudaEventRecord(e0, s)) != cudaSuccess || (e = launch_solve(M, cd, cfg, s)) != cudaSuccess ||
@@ -552,11 +585,27 @@ int chem_autotune(chem_cells *c, double dt, int64_t n_sample, int32_t *cells_per
   return 0;
 }
 
+int chem_staging_fallbacks(const chem_cells *c, int64_t *fallbacks, int64_t *unfinished, void *stream) {
+  g_err.clear();
+  if (!fallbacks || !unfinished) return fail(CHEM_EINVAL, "NULL argument");
+  if (!c) return noalloc_stage_counts(fallbacks, unfinished, (cudaStream_t)stream);
+  if (int rc = check_device(c)) return rc;
+  unsigned long long v[2] = {0, 0};
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(v, c->counters + 1, sizeof(v), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "staging counters");
+  *fallbacks = (int64_t)v[0];
+  *unfinished = (int64_t)v[1];
+  return 0;
+}
+
 int chem_get_state(const chem_cells *c, double *y, int32_t mem, void *stream) {
   Range range("chem_get_state");
   g_err.clear();
   if (!c || !y) return fail(CHEM_EINVAL, "NULL argument");
   if (int rc = check_mem(mem)) return rc;
+  if (int rc = check_device(c)) return rc;
   if (c->n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(y, c->y, (size_t)c->n * c->mech->m.S * sizeof(double), kind_out(mem), s);
@@ -569,6 +618,7 @@ int chem_get_stats(const chem_cells *c, chem_cell_stats *out, int32_t mem, void 
   g_err.clear();
   if (!c || !out) return fail(CHEM_EINVAL, "NULL argument");
   if (int rc = check_mem(mem)) return rc;
+  if (int rc = check_device(c)) return rc;
   if (c->n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(out, c->stats, (size_t)c->n * sizeof(chem_cell_stats), kind_out(mem), s);
@@ -589,7 +639,7 @@ CellsDev cells_dev(chem_cells *c) {
   cd.y = c->y;
   cd.stats = c->stats;
   cd.queue = nullptr;
-  cd.error = c->queue + 4;
+  cd.stage = c->counters + 1;
   cd.tape_kq = nullptr;
   cd.ytape = nullptr;
   cd.tape_val = nullptr;
@@ -605,6 +655,7 @@ int probe(chem_cells *c, int mode, double cc, const double *y, const double *b, 
   if (!c || !y || !out || (mode == 1 && !b)) return fail(CHEM_EINVAL, "NULL argument");
   if (int rc = check_mem(mem)) return rc;
   if (!c->have_state) return fail(CHEM_ESTATE, "diagnostic before set_state");
+  if (int rc = check_device(c)) return rc;
   if (c->n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)c->n * c->mech->m.S * sizeof(double);
@@ -652,6 +703,7 @@ int chem_eval_deriv_design(chem_cells *c, int32_t design, const double *y, doubl
     return fail(CHEM_EINVAL, "unknown derivative design");
   if (int rc = check_mem(mem)) return rc;
   if (!c->have_state) return fail(CHEM_ESTATE, "derivative before set_state");
+  if (int rc = check_device(c)) return rc;
   if (c->n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
   const MechDev &M = c->mech->m.dev;
@@ -693,6 +745,7 @@ int chem_sensitivity(chem_cells *c, const double *dL_dy, double *dL_dtheta, doub
   if (int rc = check_mem(mem)) return rc;
   if (!c->tape_n) return fail(CHEM_ESTATE, "the batch was created without record_adjoint");
   if (!c->have_state) return fail(CHEM_ESTATE, "sensitivity before set_state");
+  if (int rc = check_device(c)) return rc;
   const size_t n = (size_t)c->n, S = (size_t)c->mech->m.S, R = (size_t)c->mech->m.R;
   if (n == 0) {
     if (mem == CHEM_MEM_HOST) std::memset(dL_dtheta, 0, R * sizeof(double));
@@ -712,7 +765,7 @@ int chem_sensitivity(chem_cells *c, const double *dL_dy, double *dL_dtheta, doub
   cd.y = c->y;
   cd.stats = c->stats;
   cd.queue = nullptr;
-  cd.error = nullptr;
+  cd.stage = nullptr;
   cd.tape_kq = c->tape_kq;
   cd.ytape = c->ytape;
   cd.tape_val = c->tape_val;
@@ -721,11 +774,12 @@ int chem_sensitivity(chem_cells *c, const double *dL_dy, double *dL_dtheta, doub
   cd.tape_bad = c->tape_bad;
   cd.tape_cap = c->tape_cap;
   cd.row_cap = c->row_cap;
-  AdjDev ad;
+  AdjDev ad{};
   ad.dLdy = c->dLdy;
   ad.dLdy0 = c->dLdy0;
   ad.gcell = c->gcell;
   ad.dLdtheta = c->dLdtheta;
+  ad.accumulate = 0;
   // the longest tapes first
   if ((e = launch_order_tape(cd, c->order_bucket, c->order_hist, c->order, s)) != cudaSuccess)
     return cuda_fail(e, "adjoint order");
@@ -743,6 +797,67 @@ int chem_sensitivity(chem_cells *c, const double *dL_dy, double *dL_dtheta, doub
   return n_bad;
 }
 
+int chem_sensitivity_checkpointed(chem_cells *c, const double *states, int32_t n_steps, double dt,
+                                  int32_t last_recorded, const double *dL_dy, double *dL_dtheta, double *dL_dy0,
+                                  int32_t mem, void *stream) {
+  Range range("chem_sensitivity_checkpointed");
+  g_err.clear();
+  if (!c || !states || !dL_dy || !dL_dtheta || !dL_dy0) return fail(CHEM_EINVAL, "NULL argument");
+  if (int rc = check_mem(mem)) return rc;
+  if (!c->tape_n) return fail(CHEM_ESTATE, "the batch was created without record_adjoint");
+  if (!c->have_state) return fail(CHEM_ESTATE, "sensitivity before set_state");
+  if (int rc = check_device(c)) return rc;
+  if (n_steps < 1 || n_steps > CHEM_MAX_GRAPH_STEPS) return fail(CHEM_EINVAL, "n_steps out of range");
+  if (!(dt > 0.0) || !(dt < 1e300)) return fail(CHEM_EINVAL, "dt must be positive and finite");
+  const size_t n = (size_t)c->n, S = (size_t)c->mech->m.S, R = (size_t)c->mech->m.R;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    if (mem == CHEM_MEM_HOST) std::memset(dL_dtheta, 0, R * sizeof(double));
+    else cudaMemsetAsync(dL_dtheta, 0, R * sizeof(double), s);
+    return 0;
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(c->dLdy, dL_dy, n * S * sizeof(double), kind_in(mem), s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->counters + 3, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+    return cuda_fail(e, "sensitivity copy-in");
+  CellsDev cd = solve_dev(c);
+  cd.stage = nullptr;
+  // lambda ping-pongs between the batch's two adjoint vectors
+  double *lin = c->dLdy, *lout = c->dLdy0;
+  for (int k = n_steps - 1; k >= 0; --k) {
+    if (!(last_recorded && k == n_steps - 1)) {
+      // re-run step k from its kept state with a fresh tape
+      if ((e = cudaMemcpyAsync(c->y, states + (size_t)k * S * n, n * S * sizeof(double), kind_in(mem), s)) != cudaSuccess ||
+          (e = cudaMemsetAsync(c->tape_n, 0, n * sizeof(int), s)) != cudaSuccess ||
+          (e = cudaMemsetAsync(c->tape_rows, 0, n * sizeof(int), s)) != cudaSuccess ||
+          (e = cudaMemsetAsync(c->tape_bad, 0, n * sizeof(int), s)) != cudaSuccess ||
+          (e = enqueue_solve(c, dt, s)) != cudaSuccess)
+        return cuda_fail(e, "checkpointed re-solve");
+    }
+    CellsDev ca = cd;
+    if ((e = launch_order_tape(ca, c->order_bucket, c->order_hist, c->order, s)) != cudaSuccess)
+      return cuda_fail(e, "adjoint order");
+    ca.order = c->order;
+    AdjDev ad{};
+    ad.dLdy = lin;
+    ad.dLdy0 = lout;
+    ad.gcell = c->gcell;
+    ad.dLdtheta = c->dLdtheta;
+    ad.accumulate = k != n_steps - 1;
+    if ((e = launch_adjoint(c->mech->m.dev, ca, ad, s)) != cudaSuccess ||
+        (e = launch_count_flags(c->tape_bad, c->n, c->counters + 3, s)) != cudaSuccess)
+      return cuda_fail(e, "adjoint kernels");
+    std::swap(lin, lout);
+  }
+  unsigned long long n_bad = 0;
+  if ((e = cudaMemcpyAsync(dL_dy0, lin, n * S * sizeof(double), kind_out(mem), s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(dL_dtheta, c->dLdtheta, R * sizeof(double), kind_out(mem), s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&n_bad, c->counters + 3, sizeof(n_bad), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_fail(e, "sensitivity copy-out");
+  return n_bad > (unsigned long long)INT32_MAX ? INT32_MAX : (int)n_bad;
+}
+
 int chem_tangent(chem_cells *c, const double *dy0, const double *dtheta, double *dy, int32_t mem, void *stream) {
   Range range("chem_tangent");
   g_err.clear();
@@ -750,6 +865,7 @@ int chem_tangent(chem_cells *c, const double *dy0, const double *dtheta, double 
   if (int rc = check_mem(mem)) return rc;
   if (!c->tape_n) return fail(CHEM_ESTATE, "the batch was created without record_adjoint");
   if (!c->have_state) return fail(CHEM_ESTATE, "tangent before set_state");
+  if (int rc = check_device(c)) return rc;
   const size_t n = (size_t)c->n, S = (size_t)c->mech->m.S, R = (size_t)c->mech->m.R;
   if (n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
@@ -799,6 +915,7 @@ int chem_get_tape(const chem_cells *c, int64_t cell, int32_t *kind, int32_t *q, 
   if (!c || !n_events || !n_rows) return fail(CHEM_EINVAL, "NULL argument");
   if (!c->tape_n) return fail(CHEM_ESTATE, "the batch was created without record_adjoint");
   if (cell < 0 || cell >= c->n) return fail(CHEM_EINVAL, "cell index out of range");
+  if (int rc = check_device(c)) return rc;
   int n = 0, nr = 0;
   cudaError_t e;
   if ((e = cudaMemcpy(&n, c->tape_n + cell, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||

@@ -145,11 +145,15 @@ struct CellsDev {
   const double *theta;          // may be null
   double *y;                    // [S][C] in/out
   chem_cell_stats *stats;       // [C]
-  int *queue;                   // persistent driver work counter (may be null)
+  unsigned long long *queue;    // persistent driver work counter (may be null)
   const int *order;             // persistent driver: the queue hands out order[0], order[1], ...;
                                 // adjoint / tangent: warp slot i takes cell order[i] (NULL: cell i)
                                 // (null: cell index order)
-  int *error;                   // counts blocks whose table staging fell back to plain loads (may be null)
+  // staging counters (may be null): [0] blocks whose bulk copy of the tables
+  // was not seen to land within the first bounded wait (they read the tables
+  // from global memory instead), [1] blocks that exited before seeing that
+  // late copy land within the final bounded wait
+  unsigned long long *stage;
   // adjoint tape (tape_n null: not recording).  Per cell e < tape_cap events,
   // kq = kind | q << 8, val:
   //   0 INIT      val h0,   row y at the start of the solve
@@ -177,6 +181,7 @@ struct AdjDev {
   double *dLdy0;                // [S][C]
   double *gcell;                // [R][C] per-cell theta gradients
   double *dLdtheta;             // [R]
+  int accumulate;               // 0: dLdtheta = the sum over cells; 1: dLdtheta += that sum
 };
 
 // Buffers of chem_tangent (device, owned by the batch).
@@ -186,6 +191,9 @@ struct TanDev {
   double *dy;                   // [S][C] out: the directional derivative of the state
 };
 
+// Iterations of the bounded wait for a block's bulk copy of the tables.
+constexpr long long STAGE_WAIT_DEFAULT = 1LL << 22;
+
 struct LaunchCfg {
   int lu_precision;     // 64 / 32
   int driver;           // CHEM_DRIVER_*
@@ -194,6 +202,7 @@ struct LaunchCfg {
   int blocks_per_sm;
   double rtol, atol, dt;
   int max_order, max_steps;
+  long long stage_wait; // iterations of the first wait for the staged tables (chem_opts.stage_wait)
 };
 
 size_t smem_per_cell(const MechDev &m, int lu_precision);
@@ -224,6 +233,8 @@ cudaError_t launch_probe(const MechDev &M, const CellsDev &C, int lu_precision, 
 // discrete adjoint: replay (exact steps, y rows), backward sweep, theta reduction
 cudaError_t launch_adjoint(const MechDev &m, const CellsDev &c, const AdjDev &a, cudaStream_t stream);
 cudaError_t launch_tangent(const MechDev &m, const CellsDev &c, const TanDev &t, cudaStream_t stream);
+// *acc += the number of nonzero flags among flag[0..n)
+cudaError_t launch_count_flags(const int *flag, int64_t n, unsigned long long *acc, cudaStream_t stream);
 // deriv.cu: derivative-only kernels for comparing designs.  kt[R][C] rate
 // constants of the batch (launch_rates fills it); y, f [S][C] on the device.
 cudaError_t launch_rates(const MechDev &m, const CellsDev &c, double *kt, cudaStream_t stream);
@@ -235,6 +246,11 @@ cudaError_t launch_deriv_gather(const MechDev &m, const CellsDev &c, const doubl
 
 // sets the thread-local message returned by chem_last_error()
 void set_last_error(const std::string &msg);
+
+// noalloc.cu: the staging counters of chem_solve_step_noalloc's last call on
+// the current device (read on stream, which is then synchronised); a CHEM_*
+// return code
+int noalloc_stage_counts(int64_t *fallbacks, int64_t *unfinished, cudaStream_t stream);
 
 }  // namespace chemgpu
 

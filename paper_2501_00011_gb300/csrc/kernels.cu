@@ -40,7 +40,6 @@ constexpr int NEWTON_MAXITER = 3;
 constexpr double CRDOWN = 0.3, RDIV = 2.0, NLSCOEF = 0.1, DGMAX = 0.3, THRESH = 1.5;
 constexpr int MSBP = 20, MXNEF = 7, MXNCF = 10;
 constexpr double ETA_CF = 0.25, ETA_MXF = 0.2, ETA_CST_SAFETY = 0.9, ETA_CST_MIN = 0.1, STRETCH = 1e-3;
-constexpr long TMA_WAIT_LIMIT = 1L << 22;
 constexpr int ORDER_WARPS = 8;          // cells per block of the queue-order kernel
 
 struct SolveParams {
@@ -52,6 +51,7 @@ struct SolveParams {
   int prec;            // 0: FP64 LU, 1: FP32 LU
   int tab_bytes;       // staged table bytes at the start of shared memory (0 if not staged)
   int couple;          // coupled group size (warps_per_block is a multiple of it); 1: independent cells
+  long long stage_wait;   // iterations of the first bounded wait for the staged tables
 };
 
 // Newton-Raphson refinement of the hardware reciprocal approximation:
@@ -203,8 +203,8 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
       : "memory");
 }
 // bounded wait for phase `parity` of the barrier; false if the limit ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long limit) {
-  for (long it = 0; it < limit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -944,24 +944,21 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
 }
 
 // Stage the table blob into the first `bytes` of shared memory with one TMA
-// bulk copy.  The wait is bounded; if it runs out the block copies the blob
-// with ordinary loads instead (a late bulk copy writes the same bytes) and
-// counts the event in *err.
-__device__ bool stage_tables(const unsigned char *blob, int bytes, unsigned char *smem, uint64_t *bar, int *err) {
+// bulk copy.  The wait is bounded (`limit` polls of the barrier); if it runs
+// out, the block counts the event in stage[0] and returns false, and the
+// caller reads the tables from the blob in global memory instead (the same
+// bytes), leaving the staged region to the late copy.  Nothing else is placed
+// in that region, so a late copy cannot overwrite live data.
+__device__ bool stage_tables(const unsigned char *blob, int bytes, unsigned char *smem, uint64_t *bar,
+                             unsigned long long *stage, long long limit) {
   if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
   if (threadIdx.x == 0) {
     mbar_expect_tx(bar, (uint32_t)bytes);
     tma_load_1d(smem, blob, (uint32_t)bytes, bar);
   }
-  const bool ok = __syncthreads_and(mbar_wait(bar, 0, TMA_WAIT_LIMIT));
-  if (!ok) {
-    const uint4 *src = reinterpret_cast<const uint4 *>(blob);
-    uint4 *dst = reinterpret_cast<uint4 *>(smem);
-    for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
-    __syncthreads();
-    if (threadIdx.x == 0 && err) atomicAdd(err, 1);
-  }
+  const bool ok = __syncthreads_and(mbar_wait(bar, 0, limit));
+  if (!ok && threadIdx.x == 0 && stage) atomicAdd(stage, 1ull);
   return ok;
 }
 
@@ -977,8 +974,8 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const
   tb.gbase = M.blob[P.prec];
   bool staged_ok = true;
   if (STAGED) {
-    staged_ok = stage_tables(M.blob[P.prec], P.tab_bytes, smem, &tma_bar, C.error);
-    tb.base = smem;
+    staged_ok = stage_tables(M.blob[P.prec], P.tab_bytes, smem, &tma_bar, C.stage, P.stage_wait);
+    tb.base = staged_ok ? smem : M.blob[P.prec];
   } else {
     tb.base = M.blob[P.prec];
   }
@@ -999,7 +996,7 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const
       for (int64_t gi = (int64_t)blockIdx.x * gpb + gl;;) {
         if (C.queue) {
           grp.sync();
-          if (grp.w == 0 && lane == 0) grp_next[gl] = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(C.queue), 1ull);
+          if (grp.w == 0 && lane == 0) grp_next[gl] = (long long)atomicAdd(C.queue, 1ull);
           grp.sync();
           gi = grp_next[gl];
           if (C.order && gi * G < C.n_cells) gi = __ldg(C.order + gi);   // groups most expensive first
@@ -1015,7 +1012,7 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const
   } else if (C.queue) {
     for (;;) {
       long long cell = 0;
-      if (lane == 0) cell = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(C.queue), 1ull);
+      if (lane == 0) cell = (long long)atomicAdd(C.queue, 1ull);
       cell = __shfl_sync(FULL, cell, 0);
       if (cell >= C.n_cells) break;
       if (C.order) cell = __ldg(C.order + cell);
@@ -1025,9 +1022,11 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const
     const int64_t cell = (int64_t)blockIdx.x * P.warps_per_block + warp;
     if (cell < C.n_cells) solve_cell<T, KS, STAGED, REC, COUPLED>(M, C, P, tb, Wd, WL, lane, cell, grp, invS);
   }
-  if (STAGED && !staged_ok) {
-    __syncthreads();
-    mbar_wait(&tma_bar, 0, TMA_WAIT_LIMIT);   // let a late bulk copy land before the block exits
+  // a late bulk copy must land before the block exits (its shared memory is
+  // then handed to another block); one thread waits, bounded, and counts a
+  // wait that ran out in stage[1]
+  if (STAGED && !staged_ok && threadIdx.x == 0) {
+    if (!mbar_wait(&tma_bar, 0, STAGE_WAIT_DEFAULT) && C.stage) atomicAdd(C.stage + 1, 1ull);
   }
 }
 
@@ -1681,13 +1680,20 @@ cudaError_t launch_tan_t(const MechDev &M, const CellsDev &C, const TanDev &A, c
   return cudaGetLastError();
 }
 
-// dL/dtheta_j = sum over cells of the per-cell gradients, in cell order
-__global__ void theta_reduce_kernel(const double *gcell, int64_t n_cells, int R, double *out) {
+// dL/dtheta_j = sum over cells of the per-cell gradients, in cell order (added
+// to out[j] when accumulating over the steps of a checkpointed backward)
+__global__ void theta_reduce_kernel(const double *gcell, int64_t n_cells, int R, double *out, int accumulate) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= R) return;
   double s = 0.0;
   for (int64_t c = 0; c < n_cells; ++c) s += gcell[(int64_t)j * n_cells + c];
-  out[j] = s;
+  out[j] = accumulate ? out[j] + s : s;
+}
+
+__global__ void count_flags_kernel(const int *flag, int64_t n, unsigned long long *acc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned v = __reduce_add_sync(FULL, (i < n && flag[i] != 0) ? 1u : 0u);
+  if ((threadIdx.x & (WARP - 1)) == 0 && v) atomicAdd(acc, (unsigned long long)v);
 }
 
 template <int KS>
@@ -1960,6 +1966,7 @@ cudaError_t launch_solve(const MechDev &M, const CellsDev &C, const LaunchCfg &c
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   P.couple = cfg.couple > 1 ? cfg.couple : 1;
+  P.stage_wait = cfg.stage_wait > 0 ? cfg.stage_wait : (cfg.stage_wait < 0 ? 0 : STAGE_WAIT_DEFAULT);
   if (P.warps_per_block % P.couple) return cudaErrorInvalidValue;
   // blocks needed to give every cell (every group) a warp (group of warps)
   const int64_t units = (C.n_cells + P.couple - 1) / P.couple, per_block = P.warps_per_block / P.couple;
@@ -2004,7 +2011,13 @@ cudaError_t launch_adjoint(const MechDev &M, const CellsDev &C, const AdjDev &A,
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
-  theta_reduce_kernel<<<(M.R + 127) / 128, 128, 0, stream>>>(A.gcell, C.n_cells, M.R, A.dLdtheta);
+  theta_reduce_kernel<<<(M.R + 127) / 128, 128, 0, stream>>>(A.gcell, C.n_cells, M.R, A.dLdtheta, A.accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_flags(const int *flag, int64_t n, unsigned long long *acc, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  count_flags_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(flag, n, acc);
   return cudaGetLastError();
 }
 

@@ -9,13 +9,16 @@
 // start-up and then call this entry point with their own T, P, y and stats
 // buffers; the call allocates nothing.
 //
-// The persistent driver needs one piece of scratch: the device work-queue
-// counter that resident warps pop cell indices from.  Here it lives in the
-// file-scope array below instead of in a chem_cells batch.  Every GPU that
-// loads this library holds the array until the process exits.
+// The persistent driver needs a few words of scratch: the device work-queue
+// counter that resident warps pop cell indices from, and the two staging
+// counters.  Here they live in the file-scope array below instead of in a
+// chem_cells batch.  Every GPU that loads this library holds the array until
+// the process exits.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "internal.h"
@@ -24,22 +27,84 @@ namespace chemgpu {
 namespace {
 
 // Scratch: word 0 is the work-queue counter, word 1 counts blocks whose table
-// staging fell back to plain loads; 256 bytes keep them alone in their line.
+// staging fell back to the global tables, word 2 blocks that exited before a
+// late staging copy was seen to land; 256 bytes keep them alone in their lines.
 constexpr int NOALLOC_SCRATCH_WORDS = 32;
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[NOALLOC_SCRATCH_WORDS];
 
 // Device address of g_noalloc_scratch, looked up once per device.  In host
 // code the symbol name is only a host-side stand-in, so the kernel must be
-// given this address instead.
+// given this address instead.  Threads making their first call on a device
+// at the same time serialise on the mutex; later calls read the atomic.
 constexpr int MAX_DEVICES = 64;
-void *g_scratch_addr[MAX_DEVICES] = {nullptr};
+std::atomic<void *> g_scratch_addr[MAX_DEVICES];
+std::mutex g_scratch_mu;
 
 int fail(int code, const std::string &msg) {
   set_last_error(msg);
   return code;
 }
 
+// The scratch address on the current device (looked up on the first call).
+int scratch_address(int dev, unsigned long long **out) {
+  void *p = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    p = g_scratch_addr[dev].load(std::memory_order_relaxed);
+    if (!p) {
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p)
+        return fail(CHEM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_scratch_addr[dev].store(p, std::memory_order_release);
+    }
+  }
+  *out = static_cast<unsigned long long *>(p);
+  return 0;
+}
+
+int current_device(int *dev) {
+  const cudaError_t e = cudaGetDevice(dev);
+  if (e != cudaSuccess) return fail(CHEM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (*dev < 0 || *dev >= MAX_DEVICES) return fail(CHEM_EINVAL, "device ordinal beyond the supported range");
+  return 0;
+}
+
+// A caller's buffer must be memory of the current device (or managed memory):
+// a kernel given a host pointer would fault.  cudaPointerGetAttributes
+// allocates nothing.
+int check_device_buffer(const void *p, int dev, const char *name) {
+  cudaPointerAttributes a;
+  std::memset(&a, 0, sizeof(a));
+  const cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();   // a failed query also sets the runtime's last error: reset it
+    return fail(CHEM_EINVAL, std::string(name) + " is not a device pointer (" + cudaGetErrorString(e) + ")");
+  }
+  if (a.type == cudaMemoryTypeManaged) return 0;
+  if (a.type != cudaMemoryTypeDevice)
+    return fail(CHEM_EINVAL, std::string(name) + " must be memory of the current device, not host memory");
+  if (a.device != dev)
+    return fail(CHEM_EINVAL, std::string(name) + " is memory of device " + std::to_string(a.device) + ", not of the current device " +
+                                 std::to_string(dev));
+  return 0;
+}
+
 }  // namespace
+
+int noalloc_stage_counts(int64_t *fallbacks, int64_t *unfinished, cudaStream_t stream) {
+  int dev = 0;
+  if (int rc = current_device(&dev)) return rc;
+  unsigned long long *scratch = nullptr;
+  if (int rc = scratch_address(dev, &scratch)) return rc;
+  unsigned long long v[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(v, scratch + 1, sizeof(v), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return fail(CHEM_ECUDA, std::string("staging counters: ") + cudaGetErrorString(e));
+  *fallbacks = (int64_t)v[0];
+  *unfinished = (int64_t)v[1];
+  return 0;
+}
+
 }  // namespace chemgpu
 
 using namespace chemgpu;
@@ -64,18 +129,25 @@ extern "C" int chem_solve_step_noalloc(const chem_mech *mech, int64_t n_cells, c
   if (o.cells_per_block < 0 || o.cells_per_block > MAX_WARPS_PER_BLOCK || o.blocks_per_sm < 0)
     return fail(CHEM_EINVAL, "bad launch shape");
   if (o.couple_cells > 1) return fail(CHEM_EINVAL, "coupled cells are not supported here");
+  if (o.record_adjoint) return fail(CHEM_EINVAL, "record_adjoint is not supported here (the tape is allocated by a batch)");
+  if (o.stage_wait < -1) return fail(CHEM_EINVAL, "stage_wait must be -1, 0 or positive");
 
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(CHEM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= MAX_DEVICES) return fail(CHEM_EINVAL, "device ordinal beyond the supported range");
-  if (!g_scratch_addr[dev]) {
-    // first call on this device: look up the scratch's device address
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return fail(CHEM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_addr[dev] = p;
-  }
+  if (int rc = current_device(&dev)) return rc;
+  if (dev != mech->m.device)
+    return fail(CHEM_EINVAL, "the mechanism belongs to device " + std::to_string(mech->m.device) +
+                                 ", which must be current");
+  if (int rc = check_device_buffer(T, dev, "T")) return rc;
+  if (int rc = check_device_buffer(P, dev, "P")) return rc;
+  if (int rc = check_device_buffer(y, dev, "y")) return rc;
+  if (int rc = check_device_buffer(stats, dev, "stats")) return rc;
+  if (J && mech->m.n_phot > 0)
+    if (int rc = check_device_buffer(J, dev, "J")) return rc;
+  if (theta)
+    if (int rc = check_device_buffer(theta, dev, "theta")) return rc;
+  unsigned long long *scratch = nullptr;
+  if (int rc = scratch_address(dev, &scratch)) return rc;
+
   const int wmax = max_warps_per_block(mech->m.dev, o.lu_precision, CHEM_DRIVER_PERSISTENT);
   if (wmax < 1) return fail(CHEM_EINVAL, "mechanism working set does not fit in shared memory");
   if (o.cells_per_block > wmax) return fail(CHEM_EINVAL, "cells_per_block exceeds the shared-memory limit");
@@ -83,20 +155,20 @@ extern "C" int chem_solve_step_noalloc(const chem_mech *mech, int64_t n_cells, c
   if (o.cells_per_block < 1) return fail(CHEM_EINVAL, "no launch shape fits on this device");
 
   cudaStream_t s = (cudaStream_t)stream;
-  // the counter must start at zero for every call
-  e = cudaMemsetAsync(g_scratch_addr[dev], 0, sizeof(unsigned long long), s);
+  // the queue counter and the staging counters start at zero for every call
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 3 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return fail(CHEM_ECUDA, std::string("scratch reset: ") + cudaGetErrorString(e));
 
   CellsDev cd{};
   cd.n_cells = n_cells;
   cd.T = T;
   cd.P = P;
-  cd.J = J;
+  cd.J = mech->m.n_phot > 0 ? J : nullptr;
   cd.theta = theta;
   cd.y = y;
   cd.stats = stats;
-  cd.queue = reinterpret_cast<int *>(g_scratch_addr[dev]);
-  cd.error = reinterpret_cast<int *>(reinterpret_cast<unsigned long long *>(g_scratch_addr[dev]) + 1);
+  cd.queue = scratch;
+  cd.stage = scratch + 1;
   LaunchCfg cfg{};
   cfg.lu_precision = o.lu_precision;
   cfg.driver = CHEM_DRIVER_PERSISTENT;
@@ -107,6 +179,7 @@ extern "C" int chem_solve_step_noalloc(const chem_mech *mech, int64_t n_cells, c
   cfg.dt = dt;
   cfg.max_order = o.max_order;
   cfg.max_steps = o.max_steps;
+  cfg.stage_wait = o.stage_wait;
   e = launch_solve(mech->m.dev, cd, cfg, s);
   if (e != cudaSuccess) return fail(CHEM_ECUDA, std::string("solve kernel launch: ") + cudaGetErrorString(e));
   return 0;

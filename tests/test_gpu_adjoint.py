@@ -105,6 +105,57 @@ def test_gpu_adjoint_matches_finite_differences(oracle_lib, cg):
         assert abs(fd - np.sum(gy0 * u)) <= 1e-5 * np.sum(np.abs(gy0 * u))
 
 
+def test_gpu_adjoint_per_component_fd(oracle_lib, cg):
+    # component by component: central differences (step 1e-6) of the oracle's
+    # replay of the GPU tapes, the iteration matrices held at the recorded run's,
+    # against the GPU gradient to 1e-5 relative, on 20 log rate constants (the 12
+    # with the largest |dL/dtheta_j| and 8 more drawn at random above 1e-3 of the
+    # largest) and, per cell, on the 20 initial concentrations through which L
+    # moves most (largest |dL/dy0_i y0_i|; the step is 1e-6 y0_i).  The floor:
+    # the replay's own rounding (about 1e-14 of L) divided by the step puts the
+    # difference quotient's error near 5e-9 of the largest component, so 1e-5
+    # relative is checkable from 1e-3 of the largest component up (measured on
+    # the oracle's own tapes: 5e-6 at 1.7e-3, 3e-5 at 1.5e-4).
+    wl = synth.workload_adjoint(8)
+    n_cells, n_steps = 3, 4
+    m, c, cells, w, gth, gy0 = _run(cg, wl, n_cells, n_steps)
+    eps = 1e-6
+    tapes = [_tape_for(oracle_lib, *c.get_tape(k)) for k in range(n_cells)]
+    kts = [oracle_lib.rate_constants(wl.mech, cells.T[k], cells.P[k]) for k in range(n_cells)]
+
+    def cell_loss(k, theta=None, y0=None):
+        kt = kts[k] if theta is None else oracle_lib.rate_constants(wl.mech, cells.T[k], cells.P[k], theta=theta)
+        y0 = cells.y[:, k] if y0 is None else y0
+        return w[:, k] @ oracle_lib.replay(wl.mech, kt, y0, tapes[k], kt_M=kts[k])
+
+    R = wl.mech.n_reactions
+    rng = np.random.default_rng(5)
+    order = np.argsort(-np.abs(gth))
+    above = np.nonzero(np.abs(gth) >= 1e-3 * np.abs(gth).max())[0]
+    pick = np.unique(np.concatenate([order[:12], rng.choice(np.setdiff1d(above, order[:12]), 8, replace=False)]))
+    worst = 0.0
+    for j in pick:
+        e = np.zeros(R)
+        e[j] = eps
+        fd = sum(cell_loss(k, e) - cell_loss(k, -e) for k in range(n_cells)) / (2 * eps)
+        err = abs(fd - gth[j]) / abs(gth[j])
+        worst = max(worst, err)
+        assert err <= 1e-5, (int(j), fd, gth[j], err)
+    for k in range(n_cells):
+        y0 = cells.y[:, k]
+        for i in np.argsort(-np.abs(gy0[:, k] * y0))[:20]:
+            h = eps * y0[i]
+            yp, ym = y0.copy(), y0.copy()
+            yp[i] += h
+            ym[i] -= h
+            fd = (cell_loss(k, y0=yp) - cell_loss(k, y0=ym)) / (2 * h)
+            err = abs(fd - gy0[i, k]) / abs(gy0[i, k])
+            worst = max(worst, err)
+            assert err <= 1e-5, (k, int(i), fd, gy0[i, k], err)
+    print(f"per-component central differences, {pick.size} theta_j and {20 * n_cells} y0 entries: "
+          f"max rel err {worst:.2e}")
+
+
 def test_autograd_function_matches_sensitivity(cg):
     wl = synth.workload_adjoint(16)
     dev = torch.device("cuda")
@@ -203,3 +254,27 @@ def test_sensitivity_requires_recording(cg):
     c.solve_step(wl.dt)
     with pytest.raises(cg.ChemError):
         c.sensitivity(np.ones((wl.mech.n_species, 4)))
+
+
+def test_sensitivity_checkpointed_host_arrays(cg):
+    # the library's checkpointed backward called directly with host arrays: the
+    # kept states of a 3-step forward, every step re-solved from its state, the
+    # adjoint chained through them, against one tape over all three steps
+    wl = synth.workload_adjoint(24)
+    m = cg.Mechanism(wl.mech)
+    cells = synth.subset(wl.cells, np.arange(24))
+    w = synth.loss_weights(wl.mech.n_species, 24)
+    c = cg.Cells(m, 24, rtol=wl.rtol, atol=wl.atol, record_adjoint=True, driver="persistent")
+    c.set_state(cells.T, cells.P, cells.y)
+    states = [cells.y.copy()]
+    for _ in range(3):
+        c.solve_step(wl.dt)
+        states.append(c.get_state())
+    g_full, l_full, n_bad = c.sensitivity(w)
+    assert n_bad == 0
+    g_ck, l_ck, n_bad = c.sensitivity_checkpointed(np.stack(states[:-1]), wl.dt, w)
+    assert n_bad == 0
+    np.testing.assert_allclose(g_ck, g_full, rtol=1e-11, atol=1e-14 * np.abs(g_full).max())
+    np.testing.assert_allclose(l_ck, l_full, rtol=1e-11, atol=1e-14 * np.abs(l_full).max())
+    # the batch holds the re-solved first step afterwards
+    assert np.array_equal(c.get_state(), states[1])

@@ -1,13 +1,16 @@
-"""Full-size workloads on the GPU, checked on sampled cells against the oracle.
+"""Full-size workloads on the GPU, every cell checked against the oracle.
 
 Each test runs a whole batch at its benchmark size and launch configuration
 (10,000 cells, persistent FP64; 50,000 cells with per-cell photolysis over six
 graph-captured steps with an autotuned launch shape; 50,000 cells with the
-FP32 LU; 2,048 cells through the discrete adjoint) and compares a sample of
-cells, which the oracle computes one by one, with the parity rules of
-parity_util.  Properties that hold at any size (every cell solved; graph and
-single steps identical; launch shape without effect on results) are checked
-on the whole batch.
+FP32 LU; 2,048 cells through the discrete adjoint) and compares every cell
+with the oracle, which runs on all host cores (oracle.pool), by the parity
+rules of parity_util.  The counts of flipped and rounding-limited cells are
+part of every assertion message and printed.  A batch of a million cells is
+checked on a sample (the oracle would need minutes of every core for it).
+Properties that hold at any size (every cell solved; graph and single steps
+identical; launch shape without effect on results) are checked on the whole
+batch.
 """
 import numpy as np
 import pytest
@@ -15,9 +18,13 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import pool  # noqa: E402
 from paper_2501_00011_gb300 import synth  # noqa: E402
 
 from parity_util import FLOOR, compare, oracle_steps, sample_cells  # noqa: E402
+
+# Flipped plus rounding-limited cells allowed at full size.
+MAX_ODD_FRAC = 0.03
 
 
 @pytest.fixture(scope="module")
@@ -44,17 +51,15 @@ def _batch(cg, mech, wl, **opts):
     return c
 
 
-def test_tropo_10k_persistent(oracle_lib, cg, tropo):
+def test_tropo_10k_persistent_all_cells(oracle_lib, cg, tropo):
     wl = synth.workload_tropo(10_000)
     c = _batch(cg, tropo, wl, driver="persistent")
     c.solve_step(wl.dt)
     y, st = c.get_state(), c.get_stats()
     assert np.all(st["status"] == 0)
-    idx = sample_cells(wl.cells.n_cells, 64, seed=1)
-    sub = synth.subset(wl.cells, idx)
-    yo, so = oracle_steps(oracle_lib, wl, sub, 1)
-    err, flips, odd = compare(y[:, idx], st[idx], yo, so, oracle_lib, wl, sub)
-    print(f"10k persistent FP64, {idx.size} sampled cells: max rel err {err:.2e}, flips {flips}, rounding-limited {odd}")
+    yo, so = oracle_steps(oracle_lib, wl, wl.cells, 1)
+    rep = compare(y, st, yo, so, oracle_lib, wl, wl.cells, max_odd_frac=MAX_ODD_FRAC, label="10k persistent FP64")
+    print("10k persistent FP64, all cells:", rep.summary())
 
 
 def test_one_million_cells(oracle_lib, cg, tropo):
@@ -65,14 +70,14 @@ def test_one_million_cells(oracle_lib, cg, tropo):
     c.solve_step(wl.dt)
     y, st = c.get_state(), c.get_stats()
     assert np.all(st["status"] == 0) and np.all(np.isfinite(y))
-    idx = sample_cells(wl.cells.n_cells, 12, seed=7)
+    idx = sample_cells(wl.cells.n_cells, 64, seed=7)
     sub = synth.subset(wl.cells, idx)
     yo, so = oracle_steps(oracle_lib, wl, sub, 1)
-    compare(y[:, idx], st[idx], yo, so, oracle_lib, wl, sub)
+    compare(y[:, idx], st[idx], yo, so, oracle_lib, wl, sub, label="1M sampled")
     c.close()
 
 
-def test_batching_50k_graph_autotuned(oracle_lib, cg, tropo):
+def test_batching_50k_graph_autotuned_all_cells(oracle_lib, cg, tropo):
     wl = synth.workload_batching(50_000)
     c = _batch(cg, tropo, wl, driver="persistent")
     w, b = c.autotune(wl.dt)
@@ -82,13 +87,11 @@ def test_batching_50k_graph_autotuned(oracle_lib, cg, tropo):
     assert np.all(st["status"] == 0)
     # uneven work: night cells and warm/cold cells take very different step counts
     assert st["steps"].max() >= 2 * max(1, np.percentile(st["steps"], 5))
-    idx = sample_cells(wl.cells.n_cells, 40, seed=2)
-    sub = synth.subset(wl.cells, idx)
-    yo, so = oracle_steps(oracle_lib, wl, sub, wl.n_steps)
-    err, flips, odd = compare(y[:, idx], st[idx], yo, so, oracle_lib, wl, sub, n_steps=wl.n_steps)
-    print(f"50k batching, 6 graph steps, shape w={w} b={b}: max rel err {err:.2e}, flips {flips}, "
-          f"rounding-limited {odd}; steps per cell (last step) min/median/max "
-          f"{st['steps'].min()}/{int(np.median(st['steps']))}/{st['steps'].max()}")
+    yo, so = oracle_steps(oracle_lib, wl, wl.cells, wl.n_steps)
+    rep = compare(y, st, yo, so, oracle_lib, wl, wl.cells, n_steps=wl.n_steps, max_odd_frac=MAX_ODD_FRAC,
+                  label="50k batching, 6 graph steps")
+    print(f"50k batching, 6 graph steps, shape w={w} b={b}, all cells: {rep.summary()}; steps per cell "
+          f"(last step) min/median/max {st['steps'].min()}/{int(np.median(st['steps']))}/{st['steps'].max()}")
 
 
 @pytest.mark.parametrize("driver", ["plain", "persistent"])
@@ -130,10 +133,39 @@ def test_autotune_keeps_state_and_results(cg, tropo):
     assert np.array_equal(p.get_state(), ref.get_state())
 
 
-def test_fp32_lu_50k(oracle_lib, cg, tropo):
-    # accuracy bound of the FP32-LU form (see test_gpu_parity): within 50
-    # tolerance units of the FP64 oracle and as accurate as it against a tight
-    # reference, on a sample of the full 50,000-cell batch
+def test_staging_fallback_counter(cg, tropo):
+    # stage_wait = -1: every block skips its bounded wait for the staged tables and
+    # reads them from global memory (the same bytes): identical results, one
+    # fallback per block (5 cells per block, one block per SM), counted per call
+    # over all its steps; no copy is left unfinished
+    wl = synth.workload_batching(3001)
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = min(n_sm, -(-wl.cells.n_cells // 5))
+    a = _batch(cg, tropo, wl, driver="persistent", cells_per_block=5, blocks_per_sm=1)
+    a.solve_step(wl.dt)
+    assert a.staging_fallbacks() == (0, 0)
+    b = _batch(cg, tropo, wl, driver="persistent", cells_per_block=5, blocks_per_sm=1, stage_wait=-1)
+    b.solve_step(wl.dt)
+    assert b.staging_fallbacks() == (blocks, 0)
+    assert np.array_equal(a.get_state(), b.get_state()) and np.array_equal(a.get_stats(), b.get_stats())
+    b.set_state(wl.cells.T, wl.cells.P, wl.cells.y)
+    b.solve_steps(wl.dt, 3)
+    assert b.staging_fallbacks() == (3 * blocks, 0)
+    a.set_state(wl.cells.T, wl.cells.P, wl.cells.y)
+    a.solve_steps(wl.dt, 3)
+    assert a.staging_fallbacks() == (0, 0)
+    assert np.array_equal(a.get_state(), b.get_state())
+
+
+def test_fp32_lu_50k_all_cells(oracle_lib, cg, tropo):
+    # The FP32-LU form's stated bound: no less accurate than the FP64 oracle
+    # against a tight reference (the oracle at rtol 1e-10), max over cells within
+    # 1.25x and median within 1.1x of the FP64 oracle's error, on the 100 cells
+    # where the FP32 form differs most from the FP64 oracle and on 100 random
+    # cells.  The per-species relative-error distribution against the FP64
+    # oracle over all 50,000 cells is printed beside it (a 1e-6 bar cannot hold:
+    # the FP32 factor changes the corrector iterates, so borderline decisions
+    # flip and step sequences differ).
     wl = synth.workload_precision(50_000)
     c32 = _batch(cg, tropo, wl, driver="persistent", lu_precision=32)
     c32.solve_step(wl.dt)
@@ -142,57 +174,57 @@ def test_fp32_lu_50k(oracle_lib, cg, tropo):
     c64.solve_step(wl.dt)
     st64 = c64.get_stats()
     assert np.all(st["status"] == 0) and np.all(st64["status"] == 0)
-    idx = sample_cells(wl.cells.n_cells, 40, seed=3)
-    sub = synth.subset(wl.cells, idx)
-    yo, so = oracle_lib.solve_cells(wl.mech, sub, wl.dt, wl.rtol, wl.atol)
-    yt, stt = oracle_lib.solve_cells(wl.mech, sub, wl.dt, 1e-10, 1e-18)
-    assert np.all(stt["status"] == 0)
-    ys = y[:, idx]
+    yo, so = pool.solve(wl.mech, wl.cells, wl.dt, wl.rtol, wl.atol)
+    assert np.all(so["status"] == 0)
     tol = wl.rtol * np.abs(yo) + wl.atol
-    assert (np.abs(ys - yo) / tol).max() <= 50.0
-    acc32 = (np.abs(ys - yt) / (wl.rtol * np.abs(yt) + wl.atol)).max(axis=0)
-    acc64 = (np.abs(yo - yt) / (wl.rtol * np.abs(yt) + wl.atol)).max(axis=0)
-    assert acc32.max() <= 1.25 * acc64.max() and np.median(acc32) <= 1.1 * np.median(acc64)
-    # the cells where the two forms differ most: there too FP32 is as accurate as FP64
-    y64 = c64.get_state()
-    diff = (np.abs(y - y64) / (wl.rtol * np.abs(y64) + wl.atol)).max(axis=0)
-    worst = np.argsort(-diff)[:10]
-    ywt, swt = oracle_lib.solve_cells(wl.mech, synth.subset(wl.cells, worst), wl.dt, 1e-10, 1e-18)
-    assert np.all(swt["status"] == 0)
-    unit = wl.rtol * np.abs(ywt) + wl.atol
-    w32 = (np.abs(y[:, worst] - ywt) / unit).max(axis=0)
-    w64 = (np.abs(y64[:, worst] - ywt) / unit).max(axis=0)
-    assert w32.max() <= 1.25 * w64.max() and np.median(w32) <= 1.1 * np.median(w64), (w32, w64)
-    assert diff.max() <= 50.0
-    rel = np.where(np.abs(yo) > FLOOR, np.abs(ys - yo) / np.maximum(np.abs(yo), 1e-300), 0.0).max(axis=1)
-    print(f"fp32 LU 50k: per-species max rel err vs FP64 oracle on {idx.size} cells: median {np.median(rel):.2e}, "
-          f"max {rel.max():.2e}; Newton iterations {st['newton_iters'].sum() / st64['newton_iters'].sum():.3f}x "
-          f"the FP64 GPU path's over all cells")
+    units = (np.abs(y - yo) / tol).max(axis=0)
+    rng = np.random.default_rng(3)
+    idx = np.unique(np.concatenate([np.argsort(-units)[:100], rng.integers(0, wl.cells.n_cells, 100)]))
+    sub = synth.subset(wl.cells, idx)
+    yt, stt = pool.solve(wl.mech, sub, wl.dt, 1e-10, 1e-18, max_steps=200_000)
+    assert np.all(stt["status"] == 0)
+    unit_t = wl.rtol * np.abs(yt) + wl.atol
+    acc32 = (np.abs(y[:, idx] - yt) / unit_t).max(axis=0)
+    acc64 = (np.abs(yo[:, idx] - yt) / unit_t).max(axis=0)
+    msg = (f"FP32 LU vs tight reference on {idx.size} cells: max {acc32.max():.2f} (FP64 oracle {acc64.max():.2f}), "
+           f"median {np.median(acc32):.2f} (FP64 oracle {np.median(acc64):.2f}) tolerance units")
+    assert acc32.max() <= 1.25 * acc64.max() and np.median(acc32) <= 1.1 * np.median(acc64), msg
+    mask = np.abs(yo) > FLOOR
+    rel = np.where(mask, np.abs(y - yo) / np.where(mask, np.abs(yo), 1.0), 0.0)
+    per_species = rel.max(axis=1)
+    per_cell = rel.max(axis=0)
+    print(f"fp32 LU 50k, all cells against the FP64 oracle: per-species max rel err median "
+          f"{np.median(per_species):.2e}, max {per_species.max():.2e}; per-cell max rel err percentiles "
+          f"50/90/99/99.9/100: {np.percentile(per_cell, [50, 90, 99, 99.9, 100])}; tolerance units max "
+          f"{units.max():.1f}, cells above 10 units {int(np.sum(units > 10))}; {msg}; Newton iterations "
+          f"{st['newton_iters'].sum() / st64['newton_iters'].sum():.4f}x the FP64 GPU path's")
 
 
-def test_adjoint_2048_sampled(oracle_lib, cg, tropo):
-    # the whole 2,048-cell batch runs forward (4 steps) and backward; the loss
-    # weights are nonzero on sampled cells only, so dL/dtheta is their sum and
-    # the oracle adjoint of each sampled cell's GPU tape gives it exactly
+def test_adjoint_2048_all_cells(oracle_lib, cg, tropo):
+    # the whole 2,048-cell batch forward (4 steps, tape recorded) and backward with
+    # the workload's loss weights on every cell; the oracle adjoint of every
+    # cell's GPU tape gives dL/dy0 per cell and dL/dtheta as their sum
     wl = synth.workload_adjoint(2048)
     c = _batch(cg, tropo, wl, driver="persistent", record_adjoint=True)
     for _ in range(wl.n_steps):
         c.solve_step(wl.dt)
-    idx = sample_cells(wl.cells.n_cells, 8, seed=4)
-    w = np.zeros((wl.mech.n_species, wl.cells.n_cells))
-    w[:, idx] = synth.loss_weights(wl.mech.n_species, wl.cells.n_cells)[:, idx]
+    w = synth.loss_weights(wl.mech.n_species, wl.cells.n_cells)
     gth, gy0, n_bad = c.sensitivity(w)
     assert n_bad == 0
-    assert np.all(gy0[:, np.setdiff1d(np.arange(wl.cells.n_cells), idx)] == 0.0)
-    g_sum = np.zeros(wl.mech.n_reactions)
-    for k in idx:
+    tapes = []
+    for k in range(wl.cells.n_cells):
         kind, q, val, rows = c.get_tape(k)
         has_row = (kind == 0) | (kind == 4) | (kind == 5)
         yrow = np.zeros((kind.size, wl.mech.n_species))
         yrow[has_row] = rows
-        tape = oracle_lib.Tape(kind, q, val, yrow)
-        kt = oracle_lib.rate_constants(wl.mech, wl.cells.T[k], wl.cells.P[k])
-        ly0, g = oracle_lib.adjoint(wl.mech, kt, wl.cells.y[:, k], tape, w[:, k])
-        g_sum += g
-        assert np.all(np.abs(gy0[:, k] - ly0) <= 1e-8 * np.abs(ly0) + 1e-12 * np.abs(ly0).max()), k
+        tapes.append(oracle_lib.Tape(kind, q, val, yrow))
+    ly0, g = pool.adjoint(wl.mech, wl.cells, tapes, w)
+    scale = np.abs(ly0).max(axis=0)
+    bad = np.nonzero(np.any(np.abs(gy0 - ly0) > 1e-8 * np.abs(ly0) + 1e-12 * scale, axis=0))[0]
+    rel = np.abs(gy0 - ly0) / np.maximum(np.abs(ly0), 1e-300)
+    assert bad.size == 0, f"dL/dy0 differs from the oracle adjoint beyond 1e-8 on {bad.size} of 2048 cells: {bad[:8]}"
+    g_sum = g.sum(axis=0)
     assert np.all(np.abs(gth - g_sum) <= 1e-8 * np.abs(g_sum) + 1e-12 * np.abs(g_sum).max())
+    big = np.abs(ly0) > 1e-6 * scale
+    print(f"adjoint 2048 cells, all cells: dL/dy0 max rel diff {rel[big].max():.2e}, dL/dtheta max rel diff "
+          f"{(np.abs(gth - g_sum) / np.maximum(np.abs(g_sum), 1e-300)).max():.2e}")

@@ -38,6 +38,11 @@ def _host_step(y, T, c0, c1, step):
     T[c0:c1] += 1.5
 
 
+def _host_step_cells(y, T, step):
+    """The same host work on every column of a batch (the oracle's runs)."""
+    _host_step(y, T, 0, y.shape[1], step)
+
+
 def _reference(cg, mech, wl, cells, n_steps, driver, J=None, prec=64):
     c = cg.Cells(mech, cells.n_cells, rtol=wl.rtol, atol=wl.atol, driver=driver, lu_precision=prec)
     y, T, P = cells.y.copy(), cells.T.copy(), cells.P.copy()
@@ -81,6 +86,32 @@ def test_pipeline_equals_one_batch(cg, tropo, n, K, driver, prec):
         assert all(b == a2 for (_, b), (a2, _) in zip(chunks, chunks[1:]))
         sizes = [b - a for a, b in chunks]
         assert max(sizes) - min(sizes) <= 1
+
+
+@pytest.mark.parametrize("K,driver", [(4, "persistent"), (3, "plain")])
+def test_pipeline_matches_oracle(oracle_lib, cg, tropo, K, driver):
+    # the pipeline with the host's work between chemistry steps, cell by cell against
+    # the oracle applying the same work between its own solves: solve, host work,
+    # solve, host work, solve (per-cell photolysis), by the parity rules
+    from parity_util import compare
+    wl = synth.workload_batching(301)
+    n_steps = 3
+    y = cg.pinned_empty(wl.cells.y.shape)
+    y[:] = wl.cells.y
+    T, P, J = wl.cells.T.copy(), wl.cells.P.copy(), wl.cells.J.copy()
+
+    def fn(c0, c1, step):
+        if step + 1 < n_steps:
+            _host_step(y, T, c0, c1, step)
+
+    p = cg.Pipeline(tropo, wl.cells.n_cells, K, rtol=wl.rtol, atol=wl.atol, driver=driver)
+    st = p.run(T, P, y, wl.dt, n_steps, fn=fn, J=J, stats=True)
+    p.close()
+    from parity_util import oracle_steps
+    yo, so = oracle_steps(oracle_lib, wl, wl.cells, n_steps, between=_host_step_cells)
+    rep = compare(np.array(y), st, yo, so, oracle_lib, wl, wl.cells, n_steps=n_steps, between=_host_step_cells,
+                  label=f"pipeline {K} chunks {driver}")
+    print(f"pipeline, {K} chunks, {driver}, host work between 3 steps:", rep.summary())
 
 
 def test_pipeline_per_cell_photolysis_and_pageable_memory(cg, tropo):
