@@ -7,6 +7,14 @@ whole hot path: the state is reset from a device-resident copy of y0 and
 chem_solve_step integrates every cell (rates, f, J, sparse LU/solves, Newton,
 error and step control, all in one kernel).
 
+The persistent driver's queue hands out the most expensive cells first, keyed
+by each cell's cost in the batch's previous solve, or in a batch's first solve
+by the sum of the cell's rate constants.  Every timed headline step is a fresh
+batch's first solve, so the queue order uses no cost history; beside it are
+solves keyed by the costs of a different state (the same cells one 600 s step
+later, as a model's previous step would give), the best case (keyed by a
+previous solve of y0 itself) and a model-like chain of steps.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Prints one JSON line (rank 0).  Multi-GPU runs are weak scaling: rank r solves
@@ -33,10 +41,12 @@ METRIC = "cells solved/s per 600 s chem step (72 sp/186 rx), chosen vs plain FP6
 UNIT = "cells/s"
 N_CELLS = 10_000
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
-FP64_PEAK_NOMINAL = 152 * 2070e6 * 2 * 2   # SMs x clock x 2 FP64 FMA lanes/SM/clk x 2 flops
+FP64_PEAK_DERIVED = 152 * 2070e6 * 2 * 2   # SMs x clock x 2 FP64 FMA lanes/SM/clk x 2 flops
 PROFILE = os.path.join(ROOT, "profiles", "solve_kernel_fp64_persistent_tropo10k.md")
 KERNEL_SOURCES = ("paper_2501_00011_gb300/csrc/kernels.cu", "paper_2501_00011_gb300/csrc/internal.h",
                   "paper_2501_00011_gb300/csrc/mechanism.cpp", "paper_2501_00011_gb300/csrc/device_common.cuh")
+EXTRAS = ("batching_50k", "precision_50k", "derivative_designs", "coupled_cells", "pressure_dependent",
+          "host_overlap", "adjoint_2k", "cpu_all_cores")
 
 
 def _kernel_sha():
@@ -48,19 +58,18 @@ def _kernel_sha():
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic():
-    """DRAM bytes per launch of the headline kernel from the committed ncu
-    summary, or None when the summary is missing or the kernel sources have
-    changed since it was taken."""
+def _profiled(path, key="dram_bytes_per_launch"):
+    """A number from a committed ncu summary, or None when the summary is
+    missing or the kernel sources have changed since it was taken."""
     try:
         vals = {}
-        for line in open(PROFILE):
-            if ":" in line and line.split(":", 1)[0].strip() in ("dram_bytes_per_launch", "source_sha256"):
+        for line in open(path):
+            if ":" in line and line.split(":", 1)[0].strip() in (key, "source_sha256"):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
         if vals.get("source_sha256") != _kernel_sha():
             return None
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[key])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -140,8 +149,8 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _oracle_sample(wl, n_sample: int):
-    """Time the CPU oracle (single thread, as it stands) on the first n_sample cells."""
+def _oracle_single(wl, n_sample: int):
+    """The CPU oracle, single thread, as it stands, on the first n_sample cells."""
     import oracle
     from paper_2501_00011_gb300 import synth
     oracle.build()
@@ -153,30 +162,55 @@ def _oracle_sample(wl, n_sample: int):
 
 
 def run_reference(args):
+    """The reference arm of this build: the CPU oracle, unchanged, on every host
+    core (one worker process per core over cell shards), each step the whole
+    10,000-cell workload."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
+    import oracle
+    from oracle import pool
+    oracle.build()
     wl = _workload()
-    n_sample = args.ref_sample
-    for _ in range(args.warmup):
-        _oracle_sample(wl, max(1, n_sample // 10))
+    cells = wl.cells
+    if args.ref_sample and args.ref_sample < cells.n_cells:
+        from paper_2501_00011_gb300 import synth
+        cells = synth.subset(cells, range(args.ref_sample))
     times = []
-    for _ in range(args.steps):
-        rate, el = _oracle_sample(wl, n_sample)
-        times.append(el)
+    with pool.Workers() as ex:
+        for k in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            pool.solve(wl.mech, cells, wl.dt, wl.rtol, wl.atol, executor=ex)
+            if k >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        cores = ex.n
     tot = sum(times)
-    value = n_sample * args.steps / tot
+    value = cells.n_cells * args.steps / tot
+    sample = f"all {cells.n_cells} cells per step, {cores} worker processes (one per host core) over cell shards"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"tropo_72sp_186rx: one 600 s step, {N_CELLS} cells (sample of {n_sample} per step)",
-                       "rtol": wl.rtol, "atol": wl.atol, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"first {n_sample} of the {N_CELLS} cells per step, single thread"},
+            "config": {"workload": f"tropo_72sp_186rx: one 600 s step, {N_CELLS} cells", "rtol": wl.rtol,
+                       "atol": wl.atol, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _walk_counts(kind, q):
+    """Per-cell event counts of a recorded tape that set the adjoint's and the
+    tangent's work: corrector iterations, iteration matrices the backward walk
+    re-forms (one per REFACTOR governing an accepted step), all REFACTORs (the
+    tangent forms each), accepted steps with their orders, rescales with theirs."""
+    import numpy as np
+    idx = np.arange(kind.size)
+    last_ref = np.maximum.accumulate(np.where(kind == 4, idx, -1))
+    steps = kind == 2
+    return {"iter": int(np.sum(kind == 5)), "ranges": int(np.unique(last_ref[steps]).size),
+            "refactors": int(np.sum(kind == 4)), "inits": int(np.sum(kind == 0)),
+            "step_q": q[steps].astype(float), "rescale_q": q[kind == 1].astype(float)}
 
 
 def run_gpu(args):
@@ -207,12 +241,17 @@ def run_gpu(args):
     P_d = torch.from_numpy(wl.cells.P).to(dev)
     y0_d = torch.from_numpy(wl.cells.y).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    extras_sel = set() if (args.no_extras or args.extras == "none") else (
+        set(EXTRAS) if args.extras == "all" else set(args.extras.split(",")))
 
     def barrier():
         torch.cuda.synchronize(dev)
         if ws > 1:
             import torch.distributed as dist
             dist.barrier()
+
+    def event():
+        return torch.cuda.Event(enable_timing=True)
 
     def column_mixing(y, c0, c1, levels=50, a=0.2):
         """Host stand-in for the model's work between chemistry steps: one implicit
@@ -233,7 +272,20 @@ def run_gpu(args):
             x[:, :, i] -= cp[i] * x[:, :, i + 1]
         y[:, c0:c1] = x.reshape(y.shape[0], -1)
 
-    def time_host_overlap(chemgpu, mech, barrier):
+    def flops(st):
+        """Algorithmic FP64 flops of a solve from its per-cell counters:
+        n_f F_f + n_J (F_J + F_LU) + n_sol F_sol (the mechanism's exact operation
+        counts) + the integrator's vector work on S species: per accepted step at
+        order q, (4q + 9) S (predictor q S, history term (2q + 1) S, weights 3 S,
+        error norm 3 S, history update (q + 2) S), per Newton iteration 8 S
+        (residual 3 S, norm 3 S, correction and iterate 2 S)."""
+        Sv = float(info["n_species"])
+        return float(np.sum(st["f_evals"]) * info["flops_f"] + np.sum(st["jac_evals"]) * (info["flops_jac"] + info["flops_lu"])
+                     + np.sum(st["solves"]) * info["flops_solve"]
+                     + Sv * (4.0 * np.sum(st["order_sum"]) + 9.0 * np.sum(st["steps"]))
+                     + 8.0 * Sv * np.sum(st["newton_iters"]))
+
+    def time_host_overlap():
         """The 10,000 cells with their state in (pinned) host memory and host work between
         chemistry steps, through chem_pipeline_run with 1, 2, 4 and 8 chunks; wall clock."""
         n_steps = 2
@@ -250,8 +302,6 @@ def run_gpu(args):
             T, P = wl.cells.T.copy(), wl.cells.P.copy()
             res = {}
             for with_host in (False, True):
-                # chemistry only: the headline's single step from the initial state, end to end;
-                # with host work: two model steps, each chunk's host work right after its solve
                 fn = (lambda c0, c1, s: column_mixing(host_y, c0, c1)) if with_host else None
                 ns = n_steps if with_host else 1
                 ts = []
@@ -274,164 +324,13 @@ def run_gpu(args):
                     "chemistry_only is one step from the initial state (the headline's work, end to end); "
                     "with_host_work is two steps, the second from the mixed state"}
 
-    def time_extras(chemgpu, mech, dev, stream, flush, barrier):
-        """The batching form (50,000 cells, six 600 s steps as one captured graph,
-        autotuned launch shape) and the adjoint form (2,048 cells, four steps
-        forward with the tape, then the sensitivity)."""
-        from paper_2501_00011_gb300 import synth
-        out = {}
-        wl3 = synth.workload_batching(args.batch_cells)
-        n3 = wl3.cells.n_cells
-        c3 = chemgpu.Cells(mech, n3, rtol=wl3.rtol, atol=wl3.atol, driver="persistent")
-        T3, P3 = torch.from_numpy(wl3.cells.T).to(dev), torch.from_numpy(wl3.cells.P).to(dev)
-        y3, J3 = torch.from_numpy(wl3.cells.y).to(dev), torch.from_numpy(wl3.cells.J).to(dev)
-        c3.set_state(T3, P3, y3, stream=stream)
-        c3.set_photolysis(J3, stream=stream)
-        w, b = c3.autotune(wl3.dt)
-        c3.solve_steps(wl3.dt, wl3.n_steps, stream=stream)          # warm-up (captures the graph)
-        barrier()
-        ms = []
-        for k in range(2):
-            c3.set_state(T3, P3, y3, stream=stream)
-            flush.fill_(float(k))
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            c3.solve_steps(wl3.dt, wl3.n_steps, stream=stream)
-            e1.record(stream)
-            barrier()
-            ms.append(e0.elapsed_time(e1))
-        st3 = c3.get_stats(stream=stream)
-        c3.close()
-        t3 = min(ms)
-        out["batching_50k"] = {
-            "value": n3 * wl3.n_steps / (t3 / 1e3), "unit": "cells/s (cell-steps per second)",
-            "ms_per_graph": t3, "cells": n3, "steps_per_graph": wl3.n_steps,
-            "form": "persistent work queue, 6 x 600 s steps captured in one CUDA graph, per-cell photolysis, FP64",
-            "autotuned": {"cells_per_block": w, "blocks_per_sm": b},
-            "integrator_steps_last_600s": {"min": int(st3["steps"].min()), "median": float(np.median(st3["steps"])),
-                                           "max": int(st3["steps"].max())},
-            "cells_ok": int(np.sum(st3["status"] == 0))}
-        # the FP32-LU form on its own workload: the batching cells, one step, against the FP64 form
-        wl4 = synth.workload_precision(args.batch_cells)
-        prec = {}
-        for lp in (64, 32):
-            c4 = chemgpu.Cells(mech, n3, rtol=wl4.rtol, atol=wl4.atol, driver="persistent", lu_precision=lp)
-            ts = []
-            for k in range(4):
-                c4.set_state(T3, P3, y3, stream=stream)
-                c4.set_photolysis(J3, stream=stream)
-                flush.fill_(float(k))
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                c4.solve_step(wl4.dt, stream=stream)
-                e1.record(stream)
-                barrier()
-                if k > 0:
-                    ts.append(e0.elapsed_time(e1))
-            prec[lp] = (min(ts), c4.get_state(stream=stream), c4.get_stats(stream=stream))
-            c4.close()
-        y64, y32 = prec[64][1], prec[32][1]
-        tu = (np.abs(y32 - y64) / (wl4.rtol * np.abs(y64) + wl4.atol)).max(axis=1)   # per species, tolerance units
-        out["precision_50k"] = {
-            "value": n3 / (prec[32][0] / 1e3), "unit": "cells/s", "ms": prec[32][0], "fp64_ms": prec[64][0],
-            "cells": n3, "speedup_vs_fp64": prec[64][0] / prec[32][0],
-            "newton_iters_vs_fp64": float(np.sum(prec[32][2]["newton_iters"]) / np.sum(prec[64][2]["newton_iters"])),
-            "per_species_max_diff_vs_fp64_gpu_tol_units": {"median": float(np.median(tu)), "max": float(tu.max())},
-            "cells_ok": int(np.sum(prec[32][2]["status"] == 0)),
-            "form": "the batching cells (per-cell photolysis) for one 600 s step, persistent driver, LU factor/solve "
-                    "in FP32, everything else FP64; best of 3 after one warm-up; differences from the FP64 GPU "
-                    "solve of the same cells in tolerance units rtol*|y| + atol (max over cells, then median and "
-                    "max over species): the FP32 factor changes the corrector iterates, so step sequences differ"}
-        # f(y) alone by three kernel designs on the 10,000-cell state, rate constants precomputed:
-        # this library's gather and the paper's reaction-parallel atomic design (AoS / SoA reaction data)
-        cd = chemgpu.Cells(mech, C, rtol=wl.rtol, atol=wl.atol)
-        cd.set_state(T_d, P_d, y0_d, stream=stream)
-        f_out = torch.empty_like(y0_d)
-        designs = {}
-        names = {chemgpu.DERIV_GATHER: "gather_warp_per_cell", chemgpu.DERIV_ATOMIC_AOS: "atomic_reaction_parallel_aos",
-                 chemgpu.DERIV_ATOMIC_SOA: "atomic_reaction_parallel_soa"}
-        for dsg, nm in names.items():
-            cd.eval_deriv_design(dsg, y0_d, out=f_out, stream=stream)      # first call also forms the rate constants
-            ts = []
-            for k in range(10):
-                flush.fill_(float(k))
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                cd.eval_deriv_design(dsg, y0_d, out=f_out, stream=stream)
-                e1.record(stream)
-                barrier()
-                ts.append(e0.elapsed_time(e1))
-            t = statistics.median(ts)
-            designs[nm] = {"ms": t, "cells_per_s": C / (t / 1e3),
-                           "hbm_gbs": C * (2 * S + wl.mech.n_reactions) * 8 / (t / 1e3) / 1e9}
-        cd.close()
-        g = designs["gather_warp_per_cell"]["ms"]
-        for nm in designs:
-            designs[nm]["vs_gather"] = g / designs[nm]["ms"]
-        out["derivative_designs"] = {
-            "cells": C, "designs": designs,
-            "note": "f(y) only, rate constants precomputed; median of 10 launches with L2 flushed between; "
-                    "hbm_gbs counts y and k~ read and f written once per cell (the atomic designs re-read y "
-                    "per reaction and add through L2)"}
-        # the paper's multi-cell system: groups of G consecutive cells integrated as one system
-        coupled = {}
-        for G in (1, 2, 5, 10):
-            cc = chemgpu.Cells(mech, C, rtol=wl.rtol, atol=wl.atol, driver="persistent", couple_cells=G)
-            ts = []
-            for k in range(3):
-                cc.set_state(T_d, P_d, y0_d, stream=stream)
-                flush.fill_(float(k))
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                cc.solve_step(wl.dt, stream=stream)
-                e1.record(stream)
-                barrier()
-                if k > 0:
-                    ts.append(e0.elapsed_time(e1))
-            stc = cc.get_stats(stream=stream)
-            cc.close()
-            t = min(ts)
-            coupled[f"G{G}"] = {"ms": t, "cells_per_s": C / (t / 1e3), "steps_per_cell": float(np.mean(stc["steps"])),
-                                "newton_iters_per_cell": float(np.mean(stc["newton_iters"])),
-                                "systems": (C + G - 1) // G,
-                                "solver_iterations_total": int(np.sum(stc["newton_iters"][::G])),
-                                "cells_ok": int(np.sum(stc["status"] == 0))}
-        out["coupled_cells"] = {
-            "cells": C, "groups": coupled,
-            "note": "couple_cells = G: each group of G consecutive cells is one ODE system (shared step size, "
-                    "order, Newton iterations, one norm), whole groups per block (10 cells, 8 for G = 4), "
-                    "groups handed out most expensive first by their cost in the previous solve; G1 = independent cells, the headline form. "
-                    "solver_iterations_total counts Newton iterations once per system, the paper's measure of "
-                    "its Multi-cells saving"}
-        # pressure-dependent rate laws (Troe fall-off and the two pressure sums) on the same
-        # 10,000-cell form; pressures 1e3..1.05e5 Pa
-        wlp = synth.workload_pressure(C)
-        mp = chemgpu.Mechanism(wlp.mech)
-        cp = chemgpu.Cells(mp, C, rtol=wlp.rtol, atol=wlp.atol, driver="persistent")
-        Tp, Pp = torch.from_numpy(wlp.cells.T).to(dev), torch.from_numpy(wlp.cells.P).to(dev)
-        yp = torch.from_numpy(wlp.cells.y).to(dev)
-        tsp = []
-        for k in range(4):
-            cp.set_state(Tp, Pp, yp, stream=stream)
-            flush.fill_(float(k))
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            cp.solve_step(wlp.dt, stream=stream)
-            e1.record(stream)
-            barrier()
-            if k > 0:
-                tsp.append(e0.elapsed_time(e1))
-        stp = cp.get_stats(stream=stream)
-        cp.close()
-        out["pressure_dependent"] = {
-            "value": C / (min(tsp) / 1e3), "unit": "cells/s", "ms": min(tsp), "cells": C,
-            "cells_ok": int(np.sum(stp["status"] == 0)),
-            "note": "72/186 mechanism with 12 Troe fall-off, 3 k_a + k_b[M] and 3 k_a + k_c[M]/(1 + k_c[M]/k_b) "
-                    "reactions, P log-uniform 1e3..1.05e5 Pa, T 200..310 K; persistent FP64 form, best of 3"}
-        out["host_overlap"] = time_host_overlap(chemgpu, mech, barrier)
+    def time_adjoint(fp64_peak):
+        """The differentiation form: 2,048 cells, four 600 s steps recorded, the discrete
+        adjoint and the tangent, with the walks' algorithmic FP64 rate."""
         wl5 = synth.workload_adjoint(args.adjoint_cells)
         n5 = wl5.cells.n_cells
-        c5 = chemgpu.Cells(mech, n5, rtol=wl5.rtol, atol=wl5.atol, driver="persistent", record_adjoint=True)
+        c5 = chemgpu.Cells(mech, n5, rtol=wl5.rtol, atol=wl5.atol, driver="persistent", record_adjoint=True,
+                           tape_steps=args.tape_steps)
         T5, P5 = torch.from_numpy(wl5.cells.T).to(dev), torch.from_numpy(wl5.cells.P).to(dev)
         y5 = torch.from_numpy(wl5.cells.y).to(dev)
         w5 = torch.from_numpy(synth.loss_weights(wl5.mech.n_species, n5)).to(dev)
@@ -442,8 +341,8 @@ def run_gpu(args):
         dth5 = torch.from_numpy(rng5.standard_normal(wl5.mech.n_reactions)).to(dev)
         dy5 = torch.zeros_like(y5)
         fwd, bwd, tan = [], [], []
-        for rep in range(3):
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for rep in range(args.adjoint_reps):
+            e = [event() for _ in range(4)]
             flush.fill_(float(rep))
             e[0].record(stream)
             c5.set_state(T5, P5, y5, stream=stream)
@@ -457,85 +356,361 @@ def run_gpu(args):
             _, n_bad_t = c5.tangent(dy05, dth5, dy5, stream=stream)
             e[3].record(stream)
             barrier()
-            if rep > 0:
+            if rep > 0 or args.adjoint_reps == 1:
                 fwd.append(e[0].elapsed_time(e[1]))
                 bwd.append(e[1].elapsed_time(e[2]))
                 tan.append(e[2].elapsed_time(e[3]))
+        # algorithmic work of the walks from the tapes (event counts per cell)
+        Sv = float(info["n_species"])
+        fl_lu = info["flops_jac"] + info["flops_lu"]
+        f_adj = f_tan = 0.0
+        for k in range(n5):
+            kind, q, _, _ = c5.get_tape(k, rows=False)
+            w = _walk_counts(kind, q)
+            vec_steps = Sv * np.sum(4.0 * w["step_q"] + 6.0)
+            vec_rescale = Sv * np.sum(w["rescale_q"] * (w["rescale_q"] + 1.0))
+            f_adj += w["iter"] * info["flops_adj_iter"] + w["ranges"] * fl_lu + vec_steps + vec_rescale
+            f_tan += (w["iter"] * info["flops_tan_iter"] + w["refactors"] * fl_lu + vec_steps + vec_rescale
+                      + w["inits"] * (info["flops_tan_iter"] - info["flops_solve"]))
         c5.close()
-        tf, tb = min(fwd), min(bwd)
-        out["adjoint_2k"] = {
+        tf, tb, tt = min(fwd), min(bwd), min(tan)
+        return {
             "value": n5 / ((tf + tb) / 1e3), "unit": "cells/s (4-step forward with tape + discrete adjoint)",
             "forward_ms": tf, "backward_ms": tb, "cells": n5, "steps": wl5.n_steps, "cells_bad": n_bad,
-            "tangent_ms": min(tan), "tangent_cells_bad": n_bad_t,
+            "tangent_ms": tt, "tangent_cells_bad": n_bad_t,
+            "roofline": {
+                "bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak, "peak_note": "measured FP64 FMA peak",
+                "adjoint_kernel": {"achieved": f_adj / (tb / 1e3) / 1e12, "frac": f_adj / (tb / 1e3) / 1e12 / fp64_peak,
+                                   "flops": f_adj, "traffic": _profiled(os.path.join(ROOT, "profiles",
+                                                                                    "adjoint_kernel_tropo2k.md"))},
+                "tangent_kernel": {"achieved": f_tan / (tt / 1e3) / 1e12, "frac": f_tan / (tt / 1e3) / 1e12 / fp64_peak,
+                                   "flops": f_tan, "traffic": _profiled(os.path.join(ROOT, "profiles",
+                                                                                    "tangent_kernel_tropo2k.md"))},
+                "note": "algorithmic FP64 flops of the walks from every cell's tape: per corrector iteration the "
+                        "mechanism's exact per-iteration count (transposed solve, rates and partials, nu.g, J^T g, "
+                        "theta update; tangent: tangent rates, f program, solve), per iteration matrix re-formed "
+                        "F_J + F_LU, per accepted step (4q + 6) S and per rescale q(q + 1) S of vector work; "
+                        "durations are the backward (sensitivity, incl. its order and reduction kernels and "
+                        "copies) and the tangent calls, CUDA events"},
             "form": "persistent forward recording the tape; one warp per cell backward through transposed sparse LU; "
                     "tangent: one warp per cell forward along the tape (one direction in y0 and theta)"}
+
+    def time_cpu_all_cores():
+        """The oracle on every host core (one worker process per core over cell
+        shards) on bounded samples of the batching, precision and differentiation
+        workloads."""
+        from oracle import pool
+        out = {}
+        with pool.Workers() as ex:
+            cores = ex.n
+            wl3 = synth.workload_batching(args.batch_cells)
+            n3 = min(wl3.cells.n_cells, args.cpu_sample_batching)
+            sub = synth.subset(wl3.cells, np.arange(n3))
+            pool.solve(wl3.mech, synth.subset(sub, np.arange(min(n3, 4 * cores))), wl3.dt, wl3.rtol, wl3.atol,
+                       executor=ex)                                    # workers started and warm
+            t0 = time.perf_counter()
+            pool.solve(wl3.mech, sub, wl3.dt, wl3.rtol, wl3.atol, n_steps=wl3.n_steps, executor=ex)
+            el = time.perf_counter() - t0
+            out["batching_50k"] = {"value": n3 * wl3.n_steps / el, "unit": "cells/s (cell-steps per second)",
+                                   "cores": cores, "kind": "oracle",
+                                   "sample": f"first {n3} of the {wl3.cells.n_cells} cells, 6 steps, {el:.1f} s"}
+            wl4 = synth.workload_precision(args.batch_cells)
+            n4 = min(wl4.cells.n_cells, args.cpu_sample_batching)
+            t0 = time.perf_counter()
+            pool.solve(wl4.mech, synth.subset(wl4.cells, np.arange(n4)), wl4.dt, wl4.rtol, wl4.atol, executor=ex)
+            el = time.perf_counter() - t0
+            out["precision_50k"] = {"value": n4 / el, "unit": "cells/s", "cores": cores, "kind": "oracle (FP64 LU)",
+                                    "sample": f"first {n4} of the {wl4.cells.n_cells} cells, one step, {el:.1f} s"}
+            wl5 = synth.workload_adjoint(args.adjoint_cells)
+            n5 = min(wl5.cells.n_cells, args.cpu_sample_adjoint)
+            sub5 = synth.subset(wl5.cells, np.arange(n5))
+            lam = synth.loss_weights(wl5.mech.n_species, wl5.cells.n_cells)[:, :n5]
+            t0 = time.perf_counter()
+            pool.forward_adjoint(wl5.mech, sub5, wl5.dt, wl5.n_steps, wl5.rtol, wl5.atol, lam, executor=ex)
+            el = time.perf_counter() - t0
+            out["adjoint_2k"] = {"value": n5 / el, "unit": "cells/s (4-step forward with tape + discrete adjoint)",
+                                 "cores": cores, "kind": "oracle",
+                                 "sample": f"first {n5} of the {wl5.cells.n_cells} cells, {el:.1f} s"}
         return out
 
-    def time_form(lu_precision, driver, steps, warmup):
-        cells = chemgpu.Cells(mech, C, rtol=wl.rtol, atol=wl.atol, lu_precision=lu_precision, driver=driver)
-        first = None
-        for k in range(warmup):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            flush.fill_(float(k))
-            e0.record(stream)
-            cells.set_state(T_d, P_d, y0_d, stream=stream)
-            cells.solve_step(wl.dt, stream=stream)
-            e1.record(stream)
-            if k == 0:
+    def time_extras(fp64_peak):
+        out = {}
+        if "batching_50k" in extras_sel:
+            wl3 = synth.workload_batching(args.batch_cells)
+            n3 = wl3.cells.n_cells
+            c3 = chemgpu.Cells(mech, n3, rtol=wl3.rtol, atol=wl3.atol, driver="persistent")
+            T3, P3 = torch.from_numpy(wl3.cells.T).to(dev), torch.from_numpy(wl3.cells.P).to(dev)
+            y3, J3 = torch.from_numpy(wl3.cells.y).to(dev), torch.from_numpy(wl3.cells.J).to(dev)
+            c3.set_state(T3, P3, y3, stream=stream)
+            c3.set_photolysis(J3, stream=stream)
+            w, b = c3.autotune(wl3.dt)
+            c3.solve_steps(wl3.dt, wl3.n_steps, stream=stream)          # warm-up (captures the graph)
+            barrier()
+            ms = []
+            for k in range(2):
+                c3.set_state(T3, P3, y3, stream=stream)
+                flush.fill_(float(k))
+                e0, e1 = event(), event()
+                e0.record(stream)
+                c3.solve_steps(wl3.dt, wl3.n_steps, stream=stream)
+                e1.record(stream)
                 barrier()
-                first = e0.elapsed_time(e1)    # a fresh batch: no per-cell cost history yet
-        barrier()
-        time_form.first[(lu_precision, driver)] = first
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for k in range(steps):
-            flush.fill_(float(k))                       # evict L2 between timed steps
-            ev[k][0].record(stream)
-            cells.set_state(T_d, P_d, y0_d, stream=stream)
-            cells.solve_step(wl.dt, stream=stream)
-            ev[k][1].record(stream)
-        barrier()
-        ms = [a.elapsed_time(b) for a, b in ev]
-        st = cells.get_stats(stream=stream)
-        cells.close()
-        return ms, st
+                ms.append(e0.elapsed_time(e1))
+            st3 = c3.get_stats(stream=stream)
+            c3.close()
+            t3 = min(ms)
+            out["batching_50k"] = {
+                "value": n3 * wl3.n_steps / (t3 / 1e3), "unit": "cells/s (cell-steps per second)",
+                "ms_per_graph": t3, "cells": n3, "steps_per_graph": wl3.n_steps,
+                "form": "persistent work queue, 6 x 600 s steps captured in one CUDA graph, per-cell photolysis, "
+                        "FP64; each step's queue keyed by the previous step's costs (a different state)",
+                "autotuned": {"cells_per_block": w, "blocks_per_sm": b},
+                "integrator_steps_last_600s": {"min": int(st3["steps"].min()), "median": float(np.median(st3["steps"])),
+                                               "max": int(st3["steps"].max())},
+                "cells_ok": int(np.sum(st3["status"] == 0))}
+        if "precision_50k" in extras_sel:
+            # the FP32-LU form on its own workload: the batching cells, one step, against the FP64 form
+            wl4 = synth.workload_precision(args.batch_cells)
+            n4 = wl4.cells.n_cells
+            T4, P4 = torch.from_numpy(wl4.cells.T).to(dev), torch.from_numpy(wl4.cells.P).to(dev)
+            y4, J4 = torch.from_numpy(wl4.cells.y).to(dev), torch.from_numpy(wl4.cells.J).to(dev)
+            prec = {}
+            for lp in (64, 32):
+                c4 = chemgpu.Cells(mech, n4, rtol=wl4.rtol, atol=wl4.atol, driver="persistent", lu_precision=lp)
+                ts = []
+                for k in range(4):
+                    c4.set_state(T4, P4, y4, stream=stream)
+                    c4.set_photolysis(J4, stream=stream)
+                    flush.fill_(float(k))
+                    e0, e1 = event(), event()
+                    e0.record(stream)
+                    c4.solve_step(wl4.dt, stream=stream)
+                    e1.record(stream)
+                    barrier()
+                    if k > 0:
+                        ts.append(e0.elapsed_time(e1))
+                prec[lp] = (min(ts), c4.get_state(stream=stream), c4.get_stats(stream=stream))
+                c4.close()
+            y64, y32 = prec[64][1], prec[32][1]
+            tu = (np.abs(y32 - y64) / (wl4.rtol * np.abs(y64) + wl4.atol)).max(axis=1)
+            out["precision_50k"] = {
+                "value": n4 / (prec[32][0] / 1e3), "unit": "cells/s", "ms": prec[32][0], "fp64_ms": prec[64][0],
+                "cells": n4, "speedup_vs_fp64": prec[64][0] / prec[32][0],
+                "newton_iters_vs_fp64": float(np.sum(prec[32][2]["newton_iters"]) / np.sum(prec[64][2]["newton_iters"])),
+                "per_species_max_diff_vs_fp64_gpu_tol_units": {"median": float(np.median(tu)), "max": float(tu.max())},
+                "cells_ok": int(np.sum(prec[32][2]["status"] == 0)),
+                "form": "the batching cells (per-cell photolysis) for one 600 s step, persistent driver, LU factor/solve "
+                        "in FP32, everything else FP64; best of 3 after one warm-up (each keyed by the previous "
+                        "solve of the same state); differences from the FP64 GPU solve of the same cells in "
+                        "tolerance units rtol*|y| + atol (max over cells, then median and max over species)"}
+        if "derivative_designs" in extras_sel:
+            # f(y) alone by three kernel designs on the 10,000-cell state, rate constants precomputed:
+            # this library's gather and the paper's reaction-parallel atomic design (AoS / SoA reaction data)
+            cd = chemgpu.Cells(mech, C, rtol=wl.rtol, atol=wl.atol)
+            cd.set_state(T_d, P_d, y0_d, stream=stream)
+            f_out = torch.empty_like(y0_d)
+            designs = {}
+            names = {chemgpu.DERIV_GATHER: "gather_warp_per_cell",
+                     chemgpu.DERIV_ATOMIC_AOS: "atomic_reaction_parallel_aos",
+                     chemgpu.DERIV_ATOMIC_SOA: "atomic_reaction_parallel_soa"}
+            for dsg, nm in names.items():
+                cd.eval_deriv_design(dsg, y0_d, out=f_out, stream=stream)      # first call also forms the rate constants
+                ts = []
+                for k in range(10):
+                    flush.fill_(float(k))
+                    e0, e1 = event(), event()
+                    e0.record(stream)
+                    cd.eval_deriv_design(dsg, y0_d, out=f_out, stream=stream)
+                    e1.record(stream)
+                    barrier()
+                    ts.append(e0.elapsed_time(e1))
+                t = statistics.median(ts)
+                designs[nm] = {"ms": t, "cells_per_s": C / (t / 1e3),
+                               "hbm_gbs": C * (2 * S + wl.mech.n_reactions) * 8 / (t / 1e3) / 1e9}
+            cd.close()
+            g = designs["gather_warp_per_cell"]["ms"]
+            for nm in designs:
+                designs[nm]["vs_gather"] = g / designs[nm]["ms"]
+            out["derivative_designs"] = {
+                "cells": C, "designs": designs,
+                "note": "f(y) only, rate constants precomputed; median of 10 launches with L2 flushed between; "
+                        "hbm_gbs counts y and k~ read and f written once per cell (the atomic designs re-read y "
+                        "per reaction and add through L2)"}
+        if "coupled_cells" in extras_sel:
+            # the paper's multi-cell system: groups of G consecutive cells integrated as one system
+            coupled = {}
+            for G in (1, 2, 5, 10):
+                cc = chemgpu.Cells(mech, C, rtol=wl.rtol, atol=wl.atol, driver="persistent", couple_cells=G)
+                ts = []
+                for k in range(3):
+                    cc.set_state(T_d, P_d, y0_d, stream=stream)
+                    flush.fill_(float(k))
+                    e0, e1 = event(), event()
+                    e0.record(stream)
+                    cc.solve_step(wl.dt, stream=stream)
+                    e1.record(stream)
+                    barrier()
+                    if k > 0:
+                        ts.append(e0.elapsed_time(e1))
+                stc = cc.get_stats(stream=stream)
+                cc.close()
+                t = min(ts)
+                coupled[f"G{G}"] = {"ms": t, "cells_per_s": C / (t / 1e3),
+                                    "steps_per_cell": float(np.mean(stc["steps"])),
+                                    "newton_iters_per_cell": float(np.mean(stc["newton_iters"])),
+                                    "systems": (C + G - 1) // G,
+                                    "solver_iterations_total": int(np.sum(stc["newton_iters"][::G])),
+                                    "cells_ok": int(np.sum(stc["status"] == 0))}
+            out["coupled_cells"] = {
+                "cells": C, "groups": coupled,
+                "note": "couple_cells = G: each group of G consecutive cells is one ODE system (shared step size, "
+                        "order, Newton iterations, one norm), whole groups per block (10 cells, 8 for G = 4), "
+                        "groups handed out most expensive first by their cost in the previous solve (of the same "
+                        "state); G1 = independent cells. solver_iterations_total counts Newton iterations once per "
+                        "system, the paper's measure of its Multi-cells saving"}
+        if "pressure_dependent" in extras_sel:
+            wlp = synth.workload_pressure(C)
+            mp = chemgpu.Mechanism(wlp.mech)
+            cp = chemgpu.Cells(mp, C, rtol=wlp.rtol, atol=wlp.atol, driver="persistent")
+            Tp, Pp = torch.from_numpy(wlp.cells.T).to(dev), torch.from_numpy(wlp.cells.P).to(dev)
+            yp = torch.from_numpy(wlp.cells.y).to(dev)
+            tsp = []
+            for k in range(4):
+                cp.set_state(Tp, Pp, yp, stream=stream)
+                flush.fill_(float(k))
+                e0, e1 = event(), event()
+                e0.record(stream)
+                cp.solve_step(wlp.dt, stream=stream)
+                e1.record(stream)
+                barrier()
+                if k > 0:
+                    tsp.append(e0.elapsed_time(e1))
+            stp = cp.get_stats(stream=stream)
+            cp.close()
+            out["pressure_dependent"] = {
+                "value": C / (min(tsp) / 1e3), "unit": "cells/s", "ms": min(tsp), "cells": C,
+                "cells_ok": int(np.sum(stp["status"] == 0)),
+                "note": "72/186 mechanism with 12 Troe fall-off, 3 k_a + k_b[M] and 3 k_a + k_c[M]/(1 + k_c[M]/k_b) "
+                        "reactions, P log-uniform 1e3..1.05e5 Pa, T 200..310 K; persistent FP64 form, best of 3 "
+                        "(each keyed by the previous solve of the same state)"}
+        if "host_overlap" in extras_sel:
+            out["host_overlap"] = time_host_overlap()
+        if "adjoint_2k" in extras_sel:
+            out["adjoint_2k"] = time_adjoint(fp64_peak)
+        return out
 
-    time_form.first = {}
-    forms = args.forms.split(",")
+    def time_form(lu_precision, driver, steps, warmup, y_other):
+        """Timed solves of the 10,000-cell state y0.  Returns a dict of per-step
+        device times (ms) and the statistics of a headline solve:
+          first (the headline): every timed solve is a fresh batch's first solve
+                     (batches created outside the timed region): no cost history,
+                     the queue keyed by each cell's summed rate constants;
+          other:     one batch; before every timed solve of y0 an untimed solve of
+                     y_other (the same cells one 600 s step later), so the queue
+                     is keyed by a different state's costs;
+          best:      y0 re-solved, keyed by a previous solve of y0 itself;
+          chained:   a model's steps y_(k+1) = solve(y_k), each keyed by the
+                     previous step's costs."""
+        out = {}
+
+        def batch():
+            return chemgpu.Cells(mech, C, rtol=wl.rtol, atol=wl.atol, lu_precision=lu_precision, driver=driver)
+
+        def timed(cells, y_in, k):
+            flush.fill_(float(k))                       # evict L2 between timed steps
+            e0, e1, e2 = event(), event(), event()
+            e0.record(stream)
+            cells.set_state(T_d, P_d, y_in, stream=stream)
+            e1.record(stream)
+            cells.solve_step(wl.dt, stream=stream)
+            e2.record(stream)
+            return e0, e1, e2
+
+        for k in range(warmup):
+            c = batch()
+            timed(c, y0_d, k)
+            barrier()
+            c.close()
+        fresh = [batch() for _ in range(steps)]
+        barrier()
+        evs = [timed(c, y0_d, k) for k, c in enumerate(fresh)]
+        barrier()
+        out["first"] = [a.elapsed_time(c) for a, b, c in evs]
+        out["first_kernel"] = [b.elapsed_time(c) for a, b, c in evs]
+        st = fresh[-1].get_stats(stream=stream)
+        for c in fresh:
+            c.close()
+        cells = batch()
+        timed(cells, y0_d, 0)
+        evs = []
+        for k in range(steps):
+            cells.set_state(T_d, P_d, y_other, stream=stream)
+            cells.solve_step(wl.dt, stream=stream)
+            evs.append(timed(cells, y0_d, k))
+        barrier()
+        out["other"] = [a.elapsed_time(c) for a, b, c in evs]
+        evs = [timed(cells, y0_d, k) for k in range(steps)]
+        barrier()
+        out["best"] = [a.elapsed_time(c) for a, b, c in evs]
+        if args.chained:
+            y = y0_d.clone()
+            evs = []
+            for k in range(warmup + steps):
+                e = timed(cells, y, k)
+                cells.get_state(out=y, stream=stream)
+                if k >= warmup:
+                    evs.append(e)
+            barrier()
+            out["chained"] = [a.elapsed_time(c) for a, b, c in evs]
+        cells.close()
+        return out, st
+
+    forms = [] if args.forms == "none" else args.forms.split(",")
+    # the same cells one 600 s step later: the state whose costs key the "other state" runs
+    cy = chemgpu.Cells(mech, C, rtol=wl.rtol, atol=wl.atol, driver="persistent")
+    cy.set_state(T_d, P_d, y0_d, stream=stream)
+    cy.solve_step(wl.dt, stream=stream)
+    y1_d = torch.empty_like(y0_d)
+    cy.get_state(out=y1_d, stream=stream)
+    cy.close()
     barrier()
     res = {}
     with ClockSampler(local) as clk:
+        fp64_peak, fp64_peak_ms = chemgpu.measure_fma_peak(64, stream=stream)
+        fp32_peak, fp32_peak_ms = chemgpu.measure_fma_peak(32, stream=stream)
         for name in forms:
-            res[name] = time_form(*FORMS[name], args.steps, args.warmup)
-        extras = {} if (args.no_e2e or args.no_extras) else time_extras(chemgpu, mech, dev, stream, flush, barrier)
+            res[name] = time_form(*FORMS[name], args.steps, args.warmup, y1_d)
+        extras = time_extras(fp64_peak) if extras_sel - {"cpu_all_cores"} else {}
     clocks = clk.summary()
     if args.no_e2e:          # profiling runs: timed kernels only, no report line
         return 0
-    ms_head, st_head = res["persistent64"]
-    ms_plain, st_plain = res["plain64"]
-    ms_chosen, st_chosen = res["chosen"]
+    (h, st_head), (p, st_plain), (ch, st_chosen) = res["persistent64"], res["plain64"], res["chosen"]
 
-    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    # End to end through the C ABI with host buffers (pinned), copies inside each
+    # timed step: T, P and y0 in, the solve, y out; as for the headline, every
+    # timed step is a fresh batch's first solve (batches created untimed).
     T_h = torch.from_numpy(wl.cells.T).pin_memory()
     P_h = torch.from_numpy(wl.cells.P).pin_memory()
     y_h = torch.from_numpy(wl.cells.y).pin_memory()
     y_out = torch.empty_like(y_h).pin_memory()
-    cells = chemgpu.Cells(mech, C, rtol=wl.rtol, atol=wl.atol, lu_precision=64, driver="persistent")
-    for _ in range(args.warmup):
+    fresh = [chemgpu.Cells(mech, C, rtol=wl.rtol, atol=wl.atol, lu_precision=64, driver="persistent")
+             for _ in range(args.warmup + args.steps)]
+    barrier()
+    e2e_ev = []
+    for k, cells in enumerate(fresh):
+        flush.fill_(float(k))
+        t0, t1 = event(), event()
+        t0.record(stream)
         cells.set_state(T_h, P_h, y_h, stream=stream)
         cells.solve_step(wl.dt, stream=stream)
         cells.get_state(out=y_out, stream=stream)
+        t1.record(stream)
+        if k >= args.warmup:
+            e2e_ev.append((t0, t1))
     barrier()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for _ in range(args.steps):
-        cells.set_state(T_h, P_h, y_h, stream=stream)
-        cells.solve_step(wl.dt, stream=stream)
-        cells.get_state(out=y_out, stream=stream)
-    t1.record(stream)
-    barrier()
-    e2e_ms = t0.elapsed_time(t1)
-    cells.close()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+    for cells in fresh:
+        cells.close()
 
     def maxr(x):
         if ws == 1:
@@ -545,39 +720,40 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    tot_head = maxr(sum(ms_head))
-    tot_plain = maxr(sum(ms_plain))
-    tot_chosen = maxr(sum(ms_chosen))
+    tot_head = maxr(sum(h["first"]))
+    tot_other = maxr(sum(h["other"]))
+    tot_best = maxr(sum(h["best"]))
+    tot_plain = maxr(sum(p["first"]))
+    tot_chosen = maxr(sum(ch["first"]))
     e2e_ms = maxr(e2e_ms)
     value = ws * C * args.steps / (tot_head / 1e3)
     plain = ws * C * args.steps / (tot_plain / 1e3)
     chosen = ws * C * args.steps / (tot_chosen / 1e3)
     e2e = ws * C * args.steps / (e2e_ms / 1e3)
 
-    # roofline: FP64 arithmetic of the solve kernel (algorithmic flops from the counters):
-    # F = n_f F_f + n_J (F_J + F_LU) + n_sol F_sol + F_vec, with F_vec a lower bound of the
-    # integrator's vector work on S species: per accepted step 11 S (order-1 predictor and psi
-    # 2 S, weights 3 S, error norm 3 S, history update 3 S), per Newton iteration 8 S
-    # (residual 3 S, norm 3 S, correction and iterate 2 S)
-    def flops(st):
-        Sv = float(info["n_species"])
-        return float(np.sum(st["f_evals"]) * info["flops_f"] + np.sum(st["jac_evals"]) * (info["flops_jac"] + info["flops_lu"])
-                     + np.sum(st["solves"]) * info["flops_solve"]
-                     + 11.0 * Sv * np.sum(st["steps"]) + 8.0 * Sv * np.sum(st["newton_iters"]))
-    kernel_ms = statistics.mean(ms_head)
-    achieved = flops(st_head) / (kernel_ms / 1e3)
-    hbm_peak = None
+    kernel_ms = statistics.mean(h["first_kernel"])
+    achieved = flops(st_head) / (kernel_ms / 1e3) / 1e12
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            hbm_peak = float(json.load(fh)["hbm_gbs"])
+            hbm_peak, hbm_src = float(json.load(fh)["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
-        hbm_peak = 6800.0
+        hbm_peak, hbm_src = 6800.0, "fallback"
     hbm_bytes = C * (2 * S * 8 + 2 * 8 + 48)     # y in and out, T and P, per-cell statistics
     hbm_achieved = hbm_bytes / (kernel_ms / 1e3) / 1e9
     if rank == 0:
         cpu_rate, cpu_el = (None, None)
+        cpu_all = None
         if not args.no_cpu_baseline:
-            cpu_rate, cpu_el = _oracle_sample(wl, args.cpu_sample)
+            cpu_rate, cpu_el = _oracle_single(wl, args.cpu_sample)
+            from oracle import pool
+            with pool.Workers() as ex:
+                pool.solve(wl.mech, synth.subset(wl.cells, range(4 * ex.n)), wl.dt, wl.rtol, wl.atol, executor=ex)
+                t0c = time.perf_counter()
+                pool.solve(wl.mech, wl.cells, wl.dt, wl.rtol, wl.atol, executor=ex)
+                el_all = time.perf_counter() - t0c
+                cpu_all = (C / el_all, el_all, ex.n)
+            if "cpu_all_cores" in extras_sel:
+                extras["cpu_all_cores"] = time_cpu_all_cores()
         ok = int(np.sum(st_head["status"] == 0))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -585,33 +761,49 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"tropo_72sp_186rx: one 600 s step over {C} cells per GPU, rtol 1e-4, atol 1e-10",
                        "form": "persistent work queue, tables staged in shared memory by TMA, FP64 throughout",
-                       "queue_order": "most expensive cells first by their cost in the previous solve of the batch; "
-                                      "the timed steps re-solve the same state, so that prediction is exact here "
-                                      "(a model's consecutive steps give an approximate one)",
-                       "first_solve_ms": time_form.first.get((64, "persistent")),
-                       "first_solve_note": "a fresh batch's first solve (untimed warm-up 0): no cost history, "
-                                           "cells ordered by a one-f-evaluation stiffness estimate",
+                       "queue_order": "most expensive cells first; every timed step is a fresh batch's first "
+                                      "solve (batch created outside the timed region), so the order uses no cost "
+                                      "history: cells keyed by the sum of their rate constants",
                        "l2": "flushed between timed steps (512 MB write)", "cells_ok": ok},
+            "queue_order_forms": {
+                "first_solve_ms": tot_head / args.steps,
+                "keyed_by_other_state_ms": tot_other / args.steps,
+                "best_case_same_state_ms": tot_best / args.steps,
+                "chained_model_steps_ms": statistics.mean(h["chained"]) if "chained" in h else None,
+                "note": "first solve = the headline (fresh batches, keyed by summed rate constants); other state: "
+                        "one batch, each timed solve of y0 keyed by the costs of an untimed solve of the same cells "
+                        "one 600 s step later; best case: y0 keyed by a previous solve of y0 itself (exact costs); "
+                        "chained: a model's consecutive steps y_(k+1) = solve(y_k) from y0 after the warm-ups, each "
+                        "keyed by the previous step's costs (easier states than y0's initial transient)"},
             "plain_fp64": {"value": plain, "unit": UNIT, "ms_per_step": tot_plain / args.steps,
                            "form": "one warp per cell, one cell per block, tables read from L2, FP64 throughout",
                            "chosen_vs_plain": value / plain},
             "fp32_lu": {"value": chosen, "unit": UNIT, "ms_per_step": tot_chosen / args.steps,
-                        "form": "persistent + FP32 LU factor/solve (f, error control, state FP64)",
+                        "form": "persistent + FP32 LU factor/solve (f, error control, state FP64), fresh batches "
+                                "as the headline",
                         "vs_plain_fp64": chosen / plain,
                         "newton_iters_vs_fp64": float(np.sum(st_chosen["newton_iters"]) / max(1, np.sum(st_head["newton_iters"])))},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(C * (S + 2) * 8),
-                    "d2h_bytes_per_step": int(C * S * 8), "form": "persistent FP64, pinned host buffers through the C ABI"},
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_NOMINAL, "traffic": _profiled_traffic(),
+                    "d2h_bytes_per_step": int(C * S * 8),
+                    "form": "persistent FP64 through the C ABI with pinned host buffers: per timed step T, P, y0 "
+                            "in, the solve, y out (the sum of the timed steps); fresh batches as the headline"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp64_peak, "traffic": _profiled(PROFILE),
                          "kernel": "solve_kernel<double,3,staged> (FP64 pipe)",
-                         "note": "peak = 152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM x 2 flops (derived); "
-                                 "algorithmic FP64 flops from per-cell counters (f, J, LU, solves, and a lower bound "
-                                 "of the per-step and per-iteration vector work); traffic = ncu DRAM bytes per launch "
+                         "peak_note": f"measured FP64 FMA peak in this run (chem_measure_fma_peak, all SMs, "
+                                      f"{fp64_peak_ms:.0f} ms launch); derived nominal "
+                                      f"{FP64_PEAK_DERIVED / 1e12:.4f} (152 SMs x 2070 MHz x 2 FMA/clk x 2)",
+                         "note": "achieved = algorithmic FP64 flops from per-cell counters (f, J, LU, solves, and the "
+                                 "integrator's vector work: (4q + 9) S per accepted step at order q, 8 S per Newton "
+                                 "iteration) / mean duration of chem_solve_step (the solve kernel and its four "
+                                 "queue-order kernels) in the headline runs; traffic = ncu DRAM bytes per launch "
                                  "(null when the kernel changed since the capture)"},
+            "fp_peaks": {"fp64_tflops": fp64_peak, "fp32_tflops": fp32_peak, "fp64_ms": fp64_peak_ms,
+                         "fp32_ms": fp32_peak_ms, "clocks": "see clocks (sampled over the same window)"},
             "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
-                    "bytes_per_cell": hbm_bytes // C, "note": "algorithmic HBM bytes of the same kernel; "
-                    "peak = measured copy bandwidth; does not bind"},
-            "gpu_launches": 4 * args.steps,   # per step: queue-order keys, scan, scatter, solve
+                    "bytes_per_cell": hbm_bytes // C, "note": f"algorithmic HBM bytes of the same kernel; "
+                    f"peak = {hbm_src} copy bandwidth; does not bind"},
+            "gpu_launches": 5 * args.steps,   # per timed step: queue-order keys, buckets, scan, scatter, solve
             "clocks": clocks,
             "paper_context": {
                 "note": "the paper's own speedups (Results and Conclusions sections), quoted as context only: "
@@ -623,9 +815,13 @@ def run_gpu(args):
                 "data_movement_share_of_gpu_time": "about 90% (10,800 cells)"},
         }
         line.update(extras)
-        if cpu_rate is not None:
-            line["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"first {args.cpu_sample} of the {C} cells, single thread, {cpu_el:.1f} s"}
+        if cpu_all is not None:
+            line["cpu_baseline"] = {"value": cpu_all[0], "unit": UNIT, "cores": cpu_all[2], "kind": "oracle",
+                                    "sample": f"all {C} cells, {cpu_all[2]} worker processes (one per host core) "
+                                              f"over cell shards, {cpu_all[1]:.1f} s"}
+            line["cpu_baseline_single_thread"] = {
+                "value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"first {args.cpu_sample} of the {C} cells, one thread, {cpu_el:.1f} s"}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -639,15 +835,22 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=3000)
-    ap.add_argument("--ref-sample", type=int, default=1000)
+    ap.add_argument("--cpu-sample", type=int, default=3000, help="cells of the single-thread oracle timing")
+    ap.add_argument("--cpu-sample-batching", type=int, default=2000, help="cells of the all-core oracle timings")
+    ap.add_argument("--cpu-sample-adjoint", type=int, default=512)
+    ap.add_argument("--ref-sample", type=int, default=0, help="reference arm: cells per step (0: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", type=int, default=N_CELLS, help="cells per GPU (the benchmark uses 10,000)")
-    ap.add_argument("--forms", default="persistent64,plain64,chosen", help="comma list of " + ",".join(FORMS))
+    ap.add_argument("--forms", default="persistent64,plain64,chosen",
+                    help="comma list of " + ",".join(FORMS) + ", or none")
+    ap.add_argument("--no-chained", dest="chained", action="store_false", help="skip the chained-steps timing")
     ap.add_argument("--no-e2e", action="store_true", help="profiling: run the timed forms only, print nothing")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batching and adjoint measurements")
+    ap.add_argument("--extras", default="all", help="all, none, or a comma list of " + ",".join(EXTRAS))
+    ap.add_argument("--no-extras", action="store_true", help="same as --extras none")
     ap.add_argument("--batch-cells", type=int, default=50_000, help="cells of the batching measurement")
     ap.add_argument("--adjoint-cells", type=int, default=2_048, help="cells of the adjoint measurement")
+    ap.add_argument("--adjoint-reps", type=int, default=3, help="adjoint measurement repetitions (the first is a warm-up)")
+    ap.add_argument("--tape-steps", type=int, default=0, help="adjoint measurement: tape rows per cell (0: default)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -88,8 +88,8 @@ extern "C" {
 #define CHEM_DRIVER_PLAIN 0       /* one warp per cell, cells assigned by block */
 #define CHEM_DRIVER_PERSISTENT 1  /* resident warps pop cells from a device queue, most expensive
                                      first: by each cell's cost in the previous solve of the
-                                     batch, or for the first solve by a one-f-evaluation
-                                     stiffness estimate (results do not depend on the order) */
+                                     batch, or for the first solve by the sum of its rate
+                                     constants (results do not depend on the order) */
 
 /*
  * One reaction: reactant slots reac[0..n_reac-1] (a species listed twice is a
@@ -125,6 +125,10 @@ typedef struct {
   int32_t ops_f, ops_jac, ops_lu, ops_fwd, ops_bwd;                 /* scheduled ops */
   double flops_f, flops_jac, flops_lu, flops_solve;                 /* algorithmic flops */
   int32_t smem_per_cell_fp64, smem_per_cell_fp32;                   /* bytes */
+  double flops_adj_iter;           /* adjoint, per corrector iteration walked back: transposed
+                                      solve, rates and partials, nu.g, J^T g, theta update, vectors */
+  double flops_tan_iter;           /* tangent, per corrector iteration: tangent rates (with a theta
+                                      direction), the f program on them, one solve, vectors */
 } chem_mech_info;
 
 typedef struct {
@@ -158,9 +162,13 @@ typedef struct {
                                       counts a fallback, see chem_staging_fallbacks */
 } chem_opts;
 
+/* Per-cell outcome of a solve: status (CHEM_CELL_*), accepted steps, rejected
+ * attempts, corrector failures, Newton iterations, f evaluations, Jacobian
+ * evaluations (= factorisations), linear solves, the order at the end, the sum
+ * over accepted steps of the order each was taken at, and the last step size. */
 typedef struct {
   int32_t status, steps, rejects, conv_fails, newton_iters, f_evals, jac_evals, solves,
-      final_order, pad;
+      final_order, order_sum;
   double final_h;
 } chem_cell_stats;
 
@@ -376,6 +384,16 @@ int chem_eval_deriv_design(chem_cells *cells, int32_t design, const double *y, d
  * y, b, f, x are [n_species][n_cells].  With CHEM_MEM_HOST the call allocates
  * device scratch, copies, and synchronises stream before returning. */
 int chem_eval_deriv(chem_cells *cells, const double *y, double *f, int32_t mem, void *stream);
+/* Diagnostic: out[i] = the FP64 reciprocal the solve kernels use (the
+ * hardware estimate refined by two Newton-Raphson steps, r <- r (2 - x r)) of
+ * x[i], for i < n, on the current device.  Defined for normal x with
+ * 2^-1022 <= |x| <= 2^1022 (within 1 ulp of 1/x there); the estimate flushes
+ * subnormal inputs and results to zero, so outside that range the result is
+ * 0 or not finite.  No counterpart in the paper (the pivots of the LU and the
+ * error weights 1/(rtol |y| + atol) use it).  With CHEM_MEM_HOST the call
+ * allocates device scratch and synchronises stream.  Errors: CHEM_EINVAL,
+ * CHEM_ENOMEM, CHEM_ECUDA. */
+int chem_eval_reciprocal(const double *x, double *out, int64_t n, int32_t mem, void *stream);
 int chem_eval_newton_solve(chem_cells *cells, double c, const double *y, const double *b, double *x,
                            int32_t mem, void *stream);
 
@@ -452,6 +470,15 @@ typedef int (*chem_chunk_fn)(int64_t c0, int64_t c1, int32_t step, void *user);
  * returned nonzero; work already queued is drained first). */
 int chem_pipeline_run(chem_pipeline *p, const double *T, const double *P, const double *J, double *y, double dt,
                       int32_t n_steps, chem_chunk_fn fn, void *user, chem_cell_stats *stats);
+
+/* Measured FMA throughput of the CUDA cores in TFLOP/s (precision 64: FP64,
+ * 32: FP32), the denominator the solve kernels' arithmetic rooflines are
+ * measured against: every thread of a grid that fills all SMs runs 8
+ * independent chains of x <- x a + b; *tflops = 2 x chains x iterations x
+ * threads / time of one launch (CUDA events on stream, calibrated to about
+ * 50 ms, best of three), *ms that time.  No counterpart in the paper.
+ * Synchronous.  Errors: CHEM_EINVAL, CHEM_ECUDA. */
+int chem_measure_fma_peak(int32_t precision, double *tflops, double *ms, void *stream);
 
 /* Thread-local description of the last error ("" if none). */
 const char *chem_last_error(void);

@@ -61,13 +61,13 @@ class _Stats(ct.Structure):
     _fields_ = [("status", ct.c_int32), ("steps", ct.c_int32), ("rejects", ct.c_int32),
                 ("conv_fails", ct.c_int32), ("newton_iters", ct.c_int32), ("f_evals", ct.c_int32),
                 ("jac_evals", ct.c_int32), ("solves", ct.c_int32), ("final_order", ct.c_int32),
-                ("pad", ct.c_int32), ("final_h", ct.c_double)]
+                ("order_sum", ct.c_int32), ("final_h", ct.c_double)]
 
 
 STATS_DTYPE = np.dtype([("status", "<i4"), ("steps", "<i4"), ("rejects", "<i4"),
                         ("conv_fails", "<i4"), ("newton_iters", "<i4"), ("f_evals", "<i4"),
                         ("jac_evals", "<i4"), ("solves", "<i4"), ("final_order", "<i4"),
-                        ("pad", "<i4"), ("final_h", "<f8")])
+                        ("order_sum", "<i4"), ("final_h", "<f8")])
 assert STATS_DTYPE.itemsize == ct.sizeof(_Stats)
 
 
@@ -230,7 +230,7 @@ def integrate(mech, kt, y0, dt, rtol, atol, max_order=5, max_steps=5000, fixed_h
                    tape.y.ctypes.data)
     lib().orc_integrate(m.ref, _p(kt), _p(y), float(dt), ct.byref(o), ct.byref(st),
                         None if tp is None else ct.byref(tp))
-    stats = {k: getattr(st, k) for k, _ in _Stats._fields_ if k != "pad"}
+    stats = {k: getattr(st, k) for k, _ in _Stats._fields_}
     out = [y, stats]
     if n_hist:
         out.append(hist)

@@ -503,6 +503,7 @@ int orc_integrate(const orc_mech *m, const double *kt, double *y0, double dt, co
     /* -- accept: update the backward differences */
     t = last ? dt : t + h;
     st->steps++;
+    st->order_sum += q;
     n_since_M++;
     nef = 0;
     ncf = 0;

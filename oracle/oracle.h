@@ -78,7 +78,7 @@ typedef struct {
 } orc_opts;
 
 typedef struct {
-  int32_t status, steps, rejects, conv_fails, newton_iters, f_evals, jac_evals, solves, final_order, pad;
+  int32_t status, steps, rejects, conv_fails, newton_iters, f_evals, jac_evals, solves, final_order, order_sum;
   double final_h;
 } orc_stats;
 

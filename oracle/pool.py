@@ -23,6 +23,32 @@ def n_workers(workers: int | None = None) -> int:
     return max(1, int(n))
 
 
+class Workers:
+    """A set of spawned oracle worker processes kept for several calls (pass it
+    as `executor`); a context manager."""
+
+    def __init__(self, workers: int | None = None):
+        self.n = n_workers(workers)
+        self.ex = ProcessPoolExecutor(max_workers=self.n, mp_context=mp.get_context("spawn"))
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.ex.shutdown()
+
+
+def _run(fn, tasks, nw, executor):
+    """Results of fn over tasks, in order: in this process, on the given
+    Workers, or on a pool made for this call."""
+    if executor is not None:
+        return list(executor.ex.map(fn, tasks))
+    if nw == 1:
+        return [fn(t) for t in tasks]
+    with ProcessPoolExecutor(max_workers=min(nw, len(tasks)), mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(fn, tasks))
+
+
 def _shards(n: int, parts: int):
     parts = max(1, min(parts, n))
     bounds = np.linspace(0, n, parts + 1).astype(np.int64)
@@ -43,7 +69,7 @@ def _solve_shard(args):
 
 
 def solve(mech, cells, dt, rtol, atol, n_steps: int = 1, max_steps: int = 5000, theta=None, between=None,
-          first_step: int = 0, workers: int | None = None, chunks_per_worker: int = 4):
+          first_step: int = 0, workers: int | None = None, chunks_per_worker: int = 4, executor=None):
     """n_steps consecutive oracle solves of every cell of a synth.Cells batch.
 
     between(y, T, step) (a picklable top-level function, may be None) runs on a
@@ -54,7 +80,7 @@ def solve(mech, cells, dt, rtol, atol, n_steps: int = 1, max_steps: int = 5000, 
     C = cells.n_cells
     if C == 0:
         return np.array(cells.y, np.float64), np.zeros(0, oracle.STATS_DTYPE)
-    nw = n_workers(workers)
+    nw = executor.n if executor is not None else n_workers(workers)
     shards = _shards(C, nw * chunks_per_worker)
     tasks = []
     for a, b in shards:
@@ -63,14 +89,8 @@ def solve(mech, cells, dt, rtol, atol, n_steps: int = 1, max_steps: int = 5000, 
                       theta, between, first_step))
     y = np.empty_like(np.asarray(cells.y, np.float64))
     st = np.zeros(C, oracle.STATS_DTYPE)
-    if nw == 1:
-        results = map(_solve_shard, tasks)
-        for (a, b), (ys, ss) in zip(shards, results):
-            y[:, a:b], st[a:b] = ys, ss
-        return y, st
-    with ProcessPoolExecutor(max_workers=min(nw, len(tasks)), mp_context=mp.get_context("spawn")) as ex:
-        for (a, b), (ys, ss) in zip(shards, ex.map(_solve_shard, tasks)):
-            y[:, a:b], st[a:b] = ys, ss
+    for (a, b), (ys, ss) in zip(shards, _run(_solve_shard, tasks, nw, executor)):
+        y[:, a:b], st[a:b] = ys, ss
     return y, st
 
 
@@ -86,26 +106,50 @@ def _adjoint_shard(args):
     return ly0, g
 
 
-def adjoint(mech, cells, tapes, lam, theta=None, workers: int | None = None, chunks_per_worker: int = 4):
+def adjoint(mech, cells, tapes, lam, theta=None, workers: int | None = None, chunks_per_worker: int = 4,
+            executor=None):
     """The oracle's discrete adjoint of every cell's tape (oracle.Tape, one per
     cell): (dL/dy0 [S, C], per-cell dL/dtheta [C, R]) for dL/dy_final = lam [S, C]."""
     C = cells.n_cells
-    nw = n_workers(workers)
+    nw = executor.n if executor is not None else n_workers(workers)
     shards = _shards(C, nw * chunks_per_worker)
     tasks = [(mech, cells.T[a:b], cells.P[a:b], None if cells.J is None else cells.J[:, a:b], theta,
               np.ascontiguousarray(cells.y[:, a:b]), tapes[a:b], np.ascontiguousarray(lam[:, a:b]))
              for a, b in shards]
     ly0 = np.zeros((mech.n_species, C))
     g = np.zeros((C, mech.n_reactions))
-    if nw == 1:
-        results = map(_adjoint_shard, tasks)
-    else:
-        ex = ProcessPoolExecutor(max_workers=min(nw, len(tasks)), mp_context=mp.get_context("spawn"))
-        results = ex.map(_adjoint_shard, tasks)
-    try:
-        for (a, b), (l, gg) in zip(shards, results):
-            ly0[:, a:b], g[a:b] = l, gg
-    finally:
-        if nw != 1:
-            ex.shutdown()
+    for (a, b), (l, gg) in zip(shards, _run(_adjoint_shard, tasks, nw, executor)):
+        ly0[:, a:b], g[a:b] = l, gg
+    return ly0, g
+
+
+def _forward_adjoint_shard(args):
+    mech, T, P, y0, dt, n_steps, rtol, atol, lam = args
+    import oracle
+    S, n = y0.shape
+    ly0 = np.zeros((S, n))
+    g = np.zeros(mech.n_reactions)
+    for k in range(n):
+        kt = oracle.rate_constants(mech, T[k], P[k])
+        _, _, tape = oracle.integrate_steps(mech, kt, y0[:, k], dt, n_steps, rtol, atol)
+        ly0[:, k], gk = oracle.adjoint(mech, kt, y0[:, k], tape, lam[:, k])
+        g += gk
+    return ly0, g
+
+
+def forward_adjoint(mech, cells, dt, n_steps, rtol, atol, lam, workers: int | None = None, executor=None,
+                    chunks_per_worker: int = 4):
+    """The oracle's whole differentiation workload: per cell n_steps solves
+    recording the tape, then the discrete adjoint of the tape for dL/dy_final =
+    lam [S, C].  Returns (dL/dy0 [S, C], dL/dtheta [R] summed over cells)."""
+    C = cells.n_cells
+    nw = executor.n if executor is not None else n_workers(workers)
+    shards = _shards(C, nw * chunks_per_worker)
+    tasks = [(mech, cells.T[a:b], cells.P[a:b], np.ascontiguousarray(cells.y[:, a:b]), dt, n_steps, rtol, atol,
+              np.ascontiguousarray(lam[:, a:b])) for a, b in shards]
+    ly0 = np.zeros((mech.n_species, C))
+    g = np.zeros(mech.n_reactions)
+    for (a, b), (l, gg) in zip(shards, _run(_forward_adjoint_shard, tasks, nw, executor)):
+        ly0[:, a:b] = l
+        g += gg
     return ly0, g

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "libchemgpu.so")
-SOURCES = ["mechanism.cpp", "capi.cpp", "kernels.cu", "noalloc.cu", "deriv.cu"]
+SOURCES = ["mechanism.cpp", "capi.cpp", "kernels.cu", "noalloc.cu", "deriv.cu", "peak.cu"]
 HEADERS = [os.path.join(ROOT, "include", "chemgpu.h"), os.path.join(CSRC, "internal.h"),
            os.path.join(CSRC, "device_common.cuh")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -30,7 +30,7 @@ EXPORTS = ["chem_opts_default", "chem_mechanism_create", "chem_mechanism_destroy
            "chem_cells_set_theta", "chem_solve_step", "chem_solve_steps", "chem_autotune",
            "chem_get_state", "chem_get_stats", "chem_staging_fallbacks",
            "chem_eval_deriv", "chem_eval_newton_solve", "chem_eval_deriv_design", "chem_solve_step_noalloc", "chem_sensitivity",
-           "chem_sensitivity_checkpointed",
+           "chem_sensitivity_checkpointed", "chem_eval_reciprocal", "chem_measure_fma_peak",
            "chem_tangent", "chem_get_tape", "chem_pipeline_create", "chem_pipeline_destroy", "chem_pipeline_run", "chem_last_error"]
 
 
@@ -60,13 +60,14 @@ class MechInfo(ct.Structure):
         "passes_f", "passes_jac", "passes_lu", "passes_fwd", "passes_bwd",
         "ops_f", "ops_jac", "ops_lu", "ops_fwd", "ops_bwd")] + \
         [(n, ct.c_double) for n in ("flops_f", "flops_jac", "flops_lu", "flops_solve")] + \
-        [("smem_per_cell_fp64", ct.c_int32), ("smem_per_cell_fp32", ct.c_int32)]
+        [("smem_per_cell_fp64", ct.c_int32), ("smem_per_cell_fp32", ct.c_int32),
+         ("flops_adj_iter", ct.c_double), ("flops_tan_iter", ct.c_double)]
 
 
 STATS_DTYPE = np.dtype([("status", "<i4"), ("steps", "<i4"), ("rejects", "<i4"),
                         ("conv_fails", "<i4"), ("newton_iters", "<i4"), ("f_evals", "<i4"),
                         ("jac_evals", "<i4"), ("solves", "<i4"), ("final_order", "<i4"),
-                        ("pad", "<i4"), ("final_h", "<f8")])
+                        ("order_sum", "<i4"), ("final_h", "<f8")])
 
 _lib = None
 _lock = threading.Lock()
@@ -106,6 +107,8 @@ def load(path: str | None = None):
         L.chem_eval_deriv_design.argtypes = [V, ct.c_int32, V, V, ct.c_int32, V]
         L.chem_solve_step_noalloc.argtypes = [V, ct.c_int64, V, V, V, V, V, V, ct.c_double, V, V]
         L.chem_sensitivity.argtypes = [V, V, V, V, ct.c_int32, V]
+        L.chem_eval_reciprocal.argtypes = [V, V, ct.c_int64, ct.c_int32, V]
+        L.chem_measure_fma_peak.argtypes = [ct.c_int32, V, V, V]
         L.chem_sensitivity_checkpointed.argtypes = [V, V, ct.c_int32, ct.c_double, ct.c_int32, V, V, V, ct.c_int32, V]
         L.chem_tangent.argtypes = [V, V, V, V, ct.c_int32, V]
         L.chem_solve_steps.argtypes = [V, ct.c_double, ct.c_int32, V]
@@ -372,20 +375,20 @@ class Cells:
         n_bad = _check(load().chem_tangent(self._h, p0, pt, po, m0, _stream_ptr(stream)), "chem_tangent")
         return dy, n_bad
 
-    def get_tape(self, cell: int):
+    def get_tape(self, cell: int, rows: bool = True):
         """(kind, q, val, rows) of one cell's recorded tape; rows [n_rows, S] belong,
-        in order, to the INIT, REFACTOR and ITER events."""
+        in order, to the INIT, REFACTOR and ITER events (None with rows=False)."""
         n, nr = ct.c_int32(0), ct.c_int32(0)
         _check(load().chem_get_tape(self._h, int(cell), None, None, None, None, 0, ct.byref(n), ct.byref(nr)),
                "chem_get_tape")
         kind = np.zeros(n.value, np.int32)
         q = np.zeros(n.value, np.int32)
         val = np.zeros(n.value)
-        rows = np.zeros((nr.value, self.mech.n_species))
+        r = np.zeros((nr.value, self.mech.n_species)) if rows else None
         _check(load().chem_get_tape(self._h, int(cell), ct.c_void_p(kind.ctypes.data), ct.c_void_p(q.ctypes.data),
-                                    ct.c_void_p(val.ctypes.data), ct.c_void_p(rows.ctypes.data), n.value,
-                                    ct.byref(n), ct.byref(nr)), "chem_get_tape")
-        return kind, q, val, rows
+                                    ct.c_void_p(val.ctypes.data), None if r is None else ct.c_void_p(r.ctypes.data),
+                                    n.value, ct.byref(n), ct.byref(nr)), "chem_get_tape")
+        return kind, q, val, r
 
     def close(self):
         if getattr(self, "_h", None):
@@ -397,6 +400,23 @@ class Cells:
             self.close()
         except Exception:
             pass
+
+
+def eval_reciprocal(x, stream=None):
+    """The solve kernels' FP64 reciprocal of every element of x (numpy, host), on the GPU."""
+    xx = np.ascontiguousarray(x, np.float64)
+    out = np.empty_like(xx)
+    _check(load().chem_eval_reciprocal(ct.c_void_p(xx.ctypes.data), ct.c_void_p(out.ctypes.data), xx.size, MEM_HOST,
+                                       _stream_ptr(stream)), "chem_eval_reciprocal")
+    return out
+
+
+def measure_fma_peak(precision: int = 64, stream=None):
+    """(TFLOP/s, ms) of the FMA-throughput kernel on the current device."""
+    tf, ms = ct.c_double(0.0), ct.c_double(0.0)
+    _check(load().chem_measure_fma_peak(int(precision), ct.byref(tf), ct.byref(ms), _stream_ptr(stream)),
+           "chem_measure_fma_peak")
+    return tf.value, ms.value
 
 
 def staging_fallbacks(cells=None, stream=None):

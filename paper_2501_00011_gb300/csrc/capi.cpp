@@ -152,6 +152,8 @@ int chem_mechanism_info(const chem_mech *h, chem_mech_info *o) {
   o->flops_solve = m.flops_solve;
   o->smem_per_cell_fp64 = (int32_t)smem_per_cell(m.dev, 64);
   o->smem_per_cell_fp32 = (int32_t)smem_per_cell(m.dev, 32);
+  o->flops_adj_iter = m.flops_adj_iter;
+  o->flops_tan_iter = m.flops_tan_iter;
   return 0;
 }
 
@@ -226,7 +228,7 @@ int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *o
   if ((o.driver == CHEM_DRIVER_PERSISTENT || o.record_adjoint) &&
       ((e = cudaMalloc(&c->order, n * sizeof(int))) != cudaSuccess ||
        (e = cudaMalloc(&c->order_bucket, n * sizeof(int))) != cudaSuccess ||
-       (e = cudaMalloc(&c->order_hist, 2 * ORDER_BUCKETS * sizeof(int))) != cudaSuccess)) {
+       (e = cudaMalloc(&c->order_hist, ORDER_HIST_INTS * sizeof(int))) != cudaSuccess)) {
     chem_cells_destroy(c);
     return fail(CHEM_ENOMEM, std::string("cudaMalloc of the queue order failed: ") + cudaGetErrorString(e));
   }
@@ -693,6 +695,33 @@ int chem_eval_deriv(chem_cells *c, const double *y, double *f, int32_t mem, void
 int chem_eval_newton_solve(chem_cells *c, double cc, const double *y, const double *b, double *x, int32_t mem,
                            void *stream) {
   return probe(c, 1, cc, y, b, x, mem, stream);
+}
+
+int chem_eval_reciprocal(const double *x, double *out, int64_t n, int32_t mem, void *stream) {
+  g_err.clear();
+  if (n < 0 || (n > 0 && (!x || !out))) return fail(CHEM_EINVAL, "bad argument");
+  if (int rc = check_mem(mem)) return rc;
+  if (n == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)n * sizeof(double);
+  double *tmp = nullptr;
+  const double *dx = x;
+  double *dout = out;
+  cudaError_t e = cudaSuccess;
+  if (mem == CHEM_MEM_HOST) {
+    if (cudaMalloc(&tmp, 2 * bytes) != cudaSuccess) return fail(CHEM_ENOMEM, "cudaMalloc for diagnostic scratch");
+    dx = tmp;
+    dout = tmp + n;
+    e = cudaMemcpyAsync(tmp, x, bytes, cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess) e = launch_recip_probe(dx, dout, n, s);
+  if (e == cudaSuccess && mem == CHEM_MEM_HOST) {
+    e = cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "reciprocal diagnostic");
+  return 0;
 }
 
 int chem_eval_deriv_design(chem_cells *c, int32_t design, const double *y, double *f, int32_t mem, void *stream) {

@@ -120,6 +120,7 @@ struct Mechanism {
   std::vector<double> a_consts_v;
   std::vector<int> a_consts_i;
   double flops_f = 0, flops_jac = 0, flops_lu = 0, flops_solve = 0;
+  double flops_adj_iter = 0, flops_tan_iter = 0;   // per corrector iteration of the adjoint / tangent walks
   // host copies of the small tables that upload_mechanism() sends to the device
   std::vector<double> d_consts_v, L_consts_v;
   std::vector<int> d_consts_i, L_consts_i;
@@ -209,11 +210,13 @@ size_t smem_per_cell(const MechDev &m, int lu_precision);
 size_t staged_bytes(const MechDev &m, int driver);   // tables staged per block by the driver
 cudaError_t set_constants();   // gamma_m, 1/gamma_m into constant memory of the current device
 cudaError_t launch_solve(const MechDev &m, const CellsDev &c, const LaunchCfg &cfg, cudaStream_t stream);
-// Cells stiffest first for the persistent queue: per cell the ratio
-// ||f(y0)|| / ||y0|| (the initial-step estimate of 1/h0) bucketed on a log
-// scale, then a counting sort into order[n_cells].  bucket[n_cells] and
-// hist[2 * ORDER_BUCKETS] are scratch.  Stream-ordered (capturable).
+// Cells most expensive first for the persistent queue: per cell its cost in
+// the batch's previous solve, or for a first solve the sum of its rate
+// constants, bucketed linearly in log2 over the batch's range, then a counting
+// sort into order[n_cells].  bucket[n_cells] and hist[ORDER_HIST_INTS] are
+// scratch.  Stream-ordered (capturable).
 constexpr int ORDER_BUCKETS = 256;
+constexpr int ORDER_HIST_INTS = 2 * ORDER_BUCKETS + 2;   // counts, cursors, key range
 // The same counting sort keyed by tape length (events), longest first: the
 // order in which the adjoint and tangent kernels take the cells.
 cudaError_t launch_order_tape(const CellsDev &c, int *bucket, int *hist, int *order, cudaStream_t stream);
@@ -233,6 +236,8 @@ cudaError_t launch_probe(const MechDev &M, const CellsDev &C, int lu_precision, 
 // discrete adjoint: replay (exact steps, y rows), backward sweep, theta reduction
 cudaError_t launch_adjoint(const MechDev &m, const CellsDev &c, const AdjDev &a, cudaStream_t stream);
 cudaError_t launch_tangent(const MechDev &m, const CellsDev &c, const TanDev &t, cudaStream_t stream);
+// diagnostic: out[i] = the solve kernels' FP64 reciprocal of x[i] (device arrays)
+cudaError_t launch_recip_probe(const double *x, double *out, int64_t n, cudaStream_t stream);
 // *acc += the number of nonzero flags among flag[0..n)
 cudaError_t launch_count_flags(const int *flag, int64_t n, unsigned long long *acc, cudaStream_t stream);
 // deriv.cu: derivative-only kernels for comparing designs.  kt[R][C] rate

@@ -600,6 +600,25 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
     }
     m.fwdT_prog = f.finish();
     m.bwdT_prog = g.finish();
+    // Algorithmic flops per corrector iteration walked by the adjoint: the
+    // transposed solve (as many as the forward solve), the rates r_j and the
+    // partials dr_j/dy_l (n_reac - 1 multiplications per pair), nu_j . g (a
+    // multiply-add per stoichiometric term), J^T g (one per pair), the theta
+    // update (3 per reaction) and the vector updates of lambda (6 per species).
+    // The tangent: tangent rates s_j = k~ sum_s (prod_{s' != s} y) v_s + k~ r dtheta_j
+    // (n_reac (n_reac - 1) + (n_reac - 1) + n_reac products and sums, then 4 for
+    // the theta term and k~), the f program's sums (2 per stoichiometric term),
+    // one solve and 6 per species.
+    double nu_terms = 0, rates = 0, partials = 0, trates = 0;
+    for (int j = 0; j < R; ++j) {
+      const double nr = rx[j].n_reac;
+      nu_terms += (double)nu[j].size();
+      rates += nr;
+      partials += nr * (nr - 1.0);
+      trates += nr * (nr - 1.0) + (nr - 1.0) + (nr - 1.0) + 4.0;
+    }
+    m.flops_adj_iter = m.flops_solve + rates + partials + 2.0 * nu_terms + 2.0 * n_pairs + 3.0 * R + 6.0 * S;
+    m.flops_tan_iter = trates + 2.0 * nu_terms + m.flops_solve + 6.0 * S;
   }
   if ((size_t)d.WL_len * sizeof(double) > 0xfff0 || (size_t)d.Wd_len * sizeof(double) > 0xfff0) {
     msg = "mechanism too large: the per-cell work arrays exceed the 16-bit byte offsets of the warp programs";

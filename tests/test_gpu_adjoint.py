@@ -109,13 +109,13 @@ def test_gpu_adjoint_per_component_fd(oracle_lib, cg):
     # component by component: central differences (step 1e-6) of the oracle's
     # replay of the GPU tapes, the iteration matrices held at the recorded run's,
     # against the GPU gradient to 1e-5 relative, on 20 log rate constants (the 12
-    # with the largest |dL/dtheta_j| and 8 more drawn at random above 1e-3 of the
+    # with the largest |dL/dtheta_j| and 8 more drawn at random above 1e-2 of the
     # largest) and, per cell, on the 20 initial concentrations through which L
     # moves most (largest |dL/dy0_i y0_i|; the step is 1e-6 y0_i).  The floor:
-    # the replay's own rounding (about 1e-14 of L) divided by the step puts the
-    # difference quotient's error near 5e-9 of the largest component, so 1e-5
-    # relative is checkable from 1e-3 of the largest component up (measured on
-    # the oracle's own tapes: 5e-6 at 1.7e-3, 3e-5 at 1.5e-4).
+    # the loss is evaluated to a few ulp, so the difference quotient carries an
+    # error of about 4e-16 |L| / 2e-6 = 2e-10 |L|; here the largest |dL/dtheta_j|
+    # is about 0.017 |L|, so 1e-5 relative is checkable from 1e-2 of it up
+    # (observed: 1.3e-5 at about 1e-3 of the largest, 2.8e-6 at 1.7e-3).
     wl = synth.workload_adjoint(8)
     n_cells, n_steps = 3, 4
     m, c, cells, w, gth, gy0 = _run(cg, wl, n_cells, n_steps)
@@ -131,7 +131,7 @@ def test_gpu_adjoint_per_component_fd(oracle_lib, cg):
     R = wl.mech.n_reactions
     rng = np.random.default_rng(5)
     order = np.argsort(-np.abs(gth))
-    above = np.nonzero(np.abs(gth) >= 1e-3 * np.abs(gth).max())[0]
+    above = np.nonzero(np.abs(gth) >= 1e-2 * np.abs(gth).max())[0]
     pick = np.unique(np.concatenate([order[:12], rng.choice(np.setdiff1d(above, order[:12]), 8, replace=False)]))
     worst = 0.0
     for j in pick:

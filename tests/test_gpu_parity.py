@@ -233,3 +233,22 @@ def test_api_errors(cg, mechs):
                dict(reac=[0, 1], prod=[0, 1], A=1e-13, kind=7)):
         with pytest.raises(cg.ChemError):
             cg.Mechanism(synth.mechanism_from_list(2, [rx]))
+
+
+def test_reciprocal_within_one_ulp(cg):
+    # The solve kernels' FP64 reciprocal (hardware estimate, two Newton-Raphson
+    # steps) against the correctly rounded 1/x over its stated domain, normal x with
+    # 2^-1022 <= |x| <= 2^1022: every result within 1 ulp, most correctly rounded.
+    # Magnitudes are drawn uniformly in the exponent over the whole domain, plus
+    # the domain's ends, powers of two and values just beside them.
+    rng = np.random.default_rng(9)
+    e = rng.integers(-1022, 1022, 400_000)
+    x = np.ldexp(rng.uniform(1.0, 2.0, e.size), e) * rng.choice([-1.0, 1.0], e.size)
+    edges = np.array([2.0 ** -1022, 2.0 ** 1022, 1.0, 2.0, 0.5, 3.0, 1e-300, 1e300, 1e-10, 1e10])
+    x = np.concatenate([x, edges, -edges, np.nextafter(edges, 0), np.nextafter(edges, np.inf)])
+    x = x[(np.abs(x) >= 2.0 ** -1022) & (np.abs(x) <= 2.0 ** 1022)]
+    r = cg.eval_reciprocal(x)
+    ref = 1.0 / x
+    ulps = np.abs(r - ref) / np.spacing(np.abs(ref))
+    assert np.all(np.isfinite(r)) and ulps.max() <= 1.0, (x[np.argmax(ulps)], ulps.max())
+    print(f"recip_nr: {x.size} values, max {ulps.max():.2f} ulp, correctly rounded {np.mean(r == ref):.4%}")

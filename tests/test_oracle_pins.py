@@ -273,18 +273,32 @@ def test_fixed_order_convergence_slope(oracle_lib, k):
 # -------------------------------------------------- adaptive solve vs closed forms
 
 # A locally error-controlled BDF accumulates global error over its accepted
-# steps.  On these non-expanding problems (linear decay, relaxation to
-# equilibrium, second-order decay) an error made at one step is never
-# amplified later, so the global error is at most the sum of the local errors.
-# A weighted-RMS local error of 1 allows sqrt(S) on one component, and the
-# estimate d/(q+1) is asymptotic, hence the bound 2 sqrt(S) x (accepted steps)
-# x tolerance; separately the error must shrink with the tolerance.  scipy's BDF lands at 1.5-47x the local
-# tolerance on the same problems.
-def _check_global(y, ref, rtol, atol, st):
+# steps, so its global error is not bounded by the tolerance alone: on these
+# problems it reaches 0.0003 to 120 tolerance units (rtol |y| + atol).  What
+# pins the controller (its error estimate, error constant, step-size and order
+# selection) is an independent implementation of the same method family:
+# scipy's variable-order BDF/NDF (Shampine & Reichelt's quasi-constant-step
+# backward differences), run on the same problem, tolerance and closed-form
+# reference.  The oracle's global error must lie within 4x of scipy's (or below
+# 2 tolerance units) and its accepted steps within 0.5x..2x of scipy's: an
+# error constant or bias off by a factor 10 moves both well outside.  Measured
+# ratios of the errors: 0.7-3.1 (one case at 1.9 units against 0.18), of the
+# steps: 0.86-1.15.
+def _check_global(y, ref, rtol, atol, st, problem=None):
     assert st["status"] == 0
-    err = np.abs(y - ref) / (rtol * np.abs(ref) + atol)
-    bound = 2.0 * math.sqrt(y.size) * max(5, st["steps"])
-    assert err.max() <= bound, (err.max(), st["steps"])
+    err = float(np.max(np.abs(y - ref) / (rtol * np.abs(ref) + atol)))
+    if problem is None:
+        assert err <= 2.0, err
+        return
+    scipy_integrate = pytest.importorskip("scipy.integrate")
+    oracle_lib, m, kt, y0, t_end = problem
+    sol = scipy_integrate.solve_ivp(lambda t, yy: oracle_lib.deriv(m, kt, yy), (0.0, t_end), y0, method="BDF",
+                                    rtol=rtol, atol=atol, jac=lambda t, yy: oracle_lib.jacobian(m, kt, yy))
+    assert sol.success
+    err_ref = float(np.max(np.abs(sol.y[:, -1] - ref) / (rtol * np.abs(ref) + atol)))
+    steps_ref = sol.t.size - 1
+    assert err <= max(4.0 * err_ref, 2.0), (err, err_ref)
+    assert 0.5 * steps_ref <= st["steps"] <= 2.0 * steps_ref, (st["steps"], steps_ref)
 
 
 def test_adaptive_chain_stiff(oracle_lib):
@@ -293,9 +307,9 @@ def test_adaptive_chain_stiff(oracle_lib):
     kt = oracle_lib.rate_constants(m, 300.0, 1e5)
     y0 = np.array([1.0, 0.0, 0.0])
     rtol, atol = 1e-6, 1e-12
-    y, st = oracle_lib.integrate(m, kt, y0, 600.0, rtol, atol)
-    assert st["status"] == 0
-    _check_global(y, chain_exact(600.0, y0, k1, k2), rtol, atol, st)
+    for rtol, atol in ((1e-4, 1e-12), (1e-6, 1e-12), (1e-8, 1e-12)):
+        y, st = oracle_lib.integrate(m, kt, y0, 600.0, rtol, atol)
+        _check_global(y, chain_exact(600.0, y0, k1, k2), rtol, atol, st, (oracle_lib, m, kt, y0, 600.0))
 
 
 def test_adaptive_error_shrinks_with_tolerance(oracle_lib):
@@ -312,6 +326,69 @@ def test_adaptive_error_shrinks_with_tolerance(oracle_lib):
     assert errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10
 
 
+def _accepted_orders(tape):
+    return tape.q[tape.kind == 2]
+
+
+@pytest.mark.parametrize("qmax", [5, 3])
+def test_order_selection_climbs_to_qmax_on_smooth_decay(oracle_lib, qmax):
+    # y' = -0.01 y over 600 s: a smooth problem on which a variable-order BDF
+    # starts at order 1 and raises the order to its cap (the higher-order error
+    # estimate wins once the solution is resolved); the hysteresis rule holds:
+    # the order only changes after q + 1 accepted steps at order q
+    m = synth.mechanism_from_list(2, [dict(reac=[0], prod=[1], A=0.01)])
+    kt = oracle_lib.rate_constants(m, 300.0, 1e5)
+    y, st, tape = oracle_lib.integrate(m, kt, np.array([1.0, 0.0]), 600.0, 1e-6, 1e-12, max_order=qmax,
+                                       tape_cap=5000)
+    assert st["status"] == 0
+    q = _accepted_orders(tape)
+    assert q[0] == 1 and q.max() == qmax and st["final_order"] == qmax
+    assert np.all(np.diff(q) >= 0) and np.all(np.diff(q) <= 1)      # never down, one order at a time
+    runs = np.diff(np.concatenate([[0], np.nonzero(np.diff(q))[0] + 1]))   # lengths of runs before each change
+    assert np.all(runs >= q[np.cumsum(runs) - 1] + 1), runs
+
+
+def test_order_drops_after_repeated_error_failures(oracle_lib):
+    # a stiff transient after a smooth stretch: A -> B (slow) plus a fast pair that
+    # a high-order step overshoots; after three error-test failures in one step the
+    # order is lowered (the order sequence goes down at least once)
+    k1, k2 = 50.0, 0.02
+    m = chain_mechanism(k1, k2)
+    kt = oracle_lib.rate_constants(m, 300.0, 1e5)
+    y, st, tape = oracle_lib.integrate(m, kt, np.array([1.0, 0.0, 0.0]), 600.0, 1e-6, 1e-12, tape_cap=20000)
+    assert st["status"] == 0 and st["rejects"] > 0
+    q = _accepted_orders(tape)
+    assert q.max() >= 3 and np.any(np.diff(q) < 0)
+
+
+@pytest.mark.parametrize("case", ["two_norms", "tiny_state", "no_dynamics"])
+def test_initial_step_hand_worked(oracle_lib, case):
+    # The starting step of the Hairer-Norsett-Wanner heuristic (Solving ODEs I,
+    # II.4) worked by hand for the linear problem A -> B, y' = K y with
+    # K = [[-k, 0], [k, 0]], y0 = (a, 0), dt = 600 s, weights w = 1/(rtol |y0| + atol):
+    #   d0 = ||y0||, d1 = ||K y0||, h0 = 0.01 d0/d1 (1e-6 dt if d0 or d1 < 1e-5);
+    #   for a linear f, f(y0 + h0 f0) - f(y0) = h0 K^2 y0 exactly, so
+    #   d2 = ||K^2 y0|| = k ||K y0|| = k d1;
+    #   h1 = sqrt(0.01 / max(d1, d2)) (max(1e-6 dt, 1e-3 h0) if max(d1, d2) <= 1e-15);
+    #   h = min(100 h0, h1, dt).
+    # two_norms: k = 2, a = 1, rtol 1e-2, atol 1: w = (1/1.01, 1),
+    #   d1 = 2 sqrt((1/1.01^2 + 1)/2), d2 = 2 d1, h = sqrt(0.01 / d2) (h0 = 0.01 d0/d1 makes 100 h0
+    #   the larger);
+    # tiny_state: k = 2, a = 1e-7, atol 1: d0 < 1e-5, h0 = 1e-6 * 600, h = 100 h0 = 0.06;
+    # no_dynamics: k = 1e-20, a = 1, atol 1: d1 < 1e-5, h0 = 6e-4, max(d1, d2) <= 1e-15,
+    #   h1 = max(6e-4, 6e-7), h = 6e-4.
+    k, a, rtol, atol = {"two_norms": (2.0, 1.0, 1e-2, 1.0), "tiny_state": (2.0, 1e-7, 1e-2, 1.0),
+                        "no_dynamics": (1e-20, 1.0, 1e-2, 1.0)}[case]
+    expect = {"two_norms": math.sqrt(0.01 / (2.0 * 2.0 * math.sqrt((1.0 / 1.01 ** 2 + 1.0) / 2.0))),
+              "tiny_state": 0.06, "no_dynamics": 6e-4}[case]
+    m = synth.mechanism_from_list(2, [dict(reac=[0], prod=[1], A=k)])
+    kt = oracle_lib.rate_constants(m, 300.0, 1e5)
+    assert kt[0] == pytest.approx(k, rel=1e-15)
+    _, _, tape = oracle_lib.integrate(m, kt, np.array([a, 0.0]), 600.0, rtol, atol, tape_cap=100000)
+    assert tape.kind[0] == 0
+    assert tape.val[0] == pytest.approx(expect, rel=1e-12), (tape.val[0], expect)
+
+
 def test_adaptive_reversible_pair(oracle_lib):
     kf, kb = 3.0, 1.0
     m = synth.mechanism_from_list(2, [dict(reac=[0], prod=[1], A=kf), dict(reac=[1], prod=[0], A=kb)])
@@ -322,7 +399,7 @@ def test_adaptive_reversible_pair(oracle_lib):
         y, st = oracle_lib.integrate(m, kt, y0, t_end, rtol, atol)
         Aeq = (y0.sum()) * kb / (kf + kb)
         A = Aeq + (y0[0] - Aeq) * math.exp(-(kf + kb) * t_end)
-        _check_global(y, np.array([A, y0.sum() - A]), rtol, atol, st)
+        _check_global(y, np.array([A, y0.sum() - A]), rtol, atol, st, (oracle_lib, m, kt, y0, t_end))
 
 
 def test_adaptive_paper_test_mechanism(oracle_lib):
@@ -344,7 +421,7 @@ def test_adaptive_paper_test_mechanism(oracle_lib):
         ks = k1 + k2
         A = y0[0] * math.exp(-ks * 600.0)
         ref = np.array([A, y0[1] + (y0[0] - A) * k1 / ks, y0[2] + (y0[0] - A) * k2 / ks])
-        _check_global(y, ref, rtol, atol, st)
+        _check_global(y, ref, rtol, atol, st, (oracle_lib, m, kt, y0, 600.0))
 
 
 def test_adaptive_second_order_self_reaction(oracle_lib):
@@ -358,7 +435,7 @@ def test_adaptive_second_order_self_reaction(oracle_lib):
     y, st = oracle_lib.integrate(m, kt, y0, 600.0, rtol, atol)
     assert st["status"] == 0
     A = 1.0 / (1.0 / y0[0] + 2.0 * kt[0] * 600.0)
-    _check_global(y, np.array([A, (y0[0] - A) / 2.0]), rtol, atol, st)
+    _check_global(y, np.array([A, (y0[0] - A) / 2.0]), rtol, atol, st, (oracle_lib, m, kt, y0, 600.0))
 
 
 def test_adaptive_small_mechanism_vs_radau(oracle_lib):
@@ -372,8 +449,9 @@ def test_adaptive_small_mechanism_vs_radau(oracle_lib):
         sol = scipy_integrate.solve_ivp(lambda t, yy: oracle_lib.deriv(m, kt, yy), (0.0, wl.dt),
                                         wl.cells.y[:, c], method="Radau", rtol=1e-12, atol=1e-20,
                                         jac=lambda t, yy: oracle_lib.jacobian(m, kt, yy))
-        _check_global(y[:, c], sol.y[:, -1], wl.rtol, wl.atol,
-                      {k: st[k][c] for k in ("status", "steps")})
+        # Radau at rtol 1e-12 is the reference; scipy's BDF at the workload's tolerance the comparison
+        _check_global(y[:, c], sol.y[:, -1], wl.rtol, wl.atol, {k: st[k][c] for k in ("status", "steps")},
+                      (oracle_lib, m, kt, wl.cells.y[:, c], wl.dt))
 
 
 # ------------------------------------------------------ invariants and status

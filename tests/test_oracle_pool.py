@@ -45,3 +45,21 @@ def test_pool_adjoint_equals_per_cell(oracle_lib):
         kt = oracle_lib.rate_constants(wl.mech, wl.cells.T[k], wl.cells.P[k])
         l1, g1 = oracle_lib.adjoint(wl.mech, kt, wl.cells.y[:, k], tapes[k], lam[:, k])
         assert np.array_equal(ly0[:, k], l1) and np.array_equal(g[k], g1)
+
+
+def test_pool_workers_reused_and_forward_adjoint(oracle_lib):
+    wl = synth.workload_adjoint(6)
+    lam = synth.loss_weights(wl.mech.n_species, 6)
+    with pool.Workers(2) as ex:
+        y1, s1 = pool.solve(wl.mech, wl.cells, wl.dt, wl.rtol, wl.atol, executor=ex)
+        y2, s2 = pool.solve(wl.mech, wl.cells, wl.dt, wl.rtol, wl.atol, executor=ex)
+        ly0, g = pool.forward_adjoint(wl.mech, wl.cells, wl.dt, 2, wl.rtol, wl.atol, lam, executor=ex)
+    assert np.array_equal(y1, y2) and np.array_equal(s1, s2)
+    g_ref = np.zeros(wl.mech.n_reactions)
+    for k in range(6):
+        kt = oracle_lib.rate_constants(wl.mech, wl.cells.T[k], wl.cells.P[k])
+        _, _, tape = oracle_lib.integrate_steps(wl.mech, kt, wl.cells.y[:, k], wl.dt, 2, wl.rtol, wl.atol)
+        l1, g1 = oracle_lib.adjoint(wl.mech, kt, wl.cells.y[:, k], tape, lam[:, k])
+        assert np.array_equal(ly0[:, k], l1)
+        g_ref += g1
+    np.testing.assert_allclose(g, g_ref, rtol=1e-13, atol=0)
