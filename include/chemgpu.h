@@ -157,8 +157,8 @@ typedef struct {
                                       their cost in the previous solve. */
   int32_t stage_wait;              /* persistent driver, test hook: polls of the bounded wait for a
                                       block's bulk copy of the tables into shared memory.  0 (default):
-                                      2^22; -1: none, so every block reads the tables from global
-                                      memory instead (the same bytes; results are identical) and
+                                      2^22; -1: none, so every block copies the tables with ordinary
+                                      loads instead (the same bytes; results are identical) and
                                       counts a fallback, see chem_staging_fallbacks */
 } chem_opts;
 
@@ -273,9 +273,9 @@ int chem_get_stats(const chem_cells *cells, chem_cell_stats *out, int32_t mem, v
 /* Staging counters of the last chem_solve_step / chem_solve_steps call on the
  * batch (persistent driver; every step of a graph launch): *fallbacks = blocks
  * whose bulk copy of the tables into shared memory was not seen to land within
- * the bounded wait (they read the tables from global memory: same results,
- * slower); *unfinished = blocks that exited before such a late copy was seen
- * to land within a second bounded wait.  Both are 0 in normal operation.  With
+ * the bounded wait (they copied the tables with ordinary loads: same results);
+ * *unfinished = blocks that exited before such a late copy was seen to land
+ * within a second bounded wait.  Both are 0 in normal operation.  With
  * cells NULL: the counters of chem_solve_step_noalloc's last call on the
  * current device.  Reads on stream and synchronises it.  The paper has no
  * counterpart (it is a diagnostic of this library's table staging).  Errors:

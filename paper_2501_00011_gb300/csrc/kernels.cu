@@ -950,10 +950,11 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
 
 // Stage the table blob into the first `bytes` of shared memory with one TMA
 // bulk copy.  The wait is bounded (`limit` polls of the barrier); if it runs
-// out, the block counts the event in stage[0] and returns false, and the
-// caller reads the tables from the blob in global memory instead (the same
-// bytes), leaving the staged region to the late copy.  Nothing else is placed
-// in that region, so a late copy cannot overwrite live data.
+// out, the block counts the event in stage[0] and copies the blob with
+// ordinary loads instead.  A late bulk copy then writes the same bytes to the
+// same place, so whichever lands last leaves the tables intact; the block
+// waits (bounded again) for that copy before it exits.  Keeping the tables in
+// shared memory on both paths lets every table read use shared-memory loads.
 __device__ bool stage_tables(const unsigned char *blob, int bytes, unsigned char *smem, uint64_t *bar,
                              unsigned long long *stage, long long limit) {
   if (threadIdx.x == 0) mbar_init(bar, 1);
@@ -963,7 +964,13 @@ __device__ bool stage_tables(const unsigned char *blob, int bytes, unsigned char
     tma_load_1d(smem, blob, (uint32_t)bytes, bar);
   }
   const bool ok = __syncthreads_and(mbar_wait(bar, 0, limit));
-  if (!ok && threadIdx.x == 0 && stage) atomicAdd(stage, 1ull);
+  if (!ok) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(blob);
+    uint4 *dst = reinterpret_cast<uint4 *>(smem);
+    for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    if (threadIdx.x == 0 && stage) atomicAdd(stage, 1ull);
+  }
   return ok;
 }
 
@@ -980,7 +987,7 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const
   bool staged_ok = true;
   if (STAGED) {
     staged_ok = stage_tables(M.blob[P.prec], P.tab_bytes, smem, &tma_bar, C.stage, P.stage_wait);
-    tb.base = staged_ok ? smem : M.blob[P.prec];
+    tb.base = smem;
   } else {
     tb.base = M.blob[P.prec];
   }

@@ -23,8 +23,10 @@ from paper_2501_00011_gb300 import synth  # noqa: E402
 
 from parity_util import FLOOR, compare, oracle_steps, sample_cells  # noqa: E402
 
-# Flipped plus rounding-limited cells allowed at full size.
-MAX_ODD_FRAC = 0.03
+# Flipped plus rounding-limited cells allowed at full size: 0.6% of the cells.
+# Measured: 34 of the 10,000 headline cells (0.34%), 107 of the 50,000 batching
+# cells after six steps (0.21%), 8 of the 2,048 adjoint cells (0.39%).
+MAX_ODD_FRAC = 0.006
 
 
 @pytest.fixture(scope="module")
