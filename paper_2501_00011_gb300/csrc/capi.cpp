@@ -809,10 +809,12 @@ int chem_sensitivity(chem_cells *c, const double *dL_dy, double *dL_dtheta, doub
   ad.gcell = c->gcell;
   ad.dLdtheta = c->dLdtheta;
   ad.accumulate = 0;
-  // the longest tapes first
-  if ((e = launch_order_tape(cd, c->order_bucket, c->order_hist, c->order, s)) != cudaSuccess)
+  // the longest tapes first, popped from the batch's work counter
+  if ((e = launch_order_tape(cd, c->order_bucket, c->order_hist, c->order, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long), s)) != cudaSuccess)
     return cuda_fail(e, "adjoint order");
   cd.order = c->order;
+  cd.queue = c->counters;
   if ((e = launch_adjoint(c->mech->m.dev, cd, ad, s)) != cudaSuccess) return cuda_fail(e, "adjoint kernels");
   if ((e = cudaMemcpyAsync(dL_dy0, c->dLdy0, n * S * sizeof(double), kind_out(mem), s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(dL_dtheta, c->dLdtheta, R * sizeof(double), kind_out(mem), s)) != cudaSuccess)
@@ -864,9 +866,11 @@ int chem_sensitivity_checkpointed(chem_cells *c, const double *states, int32_t n
         return cuda_fail(e, "checkpointed re-solve");
     }
     CellsDev ca = cd;
-    if ((e = launch_order_tape(ca, c->order_bucket, c->order_hist, c->order, s)) != cudaSuccess)
+    if ((e = launch_order_tape(ca, c->order_bucket, c->order_hist, c->order, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long), s)) != cudaSuccess)
       return cuda_fail(e, "adjoint order");
     ca.order = c->order;
+    ca.queue = c->counters;
     AdjDev ad{};
     ad.dLdy = lin;
     ad.dLdy0 = lout;
@@ -923,9 +927,11 @@ int chem_tangent(chem_cells *c, const double *dy0, const double *dtheta, double 
   td.dy0 = c->dLdy;
   td.dtheta = (dtheta && R > 0) ? c->dLdtheta : nullptr;
   td.dy = c->dLdy0;
-  if ((e = launch_order_tape(cd, c->order_bucket, c->order_hist, c->order, s)) != cudaSuccess)
+  if ((e = launch_order_tape(cd, c->order_bucket, c->order_hist, c->order, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long), s)) != cudaSuccess)
     return cuda_fail(e, "tangent order");
   cd.order = c->order;
+  cd.queue = c->counters;
   if ((e = launch_tangent(c->mech->m.dev, cd, td, s)) != cudaSuccess) return cuda_fail(e, "tangent kernel");
   if ((e = cudaMemcpyAsync(dy, c->dLdy0, n * S * sizeof(double), kind_out(mem), s)) != cudaSuccess)
     return cuda_fail(e, "tangent copy-out");

@@ -1454,19 +1454,29 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) adjoint_kernel(con
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & (WARP - 1);
   const int warp = threadIdx.x / WARP;
-  const int64_t slot = (int64_t)blockIdx.x * P.warps_per_block + warp;
-  if (slot >= C.n_cells) return;
-  const int64_t cell = C.order ? (int64_t)C.order[slot] : slot;
   Tabs tb;
   tb.base = tb.gbase = M.blob[0];
   double *Wd = reinterpret_cast<double *>(smem + (size_t)warp * P.cell_bytes);
   double *WL = Wd + P.wd_pad;
-  if (C.tape_bad[cell]) {
-    for (int i = lane; i < M.S; i += WARP) A.dLdy0[(int64_t)i * C.n_cells + cell] = 0.0;
-    for (int j = lane; j < M.R; j += WARP) A.gcell[(int64_t)j * C.n_cells + cell] = 0.0;
-    return;
+  // with a queue, every warp takes the next slot of C.order (longest tapes
+  // first) until none is left; without one, slot = its global warp index
+  for (int64_t slot = (int64_t)blockIdx.x * P.warps_per_block + warp;;) {
+    if (C.queue) {
+      long long q = 0;
+      if (lane == 0) q = (long long)atomicAdd(C.queue, 1ull);
+      slot = __shfl_sync(FULL, q, 0);
+    }
+    if (slot >= C.n_cells) break;
+    const int64_t cell = C.order ? (int64_t)C.order[slot] : slot;
+    if (C.tape_bad[cell]) {
+      for (int i = lane; i < M.S; i += WARP) A.dLdy0[(int64_t)i * C.n_cells + cell] = 0.0;
+      for (int j = lane; j < M.R; j += WARP) A.gcell[(int64_t)j * C.n_cells + cell] = 0.0;
+    } else {
+      backward_cell<KS>(M, C, A, P, tb, Wd, WL, lane, cell);
+    }
+    __syncwarp();
+    if (!C.queue) break;
   }
-  backward_cell<KS>(M, C, A, P, tb, Wd, WL, lane, cell);
 }
 
 // ---------------------------------------------------------------- tangent
@@ -1668,26 +1678,73 @@ __global__ void __launch_bounds__(ADJ_WARPS_PER_BLOCK * WARP) tangent_kernel(con
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & (WARP - 1);
   const int warp = threadIdx.x / WARP;
-  const int64_t slot = (int64_t)blockIdx.x * P.warps_per_block + warp;
-  if (slot >= C.n_cells) return;
-  const int64_t cell = C.order ? (int64_t)C.order[slot] : slot;
   Tabs tb;
   tb.base = tb.gbase = M.blob[0];
   double *Wd = reinterpret_cast<double *>(smem + (size_t)warp * P.cell_bytes);
   double *WL = Wd + P.wd_pad;
-  if (C.tape_bad[cell]) {
-    for (int i = lane; i < M.S; i += WARP) A.dy[(int64_t)i * C.n_cells + cell] = 0.0;
-    return;
+  for (int64_t slot = (int64_t)blockIdx.x * P.warps_per_block + warp;;) {   // as in adjoint_kernel
+    if (C.queue) {
+      long long q = 0;
+      if (lane == 0) q = (long long)atomicAdd(C.queue, 1ull);
+      slot = __shfl_sync(FULL, q, 0);
+    }
+    if (slot >= C.n_cells) break;
+    const int64_t cell = C.order ? (int64_t)C.order[slot] : slot;
+    if (C.tape_bad[cell]) {
+      for (int i = lane; i < M.S; i += WARP) A.dy[(int64_t)i * C.n_cells + cell] = 0.0;
+    } else {
+      tangent_cell<KS>(M, C, A, P, tb, Wd, WL, lane, cell);
+    }
+    __syncwarp();
+    if (!C.queue) break;
   }
-  tangent_cell<KS>(M, C, A, P, tb, Wd, WL, lane, cell);
+}
+
+// Cells per block of a walk kernel: the block size that keeps the most cells
+// resident per SM (shared memory bounds the walks' occupancy), ties to the
+// smaller block.  The kernel's dynamic shared-memory limit must be raised first.
+template <typename K>
+int walk_warps_per_block(K kernel, int cell_bytes, int *blocks_per_sm) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int best_w = 0, best_cells = 0;
+  *blocks_per_sm = 0;
+  for (int w = 1; w <= ADJ_WARPS_PER_BLOCK && (long)w * cell_bytes <= (long)optin; ++w) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, w * WARP, (size_t)w * cell_bytes) != cudaSuccess)
+      continue;
+    if (w * nb > best_cells) {
+      best_cells = w * nb;
+      best_w = w;
+      *blocks_per_sm = nb;
+    }
+  }
+  return best_w;
+}
+
+// Grid of a walk launch: with the queue, enough resident blocks to fill every
+// SM (never more than the cells need); without, one warp per cell.
+int walk_blocks(const CellsDev &C, int warps_per_block, int blocks_per_sm) {
+  const int64_t need = (C.n_cells + warps_per_block - 1) / warps_per_block;
+  if (!C.queue) return (int)need;
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t full = (int64_t)n_sm * (blocks_per_sm > 0 ? blocks_per_sm : 1);
+  return (int)(full < need ? full : need);
 }
 
 template <int KS>
-cudaError_t launch_tan_t(const MechDev &M, const CellsDev &C, const TanDev &A, const SolveParams &P, cudaStream_t stream) {
-  const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
+cudaError_t launch_tan_t(const MechDev &M, const CellsDev &C, const TanDev &A, const SolveParams &P0, cudaStream_t stream) {
   cudaError_t e = allow_max_smem<tangent_kernel<KS>>();
   if (e != cudaSuccess) return e;
-  const int blocks = (int)((C.n_cells + P.warps_per_block - 1) / P.warps_per_block);
+  SolveParams P = P0;
+  int bps = 0;
+  P.warps_per_block = walk_warps_per_block(tangent_kernel<KS>, P.cell_bytes, &bps);
+  if (P.warps_per_block < 1) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
+  const int blocks = walk_blocks(C, P.warps_per_block, bps);
   tangent_kernel<KS><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, A, P);
   return cudaGetLastError();
 }
@@ -1709,11 +1766,15 @@ __global__ void count_flags_kernel(const int *flag, int64_t n, unsigned long lon
 }
 
 template <int KS>
-cudaError_t launch_adj_t(const MechDev &M, const CellsDev &C, const AdjDev &A, const SolveParams &P, cudaStream_t stream) {
-  const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
+cudaError_t launch_adj_t(const MechDev &M, const CellsDev &C, const AdjDev &A, const SolveParams &P0, cudaStream_t stream) {
   cudaError_t e = allow_max_smem<adjoint_kernel<KS>>();
   if (e != cudaSuccess) return e;
-  const int blocks = (int)((C.n_cells + P.warps_per_block - 1) / P.warps_per_block);
+  SolveParams P = P0;
+  int bps = 0;
+  P.warps_per_block = walk_warps_per_block(adjoint_kernel<KS>, P.cell_bytes, &bps);
+  if (P.warps_per_block < 1) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
+  const int blocks = walk_blocks(C, P.warps_per_block, bps);
   adjoint_kernel<KS><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, A, P);
   return cudaGetLastError();
 }
@@ -2049,14 +2110,6 @@ cudaError_t launch_adjoint(const MechDev &M, const CellsDev &C, const AdjDev &A,
   P.cell_bytes = (int)(((size_t)P.wd_pad * sizeof(double) + (size_t)M.WL_len * sizeof(double) + 15) & ~(size_t)15);
   P.prec = 0;
   P.tab_bytes = 0;
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  // several cells per block, as many as shared memory allows up to the cap
-  int w = optin / P.cell_bytes;
-  if (w > ADJ_WARPS_PER_BLOCK) w = ADJ_WARPS_PER_BLOCK;
-  if (w < 1) return cudaErrorInvalidValue;
-  P.warps_per_block = w;
   cudaError_t e = cudaSuccess;
   switch ((M.S + WARP - 1) / WARP) {
     case 1: e = launch_adj_t<1>(M, C, A, P, stream); break;
@@ -2079,16 +2132,11 @@ cudaError_t launch_count_flags(const int *flag, int64_t n, unsigned long long *a
 cudaError_t launch_tangent(const MechDev &M, const CellsDev &C, const TanDev &A, cudaStream_t stream) {
   if (C.n_cells <= 0) return cudaSuccess;
   SolveParams P{};
-  P.wd_pad = (M.Wda_len + 1) & ~1;
+  // the tangent walk uses the forward's Wd and one species vector after it
+  // (the direction v at a_MU), not the adjoint's extended array
+  P.wd_pad = (M.a_MU + M.S + 1) & ~1;
   P.cell_bytes = (int)(((size_t)P.wd_pad * sizeof(double) + (size_t)M.WL_len * sizeof(double) + 15) & ~(size_t)15);
   P.prec = 0;
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  int w = optin / P.cell_bytes;
-  if (w > ADJ_WARPS_PER_BLOCK) w = ADJ_WARPS_PER_BLOCK;
-  if (w < 1) return cudaErrorInvalidValue;
-  P.warps_per_block = w;
   switch ((M.S + WARP - 1) / WARP) {
     case 1: return launch_tan_t<1>(M, C, A, P, stream);
     case 2: return launch_tan_t<2>(M, C, A, P, stream);

@@ -539,10 +539,15 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
   // (the forward prefix keeps y, ONE, ZERO and k~ where the forward tables
   // expect them) and the transposed triangular solves on WL.
   {
+    // The partials dr_j/dy_l (PP) share the per-cell slice with the iteration
+    // matrix's pair products (WL[L_P], FP64 in the adjoint): the walk forms and
+    // factors M before it computes the partials of a step's iterations, and the
+    // factored M no longer reads its pair products, so the two never overlap in
+    // time.  Element index from the start of Wd: the extended Wd rounded to an
+    // even length (where WL starts), then L_P.
     d.a_MU = d.Wd_len;
     d.a_NM = d.a_MU + S;
-    d.a_PP = d.a_NM + R;
-    d.a_JTM = d.a_PP + n_pairs;
+    d.a_JTM = d.a_NM + R;
     d.a_G = d.a_JTM + S;
     int temp0 = d.a_G + R;
     // nu_j . mu for every reaction, and J^T mu for every species
@@ -560,13 +565,17 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
     for (int l = 0; l < S; ++l) n_temp += (int)std::max<size_t>(1, (jt_terms[l].size() + CHUNK - 1) / CHUNK) - 1;
     ConstTable ct;
     ct.base = temp0 + n_temp;
-    Scheduler a(ct.base + 64 + 2 * R), b(ct.base + 64 + 2 * R);
+    Scheduler a(ct.base + 64 + 2 * R);
     int temp_next = temp0;
     for (int j = 0; j < R; ++j) {
       std::vector<std::pair<int, int>> terms;
       for (auto &t : nd_terms[j]) terms.push_back({ct.get(t.first), d.a_MU + t.second});
       add_sum(a, d.a_NM + j, true, terms, CHUNK, temp_next, d.d_ZERO, d.d_ONE);
     }
+    // the constants are all known now, so the extended Wd's length and with it PP
+    const int wda_len = ct.base + (int)ct.vals.size();
+    d.a_PP = ((wda_len + 1) & ~1) + d.L_P;
+    Scheduler b(d.a_PP + n_pairs + 1);
     for (int l = 0; l < S; ++l) {
       std::vector<std::pair<int, int>> terms;
       for (auto &t : jt_terms[l]) terms.push_back({d.a_PP + t.first, d.a_NM + t.second});
@@ -574,11 +583,11 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
     }
     m.nudot_prog = a.finish();
     m.jt_prog = b.finish();
-    d.Wda_len = ct.base + (int)ct.vals.size();
+    d.Wda_len = wda_len;
     m.a_consts_v = ct.vals;
     m.a_consts_i.clear();
     for (size_t k = 0; k < ct.vals.size(); ++k) m.a_consts_i.push_back(ct.base + (int)k);
-    if ((size_t)d.Wda_len * sizeof(double) > 0xfff0) {
+    if ((size_t)(d.a_PP + n_pairs) * sizeof(double) > 0xfff0 || (size_t)d.Wda_len * sizeof(double) > 0xfff0) {
       msg = "mechanism too large for the adjoint's 16-bit byte offsets";
       return CHEM_EINVAL;
     }

@@ -115,7 +115,10 @@ def test_adjoint_programs_compute_J_transpose_mu(oracle_lib, compiled, name):
     for k in range(cells.n_cells):
         kt = oracle_lib.rate_constants(om, cells.T[k], cells.P[k])
         y = cells.y[:, k]
-        W = np.full(adj["Wda_len"], np.nan)
+        # the cell's whole slice as the adjoint kernel sees it: the extended Wd
+        # (rounded to an even length), then WL, whose pair-product region holds PP
+        W = np.full(((adj["Wda_len"] + 1) & ~1) + lay["WL_len"], np.nan)
+        assert adj["a_PP"] == ((adj["Wda_len"] + 1) & ~1) + lay["L_P"]
         for i, v in np.concatenate([cp.dconst, cp.aconst]):
             W[int(i)] = v
         W[lay["d_Y"]:lay["d_Y"] + S] = y
