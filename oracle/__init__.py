@@ -54,7 +54,7 @@ class _Opts(ct.Structure):
                 ("max_order", ct.c_int32), ("max_steps", ct.c_int32),
                 ("fixed_h", ct.c_double), ("fixed_order", ct.c_int32),
                 ("newton_maxiter", ct.c_int32), ("newton_tol", ct.c_double),
-                ("init_D", ct.c_void_p), ("y_hist", ct.c_void_p)]
+                ("init_D", ct.c_void_p), ("y_hist", ct.c_void_p), ("plain_form", ct.c_int32)]
 
 
 class _Stats(ct.Structure):
@@ -205,10 +205,10 @@ class Tape:
 
 
 def _opts(rtol, atol, max_order=5, max_steps=5000, fixed_h=0.0, fixed_order=0, newton_maxiter=0,
-          newton_tol=0.0, init_D=None, y_hist=None):
+          newton_tol=0.0, init_D=None, y_hist=None, plain_form=False):
     return _Opts(rtol, atol, max_order, max_steps, fixed_h, fixed_order, newton_maxiter, newton_tol,
                  None if init_D is None else init_D.ctypes.data,
-                 None if y_hist is None else y_hist.ctypes.data)
+                 None if y_hist is None else y_hist.ctypes.data, int(bool(plain_form)))
 
 
 def integrate(mech, kt, y0, dt, rtol, atol, max_order=5, max_steps=5000, fixed_h=0.0, fixed_order=0,
@@ -242,11 +242,14 @@ def integrate(mech, kt, y0, dt, rtol, atol, max_order=5, max_steps=5000, fixed_h
     return tuple(out)
 
 
-def solve_cells(mech, cells, dt, rtol, atol, max_order=5, max_steps=5000, theta=None, jphot="cells"):
+def solve_cells(mech, cells, dt, rtol, atol, max_order=5, max_steps=5000, theta=None, jphot="cells",
+                plain_form=False):
     """Solve every cell of a synth.Cells batch once over [0, dt].
 
     Returns (y [S, C], stats structured array [C]).  ``jphot="cells"`` uses the
-    batch's per-cell photolysis rates when it has them."""
+    batch's per-cell photolysis rates when it has them.  plain_form: make every
+    test in its plain form (square-root norms, divisions), for the pin that
+    the default squared form decides the same."""
     m = _mk(mech)
     y = np.array(cells.y, np.float64, order="C")
     C = y.shape[1]
@@ -256,7 +259,7 @@ def solve_cells(mech, cells, dt, rtol, atol, max_order=5, max_steps=5000, theta=
     jp = None if jp is None else np.ascontiguousarray(jp, np.float64)
     th = None if theta is None else np.ascontiguousarray(theta, np.float64)
     st = np.zeros(C, STATS_DTYPE)
-    o = _opts(rtol, atol, max_order, max_steps)
+    o = _opts(rtol, atol, max_order, max_steps, plain_form=plain_form)
     lib().orc_solve_cells(m.ref, C, _p(T), _p(P), _p(jp), _p(th), _p(y), float(dt), ct.byref(o), _p(st))
     return y, st
 

@@ -241,6 +241,15 @@ double orc_grid_eta(double err2, int p, double bias) {
   return exp2((double)GRID_IMIN / 8.0);
 }
 
+/* The same grid in the plain form: err against 1 / (bias * 2^(i(p+1)/8)). */
+static double grid_eta_plain(double err, int p, double bias) {
+  for (int i = GRID_IMAX; i >= GRID_IMIN; --i) {
+    const double thr = 1.0 / (bias * exp2((double)i * (double)(p + 1) / 8.0));
+    if (err <= thr) return exp2((double)i / 8.0);
+  }
+  return exp2((double)GRID_IMIN / 8.0);
+}
+
 /* ---------------------------------------------------------- helpers */
 
 static double wrms(int S, const double *v, const double *w) {
@@ -352,6 +361,8 @@ int orc_integrate(const orc_mech *m, const double *kt, double *y0, double dt, co
   int n_iters = 0;
   int n_eq = 0, have_M = 0, force_M = 0, n_since_M = 0, nef = 0, ncf = 0, last = 0;
   double cM = 0.0, icM = 0.0, rho2 = 1.0;    /* rho2: squared convergence-rate estimate */
+  double rho = 1.0;                          /* the estimate itself (plain form) */
+  const int plain = o->plain_form;
   int status = ORC_OK;
 
   for (;;) {
@@ -391,7 +402,8 @@ int orc_integrate(const orc_mech *m, const double *kt, double *y0, double dt, co
 
     /* -- iteration matrix M = I - c J(y_pred), re-formed only when stale (a4, a5) */
     int fresh = 0;
-    if (!have_M || force_M || fabs(c * icM - 1.0) > DGMAX || n_since_M >= MSBP) {
+    const double c_ratio = plain ? (have_M ? c / cM : 0.0) : c * icM;
+    if (!have_M || force_M || fabs(c_ratio - 1.0) > DGMAX || n_since_M >= MSBP) {
       orc_jacobian(m, kt, ypred, M);
       for (int i = 0; i < S * S; ++i) M[i] = -c * M[i];
       for (int i = 0; i < S; ++i) M[i * S + i] += 1.0;
@@ -401,19 +413,20 @@ int orc_integrate(const orc_mech *m, const double *kt, double *y0, double dt, co
       icM = 1.0 / c;
       n_since_M = 0;
       rho2 = 1.0;
+      rho = 1.0;
       fresh = 1;
       st->jac_evals++;
       tape_push(tape, S, 4 /*REFACTOR*/, 0, c, ypred);
     }
     force_M = 0;
-    const double scale = (c == cM) ? 1.0 : 2.0 / (1.0 + c * icM);
+    const double scale = (c == cM) ? 1.0 : (plain ? 2.0 / (1.0 + c / cM) : 2.0 / (1.0 + c * icM));
 
     /* -- modified Newton corrector: M dy = c f(y) - psi - d (a6) */
     const double tol = o->newton_tol > 0.0 ? o->newton_tol : NLSCOEF * (double)(q + 1);
     const double tol2 = tol * tol;
     const int maxit = o->newton_maxiter > 0 ? o->newton_maxiter : NEWTON_MAXITER;
     for (int i = 0; i < S; ++i) { d[i] = 0.0; y[i] = ypred[i]; }
-    double del2 = 0.0, del2_prev = 0.0;
+    double del2 = 0.0, del2_prev = 0.0, del = 0.0, del_prev = 0.0;
     int conv = 0;
     n_iters = 0;
     for (int it = 0; it < maxit; ++it) {
@@ -426,9 +439,17 @@ int orc_integrate(const orc_mech *m, const double *kt, double *y0, double dt, co
       st->solves++;
       if (scale != 1.0)
         for (int i = 0; i < S; ++i) dy[i] *= scale;
-      del2 = wrms2(S, dy, w);
+      if (plain) del = wrms(S, dy, w);
+      else del2 = wrms2(S, dy, w);
       for (int i = 0; i < S; ++i) { d[i] += dy[i]; y[i] = ypred[i] + d[i]; }
       st->newton_iters++;
+      if (plain) {
+        if (it > 0) rho = fmax(CRDOWN * rho, del / del_prev);
+        if (del * fmin(1.0, rho) <= tol) { conv = 1; break; }
+        if (it > 0 && del > RDIV * del_prev) break;
+        del_prev = del;
+        continue;
+      }
       if (it > 0) rho2 = fmax(CRDOWN * CRDOWN * rho2, del2 / del2_prev);
       if (del2 * fmin(1.0, rho2) <= tol2) { conv = 1; break; }
       if (it > 0 && del2 > RDIV * RDIV * del2_prev) break;
@@ -466,7 +487,7 @@ int orc_integrate(const orc_mech *m, const double *kt, double *y0, double dt, co
         }
       n_projected = 0;
       if (nv > 0) {
-        if (vs * (1.0 / (double)S) <= tol2) {
+        if (plain ? sqrt(vs / (double)S) <= tol : vs * (1.0 / (double)S) <= tol2) {
           for (int i = 0; i < S; ++i)
             if (y[i] < 0.0) { d[i] -= y[i]; y[i] = 0.0; projected[n_projected++] = i; }
         } else {
@@ -485,12 +506,13 @@ int orc_integrate(const orc_mech *m, const double *kt, double *y0, double dt, co
     }
 
     /* -- local error test (a7): err = ||d|| / (q+1), tested squared */
-    const double err2 = wrms2(S, d, w) * isq(q + 1);
-    if (!fixed && !(err2 <= 1.0)) {
+    const double err2 = plain ? 0.0 : wrms2(S, d, w) * isq(q + 1);
+    const double err = plain ? wrms(S, d, w) / (double)(q + 1) : 0.0;
+    if (!fixed && !(plain ? err <= 1.0 : err2 <= 1.0)) {
       st->rejects++;
       nef++;
       if (nef >= MXNEF) { status = ORC_ERR_FAIL; break; }
-      double eta = orc_grid_eta(err2, q, BIAS_SAME);
+      double eta = plain ? grid_eta_plain(err, q, BIAS_SAME) : orc_grid_eta(err2, q, BIAS_SAME);
       if (nef >= 2 && eta > ETA_MXF) eta = ETA_MXF;
       if (nef >= 3 && q > 1) q -= 1;
       orc_rescale(S, q, eta, D);
@@ -523,17 +545,17 @@ int orc_integrate(const orc_mech *m, const double *kt, double *y0, double dt, co
 
     /* -- step size and order for the next step */
     if (!fixed) {
-      double eta = orc_grid_eta(err2, q, BIAS_SAME);
+      double eta = plain ? grid_eta_plain(err, q, BIAS_SAME) : orc_grid_eta(err2, q, BIAS_SAME);
       int qn = q;
       if (n_eq >= q + 1) {
         if (q > 1) {
-          const double e2 = wrms2(S, D + (size_t)q * S, w) * isq(q);
-          const double em = orc_grid_eta(e2, q - 1, BIAS_DOWN);
+          const double em = plain ? grid_eta_plain(wrms(S, D + (size_t)q * S, w) / (double)q, q - 1, BIAS_DOWN)
+                                  : orc_grid_eta(wrms2(S, D + (size_t)q * S, w) * isq(q), q - 1, BIAS_DOWN);
           if (em > eta) { eta = em; qn = q - 1; }
         }
         if (q < qmax) {
-          const double e2 = wrms2(S, D + (size_t)(q + 2) * S, w) * isq(q + 2);
-          const double ep = orc_grid_eta(e2, q + 1, BIAS_UP);
+          const double ep = plain ? grid_eta_plain(wrms(S, D + (size_t)(q + 2) * S, w) / (double)(q + 2), q + 1, BIAS_UP)
+                                  : orc_grid_eta(wrms2(S, D + (size_t)(q + 2) * S, w) * isq(q + 2), q + 1, BIAS_UP);
           if (ep > eta) { eta = ep; qn = q + 1; }
         }
       }

@@ -75,6 +75,11 @@ typedef struct {
   double newton_tol;         /* >0: overrides the corrector tolerance */
   const double *init_D;      /* fixed_h: initial differences D_0..D_q, [q+1][S] */
   double *y_hist;            /* fixed_h: receives y after each step, [n][S] */
+  int32_t plain_form;        /* 1: every test in its plain form -- norms with the square root,
+                                the convergence-rate estimate on norms, divisions by q + 1, q,
+                                q + 2 and c_M, the step-factor grid on unsquared thresholds -- for
+                                the pin that the default form (squared norms against squared
+                                bounds, reciprocal multiplications) makes the same decisions */
 } orc_opts;
 
 typedef struct {
