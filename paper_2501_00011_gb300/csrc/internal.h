@@ -19,7 +19,9 @@ constexpr int GRID_IMAX = 26;
 constexpr int GRID_N = GRID_IMAX - GRID_IMIN + 1;
 constexpr int WARP = 32;
 constexpr int MAX_WARPS_PER_BLOCK = 12;  // cells per block (history and vectors live in registers)
-constexpr int ADJ_WARPS_PER_BLOCK = 12;  // most cells per block of the adjoint and tangent walks
+constexpr int ADJ_WARPS_PER_BLOCK = 12;  // most cells per block of the adjoint walk
+constexpr int TAN_WARPS_PER_BLOCK = 4;   // ... and of the tangent walk (a larger launch bound costs it
+                                         // registers and 70% more instructions)
 
 // A warp program is a sequence of passes of exactly 32 op slots; lane l runs
 // slot l of every pass and the warp synchronises between passes.  The

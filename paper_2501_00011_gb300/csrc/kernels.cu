@@ -1673,7 +1673,7 @@ __device__ void tangent_cell(const MechDev &M, const CellsDev &C, const TanDev &
 }
 
 template <int KS>
-__global__ void __launch_bounds__(ADJ_WARPS_PER_BLOCK * WARP) tangent_kernel(const __grid_constant__ MechDev M, const CellsDev C,
+__global__ void __launch_bounds__(TAN_WARPS_PER_BLOCK * WARP) tangent_kernel(const __grid_constant__ MechDev M, const CellsDev C,
                                                                     const TanDev A, const SolveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & (WARP - 1);
@@ -1704,13 +1704,13 @@ __global__ void __launch_bounds__(ADJ_WARPS_PER_BLOCK * WARP) tangent_kernel(con
 // resident per SM (shared memory bounds the walks' occupancy), ties to the
 // smaller block.  The kernel's dynamic shared-memory limit must be raised first.
 template <typename K>
-int walk_warps_per_block(K kernel, int cell_bytes, int *blocks_per_sm) {
+int walk_warps_per_block(K kernel, int cell_bytes, int max_warps, int *blocks_per_sm) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   int best_w = 0, best_cells = 0;
   *blocks_per_sm = 0;
-  for (int w = 1; w <= ADJ_WARPS_PER_BLOCK && (long)w * cell_bytes <= (long)optin; ++w) {
+  for (int w = 1; w <= max_warps && (long)w * cell_bytes <= (long)optin; ++w) {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, w * WARP, (size_t)w * cell_bytes) != cudaSuccess)
       continue;
@@ -1741,7 +1741,7 @@ cudaError_t launch_tan_t(const MechDev &M, const CellsDev &C, const TanDev &A, c
   if (e != cudaSuccess) return e;
   SolveParams P = P0;
   int bps = 0;
-  P.warps_per_block = walk_warps_per_block(tangent_kernel<KS>, P.cell_bytes, &bps);
+  P.warps_per_block = walk_warps_per_block(tangent_kernel<KS>, P.cell_bytes, TAN_WARPS_PER_BLOCK, &bps);
   if (P.warps_per_block < 1) return cudaErrorInvalidValue;
   const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
   const int blocks = walk_blocks(C, P.warps_per_block, bps);
@@ -1771,7 +1771,7 @@ cudaError_t launch_adj_t(const MechDev &M, const CellsDev &C, const AdjDev &A, c
   if (e != cudaSuccess) return e;
   SolveParams P = P0;
   int bps = 0;
-  P.warps_per_block = walk_warps_per_block(adjoint_kernel<KS>, P.cell_bytes, &bps);
+  P.warps_per_block = walk_warps_per_block(adjoint_kernel<KS>, P.cell_bytes, ADJ_WARPS_PER_BLOCK, &bps);
   if (P.warps_per_block < 1) return cudaErrorInvalidValue;
   const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
   const int blocks = walk_blocks(C, P.warps_per_block, bps);
