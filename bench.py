@@ -684,6 +684,12 @@ def run_gpu(args):
     clocks = clk.summary()
     if args.no_e2e:          # profiling runs: timed kernels only, no report line
         return 0
+    if not {"persistent64", "plain64", "chosen"} <= set(res):
+        # a subset of the forms (a comparison run): their mean times and the extras, not the report line
+        if rank == 0:
+            print(json.dumps({"forms_ms": {n: {k: float(np.mean(v)) for k, v in r[0].items()} for n, r in res.items()},
+                              "extras": extras, "clocks": clocks}), flush=True)
+        return 0
     (h, st_head), (p, st_plain), (ch, st_chosen) = res["persistent64"], res["plain64"], res["chosen"]
 
     # End to end through the C ABI with host buffers (pinned), copies inside each
