@@ -47,14 +47,18 @@ constexpr uint16_t DEV_RECIP = 0xffff;     // device marker in .w of RECIP passe
 // with one bulk copy.  Byte offsets of each section within the blob:
 struct TableOffsets {
   int f_ops, fwd_ops, bwd_ops;     // ushort4 programs (f on Wd, fwd/bwd on WL)
+  int f_runs;                      // uint32 run table of the f program
   int rx_slots;                    // uint2 [R]: byte offsets into Wd of the reactants' y
   int pair_rx;                     // int [n_pairs]
   int pair_other;                  // uint32 [n_pairs]: two 16-bit byte offsets into Wd
   int lu_diag;                     // int [S]: byte offsets into WL of the pivot diagonal
   int dconst_off, dconst_val;      // int [d_nconst] byte offsets into Wd, double values
   int Lconst_off, Lconst_val;      // int [L_nconst] byte offsets into WL, double values
-  int thr2, thr3, g;               // step-factor grid: squared thresholds (biases 2 and 3),
-                                   // double [7][GRID_N] each, and the factors g_i, [GRID_N]
+  int thr2, thr3, g;               // step-factor grid: thresholds of the raw squared-norm sums
+                                   // (biases 2 and 3), double [7][GRID_N] each, and the factors
+                                   // g_i, [GRID_N]
+  int lim;                         // double [2][8]: by order q, the raw-sum bounds of the error
+                                   // test, S (q+1)^2, and of the corrector, S (0.1 (q+1))^2
   int staged;                      // bytes of the prefix the persistent driver stages in shared
                                    // memory (programs and slots used every Newton iteration or
                                    // refactorisation; constants and the grid stay in global memory)
@@ -87,6 +91,8 @@ struct MechDev {
   int d_nconst, L_nconst;
   int m_clear;             // WL entries [0, m_clear) are cleared before forming M
   int f_npass, fwd_npass, bwd_npass, m_npass, lu_npass;
+  int f_nruns, m_nruns, lu_nruns;  // run tables (f: in the staged blob; M, LU: m_runs, lu_runs)
+  const uint32_t *m_runs, *lu_runs;
   // staged tables: blob[0] for an FP64 LU, blob[1] for an FP32 LU (global memory)
   const unsigned char *blob[2];
   TableOffsets tab;
@@ -106,10 +112,32 @@ struct MechDev {
   int nudot_npass, jt_npass, fwdT_npass, bwdT_npass;
 };
 
+// Kinds of the units a program's passes form, in its run table (one uint32 per
+// run of equal units: kind << 28 | units): a single pass of FMAs, a pair of
+// consecutive FMA passes whose 64 ops are independent of each other (the
+// interpreter loads the operands of both before it stores either result, so a
+// lane has two FMAs in flight between warp synchronisations), a pass of
+// reciprocals.
+constexpr uint32_t RUN_FMA1 = 0, RUN_FMA2 = 1, RUN_RECIP = 2;
+
 struct HostProgram {
   std::vector<Op> ops;   // n_pass * 32
+  std::vector<uint8_t> unit;   // per pass: 0 single FMA pass, 1 / 2 first / second pass of a pair, 3 reciprocals
   int n_ops = 0;
   int n_pass() const { return (int)(ops.size() / WARP); }
+  std::vector<uint32_t> runs() const {
+    std::vector<uint32_t> r;
+    uint32_t kind = 0xf, n = 0;
+    for (size_t p = 0; p < unit.size(); ++p) {
+      if (unit[p] == 2) continue;
+      const uint32_t k = unit[p] == 1 ? RUN_FMA2 : unit[p] == 3 ? RUN_RECIP : RUN_FMA1;
+      if (k != kind && n) r.push_back(kind << 28 | n), n = 0;
+      kind = k;
+      n++;
+    }
+    if (n) r.push_back(kind << 28 | n);
+    return r;
+  }
 };
 
 // Compiled mechanism (host + device copies).

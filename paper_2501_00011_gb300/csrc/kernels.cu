@@ -31,13 +31,12 @@ namespace chemgpu {
 
 __constant__ double c_gam[QMAX + 2];
 __constant__ double c_igam[QMAX + 2];
-__constant__ double c_isq[QMAX + 3];    // 1/n^2: the squared error estimates' divisors
 
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int NEWTON_MAXITER = 3;
-constexpr double CRDOWN = 0.3, RDIV = 2.0, NLSCOEF = 0.1, DGMAX = 0.3, THRESH = 1.5;
+constexpr double CRDOWN = 0.3, RDIV = 2.0, DGMAX = 0.3, THRESH = 1.5;   // corrector bound 0.1 (q+1): host table
 constexpr int MSBP = 20, MXNEF = 7, MXNCF = 10;
 constexpr double ETA_CF = 0.25, ETA_MXF = 0.2, ETA_CST_SAFETY = 0.9, ETA_CST_MIN = 0.1, STRETCH = 1e-3;
 constexpr int ORDER_WARPS = 8;          // cells per block of the queue-order kernel
@@ -135,6 +134,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// The next pass's op is read from the ring one pass ahead, so that shared-memory
+// load overlaps the current pass (the ring slot it reuses held the op read two
+// passes earlier).
 template <typename T, bool NEG, int RING>
 __device__ __forceinline__ void run_ops_ring(const ushort4 *ops, const int np, T *W, const int lane, const uint32_t ring) {
   const uint32_t wb = smem_addr(W);
@@ -146,14 +148,18 @@ __device__ __forceinline__ void run_ops_ring(const ushort4 *ops, const int np, T
     if (i < np) cp_async8(rb + 256u * i, g + (size_t)i * WARP);
     cp_async_commit();
   }
+  cp_async_wait<RING - 2>();            // pass 0's group has landed
+  uint32_t nx = 0, ny = 0;
+  if (np > 0) asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(nx), "=r"(ny) : "r"(rb) : "memory");
 #pragma unroll 1
   for (int p = 0; p < np; ++p) {
+    const uint32_t ox = nx, oy = ny;
     const int q = p + RING - 1;
     if (q < np) cp_async8(rb + 256u * (q % RING), g + (size_t)q * WARP);
     cp_async_commit();
-    cp_async_wait<RING - 1>();          // pass p's group has landed
-    uint32_t ox, oy;
-    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(ox), "=r"(oy) : "r"(rb + 256u * (p % RING)) : "memory");
+    cp_async_wait<RING - 2>();          // pass p+1's group has landed
+    if (p + 1 < np)
+      asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(nx), "=r"(ny) : "r"(rb + 256u * ((p + 1) % RING)) : "memory");
     const uint32_t ot = ox & 0xffff, oa = ox >> 16, ob = oy & 0xffff, oc = oy >> 16;
     if (oc == DEV_RECIP) {
       sts(wb + ot, -lu_recip(lds(tag, wb + oa)));
@@ -162,6 +168,143 @@ __device__ __forceinline__ void run_ops_ring(const ushort4 *ops, const int np, T
       sts(wb + ot, NEG ? fma(-a, b, c) : fma(a, b, c));
     }
     __syncwarp();
+  }
+  cp_async_wait<0>();                   // nothing in flight once the ring's memory is reused
+}
+
+// One FMA op / a pair of independent FMA ops / a reciprocal op of a lane
+// (packed ops: x = t | a << 16, y = b | c << 16, byte offsets into W at wb).
+template <typename T, bool NEG>
+__device__ __forceinline__ void op_fma(uint32_t wb, uint2 o) {
+  T *const tag = nullptr;
+  const T a = lds(tag, wb + (o.x >> 16)), b = lds(tag, wb + (o.y & 0xffff)), c = lds(tag, wb + (o.y >> 16));
+  sts(wb + (o.x & 0xffff), NEG ? fma(-a, b, c) : fma(a, b, c));
+}
+template <typename T, bool NEG>
+__device__ __forceinline__ void op_fma2(uint32_t wb, uint2 o, uint2 u) {
+  T *const tag = nullptr;
+  const T a = lds(tag, wb + (o.x >> 16)), b = lds(tag, wb + (o.y & 0xffff)), c = lds(tag, wb + (o.y >> 16));
+  const T a2 = lds(tag, wb + (u.x >> 16)), b2 = lds(tag, wb + (u.y & 0xffff)), c2 = lds(tag, wb + (u.y >> 16));
+  sts(wb + (o.x & 0xffff), NEG ? fma(-a, b, c) : fma(a, b, c));
+  sts(wb + (u.x & 0xffff), NEG ? fma(-a2, b2, c2) : fma(a2, b2, c2));
+}
+template <typename T>
+__device__ __forceinline__ void op_recip(uint32_t wb, uint2 o) {
+  T *const tag = nullptr;
+  sts(wb + (o.x & 0xffff), -lu_recip(lds(tag, wb + (o.x >> 16))));
+}
+
+// A program with a run table (RUN_* units, internal.h).  The ops of the next
+// two passes are held in registers (n0, n1) and refilled as the units consume
+// them, so a unit never waits for its own ops.  Runs are read from shared
+// memory (SMEM) or global memory like the ops; WIDE / RECIP: the program has
+// pair / reciprocal units (a run table without them compiles to a plain loop).
+template <typename T, bool NEG, bool SMEM, bool WIDE, bool RECIP>
+__device__ __forceinline__ void run_prog(const ushort4 *ops, const uint32_t *runs, const int nruns, const int np, T *W,
+                                         const int lane) {
+  const uint32_t wb = smem_addr(W);
+  ops += lane;
+  uint2 n0 = np > 0 ? ld_op<SMEM>(ops) : make_uint2(0, 0);
+  uint2 n1 = np > 1 ? ld_op<SMEM>(ops + WARP) : make_uint2(0, 0);
+  int p = 0;
+#pragma unroll 1
+  for (int r = 0; r < nruns; ++r) {
+    const uint32_t rr = SMEM ? runs[r] : __ldg(runs + r);
+    const uint32_t kind = rr >> 28;
+    int n = (int)(rr & 0x0fffffffu);
+    if (WIDE && kind == RUN_FMA2) {
+#pragma unroll 1
+      for (; n > 0; --n, p += 2) {
+        const uint2 o = n0, u = n1;
+        if (p + 2 < np) n0 = ld_op<SMEM>(ops + (size_t)(p + 2) * WARP);
+        if (p + 3 < np) n1 = ld_op<SMEM>(ops + (size_t)(p + 3) * WARP);
+        op_fma2<T, NEG>(wb, o, u);
+        __syncwarp();
+      }
+    } else if (RECIP && kind == RUN_RECIP) {
+#pragma unroll 1
+      for (; n > 0; --n, ++p) {
+        const uint2 o = n0;
+        n0 = n1;
+        if (p + 2 < np) n1 = ld_op<SMEM>(ops + (size_t)(p + 2) * WARP);
+        op_recip<T>(wb, o);
+        __syncwarp();
+      }
+    } else {
+#pragma unroll 1
+      for (; n > 0; --n, ++p) {
+        const uint2 o = n0;
+        n0 = n1;
+        if (p + 2 < np) n1 = ld_op<SMEM>(ops + (size_t)(p + 2) * WARP);
+        op_fma<T, NEG>(wb, o);
+        __syncwarp();
+      }
+    }
+  }
+}
+
+// The same for programs in global memory, the ops streamed through a ring of
+// RING x 256 bytes of shared memory (ring: 8-byte aligned shared address) as
+// in run_ops_ring.  Invariant at the start of a unit at pass p: passes up to
+// p + RING - 3 are issued and the ops of passes p and p + 1 are in n0, n1.  A
+// unit issues one pass per pass it consumes, into the slots of passes p - 2
+// (and p - 1), whose ops were read into registers and used by earlier units;
+// it then waits until pass p + 2 (and p + 3) has landed and refills n0, n1.
+template <typename T, bool NEG, int RING, bool WIDE, bool RECIP>
+__device__ __forceinline__ void run_prog_ring(const ushort4 *ops, const uint32_t *runs, const int nruns, const int np, T *W,
+                                              const int lane, const uint32_t ring) {
+  static_assert(RING >= 6, "ring too shallow to run ahead");
+  const uint32_t wb = smem_addr(W);
+  const uint2 *g = reinterpret_cast<const uint2 *>(ops) + lane;
+  const uint32_t rb = ring + 8u * lane;
+#pragma unroll 1
+  for (int i = 0; i < RING - 2; ++i) {
+    if (i < np) cp_async8(rb + 256u * i, g + (size_t)i * WARP);
+    cp_async_commit();
+  }
+  cp_async_wait<RING - 4>();            // passes 0 and 1 have landed
+  uint2 n0 = make_uint2(0, 0), n1 = make_uint2(0, 0);
+  if (np > 0) asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(n0.x), "=r"(n0.y) : "r"(rb) : "memory");
+  if (np > 1) asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(n1.x), "=r"(n1.y) : "r"(rb + 256u) : "memory");
+  int p = 0;
+#pragma unroll 1
+  for (int r = 0; r < nruns; ++r) {
+    const uint32_t rr = __ldg(runs + r);
+    const uint32_t kind = rr >> 28;
+    int n = (int)(rr & 0x0fffffffu);
+    if (WIDE && kind == RUN_FMA2) {
+#pragma unroll 1
+      for (; n > 0; --n, p += 2) {
+        const uint2 o = n0, u = n1;
+        const int q = p + RING - 2;
+        if (q < np) cp_async8(rb + 256u * (q % RING), g + (size_t)q * WARP);
+        cp_async_commit();
+        if (q + 1 < np) cp_async8(rb + 256u * ((q + 1) % RING), g + (size_t)(q + 1) * WARP);
+        cp_async_commit();
+        cp_async_wait<RING - 4>();      // passes p + 2 and p + 3 have landed
+        if (p + 2 < np)
+          asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(n0.x), "=r"(n0.y) : "r"(rb + 256u * ((p + 2) % RING)) : "memory");
+        if (p + 3 < np)
+          asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(n1.x), "=r"(n1.y) : "r"(rb + 256u * ((p + 3) % RING)) : "memory");
+        op_fma2<T, NEG>(wb, o, u);
+        __syncwarp();
+      }
+    } else {
+#pragma unroll 1
+      for (; n > 0; --n, ++p) {
+        const uint2 o = n0;
+        n0 = n1;
+        const int q = p + RING - 2;
+        if (q < np) cp_async8(rb + 256u * (q % RING), g + (size_t)q * WARP);
+        cp_async_commit();
+        cp_async_wait<RING - 4>();      // pass p + 2 has landed
+        if (p + 2 < np)
+          asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(n1.x), "=r"(n1.y) : "r"(rb + 256u * ((p + 2) % RING)) : "memory");
+        if (RECIP && kind == RUN_RECIP) op_recip<T>(wb, o);
+        else op_fma<T, NEG>(wb, o);
+        __syncwarp();
+      }
+    }
   }
   cp_async_wait<0>();                   // nothing in flight once the ring's memory is reused
 }
@@ -177,15 +320,47 @@ __device__ __forceinline__ double warp_min(double v) {
   return v;
 }
 
-// Largest grid factor g_i with err <= thr[p][i] (thr decreasing in i), else g_min.
-// Largest step factor g_i of the grid 2^(i/8) whose squared threshold
-// 1/(bias^2 2^(i(p+1)/4)) (host table, row p) the squared error err2 meets.
-__device__ __forceinline__ double grid_eta(const double *thr, const double *g, double err2, int p, int lane) {
+// Comparisons of non-negative doubles on the integer pipe.  FP64 compares,
+// min/max and conversions issue on the FP64 pipe at the cost of an FMA or more
+// (one warp instruction per 64 cycles of an SM sub-partition); the IEEE bit
+// patterns of +0 .. +inf order as the numbers do, and a NaN of either sign
+// compares above +inf as an unsigned integer, so these give the FP results
+// for operands >= +0 or NaN.
+constexpr unsigned long long INF_BITS = 0x7ff0000000000000ull, ABS_MASK = 0x7fffffffffffffffull;
+__device__ __forceinline__ unsigned long long ubits(double x) { return (unsigned long long)__double_as_longlong(x); }
+// a <= b (false if either is NaN)
+__device__ __forceinline__ bool le_nn(double a, double b) {
+  const unsigned long long ua = ubits(a), ub = ubits(b);
+  return ua <= ub && ub <= INF_BITS;
+}
+// a > b (false if either is NaN)
+__device__ __forceinline__ bool gt_nn(double a, double b) {
+  const unsigned long long ua = ubits(a), ub = ubits(b);
+  return ua > ub && ua <= INF_BITS;
+}
+// max(a, b) (a, b >= +0, not NaN)
+__device__ __forceinline__ double max_nn(double a, double b) { return ubits(a) >= ubits(b) ? a : b; }
+// a == b for any doubles (false if NaN; +0 and -0 are equal)
+__device__ __forceinline__ bool eq_fp(double a, double b) {
+  const unsigned long long ua = ubits(a), ub = ubits(b);
+  return (ua == ub && (ua & ABS_MASK) <= INF_BITS) || ((ua | ub) & ABS_MASK) == 0;
+}
+// x < 0 (false for -0 and NaN; true for -inf)
+__device__ __forceinline__ bool lt0(double x) {
+  const unsigned long long u = ubits(x), a = u & ABS_MASK;
+  return u != a && a != 0 && a <= INF_BITS;
+}
+
+// Index i of the largest step factor g_i of the grid 2^(i/8) (shifted so the
+// smallest is index 0) whose threshold (host table row p, decreasing in i)
+// the squared-norm sum e meets; 0 if none.  The thresholds are scaled on the
+// host so that the raw warp sum is compared (e >= +0 or NaN; NaN meets none).
+__device__ __forceinline__ int grid_idx(const double *thr, double e, int p, int lane) {
   const double *tp = thr + p * GRID_N;
-  const bool ok0 = err2 <= tp[lane];
-  const bool ok1 = (lane + WARP < GRID_N) && err2 <= tp[lane + WARP];
+  const bool ok0 = le_nn(e, tp[lane]);
+  const bool ok1 = (lane + WARP < GRID_N) && le_nn(e, tp[lane + WARP]);
   const int cnt = __popc(__ballot_sync(FULL, ok0)) + __popc(__ballot_sync(FULL, ok1));
-  return g[cnt > 0 ? cnt - 1 : 0];
+  return cnt > 0 ? cnt - 1 : 0;
 }
 
 // ------------------------------------------------------------- TMA staging
@@ -250,7 +425,9 @@ __device__ __forceinline__ void f_core(const MechDev &M, const unsigned char *tb
     Wd[M.d_RT + j] = r;
   }
   __syncwarp();
-  run_ops<double, false, STAGED>(reinterpret_cast<const ushort4 *>(tbase + M.tab.f_ops), M.f_npass, Wd, lane);
+  run_prog<double, false, STAGED, true, false>(reinterpret_cast<const ushort4 *>(tbase + M.tab.f_ops),
+                                               reinterpret_cast<const uint32_t *>(tbase + M.tab.f_runs), M.f_nruns,
+                                               M.f_npass, Wd, lane);
 }
 
 // a3-a5: M = I - c J(y) in the LU slots from y in Wd[Y], then factor
@@ -276,25 +453,17 @@ __device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *
   }
   __syncwarp();
   // Both programs are read from L2, so their ops are streamed ahead through a
-  // ring in memory that is dead at the time: the rates and f slots of Wd
-  // while M is formed (f is not being evaluated), then the pair products,
-  // which are dead once M is formed, while it is factored.
+  // ring in memory that is dead while M is formed and factored: the rates and
+  // f slots of Wd (f is not being evaluated).  Too small a region: ops read
+  // from L2 one unit ahead.
   const uint32_t wr = smem_addr(Wd + M.d_RT);            // 8-byte aligned (a double slot)
-  if ((M.R + M.S) * 8 >= 8 * 256)
-    run_ops_ring<T, false, 8>(M.m_ops[prec], M.m_npass, WL, lane, wr);
-  else if ((M.R + M.S) * 8 >= 4 * 256)
-    run_ops_ring<T, false, 4>(M.m_ops[prec], M.m_npass, WL, lane, wr);
-  else
-    run_ops<T, false, false>(M.m_ops[prec], M.m_npass, WL, lane);
-  const uint32_t pb = smem_addr(WL + M.L_P);
-  const uint32_t rb = (pb + 7u) & ~7u;
-  const int cap = M.n_pairs * (int)sizeof(T) - (int)(rb - pb);
-  if (cap >= 8 * 256)
-    run_ops_ring<T, false, 8>(M.lu_ops[prec], M.lu_npass, WL, lane, rb);
-  else if (cap >= 4 * 256)
-    run_ops_ring<T, false, 4>(M.lu_ops[prec], M.lu_npass, WL, lane, rb);
-  else
-    run_ops<T, false, false>(M.lu_ops[prec], M.lu_npass, WL, lane);
+  if ((M.R + M.S) * 8 >= 8 * 256) {
+    run_prog_ring<T, false, 8, true, false>(M.m_ops[prec], M.m_runs, M.m_nruns, M.m_npass, WL, lane, wr);
+    run_prog_ring<T, false, 8, true, true>(M.lu_ops[prec], M.lu_runs, M.lu_nruns, M.lu_npass, WL, lane, wr);
+  } else {
+    run_prog<T, false, false, true, false>(M.m_ops[prec], M.m_runs, M.m_nruns, M.m_npass, WL, lane);
+    run_prog<T, false, false, true, true>(M.lu_ops[prec], M.lu_runs, M.lu_nruns, M.lu_npass, WL, lane);
+  }
 }
 
 // a5: forward and backward substitution with the LDU factors on the vector in
@@ -656,10 +825,14 @@ struct Recorder {
 // One cell (COUPLED: one cell of a coupled group; cell < 0 marks a warp
 // without a cell in a ragged last group, which follows the group's control
 // flow and contributes nothing).  invN scales the norms' sums: 1/S alone,
-// 1/(cells in the group * S) coupled.
+// 1/(cells in the group * S) coupled.  The controller's tests compare the
+// raw sums sum (v_i w_i)^2 with bounds the host multiplied by S (tables thr2,
+// thr3, lim); coupled, the group's sums are first scaled by gsc = 1/(cells
+// in the group).
 template <typename T, int KS, bool STAGED, bool REC, bool COUPLED>
 __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, const SolveParams &P, const Tabs &tb, double *Wd,
-                           T *WL, const int lane, const int64_t cell, const Grp<COUPLED> &grp, const double invN) {
+                           T *WL, const int lane, const int64_t cell, const Grp<COUPLED> &grp, const double invN,
+                           const double gsc) {
   const int64_t NC = C.n_cells;
   chem_cell_stats st = {};
   int status = CHEM_CELL_OK;
@@ -718,11 +891,14 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
     const int qmax = P.max_order;
     double ypred[KS], psi[KS], d[KS], y[KS], x[KS];
 
+    const double *thr2 = gtab<double>(tb, M.tab.thr2), *thr3 = gtab<double>(tb, M.tab.thr3);
+    const double *gfac = gtab<double>(tb, M.tab.g), *lim = gtab<double>(tb, M.tab.lim);
     for (;;) {
       if (st.steps >= P.max_steps) { status = CHEM_CELL_MAX_STEPS; break; }
-      if (dt - t <= h * (1.0 + STRETCH)) {
+      // dt - t >= +0 always (t < dt inside the loop)
+      if (le_nn(dt - t, h * (1.0 + STRETCH))) {
         const double hn = dt - t;
-        if (hn != h) {
+        if (!eq_fp(hn, h)) {
           rescale<KS>(D, q, hn / h, M.rescale_coef, lane);
           rec.push(EV_RESCALE, q, hn / h, lane);
           h = hn;
@@ -732,7 +908,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
       } else {
         last = 0;
       }
-      if (!last && t + h == t) { status = CHEM_CELL_H_TOO_SMALL; break; }
+      if (!last && eq_fp(t + h, t)) { status = CHEM_CELL_H_TOO_SMALL; break; }
 
       const double iq = c_igam[q];
       const double c = h * iq;
@@ -755,7 +931,8 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
       for (int k = 0; k < KS; ++k) psi[k] *= iq;
 
       int fresh = 0;
-      if (!have_M || force_M || fabs(c * icM - 1.0) > DGMAX || n_since_M >= MSBP) {
+      if (!have_M || force_M || gt_nn(__longlong_as_double(__double_as_longlong(fma(c, icM, -1.0)) & ABS_MASK), DGMAX) ||
+          n_since_M >= MSBP) {
         cl.form_and_factor(c, ypred);
         have_M = 1;
         cM = c;
@@ -767,9 +944,10 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
         rec.push_row(EV_REFACTOR, 0, c, ypred, lane);
       }
       force_M = 0;
-      const double scale = (c == cM) ? 1.0 : 2.0 * recip_nr(fma(c, icM, 1.0));
-      const double tol = NLSCOEF * (double)(q + 1);
-      const double tol2 = tol * tol;
+      const bool scaled = !eq_fp(c, cM);
+      double scale = 1.0;
+      if (scaled) scale = 2.0 * recip_nr(fma(c, icM, 1.0));
+      const double tol2 = lim[8 + q];     // S (0.1 (q+1))^2
 
 #pragma unroll
       for (int k = 0; k < KS; ++k) {
@@ -788,21 +966,22 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
         for (int k = 0; k < KS; ++k) tmp[k] = c * f[k] - psi[k] - d[k];
         cl.solve(tmp, x);
         st.solves++;
-        if (scale != 1.0) {
+        if (scaled) {
 #pragma unroll
           for (int k = 0; k < KS; ++k) x[k] *= scale;
         }
-        del2 = grp.sum(cl.sumsq(x, w)) * invN;
+        del2 = grp.sum(cl.sumsq(x, w));
+        if (COUPLED) del2 *= gsc;
 #pragma unroll
         for (int k = 0; k < KS; ++k) {
           d[k] += x[k];
           y[k] = ypred[k] + d[k];
         }
         st.newton_iters++;
-        if (it > 0) rho2 = fmax(CRDOWN * CRDOWN * rho2, del2 * idel2_prev);
-        if (del2 * fmin(1.0, rho2) <= tol2) { conv = 1; break; }
-        if (it > 0 && del2 > RDIV * RDIV * del2_prev) break;
-        // not converged, so del2 > tol2 >= 1e-4 (q >= 1): a normal number
+        if (it > 0) rho2 = max_nn(CRDOWN * CRDOWN * rho2, del2 * idel2_prev);
+        if (le_nn(le_nn(rho2, 1.0) ? del2 * rho2 : del2, tol2)) { conv = 1; break; }
+        if (it > 0 && gt_nn(del2, RDIV * RDIV * del2_prev)) break;
+        // not converged, so del2 > tol2 >= 1e-2 S (q >= 1): a normal number
         del2_prev = del2;
         idel2_prev = recip_nr(del2);
       }
@@ -828,23 +1007,24 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
       {
         bool neg = false;
 #pragma unroll
-        for (int k = 0; k < KS; ++k) neg |= cl.own[k] && y[k] < 0.0;
+        for (int k = 0; k < KS; ++k) neg |= cl.own[k] && lt0(y[k]);
         if (grp.any(__any_sync(FULL, neg))) {
           double vs = 0.0, eta_c = 1.0;
 #pragma unroll
           for (int k = 0; k < KS; ++k)
-            if (cl.own[k] && y[k] < 0.0) {
+            if (cl.own[k] && lt0(y[k])) {
               const double v = y[k] * w[k];
               vs = fma(v, v, vs);
               const double r = (D[0][k] > 0.0) ? D[0][k] / (D[0][k] - y[k]) : 0.0;
               eta_c = fmin(eta_c, r);
             }
           vs = grp.sum(warp_sum(vs));
+          if (COUPLED) vs *= gsc;
           eta_c = grp.min(warp_min(eta_c));
-          if (vs * invN <= tol2) {
+          if (le_nn(vs, tol2)) {
 #pragma unroll
             for (int k = 0; k < KS; ++k) {
-              const bool p = cl.own[k] && y[k] < 0.0;
+              const bool p = cl.own[k] && lt0(y[k]);
               if (p) {
                 d[k] -= y[k];
                 y[k] = 0.0;
@@ -866,14 +1046,16 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
         }
       }
 
-      // local error test
-      const double err2 = grp.sum(cl.sumsq(d, w)) * invN * c_isq[q + 1];     // (||d|| / (q+1))^2
-      if (!(err2 <= 1.0)) {
+      // local error test: (||d|| / (q+1))^2 <= 1, as the raw sum against S (q+1)^2
+      double err2 = grp.sum(cl.sumsq(d, w));
+      if (COUPLED) err2 *= gsc;
+      const int ie = grid_idx(thr2, err2, q, lane);
+      if (!le_nn(err2, lim[q])) {
         st.rejects++;
         nef++;
         if (nef >= MXNEF) { status = CHEM_CELL_ERR_FAIL; break; }
-        double eta = grid_eta(gtab<double>(tb, M.tab.thr2), gtab<double>(tb, M.tab.g), err2, q, lane);
-        if (nef >= 2 && eta > ETA_MXF) eta = ETA_MXF;
+        double eta = gfac[ie];
+        if (nef >= 2 && gt_nn(eta, ETA_MXF)) eta = ETA_MXF;
         if (nef >= 3 && q > 1) q -= 1;
         rescale<KS>(D, q, eta, M.rescale_coef, lane);
         rec.push(EV_RESCALE, q, eta, lane);
@@ -896,25 +1078,29 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
       if (last) break;
       n_eq++;
 
-      double eta = grid_eta(gtab<double>(tb, M.tab.thr2), gtab<double>(tb, M.tab.g), err2, q, lane);
+      // next factor: grid indices compare as the factors do (g_i increasing)
+      int ieta = ie;
       int qn = q;
       if (n_eq >= q + 1) {
         if (q > 1) {
           double row[KS];
           get_row<KS>(D, q, row);
-          const double e2 = grp.sum(cl.sumsq(row, w)) * invN * c_isq[q];
-          const double em = grid_eta(gtab<double>(tb, M.tab.thr2), gtab<double>(tb, M.tab.g), e2, q - 1, lane);
-          if (em > eta) { eta = em; qn = q - 1; }
+          double e2 = grp.sum(cl.sumsq(row, w));       // (||D_q|| / q)^2 against row q-1
+          if (COUPLED) e2 *= gsc;
+          const int im = grid_idx(thr2, e2, q - 1, lane);
+          if (im > ieta) { ieta = im; qn = q - 1; }
         }
         if (q < qmax) {
           double row[KS];
           get_row<KS>(D, q + 2, row);
-          const double e2 = grp.sum(cl.sumsq(row, w)) * invN * c_isq[q + 2];
-          const double ep = grid_eta(gtab<double>(tb, M.tab.thr3), gtab<double>(tb, M.tab.g), e2, q + 1, lane);
-          if (ep > eta) { eta = ep; qn = q + 1; }
+          double e2 = grp.sum(cl.sumsq(row, w));       // (||D_{q+2}|| / (q+2))^2 against row q+1
+          if (COUPLED) e2 *= gsc;
+          const int ip = grid_idx(thr3, e2, q + 1, lane);
+          if (ip > ieta) { ieta = ip; qn = q + 1; }
         }
       }
-      if (eta >= THRESH) {
+      const double eta = gfac[ieta];
+      if (le_nn(THRESH, eta)) {
         q = qn;
         rescale<KS>(D, q, eta, M.rescale_coef, lane);
         rec.push(EV_RESCALE, q, eta, lane);
@@ -1017,7 +1203,8 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const
         if (c0 >= C.n_cells) break;
         const int n_act = (int)((C.n_cells - c0) < G ? (C.n_cells - c0) : G);
         const int64_t cell = grp.w < n_act ? c0 + grp.w : -1;
-        solve_cell<T, KS, STAGED, REC, COUPLED>(M, C, P, tb, Wd, WL, lane, cell, grp, 1.0 / (double)(n_act * M.S));
+        solve_cell<T, KS, STAGED, REC, COUPLED>(M, C, P, tb, Wd, WL, lane, cell, grp, 1.0 / (double)(n_act * M.S),
+                                                1.0 / (double)n_act);
         if (!C.queue) break;
       }
     }
@@ -1028,11 +1215,11 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * WARP) solve_kernel(const
       cell = __shfl_sync(FULL, cell, 0);
       if (cell >= C.n_cells) break;
       if (C.order) cell = __ldg(C.order + cell);
-      solve_cell<T, KS, STAGED, REC, COUPLED>(M, C, P, tb, Wd, WL, lane, cell, grp, invS);
+      solve_cell<T, KS, STAGED, REC, COUPLED>(M, C, P, tb, Wd, WL, lane, cell, grp, invS, 1.0);
     }
   } else {
     const int64_t cell = (int64_t)blockIdx.x * P.warps_per_block + warp;
-    if (cell < C.n_cells) solve_cell<T, KS, STAGED, REC, COUPLED>(M, C, P, tb, Wd, WL, lane, cell, grp, invS);
+    if (cell < C.n_cells) solve_cell<T, KS, STAGED, REC, COUPLED>(M, C, P, tb, Wd, WL, lane, cell, grp, invS, 1.0);
   }
   // a late bulk copy must land before the block exits (its shared memory is
   // then handed to another block); one thread waits, bounded, and counts a
@@ -2008,12 +2195,8 @@ cudaError_t set_constants() {
     gam[k] = g;
     igam[k] = 1.0 / g;
   }
-  double isq[QMAX + 3];
-  isq[0] = 0.0;
-  for (int n = 1; n <= QMAX + 2; ++n) isq[n] = 1.0 / (double)(n * n);
   cudaError_t e = cudaMemcpyToSymbol(c_gam, gam, sizeof(gam));
   if (e != cudaSuccess) return e;
-  if ((e = cudaMemcpyToSymbol(c_isq, isq, sizeof(isq))) != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_igam, igam, sizeof(igam));
 }
 

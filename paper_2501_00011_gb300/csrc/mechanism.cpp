@@ -91,7 +91,9 @@ struct Scheduler {
     const int r[1] = {a};
     add(Op{(uint16_t)(t | OP_RECIP), (uint16_t)a, 0, 0}, 1, r, 1, t);
   }
-  HostProgram finish() const {
+  // wide: ops may also be packed 64 at a time into pairs of passes (when at
+  // least 64 are ready, all of them mutually independent)
+  HostProgram finish(bool wide = false) const {
     const int n = (int)rec_op.size();
     std::vector<std::vector<int>> succ(n);
     std::vector<int> npred(n, 0);
@@ -123,12 +125,16 @@ struct Scheduler {
       else if (ready[1].empty()) k = 0;
       else k = later(ready[0].top(), ready[1].top()) ? 1 : 0;
       pass.clear();
-      while (!ready[k].empty() && pass.size() < (size_t)WARP) {
+      const size_t width = (wide && k == 0 && ready[0].size() >= 2 * (size_t)WARP) ? 2 * WARP : WARP;
+      while (!ready[k].empty() && pass.size() < width) {
         pass.push_back(ready[k].top());
         ready[k].pop();
       }
       for (int i : pass) hp.ops.push_back(rec_op[i]);
       for (size_t i = pass.size(); i < (size_t)WARP; ++i) hp.ops.push_back(Op{OP_EMPTY, 0, 0, 0});
+      if (k == 1) hp.unit.push_back(3);
+      else if (width == WARP) hp.unit.push_back(0);
+      else hp.unit.insert(hp.unit.end(), {1, 2});
       done += (int)pass.size();
       for (int i : pass)
         for (int s2 : succ[i])
@@ -138,6 +144,203 @@ struct Scheduler {
     return hp;
   }
 };
+
+// ------------------------------------------------------------- bank layout
+// Shared memory serves a warp's access in wavefronts: one distinct 4-byte word
+// per bank (32 banks) per wavefront.  Measured on GB300 with a pass
+// interpreter at 4-16 warps per SM: an 8-byte access is served per half-warp
+// (lanes 0-15, then 16-31), each half taking as many wavefronts as its most
+// loaded bank pair (distinct doubles with equal slot index mod 16); random
+// slots cost 6.4 wavefronts per operand and a pass 23 SM cycles, slots spread
+// over the bank pairs two per operand 17 cycles (the pass's FP64 FMA alone
+// needs 16).  The compiler numbers the LU slots row by row and fills a pass
+// with whatever ops are ready, so the slots of a pass's operands collide in
+// banks.  Two searches spread them, keeping every op in its pass (the
+// programs compute the same values):
+//  * lanes: per pass, swaps of ops between the half-warps that lower the
+//    8-byte cost (per operand and half, the most loaded bank pair);
+//  * slots: a permutation of the LU region by simulated annealing over swaps
+//    of two slots' positions, lowering the number of pairs of distinct slots
+//    that share a bank pair within a half (8-byte form) or a bank within the
+//    whole pass (4-byte form, half weight), summed over the four operands of
+//    every pass of the programs on WL weighted by how often each runs.
+// The lanes are searched once for the slots as numbered and again for the
+// permuted ones.  Both searches are deterministic (a fixed-seed generator).
+struct BankProg {
+  HostProgram *hp;
+  double w;            // runs per factorisation of M
+};
+
+uint32_t xorshift(uint32_t &s) {
+  s ^= s << 13;
+  s ^= s >> 17;
+  s ^= s << 5;
+  return s;
+}
+
+// element of role r (0 t, 1 a, 2 b, 3 c) of an op as the device runs it (-1: no access)
+int role_elem(const Op &o, bool recip, int r, int dummy, int zero, int one) {
+  if (o.t == OP_EMPTY) {
+    if (recip) return r == 0 ? dummy : r == 1 ? one : -1;
+    return r == 0 ? dummy : zero;
+  }
+  if (recip) return r == 0 ? (o.t & 0x7fff) : r == 1 ? o.a : -1;
+  return r == 0 ? o.t : r == 1 ? o.a : r == 2 ? o.b : o.c;
+}
+
+bool recip_pass(const HostProgram &hp, int p) {
+  for (int l = 0; l < WARP; ++l) {
+    const Op &o = hp.ops[(size_t)p * WARP + l];
+    if (o.t != OP_EMPTY && (o.t & OP_RECIP)) return true;
+  }
+  return false;
+}
+
+// The slot search: a permutation of the slots [0, n_perm) (perm[e] = new
+// position of e), improved in place.  A group is the distinct slots of one
+// operand of one pass, per half-warp in the pass's current lane order (16 bank
+// pairs: position mod 16) and whole (32 banks: position mod 32).
+void bank_permutation(const std::vector<BankProg> &progs, int n_perm, int dummy, int zero, int one, long iters,
+                      std::vector<int> &perm) {
+  constexpr int NB = 32;
+  if (n_perm < 2 * NB) return;
+  auto posof = [&](int e) { return e < n_perm ? perm[e] : e; };
+  std::vector<float> gw;
+  std::vector<uint8_t> cnt, gnb;     // [G][NB] counts, bins of each group
+  std::vector<std::vector<int>> egroups(n_perm);   // groups of each permuted slot
+  auto add_group = [&](std::vector<int> &els, float w, int nb) {
+    std::sort(els.begin(), els.end());
+    els.erase(std::unique(els.begin(), els.end()), els.end());
+    bool any = false;
+    for (int e : els) any |= e < n_perm;
+    if (!any || els.size() < 2) return;
+    const int g = (int)gw.size();
+    gw.push_back(w);
+    gnb.push_back((uint8_t)nb);
+    cnt.resize(cnt.size() + NB, 0);
+    for (int e : els) {
+      cnt[(size_t)g * NB + posof(e) % nb]++;
+      if (e < n_perm) egroups[e].push_back(g);
+    }
+  };
+  for (const BankProg &bp : progs) {
+    const HostProgram &hp = *bp.hp;
+    for (int p = 0; p < hp.n_pass(); ++p) {
+      const bool rc = recip_pass(hp, p);
+      for (int r = 0; r < 4; ++r) {
+        std::vector<int> whole;
+        for (int h = 0; h < 2; ++h) {
+          std::vector<int> half;
+          for (int l = 16 * h; l < 16 * h + 16; ++l) {
+            const int e = role_elem(hp.ops[(size_t)p * WARP + l], rc, r, dummy, zero, one);
+            if (e >= 0) half.push_back(e);
+          }
+          whole.insert(whole.end(), half.begin(), half.end());
+          add_group(half, (float)bp.w, 16);
+        }
+        add_group(whole, (float)(0.5 * bp.w), 32);
+      }
+    }
+  }
+  const int G = (int)gw.size();
+  if (G == 0) return;
+  std::vector<int> stamp(G, -1);
+  uint32_t rng = 0x9e3779b9u;
+  auto move = [&](int g, int pfrom, int pto) {
+    cnt[(size_t)g * NB + pfrom % gnb[g]]--;
+    cnt[(size_t)g * NB + pto % gnb[g]]++;
+  };
+  // Objective: pairs of distinct slots sharing a bank within a group (weighted);
+  // it falls with every collision resolved, which the most loaded bank alone
+  // does not show.  Simulated annealing over swaps of two slots' positions.
+  auto pairs_delta = [&](int g, int pfrom, int pto) {
+    const uint8_t *c = &cnt[(size_t)g * NB];
+    const int bf = pfrom % gnb[g], bt = pto % gnb[g];
+    if (bf == bt) return 0;
+    return (int)c[bt] - ((int)c[bf] - 1);
+  };
+  double temp = 2.0;
+  const double cool = std::pow(0.01 / temp, 1.0 / (double)std::max<long>(iters, 1));
+  for (long it = 0; it < iters; ++it, temp *= cool) {
+    const int e1 = (int)(xorshift(rng) % (uint32_t)n_perm);
+    const int e2 = (int)(xorshift(rng) % (uint32_t)n_perm);
+    if (e1 == e2) continue;
+    const int p1 = perm[e1], p2 = perm[e2];
+    const int tag = (int)(it & 0x3fffffff);
+    for (int g : egroups[e1]) stamp[g] = tag;
+    for (int g : egroups[e2])
+      if (stamp[g] == tag) stamp[g] = -2;               // holds both: its counts do not change
+    double delta = 0.0;
+    for (int g : egroups[e1])
+      if (stamp[g] == tag) delta += gw[g] * pairs_delta(g, p1, p2);
+    for (int g : egroups[e2])
+      if (stamp[g] != -2) delta += gw[g] * pairs_delta(g, p2, p1);
+    // (a group of e1 and a group of e2 never coincide here, so the deltas add)
+    bool accept = delta <= 0.0;
+    if (!accept) accept = (double)(xorshift(rng) & 0xffffff) < 16777216.0 * std::exp(-delta / temp);
+    if (accept) {
+      for (int g : egroups[e1])
+        if (stamp[g] == tag) move(g, p1, p2);
+      for (int g : egroups[e2])
+        if (stamp[g] != -2) move(g, p2, p1);
+      perm[e1] = p2;
+      perm[e2] = p1;
+    }
+    for (int g : egroups[e2]) stamp[g] = -1;
+    for (int g : egroups[e1]) stamp[g] = -1;
+  }
+}
+
+// 8-byte wavefronts of one pass with its ops in the given lane order
+int half_cost(const std::vector<int> (&el)[4], const std::vector<int> &lane_op) {
+  int cost = 0;
+  for (int r = 0; r < 4; ++r)
+    for (int h = 0; h < 2; ++h) {
+      int e[16], n = 0;
+      for (int l = 16 * h; l < 16 * h + 16; ++l) {
+        const int x = el[r][lane_op[l]];
+        if (x >= 0) e[n++] = x;
+      }
+      std::sort(e, e + n);
+      n = (int)(std::unique(e, e + n) - e);
+      int c[16] = {0}, m = 0;
+      for (int i = 0; i < n; ++i) m = std::max(m, ++c[e[i] % 16]);
+      cost += m;
+    }
+  return cost;
+}
+
+// The lane search over every pass of hp.
+void bank_lanes(HostProgram &hp, int dummy, int zero, int one) {
+  for (int p = 0; p < hp.n_pass(); ++p) {
+    const bool rc = recip_pass(hp, p);
+    Op *ops = &hp.ops[(size_t)p * WARP];
+    std::vector<int> el[4];
+    for (int r = 0; r < 4; ++r)
+      for (int l = 0; l < WARP; ++l) el[r].push_back(role_elem(ops[l], rc, r, dummy, zero, one));
+    std::vector<int> lane_op(WARP);
+    for (int l = 0; l < WARP; ++l) lane_op[l] = l;
+    int best = half_cost(el, lane_op);
+    for (int round = 0; round < 8; ++round) {
+      bool improved = false;
+      for (int i = 0; i < 16; ++i)
+        for (int j = 16; j < WARP; ++j) {
+          std::swap(lane_op[i], lane_op[j]);
+          const int c = half_cost(el, lane_op);
+          if (c < best) {
+            best = c;
+            improved = true;
+          } else {
+            std::swap(lane_op[i], lane_op[j]);
+          }
+        }
+      if (!improved) break;
+    }
+    Op tmp[WARP];
+    for (int l = 0; l < WARP; ++l) tmp[l] = ops[lane_op[l]];
+    for (int l = 0; l < WARP; ++l) ops[l] = tmp[l];
+  }
+}
 
 // target = (fresh ? 0 : target) + sum_k W[coef_k] * W[src_k], split into chunks
 // of at most L terms accumulated in separate temporaries and then combined.
@@ -402,7 +605,7 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
     Scheduler sch(ct.base + (int)ct.vals.size() + 8);
     int temp_next = d_temp;
     for (int i = 0; i < S; ++i) add_sum(sch, d.d_F + i, true, terms[i], CHUNK, temp_next, d.d_ZERO, d.d_ONE);
-    m.f_prog = sch.finish();
+    m.f_prog = sch.finish(true);
     m.flops_f = flops;
     d.Wd_len = ct.base + (int)ct.vals.size();
     m.d_consts_v = {1.0, 0.0};
@@ -451,7 +654,7 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
     int temp_next = L_temp;
     for (int k = 0; k < nnz; ++k)
       if (!terms[k].empty()) add_sum(sch, d.L_LU + k, false, terms[k], CHUNK, temp_next, d.L_ZERO, L_ONE);
-    m.m_prog = sch.finish();
+    m.m_prog = sch.finish(true);
     m.flops_jac = flops;
     d.WL_len = ct.base + (int)ct.vals.size();
     m.L_consts_v = {0.0, 1.0, -1.0};
@@ -497,7 +700,7 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
         sch.fma(kj, kj, nk, d.L_ZERO);
       }
     }
-    m.lu_prog = sch.finish();
+    m.lu_prog = sch.finish(true);
     m.flops_lu = flops;
   }
 
@@ -633,6 +836,40 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
     msg = "mechanism too large: the per-cell work arrays exceed the 16-bit byte offsets of the warp programs";
     return CHEM_EINVAL;
   }
+  // ---- bank layout (see bank_permutation): the LU slots, then every pass's lanes
+  {
+    const int L_ONE = d.L_ZERO + 1;
+    // weights: runs per formation of M (about 4.6 Newton solves per factorisation
+    // on the 72/186 workload; the adjoint's transposed solves once per iteration walked)
+    const std::vector<BankProg> bp = {{&m.m_prog, 1.0},   {&m.lu_prog, 1.0},   {&m.fwd_prog, 4.6},
+                                      {&m.bwd_prog, 4.6}, {&m.fwdT_prog, 1.0}, {&m.bwdT_prog, 1.0}};
+    // lanes for the slots as numbered, then the permutation for those lanes, then the lanes again
+    for (const BankProg &b : bp) bank_lanes(*b.hp, d.L_DUMMY, d.L_ZERO, L_ONE);
+    std::vector<int> perm(nnz);
+    for (int e = 0; e < nnz; ++e) perm[e] = e;
+    bank_permutation(bp, nnz, d.L_DUMMY, d.L_ZERO, L_ONE, std::min<long>(700L * nnz, 2000000L), perm);
+    auto remap = [&](uint16_t &f) {
+      if (f < nnz) f = (uint16_t)perm[f];
+    };
+    for (const BankProg &b : bp)
+      for (Op &o : b.hp->ops) {
+        if (o.t == OP_EMPTY) continue;
+        if (o.t & OP_RECIP) {
+          uint16_t t = (uint16_t)(o.t & 0x7fff);
+          remap(t);
+          o.t = (uint16_t)(t | OP_RECIP);
+          remap(o.a);
+        } else {
+          remap(o.t);
+          remap(o.a);
+          remap(o.b);
+          remap(o.c);
+        }
+      }
+    for (int &x : m.lu_diag) x = d.L_LU + perm[x - d.L_LU];
+    for (const BankProg &b : bp) bank_lanes(*b.hp, d.L_DUMMY, d.L_ZERO, L_ONE);
+    bank_lanes(m.f_prog, d.d_DUMMY, d.d_ZERO, d.d_ONE);
+  }
   m.rx_slot_idx.assign((size_t)R * 3, d.d_ONE);
   for (int j = 0; j < R; ++j)
     for (int s2 = 0; s2 < rx[j].n_reac; ++s2) m.rx_slot_idx[(size_t)j * 3 + s2] = d.d_Y + rx[j].reac[s2];
@@ -727,14 +964,22 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
     const double e[RX_EXT] = {r.A2, r.Ea2_over_R, r.B2, r.A3, r.Ea3_over_R, r.B3, r.Fc, r.N};
     for (int k = 0; k < RX_EXT; ++k) ext[(size_t)j * RX_EXT + k] = e[k];
   }
-  std::vector<double> thr2(7 * GRID_N), thr3(7 * GRID_N), g(GRID_N);
+  std::vector<double> thr2(7 * GRID_N), thr3(7 * GRID_N), g(GRID_N), lim(16, 0.0);
   for (int p = 0; p < 7; ++p)
     for (int i = GRID_IMIN; i <= GRID_IMAX; ++i) {
-      // squared thresholds 1/(bias^2 2^(i(p+1)/4)): the kernel tests squared error estimates
-      thr2[p * GRID_N + i - GRID_IMIN] = 1.0 / (2.0 * 2.0 * exp2((double)i * (double)(p + 1) / 4.0));
-      thr3[p * GRID_N + i - GRID_IMIN] = 1.0 / (3.0 * 3.0 * exp2((double)i * (double)(p + 1) / 4.0));
+      // The error estimate of order p+1 is ||v|| / (p+1) with ||v||^2 = (1/S) sum (v_i w_i)^2, and
+      // its grid thresholds are 1/(bias 2^(i(p+1)/8)); the kernel compares the raw warp sum
+      // sum (v_i w_i)^2 with the thresholds squared and multiplied by S (p+1)^2.
+      const double sc = (double)S * (double)((p + 1) * (p + 1));
+      thr2[p * GRID_N + i - GRID_IMIN] = sc / (2.0 * 2.0 * exp2((double)i * (double)(p + 1) / 4.0));
+      thr3[p * GRID_N + i - GRID_IMIN] = sc / (3.0 * 3.0 * exp2((double)i * (double)(p + 1) / 4.0));
     }
   for (int i = GRID_IMIN; i <= GRID_IMAX; ++i) g[i - GRID_IMIN] = exp2((double)i / 8.0);
+  for (int q = 0; q < 8; ++q) {
+    lim[q] = (double)S * (double)((q + 1) * (q + 1));   // error test: ||d||^2 / (q+1)^2 <= 1
+    const double tol = 0.1 * (double)(q + 1);             // corrector: ||delta||^2 <= (0.1 (q+1))^2
+    lim[8 + q] = (double)S * (tol * tol);
+  }
 
   // the staged blobs, one per LU precision (identical section offsets)
   for (int prec = 0; prec < 2; ++prec) {
@@ -742,6 +987,7 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
     BlobWriter bw;
     TableOffsets t;
     t.f_ops = bw.add(device_ops(m.f_prog, 8, d.d_DUMMY, d.d_ZERO, d.d_ONE));
+    t.f_runs = bw.add(m.f_prog.runs());
     t.fwd_ops = bw.add(device_ops(m.fwd_prog, el, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1));
     t.bwd_ops = bw.add(device_ops(m.bwd_prog, el, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1));
     std::vector<uint2> slots(R);
@@ -768,11 +1014,14 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
     t.thr2 = bw.add(thr2);
     t.thr3 = bw.add(thr3);
     t.g = bw.add(g);
+    t.lim = bw.add(lim);
     t.bytes = (int)bw.buf.size();
     d.tab = t;
     int rc = put(m, bw.buf, &d.blob[prec], msg);
     if (!rc) rc = put(m, device_ops(m.m_prog, el, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1), &d.m_ops[prec], msg);
     if (!rc) rc = put(m, device_ops(m.lu_prog, el, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1), &d.lu_ops[prec], msg);
+    if (!rc && prec == 0) rc = put(m, m.m_prog.runs(), &d.m_runs, msg);
+    if (!rc && prec == 0) rc = put(m, m.lu_prog.runs(), &d.lu_runs, msg);
     if (rc) {
       free_mechanism(m);
       return rc;
@@ -797,6 +1046,9 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
     d.bwdT_npass = m.bwdT_prog.n_pass();
   }
   d.f_npass = m.f_prog.n_pass();
+  d.f_nruns = (int)m.f_prog.runs().size();
+  d.m_nruns = (int)m.m_prog.runs().size();
+  d.lu_nruns = (int)m.lu_prog.runs().size();
   d.fwd_npass = m.fwd_prog.n_pass();
   d.bwd_npass = m.bwd_prog.n_pass();
   d.m_npass = m.m_prog.n_pass();

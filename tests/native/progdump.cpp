@@ -20,6 +20,9 @@ cudaError_t set_constants() { return cudaSuccess; }
 static void dump_prog(FILE *f, const char *name, const HostProgram &p) {
   std::fprintf(f, "%s %d\n", name, p.n_pass());
   for (const Op &o : p.ops) std::fprintf(f, "%u %u %u %u\n", o.t, o.a, o.b, o.c);
+  std::fprintf(f, "units_%s", name);
+  for (uint8_t u : p.unit) std::fprintf(f, " %d", (int)u);
+  std::fprintf(f, "\n");
 }
 
 int main(int argc, char **argv) {

@@ -134,8 +134,10 @@ def compare(y, st, yo, so, oracle_lib=None, wl=None, cells=None, n_steps=1, max_
         assert tight_flips, f"{tag}{far.size} flipped cells beyond 10 tolerance units: " \
                             f"{[(int(c), round(float(units[c]), 2)) for c in far[:8]]}"
         eg, eo = tight_errors(oracle_lib, wl, cells, far, y, yo, n_steps, between)
-        worse = far[eg > 1.25 * eo + 1.0]
-        assert worse.size == 0, f"{tag}flipped cells less accurate than the oracle: {worse[:8].tolist()}"
+        bad = eg > 1.25 * eo + 1.0
+        assert not bad.any(), f"{tag}flipped cells less accurate than the oracle (cell, GPU and oracle errors " \
+                              f"against the tight reference in tolerance units): " \
+                              f"{[(int(c), round(float(a), 2), round(float(b), 2)) for c, a, b in zip(far[bad], eg[bad], eo[bad])][:8]}"
     # relative errors of the cells with identical step sequences
     absy = np.abs(yo)
     mask = absy > FLOOR

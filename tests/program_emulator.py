@@ -73,14 +73,30 @@ class Compiled:
         self.aconst = np.array(D.get("aconst", []), float).reshape(-1, 2)
         self.fill = np.array(D["fill"], int).reshape(S, S).astype(bool)
         self.nnz_jac, self.nnz_lu = map(int, D["info"])
+        # per pass: 0 single FMA pass, 1 / 2 first / second pass of an independent pair, 3 reciprocals
+        self.units = {k: np.array(D.get("units_" + k, []), int) for k in PROGRAMS}
 
 
-def run(ops, W):
-    """Replay one program on the slot array W in place (race and bounds checked)."""
+def run(ops, W, units=None):
+    """Replay one program on the slot array W in place (race and bounds checked).
+
+    units (the compiler's per-pass unit kinds): the two passes of a pair run
+    as one group of 64 ops, which the kernels execute with every load before
+    the stores, so the check covers both passes together."""
     n = W.shape[0]
-    for p in range(ops.shape[0]):
+    groups, p = [], 0
+    while p < ops.shape[0]:
+        if units is not None and len(units) and units[p] == 1:
+            assert units[p + 1] == 2, ("unpaired pair unit", p)
+            groups.append(np.concatenate([ops[p], ops[p + 1]]))
+            p += 2
+        else:
+            assert units is None or not len(units) or units[p] in (0, 3), ("stray pair unit", p)
+            groups.append(ops[p])
+            p += 1
+    for p, group in enumerate(groups):
         writes, reads, new = set(), set(), {}
-        for t, a, b, c in ops[p]:
+        for t, a, b, c in group:
             t, a, b, c = int(t), int(a), int(b), int(c)
             if t == EMPTY:
                 continue

@@ -80,7 +80,7 @@ def test_programs_compute_f_and_solve_I_minus_cJ(oracle_lib, compiled, name):
         Wd[lay["d_KT"]:lay["d_KT"] + R] = kt
         for j in range(R):                      # a2 rates, as the kernels form them before the program
             Wd[lay["d_RT"] + j] = kt[j] * np.prod(y[m.reac[j, :m.n_reac[j]]])
-        pe.run(cp.progs["f"], Wd)
+        pe.run(cp.progs["f"], Wd, cp.units["f"])
         J = oracle_lib.jacobian(om, kt, y)
         f = Wd[lay["d_F"]:lay["d_F"] + S]
         assert np.all(np.abs(f - oracle_lib.deriv(om, kt, y)) <= 1e-13 * (np.abs(J) @ np.abs(y) + 1e-300))
@@ -92,15 +92,15 @@ def test_programs_compute_f_and_solve_I_minus_cJ(oracle_lib, compiled, name):
             WL[cp.ludiag] = 1.0
             for pidx, j in enumerate(cp.pair_rx):   # -c k~_j times the pair's other reactants
                 WL[lay["L_P"] + pidx] = -c * kt[j] * Wd[cp.pair_other[pidx, 0]] * Wd[cp.pair_other[pidx, 1]]
-            pe.run(cp.progs["m"], WL)
-            pe.run(cp.progs["lu"], WL)
+            pe.run(cp.progs["m"], WL, cp.units["m"])
+            pe.run(cp.progs["lu"], WL, cp.units["lu"])
             Mk = np.eye(S) - c * J
             b = rng.standard_normal(S)
             for prog, Mref in ((("fwd", "bwd"), Mk), (("fwdT", "bwdT"), Mk.T)):
                 W = WL.copy()
                 W[lay["L_X"] + cp.pos] = b
                 for p in prog:
-                    pe.run(cp.progs[p], W)
+                    pe.run(cp.progs[p], W, cp.units[p])
                 x = -W[lay["L_X"] + cp.pos]             # the solves leave -x
                 xr = np.linalg.solve(Mref, b)
                 assert np.max(np.abs(x - xr)) <= 1e-10 * np.max(np.abs(xr)), (name, k, c, prog)
@@ -126,8 +126,8 @@ def test_adjoint_programs_compute_J_transpose_mu(oracle_lib, compiled, name):
         W[adj["a_MU"]:adj["a_MU"] + S] = mu
         for pidx, j in enumerate(cp.pair_rx):
             W[adj["a_PP"] + pidx] = kt[j] * W[cp.pair_other[pidx, 0]] * W[cp.pair_other[pidx, 1]]
-        pe.run(cp.progs["nudot"], W)
-        pe.run(cp.progs["jt"], W)
+        pe.run(cp.progs["nudot"], W, cp.units["nudot"])
+        pe.run(cp.progs["jt"], W, cp.units["jt"])
         J = oracle_lib.jacobian(om, kt, y)
         ref = J.T @ mu
         got = W[adj["a_JTM"]:adj["a_JTM"] + S]
