@@ -385,8 +385,9 @@ int chem_eval_deriv_design(chem_cells *cells, int32_t design, const double *y, d
  * device scratch, copies, and synchronises stream before returning. */
 int chem_eval_deriv(chem_cells *cells, const double *y, double *f, int32_t mem, void *stream);
 /* Diagnostic: out[i] = the FP64 reciprocal the solve kernels use (the
- * hardware estimate refined by two Newton-Raphson steps, r <- r (2 - x r)) of
- * x[i], for i < n, on the current device.  Defined for normal x with
+ * hardware estimate refined by one cubically convergent Newton-Raphson step,
+ * r <- r (1 + e + e^2) with e = 1 - x r) of x[i], for i < n, on the current
+ * device.  Defined for normal x with
  * 2^-1022 <= |x| <= 2^1022 (within 1 ulp of 1/x there); the estimate flushes
  * subnormal inputs and results to zero, so outside that range the result is
  * 0 or not finite.  No counterpart in the paper (the pivots of the LU and the
@@ -394,6 +395,18 @@ int chem_eval_deriv(chem_cells *cells, const double *y, double *f, int32_t mem, 
  * allocates device scratch and synchronises stream.  Errors: CHEM_EINVAL,
  * CHEM_ENOMEM, CHEM_ECUDA. */
 int chem_eval_reciprocal(const double *x, double *out, int64_t n, int32_t mem, void *stream);
+/* Diagnostic: out[g] = the sum the solve kernels form of the 32 doubles
+ * x[32 g .. 32 g + 31] (x: n_groups * 32 values, out: n_groups), one warp per
+ * group, as they sum the squared weighted terms of the error norms: on the
+ * integer pipe, exactly in fixed point relative to the group's largest term,
+ * rounded once (within 1.5 ulp of the exact sum).  Defined for terms >= +0;
+ * a group with an infinite, NaN or negative term, or with every term below
+ * 2^-959, is summed by an FP64 butterfly instead.  No counterpart in the
+ * paper (its error norm is the WRMS norm of the Background section's CVODE;
+ * this is how the kernels reduce it).  With CHEM_MEM_HOST the call allocates
+ * device scratch and synchronises stream.  Errors: CHEM_EINVAL, CHEM_ENOMEM,
+ * CHEM_ECUDA. */
+int chem_eval_warp_sum(const double *x, double *out, int64_t n_groups, int32_t mem, void *stream);
 int chem_eval_newton_solve(chem_cells *cells, double c, const double *y, const double *b, double *x,
                            int32_t mem, void *stream);
 

@@ -30,7 +30,7 @@ EXPORTS = ["chem_opts_default", "chem_mechanism_create", "chem_mechanism_destroy
            "chem_cells_set_theta", "chem_solve_step", "chem_solve_steps", "chem_autotune",
            "chem_get_state", "chem_get_stats", "chem_staging_fallbacks",
            "chem_eval_deriv", "chem_eval_newton_solve", "chem_eval_deriv_design", "chem_solve_step_noalloc", "chem_sensitivity",
-           "chem_sensitivity_checkpointed", "chem_eval_reciprocal", "chem_measure_fma_peak",
+           "chem_sensitivity_checkpointed", "chem_eval_reciprocal", "chem_eval_warp_sum", "chem_measure_fma_peak",
            "chem_tangent", "chem_get_tape", "chem_pipeline_create", "chem_pipeline_destroy", "chem_pipeline_run", "chem_last_error"]
 
 
@@ -108,6 +108,7 @@ def load(path: str | None = None):
         L.chem_solve_step_noalloc.argtypes = [V, ct.c_int64, V, V, V, V, V, V, ct.c_double, V, V]
         L.chem_sensitivity.argtypes = [V, V, V, V, ct.c_int32, V]
         L.chem_eval_reciprocal.argtypes = [V, V, ct.c_int64, ct.c_int32, V]
+        L.chem_eval_warp_sum.argtypes = [V, V, ct.c_int64, ct.c_int32, V]
         L.chem_measure_fma_peak.argtypes = [ct.c_int32, V, V, V]
         L.chem_sensitivity_checkpointed.argtypes = [V, V, ct.c_int32, ct.c_double, ct.c_int32, V, V, V, ct.c_int32, V]
         L.chem_tangent.argtypes = [V, V, V, V, ct.c_int32, V]
@@ -400,6 +401,16 @@ class Cells:
             self.close()
         except Exception:
             pass
+
+
+def eval_warp_sum(x, stream=None):
+    """The solve kernels' warp sum of each row of x (numpy, host, shape (n, 32)), on the GPU."""
+    xx = np.ascontiguousarray(x, np.float64)
+    assert xx.ndim == 2 and xx.shape[1] == 32
+    out = np.empty(xx.shape[0], np.float64)
+    _check(load().chem_eval_warp_sum(ct.c_void_p(xx.ctypes.data), ct.c_void_p(out.ctypes.data), xx.shape[0], MEM_HOST,
+                                     _stream_ptr(stream)), "chem_eval_warp_sum")
+    return out
 
 
 def eval_reciprocal(x, stream=None):

@@ -724,6 +724,33 @@ int chem_eval_reciprocal(const double *x, double *out, int64_t n, int32_t mem, v
   return 0;
 }
 
+int chem_eval_warp_sum(const double *x, double *out, int64_t n_groups, int32_t mem, void *stream) {
+  g_err.clear();
+  if (n_groups < 0 || (n_groups > 0 && (!x || !out))) return fail(CHEM_EINVAL, "bad argument");
+  if (int rc = check_mem(mem)) return rc;
+  if (n_groups == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t in_bytes = (size_t)n_groups * WARP * sizeof(double), out_bytes = (size_t)n_groups * sizeof(double);
+  double *tmp = nullptr;
+  const double *dx = x;
+  double *dout = out;
+  cudaError_t e = cudaSuccess;
+  if (mem == CHEM_MEM_HOST) {
+    if (cudaMalloc(&tmp, in_bytes + out_bytes) != cudaSuccess) return fail(CHEM_ENOMEM, "cudaMalloc for diagnostic scratch");
+    dx = tmp;
+    dout = tmp + (size_t)n_groups * WARP;
+    e = cudaMemcpyAsync(tmp, x, in_bytes, cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess) e = launch_wsum_probe(dx, dout, n_groups, s);
+  if (e == cudaSuccess && mem == CHEM_MEM_HOST) {
+    e = cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "warp-sum diagnostic");
+  return 0;
+}
+
 int chem_eval_deriv_design(chem_cells *c, int32_t design, const double *y, double *f, int32_t mem, void *stream) {
   Range range("chem_eval_deriv_design");
   g_err.clear();

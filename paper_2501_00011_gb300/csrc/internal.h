@@ -268,6 +268,8 @@ cudaError_t launch_adjoint(const MechDev &m, const CellsDev &c, const AdjDev &a,
 cudaError_t launch_tangent(const MechDev &m, const CellsDev &c, const TanDev &t, cudaStream_t stream);
 // diagnostic: out[i] = the solve kernels' FP64 reciprocal of x[i] (device arrays)
 cudaError_t launch_recip_probe(const double *x, double *out, int64_t n, cudaStream_t stream);
+// diagnostic: out[g] = the solve kernels' warp sum of x[32 g .. 32 g + 31] (device arrays)
+cudaError_t launch_wsum_probe(const double *x, double *out, int64_t n_groups, cudaStream_t stream);
 // *acc += the number of nonzero flags among flag[0..n)
 cudaError_t launch_count_flags(const int *flag, int64_t n, unsigned long long *acc, cudaStream_t stream);
 // deriv.cu: derivative-only kernels for comparing designs.  kt[R][C] rate

@@ -351,6 +351,47 @@ __device__ __forceinline__ bool lt0(double x) {
   return u != a && a != 0 && a <= INF_BITS;
 }
 
+// Warp sum of non-negative doubles on the integer pipe (the five FP64 adds of
+// the butterfly cost 64 cycles of an SM sub-partition each): every lane's term
+// s = m 2^(e - 1075) (m the 53-bit significand, e the biased exponent) becomes
+// the integer F = m 2^(5 + e - emax), emax the largest exponent in the warp,
+// truncated (F < 2^58); the 32 F are summed exactly as three 27-bit limbs
+// (redux.sync.add: 32 terms below 2^27 fit 32 bits) and the total rounded once
+// to nearest even.  A truncated term loses less than 1/32 of an ulp of the
+// largest term, so the result is within 1.5 ulp of the exact sum (the
+// butterfly's five roundings, 2.5).  Terms below 2^-1022 (subnormal) are
+// dropped: with emax >= 64 they are below 2^-63 of the largest.  A warp with an
+// infinite, NaN or negative term, or with every term below 2^-959, takes the
+// FP64 butterfly.
+__device__ __forceinline__ double warp_sum_nn(double s) {
+  constexpr unsigned long long FRAC = 0x000fffffffffffffull, ONE53 = 1ull << 52;
+  const unsigned long long u = ubits(s);
+  const unsigned e = (unsigned)(u >> 52);
+  const unsigned emax = __reduce_max_sync(FULL, e);
+  if (emax >= 0x7ffu || emax < 64u) return warp_sum(s);
+  const unsigned sh = emax - e;
+  unsigned long long F = 0;
+  if (e != 0 && sh < 64u) F = (((u & FRAC) | ONE53) << 5) >> sh;
+  const unsigned s0 = __reduce_add_sync(FULL, (unsigned)F & 0x7ffffffu);
+  const unsigned s1 = __reduce_add_sync(FULL, (unsigned)(F >> 27) & 0x7ffffffu);
+  const unsigned s2 = __reduce_add_sync(FULL, (unsigned)(F >> 54));
+  const unsigned long long tot =
+      (unsigned long long)s0 + ((unsigned long long)s1 << 27) + ((unsigned long long)s2 << 54);
+  // tot >= 2^57 (a lane with e == emax holds m 2^5), tot < 2^63
+  const int b = 63 - __clzll((long long)tot);
+  const int r = b - 52;
+  unsigned long long mant = tot >> r;
+  const unsigned long long rem = tot & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+  if (rem > half || (rem == half && (mant & 1ull))) ++mant;
+  int E = (int)emax + b - 57;          // the sum is tot 2^(emax - 1080)
+  if (mant >> 53) {
+    mant >>= 1;
+    ++E;
+  }
+  if (E >= 0x7ff) return __longlong_as_double((long long)INF_BITS);
+  return __longlong_as_double((long long)(((unsigned long long)E << 52) | (mant & FRAC)));
+}
+
 // Index i of the largest step factor g_i of the grid 2^(i/8) (shifted so the
 // smallest is index 0) whose threshold (host table row p, decreasing in i)
 // the squared-norm sum e meets; 0 if none.  The thresholds are scaled on the
@@ -527,18 +568,6 @@ struct Cell {
     for (int k = lane; k < M.L_nconst; k += WARP) at<T>(wl, gtab<int>(tb, M.tab.Lconst_off)[k]) = (T)gtab<double>(tb, M.tab.Lconst_val)[k];
   }
 
-  __device__ __forceinline__ double wrms(const double (&v)[KS], const double (&w)[KS]) const {
-    double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < KS; ++k)
-      if (own[k]) {
-        const double t = v[k] * w[k];
-        s = fma(t, t, s);
-      }
-    s = warp_sum(s);
-    return sqrt(s * invS);
-  }
-
   // warp sum of (v_i w_i)^2 over this cell's species
   __device__ __forceinline__ double sumsq(const double (&v)[KS], const double (&w)[KS]) const {
     double s = 0.0;
@@ -548,20 +577,7 @@ struct Cell {
         const double t = v[k] * w[k];
         s = fma(t, t, s);
       }
-    return warp_sum(s);
-  }
-
-  // squared norm (1/S) sum (v_i w_i)^2: the corrector, constraint and error
-  // tests compare squared norms with squared bounds (no square root)
-  __device__ __forceinline__ double norm2(const double (&v)[KS], const double (&w)[KS]) const {
-    double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < KS; ++k)
-      if (own[k]) {
-        const double t = v[k] * w[k];
-        s = fma(t, t, s);
-      }
-    return warp_sum(s) * invS;
+    return warp_sum_nn(s);
   }
 
   __device__ __forceinline__ void weights(const double (&y)[KS], double (&w)[KS]) const {
@@ -1018,7 +1034,7 @@ __device__ __forceinline__ void solve_cell(const MechDev &M, const CellsDev &C, 
               const double r = (D[0][k] > 0.0) ? D[0][k] / (D[0][k] - y[k]) : 0.0;
               eta_c = fmin(eta_c, r);
             }
-          vs = grp.sum(warp_sum(vs));
+          vs = grp.sum(warp_sum_nn(vs));
           if (COUPLED) vs *= gsc;
           eta_c = grp.min(warp_min(eta_c));
           if (le_nn(vs, tol2)) {
@@ -2155,6 +2171,16 @@ __global__ void __launch_bounds__(GATHER_CELLS * WARP) deriv_gather_kernel(const
 
 bool staged_driver(int driver) { return driver == CHEM_DRIVER_PERSISTENT; }
 
+// Diagnostic: the solve kernels' warp sum of non-negative doubles, one warp
+// per group of 32 consecutive elements of x.
+__global__ void wsum_probe_kernel(const double *x, double *out, int64_t n_groups) {
+  const int64_t g = (int64_t)blockIdx.x * (blockDim.x / WARP) + threadIdx.x / WARP;
+  if (g >= n_groups) return;
+  const int lane = threadIdx.x & (WARP - 1);
+  const double s = warp_sum_nn(x[g * WARP + lane]);
+  if (lane == 0) out[g] = s;
+}
+
 // Diagnostic: the solve kernels' FP64 reciprocal, element by element.
 __global__ void recip_probe_kernel(const double *x, double *out, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2162,6 +2188,12 @@ __global__ void recip_probe_kernel(const double *x, double *out, int64_t n) {
 }
 
 }  // namespace
+
+cudaError_t launch_wsum_probe(const double *x, double *out, int64_t n_groups, cudaStream_t stream) {
+  if (n_groups <= 0) return cudaSuccess;
+  wsum_probe_kernel<<<(unsigned)((n_groups + 7) / 8), 8 * WARP, 0, stream>>>(x, out, n_groups);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_recip_probe(const double *x, double *out, int64_t n, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;

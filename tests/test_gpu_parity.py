@@ -252,3 +252,42 @@ def test_reciprocal_within_one_ulp(cg):
     ulps = np.abs(r - ref) / np.spacing(np.abs(ref))
     assert np.all(np.isfinite(r)) and ulps.max() <= 1.0, (x[np.argmax(ulps)], ulps.max())
     print(f"recip_nr: {x.size} values, max {ulps.max():.2f} ulp, correctly rounded {np.mean(r == ref):.4%}")
+
+
+def test_warp_sum_within_ulps(cg):
+    # The solve kernels sum each norm's 32 per-lane terms (squared weighted
+    # values, >= 0) on the integer pipe: fixed point relative to the largest
+    # term, an exact integer sum, one rounding.  Each truncated term loses less
+    # than 1/32 ulp of the largest, so the result is within 1.5 ulp of the exact
+    # sum (math.fsum, correctly rounded).  Groups span wide and narrow dynamic
+    # ranges, zeros, ties and carries at powers of two; the fallback groups
+    # (infinite, NaN, every term below 2^-959) take an FP64 butterfly.
+    import math
+    rng = np.random.default_rng(17)
+    groups = []
+    for span in (0, 1, 4, 16, 60, 200):
+        c = rng.uniform(-150, 150, (400, 1))
+        groups.append(10.0 ** (c + rng.uniform(-span / 2, span / 2 + 1e-12, (400, 32))))
+    g = rng.uniform(0.5, 2.0, (200, 32))
+    g[rng.random((200, 32)) < 0.5] = 0.0                           # zeros
+    groups.append(g)
+    groups.append(np.full((8, 32), 1.0))                           # carries into the next binade
+    groups.append(np.full((8, 32), 1.0 + 2.0 ** -52))              # ties at the last bit
+    t = np.full((8, 32), 2.0 ** -53)
+    t[:, 0] = 1.0                                                  # exact ties below one ulp
+    groups.append(t)
+    groups.append(np.ldexp(rng.uniform(1.0, 2.0, (50, 32)), rng.integers(900, 1000, (50, 32))))   # near overflow
+    x = np.concatenate(groups)
+    x[-1, 0] = 1.0e308
+    r = cg.eval_warp_sum(x)
+    exact = np.array([math.fsum(row) for row in x])
+    fin = np.isfinite(exact)
+    ulps = np.abs(r[fin] - exact[fin]) / np.spacing(exact[fin])
+    assert ulps.max() <= 1.5, (x[fin][np.argmax(ulps)], ulps.max())
+    assert np.all(np.isinf(r[~fin]))
+    # fallback groups
+    fb = np.array([[np.inf] + [1.0] * 31, [np.nan] + [1.0] * 31, [2.0 ** -1000] * 32, [0.0] * 32])
+    rf = cg.eval_warp_sum(fb)
+    assert np.isinf(rf[0]) and np.isnan(rf[1]) and rf[3] == 0.0
+    assert abs(rf[2] - 32 * 2.0 ** -1000) <= 4 * np.spacing(32 * 2.0 ** -1000)
+    print(f"warp sum: {x.shape[0]} groups, max {ulps.max():.2f} ulp, correctly rounded {np.mean(ulps == 0):.2%}")
