@@ -32,9 +32,10 @@ constexpr int TAN_WARPS_PER_BLOCK = 4;   // ... and of the tangent walk (a large
 //   RECIP op:  W[t & 0x7fff] = -1 / W[a]         (t has bit 15 set)
 //   empty:     t == 0xffff
 // On the device the same op holds BYTE offsets into the cell's work array,
-// empty slots become a harmless FMA into a dummy slot, and every slot of a
-// RECIP pass (empty ones included) carries c == 0xffff, so the pass kind is
-// warp-uniform and no slot needs a branch.
+// empty slots become a harmless FMA into a dummy slot, and a RECIP op (or an
+// empty slot of a pass with reciprocals) carries c == 0xffff.  A pass with
+// reciprocals may hold FMA ops in its other lanes (the interpreter runs such a
+// pass as one mixed op per lane).
 struct Op {
   uint16_t t, a, b, c;
 };
@@ -117,7 +118,7 @@ struct MechDev {
 // consecutive FMA passes whose 64 ops are independent of each other (the
 // interpreter loads the operands of both before it stores either result, so a
 // lane has two FMAs in flight between warp synchronisations), a pass of
-// reciprocals.
+// reciprocals (and FMAs in the lanes the reciprocals leave).
 constexpr uint32_t RUN_FMA1 = 0, RUN_FMA2 = 1, RUN_RECIP = 2;
 
 struct HostProgram {

@@ -188,10 +188,32 @@ __device__ __forceinline__ void op_fma2(uint32_t wb, uint2 o, uint2 u) {
   sts(wb + (o.x & 0xffff), NEG ? fma(-a, b, c) : fma(a, b, c));
   sts(wb + (u.x & 0xffff), NEG ? fma(-a2, b2, c2) : fma(a2, b2, c2));
 }
-template <typename T>
-__device__ __forceinline__ void op_recip(uint32_t wb, uint2 o) {
-  T *const tag = nullptr;
-  sts(wb + (o.x & 0xffff), -lu_recip(lds(tag, wb + (o.x >> 16))));
+// A lane of a pass with reciprocals: W[t] = -1/W[a] (c == DEV_RECIP) or an
+// FMA, without a branch.  FP64: every lane forms the estimate r of 1/W[a] and
+// the cubic step's e = 1 - x r, e + e^2 (recip_nr), and the final FMA is
+// fma(-r, e + e^2, -r) = -recip_nr(x) in a reciprocal lane, the op's own FMA
+// in the others (whose r and e are discarded).
+template <typename T, bool NEG>
+__device__ __forceinline__ void op_mixed(uint32_t wb, uint2 o);
+template <>
+__device__ __forceinline__ void op_mixed<double, false>(uint32_t wb, uint2 o) {
+  double *const tag = nullptr;
+  const uint32_t oa = o.x >> 16, oc = o.y >> 16;
+  const bool rcp = oc == DEV_RECIP;
+  const double x = lds(tag, wb + oa), b = lds(tag, wb + (rcp ? oa : (o.y & 0xffff))), c = lds(tag, wb + (rcp ? oa : oc));
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  const double e = fma(-x, r, 1.0);
+  const double ee = fma(e, e, e);
+  sts(wb + (o.x & 0xffff), rcp ? fma(-r, ee, -r) : fma(x, b, c));
+}
+template <>
+__device__ __forceinline__ void op_mixed<float, false>(uint32_t wb, uint2 o) {
+  float *const tag = nullptr;
+  const uint32_t oa = o.x >> 16, oc = o.y >> 16;
+  const bool rcp = oc == DEV_RECIP;
+  const float x = lds(tag, wb + oa), b = lds(tag, wb + (rcp ? oa : (o.y & 0xffff))), c = lds(tag, wb + (rcp ? oa : oc));
+  sts(wb + (o.x & 0xffff), rcp ? -__frcp_rn(x) : fmaf(x, b, c));
 }
 
 // A program with a run table (RUN_* units, internal.h).  The ops of the next
@@ -227,7 +249,7 @@ __device__ __forceinline__ void run_prog(const ushort4 *ops, const uint32_t *run
         const uint2 o = n0;
         n0 = n1;
         if (p + 2 < np) n1 = ld_op<SMEM>(ops + (size_t)(p + 2) * WARP);
-        op_recip<T>(wb, o);
+        op_mixed<T, NEG>(wb, o);
         __syncwarp();
       }
     } else {
@@ -300,7 +322,7 @@ __device__ __forceinline__ void run_prog_ring(const ushort4 *ops, const uint32_t
         cp_async_wait<RING - 4>();      // pass p + 2 has landed
         if (p + 2 < np)
           asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(n1.x), "=r"(n1.y) : "r"(rb + 256u * ((p + 2) % RING)) : "memory");
-        if (RECIP && kind == RUN_RECIP) op_recip<T>(wb, o);
+        if (RECIP && kind == RUN_RECIP) op_mixed<T, NEG>(wb, o);
         else op_fma<T, NEG>(wb, o);
         __syncwarp();
       }

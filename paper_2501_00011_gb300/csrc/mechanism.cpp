@@ -130,6 +130,12 @@ struct Scheduler {
         pass.push_back(ready[k].top());
         ready[k].pop();
       }
+      // wide: a pass of reciprocals takes the most urgent ready FMAs into its
+      // other lanes (the kernels run such a pass as one mixed op per lane)
+      while (wide && k == 1 && !ready[0].empty() && pass.size() < (size_t)WARP) {
+        pass.push_back(ready[0].top());
+        ready[0].pop();
+      }
       for (int i : pass) hp.ops.push_back(rec_op[i]);
       for (size_t i = pass.size(); i < (size_t)WARP; ++i) hp.ops.push_back(Op{OP_EMPTY, 0, 0, 0});
       if (k == 1) hp.unit.push_back(3);
@@ -184,7 +190,7 @@ int role_elem(const Op &o, bool recip, int r, int dummy, int zero, int one) {
     if (recip) return r == 0 ? dummy : r == 1 ? one : -1;
     return r == 0 ? dummy : zero;
   }
-  if (recip) return r == 0 ? (o.t & 0x7fff) : r == 1 ? o.a : -1;
+  if (o.t & OP_RECIP) return r == 0 ? (o.t & 0x7fff) : r == 1 ? o.a : -1;
   return r == 0 ? o.t : r == 1 ? o.a : r == 2 ? o.b : o.c;
 }
 
@@ -891,7 +897,8 @@ int put(Mechanism &m, const std::vector<T> &v, const T **dst, std::string &msg) 
 }
 
 // Device form of a program: byte offsets (element index * elem), empty slots
-// as FMAs into the dummy slot, RECIP passes marked in every slot.
+// as FMAs into the dummy slot (in a pass with reciprocals: a reciprocal of one
+// into it), RECIP ops marked by c == DEV_RECIP.
 std::vector<ushort4> device_ops(const HostProgram &hp, int elem, int dummy, int zero, int one) {
   std::vector<ushort4> v(hp.ops.size());
   const int np = hp.n_pass();
@@ -907,7 +914,7 @@ std::vector<ushort4> device_ops(const HostProgram &hp, int elem, int dummy, int 
       if (o.t == OP_EMPTY) {
         d = recip ? make_ushort4(dummy * elem, one * elem, 0, DEV_RECIP)
                   : make_ushort4(dummy * elem, zero * elem, zero * elem, zero * elem);
-      } else if (recip) {
+      } else if (o.t & OP_RECIP) {
         d = make_ushort4((o.t & 0x7fff) * elem, o.a * elem, 0, DEV_RECIP);
       } else {
         d = make_ushort4(o.t * elem, o.a * elem, o.b * elem, o.c * elem);
