@@ -111,6 +111,8 @@ struct MechDev {
   const ushort4 *nudot_ops, *jt_ops;    // programs on the extended Wd
   const ushort4 *fwdT_ops, *bwdT_ops;   // U^T and L^T solves on WL (FP64 byte offsets)
   int nudot_npass, jt_npass, fwdT_npass, bwdT_npass;
+  const uint32_t *nudot_runs, *jt_runs, *fwdT_runs, *bwdT_runs;   // their run tables
+  int nudot_nruns, jt_nruns, fwdT_nruns, bwdT_nruns;
 };
 
 // Kinds of the units a program's passes form, in its run table (one uint32 per

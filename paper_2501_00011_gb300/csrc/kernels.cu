@@ -1516,8 +1516,8 @@ __device__ __forceinline__ void jt_and_theta(const MechDev &M, double *Wd, const
   for (int k = 0; k < KS; ++k)
     if (own[k]) Wd[M.a_MU + lane + WARP * k] = v[k];
   __syncwarp();
-  run_ops<double, false, false>(M.nudot_ops, M.nudot_npass, Wd, lane);
-  run_ops<double, false, false>(M.jt_ops, M.jt_npass, Wd, lane);
+  run_prog<double, false, false, true, false>(M.nudot_ops, M.nudot_runs, M.nudot_nruns, M.nudot_npass, Wd, lane);
+  run_prog<double, false, false, true, false>(M.jt_ops, M.jt_runs, M.jt_nruns, M.jt_npass, Wd, lane);
   for (int j = lane; j < M.R; j += WARP) Wd[M.a_G + j] = fma(scale * Wd[M.d_RT + j], Wd[M.a_NM + j], Wd[M.a_G + j]);
 #pragma unroll
   for (int k = 0; k < KS; ++k) out[k] = own[k] ? Wd[M.a_JTM + lane + WARP * k] : 0.0;
@@ -1616,8 +1616,8 @@ __device__ void backward_cell(const MechDev &M, const CellsDev &C, const AdjDev 
       for (int k = 0; k < KS; ++k)
         if (cl.own[k]) WL[M.L_X + cl.pos[k]] = lamd[k];
       __syncwarp();
-      run_ops<double, false, false>(M.fwdT_ops, M.fwdT_npass, WL, lane);
-      run_ops<double, false, false>(M.bwdT_ops, M.bwdT_npass, WL, lane);
+      run_prog<double, false, false, false, false>(M.fwdT_ops, M.fwdT_runs, M.fwdT_nruns, M.fwdT_npass, WL, lane);
+      run_prog<double, false, false, false, false>(M.bwdT_ops, M.bwdT_runs, M.bwdT_nruns, M.bwdT_npass, WL, lane);
 #pragma unroll
       for (int k = 0; k < KS; ++k) g[k] = cl.own[k] ? -ss * WL[M.L_X + cl.pos[k]] : 0.0;   // the programs leave -M^{-T} lambda
       __syncwarp();
@@ -1748,7 +1748,8 @@ __device__ __forceinline__ void tangent_f(const MechDev &M, const Tabs &tb, doub
     Wd[M.d_RT + j] = sj;
   }
   __syncwarp();
-  run_ops<double, false, false>(tab<ushort4>(tb, M.tab.f_ops), M.f_npass, Wd, lane);
+  run_prog<double, false, false, true, false>(tab<ushort4>(tb, M.tab.f_ops), tab<uint32_t>(tb, M.tab.f_runs), M.f_nruns,
+                                              M.f_npass, Wd, lane);
 #pragma unroll
   for (int k = 0; k < KS; ++k) out[k] = own[k] ? Wd[M.d_F + lane + WARP * k] : 0.0;
   __syncwarp();

@@ -790,8 +790,8 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
       for (auto &t : jt_terms[l]) terms.push_back({d.a_PP + t.first, d.a_NM + t.second});
       add_sum(b, d.a_JTM + l, true, terms, CHUNK, temp_next, d.d_ZERO, d.d_ONE);
     }
-    m.nudot_prog = a.finish();
-    m.jt_prog = b.finish();
+    m.nudot_prog = a.finish(true);
+    m.jt_prog = b.finish(true);
     d.Wda_len = wda_len;
     m.a_consts_v = ct.vals;
     m.a_consts_i.clear();
@@ -1042,7 +1042,9 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
         (rc = put(m, device_ops(m.nudot_prog, 8, d.d_DUMMY, d.d_ZERO, d.d_ONE), &d.nudot_ops, msg)) ||
         (rc = put(m, device_ops(m.jt_prog, 8, d.d_DUMMY, d.d_ZERO, d.d_ONE), &d.jt_ops, msg)) ||
         (rc = put(m, device_ops(m.fwdT_prog, 8, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1), &d.fwdT_ops, msg)) ||
-        (rc = put(m, device_ops(m.bwdT_prog, 8, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1), &d.bwdT_ops, msg))) {
+        (rc = put(m, device_ops(m.bwdT_prog, 8, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1), &d.bwdT_ops, msg)) ||
+        (rc = put(m, m.nudot_prog.runs(), &d.nudot_runs, msg)) || (rc = put(m, m.jt_prog.runs(), &d.jt_runs, msg)) ||
+        (rc = put(m, m.fwdT_prog.runs(), &d.fwdT_runs, msg)) || (rc = put(m, m.bwdT_prog.runs(), &d.bwdT_runs, msg))) {
       free_mechanism(m);
       return rc;
     }
@@ -1051,6 +1053,10 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
     d.jt_npass = m.jt_prog.n_pass();
     d.fwdT_npass = m.fwdT_prog.n_pass();
     d.bwdT_npass = m.bwdT_prog.n_pass();
+    d.nudot_nruns = (int)m.nudot_prog.runs().size();
+    d.jt_nruns = (int)m.jt_prog.runs().size();
+    d.fwdT_nruns = (int)m.fwdT_prog.runs().size();
+    d.bwdT_nruns = (int)m.bwdT_prog.runs().size();
   }
   d.f_npass = m.f_prog.n_pass();
   d.f_nruns = (int)m.f_prog.runs().size();
