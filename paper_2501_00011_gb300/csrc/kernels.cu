@@ -1554,6 +1554,21 @@ __device__ void backward_cell(const MechDev &M, const CellsDev &C, const AdjDev 
   const double *vals = C.tape_val + cell * (int64_t)C.tape_cap;
   const double *yt = C.ytape + cell * (int64_t)C.row_cap * M.S;
   int row = C.tape_rows[cell];     // rows of the events before the walk position
+  // the walk reads rows row-1, row-2, ...; the next one is loaded a row ahead
+  // (its global loads complete while the current event is processed)
+  double pre[KS];
+  int pre_row = row - 1;
+  if (pre_row >= 0) read_row<KS>(yt, pre_row, M.S, cl.own, lane, pre);
+  auto take_row = [&](double (&y)[KS]) {      // row (already decremented)
+    if (pre_row == row) {
+#pragma unroll
+      for (int k = 0; k < KS; ++k) y[k] = pre[k];
+    } else {
+      read_row<KS>(yt, row, M.S, cl.own, lane, y);
+    }
+    pre_row = row - 1;
+    if (pre_row >= 0) read_row<KS>(yt, pre_row, M.S, cl.own, lane, pre);
+  };
   int er = n - 1;                  // the last REFACTOR before the walk position
   while (er >= 0 && (__ldg(kqs + er) & 0xff) != EV_REFACTOR) --er;
   int m_event = -1;                // the REFACTOR whose LU is in WL
@@ -1605,7 +1620,7 @@ __device__ void backward_cell(const MechDev &M, const CellsDev &C, const AdjDev 
         break;
       }
       double y[KS], g[KS], jtg[KS];
-      read_row<KS>(yt, row, M.S, cl.own, lane, y);
+      take_row(y);
 #pragma unroll
       for (int k = 0; k < KS; ++k)
         if (cl.own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
@@ -1649,7 +1664,7 @@ __device__ void backward_cell(const MechDev &M, const CellsDev &C, const AdjDev 
         break;
       }
       double y[KS], jtl[KS], l1[KS];
-      read_row<KS>(yt, row, M.S, cl.own, lane, y);
+      take_row(y);
 #pragma unroll
       for (int k = 0; k < KS; ++k)
         if (cl.own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
@@ -1775,6 +1790,15 @@ __device__ void tangent_cell(const MechDev &M, const CellsDev &C, const TanDev &
   const double *vals = C.tape_val + cell * (int64_t)C.tape_cap;
   const double *yt = C.ytape + cell * (int64_t)C.row_cap * M.S;
   int row = 0;
+  // the tape's rows are read in order; the next one is loaded a row ahead (its
+  // global loads complete while the current event is processed)
+  double pre[KS];
+  if (nrows > 0) read_row<KS>(yt, 0, M.S, cl.own, lane, pre);
+  auto next_row = [&](double (&y)[KS]) {
+#pragma unroll
+    for (int k = 0; k < KS; ++k) y[k] = pre[k];
+    if (++row < nrows) read_row<KS>(yt, row, M.S, cl.own, lane, pre);
+  };
   bool in_step = false, have_M = false, bad = false;
   double cM = 0.0, sc = 0.0, ss = 1.0;
   int sq = 1;
@@ -1839,7 +1863,7 @@ __device__ void tangent_cell(const MechDev &M, const CellsDev &C, const TanDev &
         break;
       }
       double y[KS], g[KS], d0[KS];
-      read_row<KS>(yt, row++, M.S, cl.own, lane, y);
+      next_row(y);
 #pragma unroll
       for (int k = 0; k < KS; ++k) {
         d0[k] = dD[0][k];
@@ -1859,7 +1883,7 @@ __device__ void tangent_cell(const MechDev &M, const CellsDev &C, const TanDev &
         break;
       }
       double yJ[KS];
-      read_row<KS>(yt, row++, M.S, cl.own, lane, yJ);
+      next_row(yJ);
       cl.form_and_factor(val, yJ);
       cM = val;
       have_M = true;
@@ -1869,7 +1893,7 @@ __device__ void tangent_cell(const MechDev &M, const CellsDev &C, const TanDev &
         break;
       }
       double y[KS], v[KS], g[KS], b[KS], x[KS];
-      read_row<KS>(yt, row++, M.S, cl.own, lane, y);
+      next_row(y);
 #pragma unroll
       for (int k = 0; k < KS; ++k) {
         v[k] = dyp[k] + dd[k];
