@@ -478,14 +478,33 @@ __device__ __forceinline__ const X *gtab(const Tabs &tb, int off) {
 // a2: r_j = k~_j prod y, then f = the f program, from y in Wd[Y]
 template <bool STAGED>
 __device__ __forceinline__ void f_core(const MechDev &M, const unsigned char *tbase, double *Wd, const int lane) {
-  unsigned char *wd = reinterpret_cast<unsigned char *>(Wd);
   const uint2 *slots = reinterpret_cast<const uint2 *>(tbase + M.tab.rx_slots);
-  for (int j = lane; j < M.R; j += WARP) {
+  // two reactions per lane and iteration, so each lane has two products' loads in flight
+  const uint32_t wb = smem_addr(Wd), kt = wb + 8u * M.d_KT, rt = wb + 8u * M.d_RT;
+  double *const tag = nullptr;
+  int j = lane;
+#pragma unroll 1
+  for (; j + WARP < M.R; j += 2 * WARP) {
+    const uint2 s0 = slots[j], s1 = slots[j + WARP];
+    double r0 = lds(tag, kt + 8u * j) * lds(tag, wb + (s0.x & 0xffff));
+    double r1 = lds(tag, kt + 8u * (j + WARP)) * lds(tag, wb + (s1.x & 0xffff));
+    if (M.max_reac > 1) {
+      r0 *= lds(tag, wb + (s0.x >> 16));
+      r1 *= lds(tag, wb + (s1.x >> 16));
+    }
+    if (M.max_reac > 2) {
+      r0 *= lds(tag, wb + (s0.y & 0xffff));
+      r1 *= lds(tag, wb + (s1.y & 0xffff));
+    }
+    sts(rt + 8u * j, r0);
+    sts(rt + 8u * (j + WARP), r1);
+  }
+  if (j < M.R) {
     const uint2 sl = slots[j];
-    double r = Wd[M.d_KT + j] * at<double>(wd, sl.x & 0xffff);
-    if (M.max_reac > 1) r *= at<double>(wd, sl.x >> 16);
-    if (M.max_reac > 2) r *= at<double>(wd, sl.y & 0xffff);
-    Wd[M.d_RT + j] = r;
+    double r = lds(tag, kt + 8u * j) * lds(tag, wb + (sl.x & 0xffff));
+    if (M.max_reac > 1) r *= lds(tag, wb + (sl.x >> 16));
+    if (M.max_reac > 2) r *= lds(tag, wb + (sl.y & 0xffff));
+    sts(rt + 8u * j, r);
   }
   __syncwarp();
   run_prog<double, false, STAGED, true, false>(reinterpret_cast<const ushort4 *>(tbase + M.tab.f_ops),
@@ -506,12 +525,32 @@ __device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *
   const unsigned *pother = reinterpret_cast<const unsigned *>(tbase + M.tab.pair_other);
   for (int k = lane; k < M.S; k += WARP) at<T>(wl, diag[k]) = (T)1;
   const double mc = -c;
-  for (int pr = lane; pr < M.n_pairs; pr += WARP) {
+  // two pairs per lane and iteration (loads in flight together)
+  const uint32_t wdb = smem_addr(Wd), kt = wdb + 8u * M.d_KT;
+  double *const tag = nullptr;
+  int pr = lane;
+#pragma unroll 1
+  for (; pr + WARP < M.n_pairs; pr += 2 * WARP) {
+    const int j0 = prx[pr], j1 = prx[pr + WARP];
+    const unsigned o0 = pother[pr], o1 = pother[pr + WARP];
+    double p0 = mc * lds(tag, kt + 8u * j0), p1 = mc * lds(tag, kt + 8u * j1);
+    if (M.max_reac > 1) {
+      p0 *= lds(tag, wdb + (o0 & 0xffff));
+      p1 *= lds(tag, wdb + (o1 & 0xffff));
+    }
+    if (M.max_reac > 2) {
+      p0 *= lds(tag, wdb + (o0 >> 16));
+      p1 *= lds(tag, wdb + (o1 >> 16));
+    }
+    WL[M.L_P + pr] = (T)p0;
+    WL[M.L_P + pr + WARP] = (T)p1;
+  }
+  if (pr < M.n_pairs) {
     const int j = prx[pr];
     const unsigned o = pother[pr];
-    double p = mc * Wd[M.d_KT + j];
-    if (M.max_reac > 1) p *= at<double>(wd, o & 0xffff);
-    if (M.max_reac > 2) p *= at<double>(wd, o >> 16);
+    double p = mc * lds(tag, kt + 8u * j);
+    if (M.max_reac > 1) p *= lds(tag, wdb + (o & 0xffff));
+    if (M.max_reac > 2) p *= lds(tag, wdb + (o >> 16));
     WL[M.L_P + pr] = (T)p;
   }
   __syncwarp();
