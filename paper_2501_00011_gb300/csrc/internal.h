@@ -49,6 +49,7 @@ constexpr uint16_t DEV_RECIP = 0xffff;     // device marker in .w of RECIP passe
 struct TableOffsets {
   int f_ops, fwd_ops, bwd_ops;     // ushort4 programs (f on Wd, fwd/bwd on WL)
   int f_runs;                      // uint32 run table of the f program
+  int m_ops, m_runs;               // the M program (on the whole per-cell slice) and its run table
   int rx_slots;                    // uint2 [R]: byte offsets into Wd of the reactants' y
   int pair_rx;                     // int [n_pairs]
   int pair_other;                  // uint32 [n_pairs]: two 16-bit byte offsets into Wd
@@ -62,7 +63,8 @@ struct TableOffsets {
                                    // test, S (q+1)^2, and of the corrector, S (0.1 (q+1))^2
   int staged;                      // bytes of the prefix the persistent driver stages in shared
                                    // memory (programs and slots used every Newton iteration or
-                                   // refactorisation; constants and the grid stay in global memory)
+                                   // formation of M; the LU program, constants and the grid stay
+                                   // in global memory)
   int bytes;                       // total, a multiple of 16
 };
 
@@ -102,8 +104,9 @@ struct MechDev {
   // history rescale T(eta)_{im} = sum_p coef[(i-1)*QMAX + m-1][p] eta^p,
   // i, m = 1..QMAX, p = 0..QMAX
   const double *rescale_coef;
-  // ---- discrete adjoint (FP64): Wd extended by mu[S], nm[R] = nu_j . mu,
-  // pp[n_pairs] = dr_j/dy_l, jtm[S] = J^T mu, g[R] (theta gradient), temps, constants
+  // ---- discrete adjoint (FP64): after the forward's Wd and WL, mu[S], nm[R] =
+  // nu_j . mu, jtm[S] = J^T mu, g[R] (theta gradient), temps, constants (up to
+  // Wda_len), then pp[n_pairs] = dr_j/dy_l at a_PP; indices from the start of Wd
   int Wda_len, a_MU, a_NM, a_PP, a_JTM, a_G;
   int a_nconst;
   const int *a_const_off;          // byte offsets into the extended Wd

@@ -513,7 +513,7 @@ __device__ __forceinline__ void f_core(const MechDev &M, const unsigned char *tb
 }
 
 // a3-a5: M = I - c J(y) in the LU slots from y in Wd[Y], then factor
-template <typename T>
+template <typename T, bool STAGED>
 __device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *tbase, const int prec, double *Wd, T *WL,
                                       const double c, const int lane) {
   for (int i = lane; i < M.m_clear; i += WARP) WL[i] = (T)0;
@@ -525,7 +525,9 @@ __device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *
   const unsigned *pother = reinterpret_cast<const unsigned *>(tbase + M.tab.pair_other);
   for (int k = lane; k < M.S; k += WARP) at<T>(wl, diag[k]) = (T)1;
   const double mc = -c;
-  // two pairs per lane and iteration (loads in flight together)
+  // two pairs per lane and iteration (loads in flight together); the pair
+  // products go to the slots of the rates, f and f temps, dead while M is formed
+  T *const pp = reinterpret_cast<T *>(Wd + M.d_RT);
   const uint32_t wdb = smem_addr(Wd), kt = wdb + 8u * M.d_KT;
   double *const tag = nullptr;
   int pr = lane;
@@ -542,8 +544,8 @@ __device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *
       p0 *= lds(tag, wdb + (o0 >> 16));
       p1 *= lds(tag, wdb + (o1 >> 16));
     }
-    WL[M.L_P + pr] = (T)p0;
-    WL[M.L_P + pr + WARP] = (T)p1;
+    pp[pr] = (T)p0;
+    pp[pr + WARP] = (T)p1;
   }
   if (pr < M.n_pairs) {
     const int j = prx[pr];
@@ -551,32 +553,36 @@ __device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *
     double p = mc * lds(tag, kt + 8u * j);
     if (M.max_reac > 1) p *= lds(tag, wdb + (o & 0xffff));
     if (M.max_reac > 2) p *= lds(tag, wdb + (o >> 16));
-    WL[M.L_P + pr] = (T)p;
+    pp[pr] = (T)p;
   }
   __syncwarp();
-  // Both programs are read from L2, so their ops are streamed ahead through a
-  // ring in memory that is dead while M is formed and factored: the rates and
-  // f slots of Wd (f is not being evaluated).  Too small a region: ops read
-  // from L2 one unit ahead.
+  // The M program runs on the whole per-cell slice (its operands are the pair
+  // products in Wd and the LU slots, constants and temporaries in WL), its ops
+  // staged in shared memory (the persistent driver) or read from L2 two passes
+  // ahead.  The LU program's ops are streamed through a ring in the rates and f
+  // slots of Wd, dead once M is formed (too small a region: read from L2 as well).
+  if (STAGED)
+    run_prog<T, false, true, true, false>(reinterpret_cast<const ushort4 *>(tbase + M.tab.m_ops),
+                                          reinterpret_cast<const uint32_t *>(tbase + M.tab.m_runs), M.m_nruns,
+                                          M.m_npass, reinterpret_cast<T *>(Wd), lane);
+  else
+    run_prog<T, false, false, true, false>(M.m_ops[prec], M.m_runs, M.m_nruns, M.m_npass, reinterpret_cast<T *>(Wd),
+                                           lane);
   const uint32_t wr = smem_addr(Wd + M.d_RT);            // 8-byte aligned (a double slot)
-  if ((M.R + M.S) * 8 >= 8 * 256) {
-    run_prog_ring<T, false, 8, true, false>(M.m_ops[prec], M.m_runs, M.m_nruns, M.m_npass, WL, lane, wr);
+  if ((M.R + M.S) * 8 >= 8 * 256)
     run_prog_ring<T, false, 8, true, true>(M.lu_ops[prec], M.lu_runs, M.lu_nruns, M.lu_npass, WL, lane, wr);
-  } else {
-    run_prog<T, false, false, true, false>(M.m_ops[prec], M.m_runs, M.m_nruns, M.m_npass, WL, lane);
+  else
     run_prog<T, false, false, true, true>(M.lu_ops[prec], M.lu_runs, M.lu_nruns, M.lu_npass, WL, lane);
-  }
 }
 
 // a5: forward and backward substitution with the LDU factors on the vector in
 // WL[X]; it leaves -x there (the programs run without negation).  Staged (the
 // persistent driver) the programs are read from shared memory; otherwise they
-// are streamed from L2 through a ring in the pair products, which are dead
-// from the end of the factorisation to the next one.  (Streaming them in the
-// staged form too would free room for an eleventh cell per SM, but measured
-// slower: 28.2 against 27.4 ms on the 10,000-cell step.)
+// are streamed from L2 through a ring in the rates and f slots of Wd, which
+// are dead during a solve.  (Streaming them in the staged form too measured
+// slower, at 10 cells per SM and at the 11 that it lets fit.)
 template <typename T, bool STAGED>
-__device__ __forceinline__ void solve_core(const MechDev &M, const unsigned char *tbase, T *WL, const int lane) {
+__device__ __forceinline__ void solve_core(const MechDev &M, const unsigned char *tbase, double *Wd, T *WL, const int lane) {
   const ushort4 *fwd = reinterpret_cast<const ushort4 *>(tbase + M.tab.fwd_ops);
   const ushort4 *bwd = reinterpret_cast<const ushort4 *>(tbase + M.tab.bwd_ops);
   if (STAGED) {
@@ -584,9 +590,8 @@ __device__ __forceinline__ void solve_core(const MechDev &M, const unsigned char
     run_ops<T, false, true>(bwd, M.bwd_npass, WL, lane);
     return;
   }
-  const uint32_t pb = smem_addr(WL + M.L_P);
-  const uint32_t rb = (pb + 7u) & ~7u;
-  const int cap = M.n_pairs * (int)sizeof(T) - (int)(rb - pb);
+  const uint32_t rb = smem_addr(Wd + M.d_RT);            // the rates and f slots: dead during a solve
+  const int cap = (M.R + M.S) * 8;
   if (cap >= 8 * 256) {
     run_ops_ring<T, false, 8>(fwd, M.fwd_npass, WL, lane, rb);
     run_ops_ring<T, false, 8>(bwd, M.bwd_npass, WL, lane, rb);
@@ -663,7 +668,7 @@ struct Cell {
 #pragma unroll
     for (int k = 0; k < KS; ++k)
       if (own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
-    mlu_core<T>(M, tb.base, P.prec, Wd, WL, c, lane);
+    mlu_core<T, STAGED>(M, tb.base, P.prec, Wd, WL, c, lane);
   }
 
   // a5: x = M^{-1} b with the factored M
@@ -672,7 +677,7 @@ struct Cell {
     for (int k = 0; k < KS; ++k)
       if (own[k]) WL[M.L_X + pos[k]] = (T)b[k];
     __syncwarp();
-    solve_core<T, STAGED>(M, tb.base, WL, lane);
+    solve_core<T, STAGED>(M, tb.base, Wd, WL, lane);
 #pragma unroll
     for (int k = 0; k < KS; ++k) x[k] = own[k] ? -(double)WL[M.L_X + pos[k]] : 0.0;
     __syncwarp();
@@ -2407,8 +2412,9 @@ cudaError_t launch_solve(const MechDev &M, const CellsDev &C, const LaunchCfg &c
 cudaError_t launch_adjoint(const MechDev &M, const CellsDev &C, const AdjDev &A, cudaStream_t stream) {
   if (C.n_cells <= 0) return cudaSuccess;
   SolveParams P{};
-  P.wd_pad = (M.Wda_len + 1) & ~1;
-  P.cell_bytes = (int)(((size_t)P.wd_pad * sizeof(double) + (size_t)M.WL_len * sizeof(double) + 15) & ~(size_t)15);
+  // the forward's Wd and WL, the adjoint's arrays, then the partials dr_j/dy_l (at a_PP)
+  P.wd_pad = (M.Wd_len + 1) & ~1;
+  P.cell_bytes = (int)(((size_t)(M.a_PP + M.n_pairs) * sizeof(double) + 15) & ~(size_t)15);
   P.prec = 0;
   P.tab_bytes = 0;
   cudaError_t e = cudaSuccess;
@@ -2433,10 +2439,10 @@ cudaError_t launch_count_flags(const int *flag, int64_t n, unsigned long long *a
 cudaError_t launch_tangent(const MechDev &M, const CellsDev &C, const TanDev &A, cudaStream_t stream) {
   if (C.n_cells <= 0) return cudaSuccess;
   SolveParams P{};
-  // the tangent walk uses the forward's Wd and one species vector after it
-  // (the direction v at a_MU), not the adjoint's extended array
-  P.wd_pad = (M.a_MU + M.S + 1) & ~1;
-  P.cell_bytes = (int)(((size_t)P.wd_pad * sizeof(double) + (size_t)M.WL_len * sizeof(double) + 15) & ~(size_t)15);
+  // the tangent walk uses the forward's Wd and WL and one species vector after
+  // them (the direction v at a_MU), not the adjoint's other arrays
+  P.wd_pad = (M.Wd_len + 1) & ~1;
+  P.cell_bytes = (int)(((size_t)(M.a_MU + M.S) * sizeof(double) + 15) & ~(size_t)15);
   P.prec = 0;
   switch ((M.S + WARP - 1) / WARP) {
     case 1: return launch_tan_t<1>(M, C, A, P, stream);

@@ -471,6 +471,7 @@ struct ConstTable {
 };
 
 constexpr int CHUNK = 8;
+constexpr int P_VIRTUAL = 0x6000;   // the M program's name for pair product 0 (above every WL slot)
 constexpr int NSTMP = 16;   // temporaries of the triangular solves
 
 }  // namespace
@@ -565,7 +566,10 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
   m.nnz_lu = nnz;
 
   // ---- per-cell array layouts
-  // Wd (double): y[S], ONE, ZERO, kt[R], rates[R], f[S], f temps, nu constants
+  // Wd (double): y[S], ONE, ZERO, nu constants of the f program, kt[R], rates[R],
+  // f[S], f temps; the Jacobian's pair products (in the LU precision) reuse the
+  // slots from rates[0] on while M is formed (rates, f and the f temps are dead
+  // then), so Wd extends past the f temps if they need more room.
   MechDev &d = m.dev;
   d.S = S;
   d.R = R;
@@ -575,17 +579,26 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
   d.d_Y = 0;
   d.d_ONE = S;
   d.d_ZERO = S + 1;
-  d.d_KT = S + 2;
+  std::vector<std::vector<std::pair<double, int>>> f_by_species(S);
+  for (int j = 0; j < R; ++j)
+    for (auto &kv : nu[j]) f_by_species[kv.first].push_back({kv.second, j});
+  ConstTable fct;                          // the f program's constants, numbered before k~
+  fct.base = S + 2;
+  for (int i = 0; i < S; ++i)
+    for (auto &t : f_by_species[i]) fct.get(t.first);
+  d.d_KT = fct.base + (int)fct.vals.size();
   d.d_RT = d.d_KT + R;
   d.d_F = d.d_RT + R;
   int d_temp = d.d_F + S;
-  // WL (LU precision): LU[nnz] (-1/u_kk in the pivot slots once factored), x[S], P[n_pairs],
-  // ZERO, ONE, M temps, nu constants, solve temporaries
+  // WL (LU precision): LU[nnz] (-1/u_kk in the pivot slots once factored), x[S],
+  // ZERO, ONE, M temps, nu constants, solve temporaries.  The M program names the
+  // pair products by the virtual indices P_VIRTUAL + pair (above every WL
+  // slot); its device form maps them to their slots in Wd.
   d.L_LU = 0;
   d.nnz_lu = nnz;
   d.L_X = nnz;
-  d.L_P = d.L_X + S;
-  d.L_ZERO = d.L_P + n_pairs;
+  d.L_P = P_VIRTUAL;
+  d.L_ZERO = d.L_X + S;
   const int L_ONE = d.L_ZERO + 1;
   const int L_NEG_ONE = L_ONE + 1;
   int L_temp = L_NEG_ONE + 1;
@@ -593,13 +606,10 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
 
   // ---- f program: f_i = sum_j nu_ij r_j, species-major, chunked
   {
-    std::vector<std::vector<std::pair<double, int>>> by_species(S);
-    for (int j = 0; j < R; ++j)
-      for (auto &kv : nu[j]) by_species[kv.first].push_back({kv.second, j});
+    const std::vector<std::vector<std::pair<double, int>>> &by_species = f_by_species;
     int n_temp = 0;
     for (int i = 0; i < S; ++i) n_temp += (int)std::max<size_t>(1, (by_species[i].size() + CHUNK - 1) / CHUNK) - 1;
-    ConstTable ct;
-    ct.base = d_temp + n_temp;
+    ConstTable &ct = fct;
     std::vector<std::vector<std::pair<int, int>>> terms(S);
     double flops = 0;
     for (int i = 0; i < S; ++i)
@@ -608,12 +618,12 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
         flops += 2;
       }
     for (int j = 0; j < R; ++j) flops += rx[j].n_reac;
-    Scheduler sch(ct.base + (int)ct.vals.size() + 8);
+    Scheduler sch(d_temp + n_temp + 8);
     int temp_next = d_temp;
     for (int i = 0; i < S; ++i) add_sum(sch, d.d_F + i, true, terms[i], CHUNK, temp_next, d.d_ZERO, d.d_ONE);
     m.f_prog = sch.finish(true);
     m.flops_f = flops;
-    d.Wd_len = ct.base + (int)ct.vals.size();
+    d.Wd_len = std::max(d_temp + n_temp, d.d_RT + n_pairs);   // the pair products' slots (8 bytes at most)
     m.d_consts_v = {1.0, 0.0};
     m.d_consts_i = {d.d_ONE, d.d_ZERO};
     for (size_t k = 0; k < ct.vals.size(); ++k) {
@@ -656,7 +666,7 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
         terms[k].push_back({ct.get(t.first), d.L_P + t.second});
         flops += 2;
       }
-    Scheduler sch(ct.base + (int)ct.vals.size() + 64);
+    Scheduler sch(std::max(ct.base + (int)ct.vals.size() + 64, P_VIRTUAL + n_pairs + 1));
     int temp_next = L_temp;
     for (int k = 0; k < nnz; ++k)
       if (!terms[k].empty()) add_sum(sch, d.L_LU + k, false, terms[k], CHUNK, temp_next, d.L_ZERO, L_ONE);
@@ -744,17 +754,13 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
   d.d_DUMMY = d.Wd_len++;
   d.L_DUMMY = d.WL_len++;
 
-  // ---- discrete adjoint: programs on Wd extended past the forward layout
-  // (the forward prefix keeps y, ONE, ZERO and k~ where the forward tables
-  // expect them) and the transposed triangular solves on WL.
+  // ---- discrete adjoint: the walks' per-cell slice is the forward's Wd and WL
+  // (where every forward program expects them, the M program's WL slots included),
+  // then the adjoint's own arrays and the partials dr_j/dy_l (PP); its programs
+  // address the slice from its start (element indices in doubles: the adjoint is
+  // FP64).
   {
-    // The partials dr_j/dy_l (PP) share the per-cell slice with the iteration
-    // matrix's pair products (WL[L_P], FP64 in the adjoint): the walk forms and
-    // factors M before it computes the partials of a step's iterations, and the
-    // factored M no longer reads its pair products, so the two never overlap in
-    // time.  Element index from the start of Wd: the extended Wd rounded to an
-    // even length (where WL starts), then L_P.
-    d.a_MU = d.Wd_len;
+    d.a_MU = ((d.Wd_len + 1) & ~1) + d.WL_len;
     d.a_NM = d.a_MU + S;
     d.a_JTM = d.a_NM + R;
     d.a_G = d.a_JTM + S;
@@ -781,9 +787,9 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
       for (auto &t : nd_terms[j]) terms.push_back({ct.get(t.first), d.a_MU + t.second});
       add_sum(a, d.a_NM + j, true, terms, CHUNK, temp_next, d.d_ZERO, d.d_ONE);
     }
-    // the constants are all known now, so the extended Wd's length and with it PP
+    // the constants are all known now, so the slice's length up to PP
     const int wda_len = ct.base + (int)ct.vals.size();
-    d.a_PP = ((wda_len + 1) & ~1) + d.L_P;
+    d.a_PP = wda_len;
     Scheduler b(d.a_PP + n_pairs + 1);
     for (int l = 0; l < S; ++l) {
       std::vector<std::pair<int, int>> terms;
@@ -838,7 +844,7 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
     m.flops_adj_iter = m.flops_solve + rates + partials + 2.0 * nu_terms + 2.0 * n_pairs + 3.0 * R + 6.0 * S;
     m.flops_tan_iter = trates + 2.0 * nu_terms + m.flops_solve + 6.0 * S;
   }
-  if ((size_t)d.WL_len * sizeof(double) > 0xfff0 || (size_t)d.Wd_len * sizeof(double) > 0xfff0) {
+  if ((size_t)(((d.Wd_len + 1) & ~1) + d.WL_len) * sizeof(double) > 0xfff0 || d.WL_len >= P_VIRTUAL) {
     msg = "mechanism too large: the per-cell work arrays exceed the 16-bit byte offsets of the warp programs";
     return CHEM_EINVAL;
   }
@@ -896,10 +902,11 @@ int put(Mechanism &m, const std::vector<T> &v, const T **dst, std::string &msg) 
   return 0;
 }
 
-// Device form of a program: byte offsets (element index * elem), empty slots
+// Device form of a program: byte offsets (off(element index)), empty slots
 // as FMAs into the dummy slot (in a pass with reciprocals: a reciprocal of one
 // into it), RECIP ops marked by c == DEV_RECIP.
-std::vector<ushort4> device_ops(const HostProgram &hp, int elem, int dummy, int zero, int one) {
+template <typename Off>
+std::vector<ushort4> device_ops_at(const HostProgram &hp, Off off, int dummy, int zero, int one) {
   std::vector<ushort4> v(hp.ops.size());
   const int np = hp.n_pass();
   for (int p = 0; p < np; ++p) {
@@ -912,16 +919,21 @@ std::vector<ushort4> device_ops(const HostProgram &hp, int elem, int dummy, int 
       const Op &o = hp.ops[(size_t)p * WARP + l];
       ushort4 &d = v[(size_t)p * WARP + l];
       if (o.t == OP_EMPTY) {
-        d = recip ? make_ushort4(dummy * elem, one * elem, 0, DEV_RECIP)
-                  : make_ushort4(dummy * elem, zero * elem, zero * elem, zero * elem);
+        d = recip ? make_ushort4(off(dummy), off(one), 0, DEV_RECIP)
+                  : make_ushort4(off(dummy), off(zero), off(zero), off(zero));
       } else if (o.t & OP_RECIP) {
-        d = make_ushort4((o.t & 0x7fff) * elem, o.a * elem, 0, DEV_RECIP);
+        d = make_ushort4(off(o.t & 0x7fff), off(o.a), 0, DEV_RECIP);
       } else {
-        d = make_ushort4(o.t * elem, o.a * elem, o.b * elem, o.c * elem);
+        d = make_ushort4(off(o.t), off(o.a), off(o.b), off(o.c));
       }
     }
   }
   return v;
+}
+
+// ... with byte offsets elem * index from the program's own array
+std::vector<ushort4> device_ops(const HostProgram &hp, int elem, int dummy, int zero, int one) {
+  return device_ops_at(hp, [elem](int e) { return (unsigned short)(e * elem); }, dummy, zero, one);
 }
 
 // polynomial coefficients (in eta) of R(eta)_{jm} = prod_{l<m} (l - j eta)/(l+1)
@@ -995,6 +1007,15 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
     TableOffsets t;
     t.f_ops = bw.add(device_ops(m.f_prog, 8, d.d_DUMMY, d.d_ZERO, d.d_ONE));
     t.f_runs = bw.add(m.f_prog.runs());
+    // the M program runs on the whole per-cell slice: WL slots after Wd (rounded to
+    // an even length), the pair products in Wd from the rates' first slot
+    const int wl_off = ((d.Wd_len + 1) & ~1) * 8, p_off = d.d_RT * 8;
+    auto moff = [&](int e) {
+      return (unsigned short)(e >= P_VIRTUAL ? p_off + (e - P_VIRTUAL) * el : wl_off + e * el);
+    };
+    const std::vector<ushort4> m_dev = device_ops_at(m.m_prog, moff, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1);
+    t.m_ops = bw.add(m_dev);
+    t.m_runs = bw.add(m.m_prog.runs());
     t.fwd_ops = bw.add(device_ops(m.fwd_prog, el, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1));
     t.bwd_ops = bw.add(device_ops(m.bwd_prog, el, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1));
     std::vector<uint2> slots(R);
@@ -1025,7 +1046,7 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
     t.bytes = (int)bw.buf.size();
     d.tab = t;
     int rc = put(m, bw.buf, &d.blob[prec], msg);
-    if (!rc) rc = put(m, device_ops(m.m_prog, el, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1), &d.m_ops[prec], msg);
+    if (!rc) rc = put(m, m_dev, &d.m_ops[prec], msg);
     if (!rc) rc = put(m, device_ops(m.lu_prog, el, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1), &d.lu_ops[prec], msg);
     if (!rc && prec == 0) rc = put(m, m.m_prog.runs(), &d.m_runs, msg);
     if (!rc && prec == 0) rc = put(m, m.lu_prog.runs(), &d.lu_runs, msg);

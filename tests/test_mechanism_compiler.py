@@ -85,7 +85,9 @@ def test_programs_compute_f_and_solve_I_minus_cJ(oracle_lib, compiled, name):
         f = Wd[lay["d_F"]:lay["d_F"] + S]
         assert np.all(np.abs(f - oracle_lib.deriv(om, kt, y)) <= 1e-13 * (np.abs(J) @ np.abs(y) + 1e-300))
         for c in (1e-3, 7.5, 600.0):
-            WL = np.full(lay["WL_len"], np.nan)
+            # the M program names the pair products by virtual slots above WL (on the
+            # device they sit in Wd's rate and f slots, dead while M is formed)
+            WL = np.full(max(lay["WL_len"], lay["L_P"] + len(cp.pair_rx)), np.nan)
             for i, v in cp.Lconst:
                 WL[int(i)] = v
             WL[:lay["m_clear"]] = 0.0
@@ -115,10 +117,10 @@ def test_adjoint_programs_compute_J_transpose_mu(oracle_lib, compiled, name):
     for k in range(cells.n_cells):
         kt = oracle_lib.rate_constants(om, cells.T[k], cells.P[k])
         y = cells.y[:, k]
-        # the cell's whole slice as the adjoint kernel sees it: the extended Wd
-        # (rounded to an even length), then WL, whose pair-product region holds PP
-        W = np.full(((adj["Wda_len"] + 1) & ~1) + lay["WL_len"], np.nan)
-        assert adj["a_PP"] == ((adj["Wda_len"] + 1) & ~1) + lay["L_P"]
+        # the cell's whole slice as the adjoint kernel sees it: the forward's Wd
+        # (rounded to an even length) and WL, the adjoint's arrays, then the partials PP
+        W = np.full(adj["a_PP"] + len(cp.pair_rx), np.nan)
+        assert adj["a_MU"] == ((lay["Wd_len"] + 1) & ~1) + lay["WL_len"] and adj["a_PP"] == adj["Wda_len"]
         for i, v in np.concatenate([cp.dconst, cp.aconst]):
             W[int(i)] = v
         W[lay["d_Y"]:lay["d_Y"] + S] = y
