@@ -49,7 +49,6 @@ constexpr uint16_t DEV_RECIP = 0xffff;     // device marker in .w of RECIP passe
 struct TableOffsets {
   int f_ops, fwd_ops, bwd_ops;     // ushort4 programs (f on Wd, fwd/bwd on WL)
   int f_runs;                      // uint32 run table of the f program
-  int m_ops, m_runs;               // the M program (on the whole per-cell slice) and its run table
   int rx_slots;                    // uint2 [R]: byte offsets into Wd of the reactants' y
   int pair_rx;                     // int [n_pairs]
   int pair_other;                  // uint32 [n_pairs]: two 16-bit byte offsets into Wd
@@ -63,8 +62,7 @@ struct TableOffsets {
                                    // test, S (q+1)^2, and of the corrector, S (0.1 (q+1))^2
   int staged;                      // bytes of the prefix the persistent driver stages in shared
                                    // memory (programs and slots used every Newton iteration or
-                                   // formation of M; the LU program, constants and the grid stay
-                                   // in global memory)
+                                   // refactorisation; constants and the grid stay in global memory)
   int bytes;                       // total, a multiple of 16
 };
 

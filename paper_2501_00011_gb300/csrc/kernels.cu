@@ -513,7 +513,7 @@ __device__ __forceinline__ void f_core(const MechDev &M, const unsigned char *tb
 }
 
 // a3-a5: M = I - c J(y) in the LU slots from y in Wd[Y], then factor
-template <typename T, bool STAGED>
+template <typename T>
 __device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *tbase, const int prec, double *Wd, T *WL,
                                       const double c, const int lane) {
   for (int i = lane; i < M.m_clear; i += WARP) WL[i] = (T)0;
@@ -558,16 +558,10 @@ __device__ __forceinline__ void mlu_core(const MechDev &M, const unsigned char *
   __syncwarp();
   // The M program runs on the whole per-cell slice (its operands are the pair
   // products in Wd and the LU slots, constants and temporaries in WL), its ops
-  // staged in shared memory (the persistent driver) or read from L2 two passes
-  // ahead.  The LU program's ops are streamed through a ring in the rates and f
-  // slots of Wd, dead once M is formed (too small a region: read from L2 as well).
-  if (STAGED)
-    run_prog<T, false, true, true, false>(reinterpret_cast<const ushort4 *>(tbase + M.tab.m_ops),
-                                          reinterpret_cast<const uint32_t *>(tbase + M.tab.m_runs), M.m_nruns,
-                                          M.m_npass, reinterpret_cast<T *>(Wd), lane);
-  else
-    run_prog<T, false, false, true, false>(M.m_ops[prec], M.m_runs, M.m_nruns, M.m_npass, reinterpret_cast<T *>(Wd),
-                                           lane);
+  // read from L2 two passes ahead.  The LU program's ops are streamed through a
+  // ring in the rates and f slots of Wd, dead once M is formed (too small a
+  // region: read from L2 as well).
+  run_prog<T, false, false, true, false>(M.m_ops[prec], M.m_runs, M.m_nruns, M.m_npass, reinterpret_cast<T *>(Wd), lane);
   const uint32_t wr = smem_addr(Wd + M.d_RT);            // 8-byte aligned (a double slot)
   if ((M.R + M.S) * 8 >= 8 * 256)
     run_prog_ring<T, false, 8, true, true>(M.lu_ops[prec], M.lu_runs, M.lu_nruns, M.lu_npass, WL, lane, wr);
@@ -585,22 +579,23 @@ template <typename T, bool STAGED>
 __device__ __forceinline__ void solve_core(const MechDev &M, const unsigned char *tbase, double *Wd, T *WL, const int lane) {
   const ushort4 *fwd = reinterpret_cast<const ushort4 *>(tbase + M.tab.fwd_ops);
   const ushort4 *bwd = reinterpret_cast<const ushort4 *>(tbase + M.tab.bwd_ops);
+  T *const W = reinterpret_cast<T *>(Wd);                 // the programs address the whole per-cell slice
   if (STAGED) {
-    run_ops<T, false, true>(fwd, M.fwd_npass, WL, lane);
-    run_ops<T, false, true>(bwd, M.bwd_npass, WL, lane);
+    run_ops<T, false, true>(fwd, M.fwd_npass, W, lane);
+    run_ops<T, false, true>(bwd, M.bwd_npass, W, lane);
     return;
   }
   const uint32_t rb = smem_addr(Wd + M.d_RT);            // the rates and f slots: dead during a solve
   const int cap = (M.R + M.S) * 8;
   if (cap >= 8 * 256) {
-    run_ops_ring<T, false, 8>(fwd, M.fwd_npass, WL, lane, rb);
-    run_ops_ring<T, false, 8>(bwd, M.bwd_npass, WL, lane, rb);
+    run_ops_ring<T, false, 8>(fwd, M.fwd_npass, W, lane, rb);
+    run_ops_ring<T, false, 8>(bwd, M.bwd_npass, W, lane, rb);
   } else if (cap >= 4 * 256) {
-    run_ops_ring<T, false, 4>(fwd, M.fwd_npass, WL, lane, rb);
-    run_ops_ring<T, false, 4>(bwd, M.bwd_npass, WL, lane, rb);
+    run_ops_ring<T, false, 4>(fwd, M.fwd_npass, W, lane, rb);
+    run_ops_ring<T, false, 4>(bwd, M.bwd_npass, W, lane, rb);
   } else {
-    run_ops<T, false, false>(fwd, M.fwd_npass, WL, lane);
-    run_ops<T, false, false>(bwd, M.bwd_npass, WL, lane);
+    run_ops<T, false, false>(fwd, M.fwd_npass, W, lane);
+    run_ops<T, false, false>(bwd, M.bwd_npass, W, lane);
   }
 }
 
@@ -668,18 +663,18 @@ struct Cell {
 #pragma unroll
     for (int k = 0; k < KS; ++k)
       if (own[k]) Wd[M.d_Y + lane + WARP * k] = y[k];
-    mlu_core<T, STAGED>(M, tb.base, P.prec, Wd, WL, c, lane);
+    mlu_core<T>(M, tb.base, P.prec, Wd, WL, c, lane);
   }
 
   // a5: x = M^{-1} b with the factored M
   __device__ __forceinline__ void solve(const double (&b)[KS], double (&x)[KS]) {
 #pragma unroll
     for (int k = 0; k < KS; ++k)
-      if (own[k]) WL[M.L_X + pos[k]] = (T)b[k];
+      if (own[k]) reinterpret_cast<T *>(Wd + M.d_Y)[pos[k]] = (T)b[k];   // the solve vector: y's slots
     __syncwarp();
     solve_core<T, STAGED>(M, tb.base, Wd, WL, lane);
 #pragma unroll
-    for (int k = 0; k < KS; ++k) x[k] = own[k] ? -(double)WL[M.L_X + pos[k]] : 0.0;
+    for (int k = 0; k < KS; ++k) x[k] = own[k] ? -(double)reinterpret_cast<const T *>(Wd + M.d_Y)[pos[k]] : 0.0;
     __syncwarp();
   }
 };
@@ -1673,12 +1668,12 @@ __device__ void backward_cell(const MechDev &M, const CellsDev &C, const AdjDev 
       // g = s M^{-T} lambda_d
 #pragma unroll
       for (int k = 0; k < KS; ++k)
-        if (cl.own[k]) WL[M.L_X + cl.pos[k]] = lamd[k];
+        if (cl.own[k]) Wd[M.d_Y + cl.pos[k]] = lamd[k];   // the solve vector: y's slots (y was consumed)
       __syncwarp();
-      run_prog<double, false, false, false, false>(M.fwdT_ops, M.fwdT_runs, M.fwdT_nruns, M.fwdT_npass, WL, lane);
-      run_prog<double, false, false, false, false>(M.bwdT_ops, M.bwdT_runs, M.bwdT_nruns, M.bwdT_npass, WL, lane);
+      run_prog<double, false, false, false, false>(M.fwdT_ops, M.fwdT_runs, M.fwdT_nruns, M.fwdT_npass, Wd, lane);
+      run_prog<double, false, false, false, false>(M.bwdT_ops, M.bwdT_runs, M.bwdT_nruns, M.bwdT_npass, Wd, lane);
 #pragma unroll
-      for (int k = 0; k < KS; ++k) g[k] = cl.own[k] ? -ss * WL[M.L_X + cl.pos[k]] : 0.0;   // the programs leave -M^{-T} lambda
+      for (int k = 0; k < KS; ++k) g[k] = cl.own[k] ? -ss * Wd[M.d_Y + cl.pos[k]] : 0.0;   // the programs leave -M^{-T} lambda
       __syncwarp();
       jt_and_theta<KS>(M, Wd, cl.own, g, sc, jtg, lane);
 #pragma unroll

@@ -471,6 +471,7 @@ struct ConstTable {
 };
 
 constexpr int CHUNK = 8;
+constexpr int X_VIRTUAL = 0x5000;   // the solve programs' name for the solve vector's slot 0 (above every WL slot)
 constexpr int P_VIRTUAL = 0x6000;   // the M program's name for pair product 0 (above every WL slot)
 constexpr int NSTMP = 16;   // temporaries of the triangular solves
 
@@ -590,15 +591,18 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
   d.d_RT = d.d_KT + R;
   d.d_F = d.d_RT + R;
   int d_temp = d.d_F + S;
-  // WL (LU precision): LU[nnz] (-1/u_kk in the pivot slots once factored), x[S],
+  // WL (LU precision): LU[nnz] (-1/u_kk in the pivot slots once factored),
   // ZERO, ONE, M temps, nu constants, solve temporaries.  The M program names the
-  // pair products by the virtual indices P_VIRTUAL + pair (above every WL
-  // slot); its device form maps them to their slots in Wd.
+  // pair products by the virtual indices P_VIRTUAL + pair, the solve programs the
+  // solve vector by X_VIRTUAL + position (above every WL slot); their device
+  // forms map them to Wd: the pair products to the rate and f slots (dead while M
+  // is formed), the solve vector to y's slots (dead during a solve: y is written
+  // before every f evaluation and formation of M).
   d.L_LU = 0;
   d.nnz_lu = nnz;
-  d.L_X = nnz;
+  d.L_X = X_VIRTUAL;
   d.L_P = P_VIRTUAL;
-  d.L_ZERO = d.L_X + S;
+  d.L_ZERO = nnz;
   const int L_ONE = d.L_ZERO + 1;
   const int L_NEG_ONE = L_ONE + 1;
   int L_temp = L_NEG_ONE + 1;
@@ -734,7 +738,7 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
   const int L_STMP = d.WL_len;
   d.WL_len += NSTMP;
   {
-    Scheduler f(d.WL_len + 8), b(d.WL_len + 8);
+    Scheduler f(X_VIRTUAL + S + 8), b(X_VIRTUAL + S + 8);
     std::vector<std::vector<std::pair<int, int>>> lt(S), ut(S);
     double flops = 0;
     for (int i = 0; i < S; ++i)
@@ -809,7 +813,7 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
     // M^T = U'^T D L^T: W = U'^{-T} b (unit lower, coefficients -u'_kj), X_k =
     // ninv_k W_k = -(D^{-1} W)_k, then Q = -mu from Q_i = X_i + sum_{k>i} (-l_ki) Q_k
     // (unit upper); mu = -X.  Both programs without negation.
-    Scheduler f(d.WL_len + 8), g(d.WL_len + 8);
+    Scheduler f(X_VIRTUAL + S + 8), g(X_VIRTUAL + S + 8);
     {
       std::vector<std::vector<std::pair<int, int>>> uT(S), lT(S);
       for (int k = 0; k < S; ++k)
@@ -844,7 +848,7 @@ int compile_mechanism(int S, int R, const chem_reaction *rx, Mechanism &m, std::
     m.flops_adj_iter = m.flops_solve + rates + partials + 2.0 * nu_terms + 2.0 * n_pairs + 3.0 * R + 6.0 * S;
     m.flops_tan_iter = trates + 2.0 * nu_terms + m.flops_solve + 6.0 * S;
   }
-  if ((size_t)(((d.Wd_len + 1) & ~1) + d.WL_len) * sizeof(double) > 0xfff0 || d.WL_len >= P_VIRTUAL) {
+  if ((size_t)(((d.Wd_len + 1) & ~1) + d.WL_len) * sizeof(double) > 0xfff0 || d.WL_len >= X_VIRTUAL) {
     msg = "mechanism too large: the per-cell work arrays exceed the 16-bit byte offsets of the warp programs";
     return CHEM_EINVAL;
   }
@@ -1007,17 +1011,18 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
     TableOffsets t;
     t.f_ops = bw.add(device_ops(m.f_prog, 8, d.d_DUMMY, d.d_ZERO, d.d_ONE));
     t.f_runs = bw.add(m.f_prog.runs());
-    // the M program runs on the whole per-cell slice: WL slots after Wd (rounded to
-    // an even length), the pair products in Wd from the rates' first slot
-    const int wl_off = ((d.Wd_len + 1) & ~1) * 8, p_off = d.d_RT * 8;
-    auto moff = [&](int e) {
-      return (unsigned short)(e >= P_VIRTUAL ? p_off + (e - P_VIRTUAL) * el : wl_off + e * el);
+    // the M and solve programs run on the whole per-cell slice: WL slots after Wd
+    // (rounded to an even length), the pair products in Wd from the rates' first
+    // slot, the solve vector in y's slots
+    const int wl_off = ((d.Wd_len + 1) & ~1) * 8, p_off = d.d_RT * 8, x_off = d.d_Y * 8;
+    auto coff = [&](int e) {
+      return (unsigned short)(e >= P_VIRTUAL   ? p_off + (e - P_VIRTUAL) * el
+                              : e >= X_VIRTUAL ? x_off + (e - X_VIRTUAL) * el
+                                               : wl_off + e * el);
     };
-    const std::vector<ushort4> m_dev = device_ops_at(m.m_prog, moff, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1);
-    t.m_ops = bw.add(m_dev);
-    t.m_runs = bw.add(m.m_prog.runs());
-    t.fwd_ops = bw.add(device_ops(m.fwd_prog, el, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1));
-    t.bwd_ops = bw.add(device_ops(m.bwd_prog, el, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1));
+    const std::vector<ushort4> m_dev = device_ops_at(m.m_prog, coff, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1);
+    t.fwd_ops = bw.add(device_ops_at(m.fwd_prog, coff, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1));
+    t.bwd_ops = bw.add(device_ops_at(m.bwd_prog, coff, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1));
     std::vector<uint2> slots(R);
     for (int j = 0; j < R; ++j)
       slots[j] = make_uint2((unsigned)(m.rx_slot_idx[j * 3] * 8) | ((unsigned)(m.rx_slot_idx[j * 3 + 1] * 8) << 16),
@@ -1057,13 +1062,16 @@ int upload_mechanism(Mechanism &m, std::string &msg) {
   }
   {
     int rc = 0;
+    // the transposed solves (FP64) on the whole per-cell slice, like the forward solves
+    const int wl_off = ((d.Wd_len + 1) & ~1) * 8, x_off = d.d_Y * 8;
+    auto xoff64 = [&](int e) { return (unsigned short)(e >= X_VIRTUAL ? x_off + (e - X_VIRTUAL) * 8 : wl_off + e * 8); };
     std::vector<int> aoff(m.a_consts_i.size());
     for (size_t k = 0; k < aoff.size(); ++k) aoff[k] = m.a_consts_i[k] * 8;
     if ((rc = put(m, aoff, &d.a_const_off, msg)) || (rc = put(m, m.a_consts_v, &d.a_const_val, msg)) ||
         (rc = put(m, device_ops(m.nudot_prog, 8, d.d_DUMMY, d.d_ZERO, d.d_ONE), &d.nudot_ops, msg)) ||
         (rc = put(m, device_ops(m.jt_prog, 8, d.d_DUMMY, d.d_ZERO, d.d_ONE), &d.jt_ops, msg)) ||
-        (rc = put(m, device_ops(m.fwdT_prog, 8, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1), &d.fwdT_ops, msg)) ||
-        (rc = put(m, device_ops(m.bwdT_prog, 8, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1), &d.bwdT_ops, msg)) ||
+        (rc = put(m, device_ops_at(m.fwdT_prog, xoff64, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1), &d.fwdT_ops, msg)) ||
+        (rc = put(m, device_ops_at(m.bwdT_prog, xoff64, d.L_DUMMY, d.L_ZERO, d.L_ZERO + 1), &d.bwdT_ops, msg)) ||
         (rc = put(m, m.nudot_prog.runs(), &d.nudot_runs, msg)) || (rc = put(m, m.jt_prog.runs(), &d.jt_runs, msg)) ||
         (rc = put(m, m.fwdT_prog.runs(), &d.fwdT_runs, msg)) || (rc = put(m, m.bwdT_prog.runs(), &d.bwdT_runs, msg))) {
       free_mechanism(m);
