@@ -564,7 +564,7 @@ def run_gpu(args):
             out["coupled_cells"] = {
                 "cells": C, "groups": coupled,
                 "note": "couple_cells = G: each group of G consecutive cells is one ODE system (shared step size, "
-                        "order, Newton iterations, one norm), whole groups per block (10 cells, 8 for G = 4), "
+                        "order, Newton iterations, one norm), whole groups per block (as many as fit: 12 cells, 10 for G = 5 and 10), "
                         "groups handed out most expensive first by their cost in the previous solve (of the same "
                         "state); G1 = independent cells. solver_iterations_total counts Newton iterations once per "
                         "system, the paper's measure of its Multi-cells saving"}
