@@ -1989,31 +1989,69 @@ __global__ void __launch_bounds__(TAN_WARPS_PER_BLOCK * WARP) tangent_kernel(con
   }
 }
 
-// Cells per block of a walk kernel: the block size that keeps the most cells
-// resident per SM (shared memory bounds the walks' occupancy), ties to the
-// smaller block.  The kernel's dynamic shared-memory limit must be raised first.
+// Launch shape of a walk kernel.  A walk's cells each take one warp (the queue
+// hands out the longest tapes first), so while the batch has fewer than
+// WALK_NARROW_CELLS cells per warp at WALK_NARROW_WARPS warps per SM, nearly
+// every cell has a warp of its own and the walk lasts as long as its slowest
+// cells, which run faster with fewer warps beside them on the SM: such batches
+// run at most WALK_NARROW_WARPS warps per SM (2,048 cells of the 72-species
+// mechanism: tangent 12.3 -> 11.2 ms, adjoint 12.5 -> 11.3 ms); larger ones at
+// the occupancy that keeps the most cells resident (shared memory bounds it),
+// ties to the larger block (fewer blocks to place).  Blocks per SM are bounded
+// by padding each block's shared memory, so the block scheduler cannot stack a
+// third block of a two-block shape on one SM while another SM has none.  The
+// kernel's dynamic shared-memory limit must be raised first.
+constexpr int WALK_NARROW_WARPS = 8;
+constexpr int WALK_NARROW_CELLS = 2;
+
+struct WalkShape {
+  int warps_per_block = 0;
+  int blocks_per_sm = 0;
+  size_t smem = 0;        // dynamic shared memory per block (>= warps_per_block * cell_bytes)
+};
+
 template <typename K>
-int walk_warps_per_block(K kernel, int cell_bytes, int max_warps, int *blocks_per_sm) {
-  int dev = 0, optin = 0;
+WalkShape walk_shape(K kernel, int cell_bytes, int max_warps, int64_t n_cells) {
+  WalkShape ws;
+  int dev = 0, optin = 0, n_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  int best_w = 0, best_cells = 0;
-  *blocks_per_sm = 0;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const bool narrow = n_cells < (int64_t)WALK_NARROW_CELLS * WALK_NARROW_WARPS * n_sm;
+  int best_w = 0, best_cells = 0, best_nb = 0;
   for (int w = 1; w <= max_warps && (long)w * cell_bytes <= (long)optin; ++w) {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, w * WARP, (size_t)w * cell_bytes) != cudaSuccess)
       continue;
-    if (w * nb > best_cells) {
-      best_cells = w * nb;
+    int cells = w * nb;
+    if (narrow && cells > WALK_NARROW_WARPS) {
+      // the most whole blocks of w warps within the narrow bound
+      nb = WALK_NARROW_WARPS / w;
+      cells = w * nb;
+    }
+    if (cells >= best_cells && cells > 0) {
+      best_cells = cells;
       best_w = w;
-      *blocks_per_sm = nb;
+      best_nb = nb;
     }
   }
-  return best_w;
+  if (best_w < 1) return ws;
+  ws.warps_per_block = best_w;
+  ws.blocks_per_sm = best_nb;
+  ws.smem = (size_t)best_w * cell_bytes;
+  // pad until no more than best_nb blocks fit on an SM
+  for (;;) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, best_w * WARP, ws.smem) != cudaSuccess || nb <= best_nb)
+      break;
+    if (ws.smem + 1024 > (size_t)optin) break;
+    ws.smem += 1024;
+  }
+  return ws;
 }
 
-// Grid of a walk launch: with the queue, enough resident blocks to fill every
-// SM (never more than the cells need); without, one warp per cell.
+// Grid of a walk launch: with the queue, the resident blocks of the shape on
+// every SM (never more than the cells need); without, one warp per cell.
 int walk_blocks(const CellsDev &C, int warps_per_block, int blocks_per_sm) {
   const int64_t need = (C.n_cells + warps_per_block - 1) / warps_per_block;
   if (!C.queue) return (int)need;
@@ -2029,12 +2067,11 @@ cudaError_t launch_tan_t(const MechDev &M, const CellsDev &C, const TanDev &A, c
   cudaError_t e = allow_max_smem<tangent_kernel<KS>>();
   if (e != cudaSuccess) return e;
   SolveParams P = P0;
-  int bps = 0;
-  P.warps_per_block = walk_warps_per_block(tangent_kernel<KS>, P.cell_bytes, TAN_WARPS_PER_BLOCK, &bps);
-  if (P.warps_per_block < 1) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
-  const int blocks = walk_blocks(C, P.warps_per_block, bps);
-  tangent_kernel<KS><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, A, P);
+  const WalkShape ws = walk_shape(tangent_kernel<KS>, P.cell_bytes, TAN_WARPS_PER_BLOCK, C.n_cells);
+  if (ws.warps_per_block < 1) return cudaErrorInvalidValue;
+  P.warps_per_block = ws.warps_per_block;
+  const int blocks = walk_blocks(C, P.warps_per_block, ws.blocks_per_sm);
+  tangent_kernel<KS><<<blocks, P.warps_per_block * WARP, ws.smem, stream>>>(M, C, A, P);
   return cudaGetLastError();
 }
 
@@ -2059,12 +2096,11 @@ cudaError_t launch_adj_t(const MechDev &M, const CellsDev &C, const AdjDev &A, c
   cudaError_t e = allow_max_smem<adjoint_kernel<KS>>();
   if (e != cudaSuccess) return e;
   SolveParams P = P0;
-  int bps = 0;
-  P.warps_per_block = walk_warps_per_block(adjoint_kernel<KS>, P.cell_bytes, ADJ_WARPS_PER_BLOCK, &bps);
-  if (P.warps_per_block < 1) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)P.cell_bytes * P.warps_per_block;
-  const int blocks = walk_blocks(C, P.warps_per_block, bps);
-  adjoint_kernel<KS><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, A, P);
+  const WalkShape ws = walk_shape(adjoint_kernel<KS>, P.cell_bytes, ADJ_WARPS_PER_BLOCK, C.n_cells);
+  if (ws.warps_per_block < 1) return cudaErrorInvalidValue;
+  P.warps_per_block = ws.warps_per_block;
+  const int blocks = walk_blocks(C, P.warps_per_block, ws.blocks_per_sm);
+  adjoint_kernel<KS><<<blocks, P.warps_per_block * WARP, ws.smem, stream>>>(M, C, A, P);
   return cudaGetLastError();
 }
 

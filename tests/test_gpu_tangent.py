@@ -105,6 +105,30 @@ def test_tangent_adjoint_identity_full_size(oracle_lib, cg):
         assert np.all(np.abs(dy[:, k] - ref) <= 1e-8 * np.abs(ref) + 1e-12 * np.abs(ref).max()), k
 
 
+def test_walks_do_not_depend_on_batch_size_or_launch_shape(cg):
+    """Each cell's walk is its own: the first 48 cells of a batch large enough
+    for the walks' full occupancy (two or more cells per warp at 8 warps per
+    SM) and the same 48 cells alone (walked at no more than 8 warps per SM)
+    give bitwise equal final states, dL/dy0 and tangents."""
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    n_big, n = 2 * 8 * n_sm + 97, 48
+    wl = synth.workload_adjoint(n_big)
+    S = wl.mech.n_species
+    w = synth.loss_weights(S, n_big)
+    dy0, dth = _directions(wl.mech, wl.cells, 23)
+    out = []
+    for cells, ww, d0 in ((wl.cells, w, dy0), (synth.subset(wl.cells, np.arange(n)), w[:, :n], dy0[:, :n])):
+        m, c = _solved(cg, wl, cells, wl.n_steps)
+        y = c.get_state()
+        gth, gy0, n_bad = c.sensitivity(ww)
+        dy, n_bad_t = c.tangent(d0, dth)
+        assert n_bad == 0 and n_bad_t == 0
+        out.append((y[:, :n], gy0[:, :n], dy[:, :n]))
+        c.close()
+    for big, small in zip(*out):
+        assert np.array_equal(big, small)
+
+
 def test_tangent_options_and_devices(cg):
     wl = synth.workload_adjoint(10)
     m, c = _solved(cg, wl, wl.cells, 1)
