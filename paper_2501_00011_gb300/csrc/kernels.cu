@@ -1990,20 +1990,14 @@ __global__ void __launch_bounds__(TAN_WARPS_PER_BLOCK * WARP) tangent_kernel(con
 }
 
 // Launch shape of a walk kernel.  A walk's cells each take one warp (the queue
-// hands out the longest tapes first), so while the batch has fewer than
-// WALK_NARROW_CELLS cells per warp at WALK_NARROW_WARPS warps per SM, nearly
-// every cell has a warp of its own and the walk lasts as long as its slowest
-// cells, which run faster with fewer warps beside them on the SM: such batches
-// run at most WALK_NARROW_WARPS warps per SM (2,048 cells of the 72-species
-// mechanism: tangent 12.3 -> 11.2 ms, adjoint 12.5 -> 11.3 ms); larger ones at
-// the occupancy that keeps the most cells resident (shared memory bounds it),
-// ties to the larger block (fewer blocks to place).  Blocks per SM are bounded
-// by padding each block's shared memory, so the block scheduler cannot stack a
+// hands out the longest tapes first); a narrow batch (internal.h) runs at most
+// NARROW_WARPS_PER_SM warps per SM (2,048 cells of the 72-species mechanism:
+// tangent 12.3 -> 11.2 ms, adjoint 12.5 -> 11.3 ms), a larger one at the
+// occupancy that keeps the most cells resident (shared memory bounds it), ties
+// to the larger block (fewer blocks to place).  Blocks per SM are bounded by
+// padding each block's shared memory, so the block scheduler cannot stack a
 // third block of a two-block shape on one SM while another SM has none.  The
 // kernel's dynamic shared-memory limit must be raised first.
-constexpr int WALK_NARROW_WARPS = 8;
-constexpr int WALK_NARROW_CELLS = 2;
-
 struct WalkShape {
   int warps_per_block = 0;
   int blocks_per_sm = 0;
@@ -2013,20 +2007,19 @@ struct WalkShape {
 template <typename K>
 WalkShape walk_shape(K kernel, int cell_bytes, int max_warps, int64_t n_cells) {
   WalkShape ws;
-  int dev = 0, optin = 0, n_sm = 1;
+  int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  const bool narrow = n_cells < (int64_t)WALK_NARROW_CELLS * WALK_NARROW_WARPS * n_sm;
+  const bool narrow = narrow_batch(n_cells);
   int best_w = 0, best_cells = 0, best_nb = 0;
   for (int w = 1; w <= max_warps && (long)w * cell_bytes <= (long)optin; ++w) {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, w * WARP, (size_t)w * cell_bytes) != cudaSuccess)
       continue;
     int cells = w * nb;
-    if (narrow && cells > WALK_NARROW_WARPS) {
+    if (narrow && cells > NARROW_WARPS_PER_SM) {
       // the most whole blocks of w warps within the narrow bound
-      nb = WALK_NARROW_WARPS / w;
+      nb = NARROW_WARPS_PER_SM / w;
       cells = w * nb;
     }
     if (cells >= best_cells && cells > 0) {
@@ -2362,7 +2355,14 @@ int occupancy(const MechDev &M, int lu_precision, int driver, int warps_per_bloc
   return f32 ? occupancy_ks<float, false>(M, warps_per_block, smem) : occupancy_ks<double, false>(M, warps_per_block, smem);
 }
 
-int best_warps_per_block(const MechDev &M, int lu_precision, int driver) {
+bool narrow_batch(int64_t n_cells) {
+  int dev = 0, n_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  return n_cells < (int64_t)NARROW_CELLS_PER_WARP * NARROW_WARPS_PER_SM * n_sm;
+}
+
+int best_warps_per_block(const MechDev &M, int lu_precision, int driver, int64_t n_cells) {
   const int wmax = max_warps_per_block(M, lu_precision, driver);
   // The plain driver runs one cell per block: a block retires only when its
   // slowest cell does, and that tail costs more than the odd extra resident
@@ -2370,10 +2370,14 @@ int best_warps_per_block(const MechDev &M, int lu_precision, int driver) {
   // block against 64.1 ms at 11).
   if (!staged_driver(driver)) return (wmax >= 1 && occupancy(M, lu_precision, driver, 1) >= 1) ? 1 : 0;
   // The persistent driver stages the tables once per block: most resident
-  // cells per SM, ties to the larger block.
+  // cells per SM, ties to the larger block; a narrow batch within
+  // NARROW_WARPS_PER_SM cells per SM (72/186: 2,048 cells 9.50 -> 8.80 ms,
+  // 1,024 cells 7.24 -> 6.43 ms; 3,072 cells, not narrow, 12.6 ms either way).
+  const bool narrow = narrow_batch(n_cells);
   int best_w = 0, best_cells = 0;
   for (int w = 1; w <= wmax; ++w) {
     const int cells = w * occupancy(M, lu_precision, driver, w);
+    if (narrow && cells > NARROW_WARPS_PER_SM) continue;
     if (cells > 0 && cells >= best_cells) {
       best_cells = cells;
       best_w = w;
