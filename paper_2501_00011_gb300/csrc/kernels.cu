@@ -51,6 +51,7 @@ struct SolveParams {
   int tab_bytes;       // staged table bytes at the start of shared memory (0 if not staged)
   int couple;          // coupled group size (warps_per_block is a multiple of it); 1: independent cells
   long long stage_wait;   // iterations of the first bounded wait for the staged tables
+  long long smem_bytes;   // host side: the launch's dynamic shared memory (0: tables + cells)
 };
 
 // Reciprocal from the hardware estimate r (relative error e = 1 - x r of
@@ -1403,7 +1404,7 @@ int occupancy_t(int warps_per_block, size_t smem) {
 
 template <typename T, int KS, bool STAGED, bool REC, bool COUPLED>
 cudaError_t launch_rec_t(const MechDev &M, const CellsDev &C, const SolveParams &P, int blocks, cudaStream_t stream) {
-  const size_t smem = (size_t)P.tab_bytes + (size_t)P.cell_bytes * P.warps_per_block;
+  const size_t smem = P.smem_bytes > 0 ? (size_t)P.smem_bytes : (size_t)P.tab_bytes + (size_t)P.cell_bytes * P.warps_per_block;
   cudaError_t e = configure_t<T, KS, STAGED, REC, COUPLED>();
   if (e != cudaSuccess) return e;
   solve_kernel<T, KS, STAGED, REC, COUPLED><<<blocks, P.warps_per_block * WARP, smem, stream>>>(M, C, P);
@@ -1989,6 +1990,22 @@ __global__ void __launch_bounds__(TAN_WARPS_PER_BLOCK * WARP) tangent_kernel(con
   }
 }
 
+// Dynamic shared memory of a block of `smem` bytes, padded so that no more
+// than bps such blocks fit on one SM (blocks per SM by shared memory:
+// floor(per-SM capacity / (block's bytes + the per-block reservation))).
+size_t pad_smem_to_blocks(size_t smem, int bps) {
+  int dev = 0, per_sm = 0, reserved = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (bps < 1 || per_sm <= 0) return smem;
+  const long need = (long)per_sm / (long)(bps + 1) - (long)reserved + 1;    // bps + 1 blocks no longer fit
+  size_t s = need > (long)smem ? (size_t)need : smem;
+  s = (s + 127) & ~(size_t)127;
+  return s <= (size_t)optin ? s : smem;
+}
+
 // Launch shape of a walk kernel.  A walk's cells each take one warp (the queue
 // hands out the longest tapes first); a narrow batch (internal.h) runs at most
 // NARROW_WARPS_PER_SM warps per SM (2,048 cells of the 72-species mechanism:
@@ -2032,14 +2049,10 @@ WalkShape walk_shape(K kernel, int cell_bytes, int max_warps, int64_t n_cells) {
   ws.warps_per_block = best_w;
   ws.blocks_per_sm = best_nb;
   ws.smem = (size_t)best_w * cell_bytes;
-  // pad until no more than best_nb blocks fit on an SM
-  for (;;) {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, best_w * WARP, ws.smem) != cudaSuccess || nb <= best_nb)
-      break;
-    if (ws.smem + 1024 > (size_t)optin) break;
-    ws.smem += 1024;
-  }
+  int natural = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&natural, kernel, best_w * WARP, ws.smem) == cudaSuccess &&
+      natural > best_nb)
+    ws.smem = pad_smem_to_blocks(ws.smem, best_nb);
   return ws;
 }
 
@@ -2362,8 +2375,9 @@ bool narrow_batch(int64_t n_cells) {
   return n_cells < (int64_t)NARROW_CELLS_PER_WARP * NARROW_WARPS_PER_SM * n_sm;
 }
 
-int best_warps_per_block(const MechDev &M, int lu_precision, int driver, int64_t n_cells) {
+int best_warps_per_block(const MechDev &M, int lu_precision, int driver, int64_t n_cells, int *blocks_per_sm) {
   const int wmax = max_warps_per_block(M, lu_precision, driver);
+  if (blocks_per_sm) *blocks_per_sm = 0;
   // The plain driver runs one cell per block: a block retires only when its
   // slowest cell does, and that tail costs more than the odd extra resident
   // cell a larger block may fit (72/186, 10,000 cells: 49.6 ms at 1 cell per
@@ -2371,18 +2385,24 @@ int best_warps_per_block(const MechDev &M, int lu_precision, int driver, int64_t
   if (!staged_driver(driver)) return (wmax >= 1 && occupancy(M, lu_precision, driver, 1) >= 1) ? 1 : 0;
   // The persistent driver stages the tables once per block: most resident
   // cells per SM, ties to the larger block; a narrow batch within
-  // NARROW_WARPS_PER_SM cells per SM (72/186: 2,048 cells 9.50 -> 8.80 ms,
-  // 1,024 cells 7.24 -> 6.43 ms; 3,072 cells, not narrow, 12.6 ms either way).
+  // NARROW_WARPS_PER_SM cells per SM, as whole blocks (72/186: 2,048 cells
+  // 9.50 -> 8.80 ms, 1,024 cells 7.24 -> 6.43 ms; 3,072 cells, not narrow,
+  // 12.6 ms either way), the blocks per SM then returned for the launch.
   const bool narrow = narrow_batch(n_cells);
-  int best_w = 0, best_cells = 0;
+  int best_w = 0, best_cells = 0, best_b = 0, best_nat = 0;
   for (int w = 1; w <= wmax; ++w) {
-    const int cells = w * occupancy(M, lu_precision, driver, w);
-    if (narrow && cells > NARROW_WARPS_PER_SM) continue;
+    const int nat = occupancy(M, lu_precision, driver, w);
+    int b = nat;
+    if (narrow && w * b > NARROW_WARPS_PER_SM) b = NARROW_WARPS_PER_SM / w;
+    const int cells = w * b;
     if (cells > 0 && cells >= best_cells) {
       best_cells = cells;
       best_w = w;
+      best_b = b;
+      best_nat = nat;
     }
   }
+  if (blocks_per_sm && best_b < best_nat) *blocks_per_sm = best_b;
   return best_w;
 }
 
@@ -2429,9 +2449,15 @@ cudaError_t launch_solve(const MechDev &M, const CellsDev &C, const LaunchCfg &c
   const int64_t units = (C.n_cells + P.couple - 1) / P.couple, per_block = P.warps_per_block / P.couple;
   const int64_t need = (units + per_block - 1) / per_block;
   int blocks;
+  P.smem_bytes = 0;
   if (cfg.driver == CHEM_DRIVER_PERSISTENT) {
-    int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : occupancy(M, cfg.lu_precision, cfg.driver, cfg.warps_per_block);
+    const int natural = occupancy(M, cfg.lu_precision, cfg.driver, cfg.warps_per_block);
+    int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : natural;
     if (bps < 1) bps = 1;
+    // fewer resident blocks than fit: pad the blocks' shared memory so that
+    // the block scheduler cannot stack more than bps of them on one SM
+    if (bps < natural)
+      P.smem_bytes = (long long)pad_smem_to_blocks((size_t)P.tab_bytes + (size_t)P.cell_bytes * P.warps_per_block, bps);
     blocks = n_sm * bps;
     if (blocks > need) blocks = (int)need;
   } else {
