@@ -198,11 +198,7 @@ int chem_cells_create(const chem_mech *mech, int64_t n_cells, const chem_opts *o
   const int wmax = max_warps_per_block(mech->m.dev, o.lu_precision, o.driver);
   if (wmax < 1) return fail(CHEM_EINVAL, "mechanism working set does not fit in shared memory");
   if (o.cells_per_block > wmax) return fail(CHEM_EINVAL, "cells_per_block exceeds the shared-memory limit");
-  if (o.cells_per_block == 0) {
-    int bps = 0;
-    o.cells_per_block = best_warps_per_block(mech->m.dev, o.lu_precision, o.driver, n_cells, &bps);
-    if (o.blocks_per_sm == 0) o.blocks_per_sm = bps;
-  }
+  if (o.cells_per_block == 0) o.cells_per_block = best_warps_per_block(mech->m.dev, o.lu_precision, o.driver);
   if (o.cells_per_block < 1) return fail(CHEM_EINVAL, "no launch shape fits on this device");
   if (o.record_adjoint && o.lu_precision != 64)
     return fail(CHEM_EINVAL, "record_adjoint needs lu_precision 64 (the adjoint differentiates the FP64 iteration)");

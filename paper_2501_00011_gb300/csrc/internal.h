@@ -261,18 +261,8 @@ cudaError_t launch_order(const MechDev &m, const CellsDev &c, double rtol, doubl
 int max_warps_per_block(const MechDev &m, int lu_precision, int driver);
 // resident blocks per SM of the solve kernel for a block of warps_per_block cells
 int occupancy(const MechDev &m, int lu_precision, int driver, int warps_per_block);
-// Small batches: fewer than NARROW_CELLS_PER_WARP cells per warp at
-// NARROW_WARPS_PER_SM warps per SM.  With about one cell per warp a solve or a
-// walk lasts as long as its slowest cells, which run faster beside fewer warps
-// on the SM, so such batches run at most NARROW_WARPS_PER_SM warps per SM.
-constexpr int NARROW_WARPS_PER_SM = 8;
-constexpr int NARROW_CELLS_PER_WARP = 2;
-bool narrow_batch(int64_t n_cells);
-// cells per block that maximises resident cells per SM (0 if nothing fits);
-// for the persistent driver and a narrow batch of n_cells, within
-// NARROW_WARPS_PER_SM cells per SM: *blocks_per_sm is then the resident
-// blocks per SM to launch with when fewer than fit (else 0: as many as fit)
-int best_warps_per_block(const MechDev &m, int lu_precision, int driver, int64_t n_cells, int *blocks_per_sm);
+// cells per block that maximises resident cells per SM (0 if nothing fits)
+int best_warps_per_block(const MechDev &m, int lu_precision, int driver);
 // diagnostic: mode 0 out = f(y); mode 1 out = (I - c J(y))^{-1} b   (all [S][C] device arrays)
 cudaError_t launch_probe(const MechDev &M, const CellsDev &C, int lu_precision, int mode, double c, const double *y,
                          const double *b, double *out, cudaStream_t stream);

@@ -2007,14 +2007,28 @@ size_t pad_smem_to_blocks(size_t smem, int bps) {
 }
 
 // Launch shape of a walk kernel.  A walk's cells each take one warp (the queue
-// hands out the longest tapes first); a narrow batch (internal.h) runs at most
-// NARROW_WARPS_PER_SM warps per SM (2,048 cells of the 72-species mechanism:
-// tangent 12.3 -> 11.2 ms, adjoint 12.5 -> 11.3 ms), a larger one at the
-// occupancy that keeps the most cells resident (shared memory bounds it), ties
-// to the larger block (fewer blocks to place).  Blocks per SM are bounded by
-// padding each block's shared memory, so the block scheduler cannot stack a
-// third block of a two-block shape on one SM while another SM has none.  The
-// kernel's dynamic shared-memory limit must be raised first.
+// hands out the longest tapes first), so while the batch has fewer than
+// NARROW_CELLS_PER_WARP cells per warp at NARROW_WARPS_PER_SM warps per SM,
+// nearly every cell has a warp of its own and the walk lasts as long as its
+// slowest cells, which run faster with fewer warps beside them on the SM: such
+// batches run at most NARROW_WARPS_PER_SM warps per SM (2,048 cells of the
+// 72-species mechanism: tangent 12.3 -> 11.2 ms, adjoint 12.5 -> 11.3 ms);
+// larger ones at the occupancy that keeps the most cells resident (shared
+// memory bounds it), ties to the larger block (fewer blocks to place).  Blocks
+// per SM are bounded by padding each block's shared memory, so the block
+// scheduler cannot stack a third block of a two-block shape on one SM while
+// another SM has none.  The kernel's dynamic shared-memory limit must be
+// raised first.
+constexpr int NARROW_WARPS_PER_SM = 8;
+constexpr int NARROW_CELLS_PER_WARP = 2;
+
+bool narrow_batch(int64_t n_cells) {
+  int dev = 0, n_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  return n_cells < (int64_t)NARROW_CELLS_PER_WARP * NARROW_WARPS_PER_SM * n_sm;
+}
+
 struct WalkShape {
   int warps_per_block = 0;
   int blocks_per_sm = 0;
@@ -2368,41 +2382,28 @@ int occupancy(const MechDev &M, int lu_precision, int driver, int warps_per_bloc
   return f32 ? occupancy_ks<float, false>(M, warps_per_block, smem) : occupancy_ks<double, false>(M, warps_per_block, smem);
 }
 
-bool narrow_batch(int64_t n_cells) {
-  int dev = 0, n_sm = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  return n_cells < (int64_t)NARROW_CELLS_PER_WARP * NARROW_WARPS_PER_SM * n_sm;
-}
-
-int best_warps_per_block(const MechDev &M, int lu_precision, int driver, int64_t n_cells, int *blocks_per_sm) {
+int best_warps_per_block(const MechDev &M, int lu_precision, int driver) {
   const int wmax = max_warps_per_block(M, lu_precision, driver);
-  if (blocks_per_sm) *blocks_per_sm = 0;
   // The plain driver runs one cell per block: a block retires only when its
   // slowest cell does, and that tail costs more than the odd extra resident
   // cell a larger block may fit (72/186, 10,000 cells: 49.6 ms at 1 cell per
   // block against 64.1 ms at 11).
   if (!staged_driver(driver)) return (wmax >= 1 && occupancy(M, lu_precision, driver, 1) >= 1) ? 1 : 0;
   // The persistent driver stages the tables once per block: most resident
-  // cells per SM, ties to the larger block; a narrow batch within
-  // NARROW_WARPS_PER_SM cells per SM, as whole blocks (72/186: 2,048 cells
-  // 9.50 -> 8.80 ms, 1,024 cells 7.24 -> 6.43 ms; 3,072 cells, not narrow,
-  // 12.6 ms either way), the blocks per SM then returned for the launch.
-  const bool narrow = narrow_batch(n_cells);
-  int best_w = 0, best_cells = 0, best_b = 0, best_nat = 0;
+  // cells per SM, ties to the larger block.  (The walks' narrow-batch bound
+  // was measured here too: a single first solve of 1,024 / 2,048 cells of the
+  // 72/186 mechanism gains 10% / 8% at 8 cells per SM, but the four recorded
+  // steps of the 2,048-cell differentiation workload lose 3%, 15.9 -> 16.4
+  // ms: after the first step the queue is keyed by exact costs and the
+  // throughput of the full occupancy wins.)
+  int best_w = 0, best_cells = 0;
   for (int w = 1; w <= wmax; ++w) {
-    const int nat = occupancy(M, lu_precision, driver, w);
-    int b = nat;
-    if (narrow && w * b > NARROW_WARPS_PER_SM) b = NARROW_WARPS_PER_SM / w;
-    const int cells = w * b;
+    const int cells = w * occupancy(M, lu_precision, driver, w);
     if (cells > 0 && cells >= best_cells) {
       best_cells = cells;
       best_w = w;
-      best_b = b;
-      best_nat = nat;
     }
   }
-  if (blocks_per_sm && best_b < best_nat) *blocks_per_sm = best_b;
   return best_w;
 }
 

@@ -151,11 +151,7 @@ extern "C" int chem_solve_step_noalloc(const chem_mech *mech, int64_t n_cells, c
   const int wmax = max_warps_per_block(mech->m.dev, o.lu_precision, CHEM_DRIVER_PERSISTENT);
   if (wmax < 1) return fail(CHEM_EINVAL, "mechanism working set does not fit in shared memory");
   if (o.cells_per_block > wmax) return fail(CHEM_EINVAL, "cells_per_block exceeds the shared-memory limit");
-  if (o.cells_per_block == 0) {
-    int bps = 0;
-    o.cells_per_block = best_warps_per_block(mech->m.dev, o.lu_precision, CHEM_DRIVER_PERSISTENT, n_cells, &bps);
-    if (o.blocks_per_sm == 0) o.blocks_per_sm = bps;
-  }
+  if (o.cells_per_block == 0) o.cells_per_block = best_warps_per_block(mech->m.dev, o.lu_precision, CHEM_DRIVER_PERSISTENT);
   if (o.cells_per_block < 1) return fail(CHEM_EINVAL, "no launch shape fits on this device");
 
   cudaStream_t s = (cudaStream_t)stream;

@@ -153,11 +153,12 @@ def test_solve_other_species_counts(oracle_lib, cg, S, R, U, Ph):
 
 
 @pytest.mark.parametrize("name", ["small", "tropo", "s128"])
-def test_persistent_default_shape_every_mechanism(cg, mechs, name):
+def test_persistent_shapes_every_mechanism(cg, mechs, name):
     """The persistent driver's default launch shape exists for every mechanism
-    size, for a small batch (fewer than two cells per warp at 8 warps per SM:
-    at most 8 cells per SM, blocks per SM bounded by padded shared memory) and
-    a larger one, and gives the plain driver's results bitwise."""
+    size, and so does a shape with fewer resident blocks per SM than fit (one
+    block of two cells per SM: the blocks' shared memory is padded so that no
+    second block joins an SM); for a small batch and one of more than two
+    cells per warp, both give the plain driver's results bitwise."""
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
     if name == "s128":
         m = synth.random_mechanism(128, 330, 100, 34, name="synthetic_128sp_330rx")
@@ -168,8 +169,9 @@ def test_persistent_default_shape_every_mechanism(cg, mechs, name):
     for n in (9, 2 * 8 * n_sm + 5):
         cells = synth.random_cells(m.n_species, n, T_range=(220.0, 310.0), P_range=(2e4, 1e5), seed=n)
         ya, sa = cg.solve(mech, cells, 600.0, 1e-4, 1e-10, driver="plain")
-        yb, sb = cg.solve(mech, cells, 600.0, 1e-4, 1e-10, driver="persistent")
-        assert np.array_equal(ya, yb) and np.array_equal(sa, sb), (name, n)
+        for shape in ({}, {"cells_per_block": 2, "blocks_per_sm": 1}):
+            yb, sb = cg.solve(mech, cells, 600.0, 1e-4, 1e-10, driver="persistent", **shape)
+            assert np.array_equal(ya, yb) and np.array_equal(sa, sb), (name, n, shape)
 
 
 def test_drivers_agree_bitwise(cg, mechs):
