@@ -22,7 +22,9 @@
  *     was launched and chem_last_error() (thread-local) describes it;
  *   - "mem" arguments say where a pointer lives: CHEM_MEM_HOST (pageable or
  *     pinned host memory) or CHEM_MEM_DEVICE (memory of the current CUDA
- *     device);
+ *     device, or managed memory); a CHEM_MEM_DEVICE pointer that is neither
+ *     (host memory, another device's memory) is refused with CHEM_EINVAL
+ *     before anything is launched or copied;
  *   - "stream" is a cudaStream_t (NULL = the legacy default stream); device
  *     work is enqueued on it and the call returns without waiting, except
  *     where a host buffer is read back;

@@ -17,7 +17,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "libchemgpu.so")
 SOURCES = ["mechanism.cpp", "capi.cpp", "kernels.cu", "noalloc.cu", "deriv.cu", "peak.cu"]
 HEADERS = [os.path.join(ROOT, "include", "chemgpu.h"), os.path.join(CSRC, "internal.h"),
-           os.path.join(CSRC, "device_common.cuh")]
+           os.path.join(CSRC, "device_common.cuh"), os.path.join(CSRC, "devbuf.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -3,11 +3,13 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <string>
 #include <utility>
 #include <vector>
 
+#include "devbuf.h"
 #include "internal.h"
 
 using namespace chemgpu;
@@ -67,6 +69,22 @@ cudaMemcpyKind kind_out(int32_t mem) { return mem == CHEM_MEM_DEVICE ? cudaMemcp
 
 int check_mem(int32_t mem) {
   if (mem != CHEM_MEM_HOST && mem != CHEM_MEM_DEVICE) return fail(CHEM_EINVAL, "mem must be CHEM_MEM_HOST or CHEM_MEM_DEVICE");
+  return 0;
+}
+
+// With CHEM_MEM_DEVICE the caller's buffers go to the kernels and to
+// device-side copies as they are: each one given (NULL entries are skipped)
+// must be memory of the current device or managed memory.
+int check_buffers(int32_t mem, std::initializer_list<std::pair<const void *, const char *>> bufs) {
+  if (mem != CHEM_MEM_DEVICE) return 0;
+  int dev = -1;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(CHEM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  for (const auto &b : bufs) {
+    if (!b.first) continue;
+    const std::string why = device_buffer_problem(b.first, dev, b.second);
+    if (!why.empty()) return fail(CHEM_EINVAL, why);
+  }
   return 0;
 }
 
@@ -300,6 +318,7 @@ int chem_cells_set_state(chem_cells *c, const double *T, const double *P, const 
   if (int rc = check_device(c)) return rc;
   c->kt_valid = false;
   if (int rc = check_mem(mem)) return rc;
+  if (int rc = check_buffers(mem, {{T, "T"}, {P, "P"}, {y, "y"}})) return rc;
   if (c->n == 0) { c->have_state = true; return 0; }
   cudaStream_t s = (cudaStream_t)stream;
   const size_t n = (size_t)c->n, S = (size_t)c->mech->m.S;
@@ -324,6 +343,7 @@ int chem_cells_set_photolysis(chem_cells *c, const double *J, int32_t mem, void 
   c->kt_valid = false;
   if (!J) { c->use_J = false; return 0; }
   if (int rc = check_mem(mem)) return rc;
+  if (int rc = check_buffers(mem, {{J, "J"}})) return rc;
   const size_t np = (size_t)c->mech->m.n_phot;
   if (np == 0 || c->n == 0) { c->use_J = false; return 0; }
   cudaError_t e = cudaMemcpyAsync(c->J, J, np * (size_t)c->n * sizeof(double), kind_in(mem), (cudaStream_t)stream);
@@ -339,6 +359,7 @@ int chem_cells_set_theta(chem_cells *c, const double *theta, int32_t mem, void *
   c->kt_valid = false;
   if (!theta) { c->use_theta = false; return 0; }
   if (int rc = check_mem(mem)) return rc;
+  if (int rc = check_buffers(mem, {{theta, "theta"}})) return rc;
   const size_t R = (size_t)c->mech->m.R;
   if (R == 0) return 0;
   cudaError_t e = cudaMemcpyAsync(c->theta, theta, R * sizeof(double), kind_in(mem), (cudaStream_t)stream);
@@ -608,6 +629,7 @@ int chem_get_state(const chem_cells *c, double *y, int32_t mem, void *stream) {
   if (!c || !y) return fail(CHEM_EINVAL, "NULL argument");
   if (int rc = check_mem(mem)) return rc;
   if (int rc = check_device(c)) return rc;
+  if (int rc = check_buffers(mem, {{y, "y"}})) return rc;
   if (c->n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(y, c->y, (size_t)c->n * c->mech->m.S * sizeof(double), kind_out(mem), s);
@@ -621,6 +643,7 @@ int chem_get_stats(const chem_cells *c, chem_cell_stats *out, int32_t mem, void 
   if (!c || !out) return fail(CHEM_EINVAL, "NULL argument");
   if (int rc = check_mem(mem)) return rc;
   if (int rc = check_device(c)) return rc;
+  if (int rc = check_buffers(mem, {{out, "out"}})) return rc;
   if (c->n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(out, c->stats, (size_t)c->n * sizeof(chem_cell_stats), kind_out(mem), s);
@@ -658,6 +681,7 @@ int probe(chem_cells *c, int mode, double cc, const double *y, const double *b, 
   if (int rc = check_mem(mem)) return rc;
   if (!c->have_state) return fail(CHEM_ESTATE, "diagnostic before set_state");
   if (int rc = check_device(c)) return rc;
+  if (int rc = check_buffers(mem, {{y, "y"}, {b, "b"}, {out, "out"}})) return rc;
   if (c->n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)c->n * c->mech->m.S * sizeof(double);
@@ -702,6 +726,7 @@ int chem_eval_reciprocal(const double *x, double *out, int64_t n, int32_t mem, v
   if (n < 0 || (n > 0 && (!x || !out))) return fail(CHEM_EINVAL, "bad argument");
   if (int rc = check_mem(mem)) return rc;
   if (n == 0) return 0;
+  if (int rc = check_buffers(mem, {{x, "x"}, {out, "out"}})) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)n * sizeof(double);
   double *tmp = nullptr;
@@ -729,6 +754,7 @@ int chem_eval_warp_sum(const double *x, double *out, int64_t n_groups, int32_t m
   if (n_groups < 0 || (n_groups > 0 && (!x || !out))) return fail(CHEM_EINVAL, "bad argument");
   if (int rc = check_mem(mem)) return rc;
   if (n_groups == 0) return 0;
+  if (int rc = check_buffers(mem, {{x, "x"}, {out, "out"}})) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t in_bytes = (size_t)n_groups * WARP * sizeof(double), out_bytes = (size_t)n_groups * sizeof(double);
   double *tmp = nullptr;
@@ -760,6 +786,7 @@ int chem_eval_deriv_design(chem_cells *c, int32_t design, const double *y, doubl
   if (int rc = check_mem(mem)) return rc;
   if (!c->have_state) return fail(CHEM_ESTATE, "derivative before set_state");
   if (int rc = check_device(c)) return rc;
+  if (int rc = check_buffers(mem, {{y, "y"}, {f, "f"}})) return rc;
   if (c->n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
   const MechDev &M = c->mech->m.dev;
@@ -802,6 +829,7 @@ int chem_sensitivity(chem_cells *c, const double *dL_dy, double *dL_dtheta, doub
   if (!c->tape_n) return fail(CHEM_ESTATE, "the batch was created without record_adjoint");
   if (!c->have_state) return fail(CHEM_ESTATE, "sensitivity before set_state");
   if (int rc = check_device(c)) return rc;
+  if (int rc = check_buffers(mem, {{dL_dy, "dL_dy"}, {dL_dtheta, "dL_dtheta"}, {dL_dy0, "dL_dy0"}})) return rc;
   const size_t n = (size_t)c->n, S = (size_t)c->mech->m.S, R = (size_t)c->mech->m.R;
   if (n == 0) {
     if (mem == CHEM_MEM_HOST) std::memset(dL_dtheta, 0, R * sizeof(double));
@@ -865,6 +893,8 @@ int chem_sensitivity_checkpointed(chem_cells *c, const double *states, int32_t n
   if (!c->tape_n) return fail(CHEM_ESTATE, "the batch was created without record_adjoint");
   if (!c->have_state) return fail(CHEM_ESTATE, "sensitivity before set_state");
   if (int rc = check_device(c)) return rc;
+  if (int rc = check_buffers(mem, {{states, "states"}, {dL_dy, "dL_dy"}, {dL_dtheta, "dL_dtheta"}, {dL_dy0, "dL_dy0"}}))
+    return rc;
   if (n_steps < 1 || n_steps > CHEM_MAX_GRAPH_STEPS) return fail(CHEM_EINVAL, "n_steps out of range");
   if (!(dt > 0.0) || !(dt < 1e300)) return fail(CHEM_EINVAL, "dt must be positive and finite");
   const size_t n = (size_t)c->n, S = (size_t)c->mech->m.S, R = (size_t)c->mech->m.R;
@@ -926,6 +956,7 @@ int chem_tangent(chem_cells *c, const double *dy0, const double *dtheta, double 
   if (!c->tape_n) return fail(CHEM_ESTATE, "the batch was created without record_adjoint");
   if (!c->have_state) return fail(CHEM_ESTATE, "tangent before set_state");
   if (int rc = check_device(c)) return rc;
+  if (int rc = check_buffers(mem, {{dy0, "dy0"}, {dtheta, "dtheta"}, {dy, "dy"}})) return rc;
   const size_t n = (size_t)c->n, S = (size_t)c->mech->m.S, R = (size_t)c->mech->m.R;
   if (n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;

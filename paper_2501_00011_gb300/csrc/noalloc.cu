@@ -21,6 +21,7 @@
 #include <mutex>
 #include <string>
 
+#include "devbuf.h"
 #include "internal.h"
 
 namespace chemgpu {
@@ -69,24 +70,10 @@ int current_device(int *dev) {
   return 0;
 }
 
-// A caller's buffer must be memory of the current device (or managed memory):
-// a kernel given a host pointer would fault.  cudaPointerGetAttributes
-// allocates nothing.
+// A caller's buffer must be memory of the current device (or managed memory).
 int check_device_buffer(const void *p, int dev, const char *name) {
-  cudaPointerAttributes a;
-  std::memset(&a, 0, sizeof(a));
-  const cudaError_t e = cudaPointerGetAttributes(&a, p);
-  if (e != cudaSuccess) {
-    cudaGetLastError();   // a failed query also sets the runtime's last error: reset it
-    return fail(CHEM_EINVAL, std::string(name) + " is not a device pointer (" + cudaGetErrorString(e) + ")");
-  }
-  if (a.type == cudaMemoryTypeManaged) return 0;
-  if (a.type != cudaMemoryTypeDevice)
-    return fail(CHEM_EINVAL, std::string(name) + " must be memory of the current device, not host memory");
-  if (a.device != dev)
-    return fail(CHEM_EINVAL, std::string(name) + " is memory of device " + std::to_string(a.device) + ", not of the current device " +
-                                 std::to_string(dev));
-  return 0;
+  const std::string why = device_buffer_problem(p, dev, name);
+  return why.empty() ? 0 : fail(CHEM_EINVAL, why);
 }
 
 }  // namespace

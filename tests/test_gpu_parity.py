@@ -174,6 +174,36 @@ def test_persistent_shapes_every_mechanism(cg, mechs, name):
             assert np.array_equal(ya, yb) and np.array_equal(sa, sb), (name, n, shape)
 
 
+def test_device_mode_refuses_host_buffers(cg, mechs):
+    """With CHEM_MEM_DEVICE the library hands the caller's buffers to its
+    kernels and device-side copies as they are, so a host pointer is refused
+    before anything is launched or copied."""
+    import ctypes as ct
+    L = cg.load()
+    wl = synth.workload_tropo(16)
+    c = cg.Cells(mechs["tropo"], 16, rtol=wl.rtol, atol=wl.atol)
+    c.set_state(wl.cells.T, wl.cells.P, wl.cells.y)
+    y_before = c.get_state()
+    host = np.ones(16 * 72)
+    dev_buf = torch.ones(16 * 72, dtype=torch.float64, device="cuda")
+    hp, dp = ct.c_void_p(host.ctypes.data), ct.c_void_p(dev_buf.data_ptr())
+    for rc in (L.chem_cells_set_state(c.handle, dp, dp, hp, cg.MEM_DEVICE, None),
+               L.chem_get_state(c.handle, hp, cg.MEM_DEVICE, None),
+               L.chem_eval_deriv(c.handle, dp, hp, cg.MEM_DEVICE, None),
+               L.chem_eval_reciprocal(hp, dp, 16, cg.MEM_DEVICE, None),
+               L.chem_eval_warp_sum(dp, hp, 1, cg.MEM_DEVICE, None)):
+        assert rc == -1 and "host memory" in L.chem_last_error().decode()
+    torch.cuda.synchronize()
+    assert np.array_equal(c.get_state(), y_before)
+    assert torch.equal(dev_buf, torch.ones_like(dev_buf))
+    # device buffers of the current device pass
+    out = torch.empty(16, dtype=torch.float64, device="cuda")
+    assert L.chem_eval_reciprocal(dp, ct.c_void_p(out.data_ptr()), 16, cg.MEM_DEVICE, None) == 0
+    torch.cuda.synchronize()
+    assert torch.all(out == 1.0)
+    c.close()
+
+
 def test_drivers_agree_bitwise(cg, mechs):
     wl = synth.workload_tropo(97)
     ya, sa = cg.solve(mechs["tropo"], wl.cells, wl.dt, wl.rtol, wl.atol, driver="plain")
