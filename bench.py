@@ -783,12 +783,14 @@ def run_gpu(args):
                         "keyed by the previous step's costs (easier states than y0's initial transient)"},
             "plain_fp64": {"value": plain, "unit": UNIT, "ms_per_step": tot_plain / args.steps,
                            "form": "one warp per cell, one cell per block, tables read from L2, FP64 throughout",
-                           "chosen_vs_plain": value / plain},
+                           "chosen_vs_plain": value / plain,
+                           "traffic": _profiled(os.path.join(ROOT, "profiles", "solve_kernel_fp64_plain_tropo10k.md"))},
             "fp32_lu": {"value": chosen, "unit": UNIT, "ms_per_step": tot_chosen / args.steps,
                         "form": "persistent + FP32 LU factor/solve (f, error control, state FP64), fresh batches "
                                 "as the headline",
                         "vs_plain_fp64": chosen / plain,
-                        "newton_iters_vs_fp64": float(np.sum(st_chosen["newton_iters"]) / max(1, np.sum(st_head["newton_iters"])))},
+                        "newton_iters_vs_fp64": float(np.sum(st_chosen["newton_iters"]) / max(1, np.sum(st_head["newton_iters"]))),
+                        "traffic": _profiled(os.path.join(ROOT, "profiles", "solve_kernel_fp32lu_persistent_tropo10k.md"))},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(C * (S + 2) * 8),
                     "d2h_bytes_per_step": int(C * S * 8),
                     "form": "persistent FP64 through the C ABI with pinned host buffers: per timed step T, P, y0 "
