@@ -142,7 +142,9 @@ typedef struct {
   int32_t cells_per_block;         /* warps (= concurrent cells) per block; 0 = auto: 1 for the
                                       plain driver, the most resident cells per SM for the
                                       persistent one (chem_autotune measures instead) */
-  int32_t blocks_per_sm;           /* persistent driver: resident blocks per SM; 0 = auto */
+  int32_t blocks_per_sm;           /* persistent driver: resident blocks per SM; 0 = auto (as
+                                      many as fit); fewer than fit are kept to by padding each
+                                      block's shared memory, so the blocks spread over the SMs */
   int32_t record_adjoint;          /* 1: record the tape for chem_sensitivity (needs lu_precision 64) */
   int32_t tape_steps;              /* tape rows per cell: states stored, one per solve, per
                                       refactorisation and per accepted corrector iteration
